@@ -1,0 +1,230 @@
+/*
+ * mstep.h -- C ABI of the GB300 (sm_103a) library for the multi-step
+ * reconstruction of radio-interferometric images (Wang, Prunet, Mignot,
+ * Ferrari, "Multi-Step Reconstruction of Radio-Interferometric Images").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an ms_status; nothing throws or exits across the
+ *   ABI.  On failure, ms_last_error(plan) describes the cause (a string owned
+ *   by the plan, valid until its next call).
+ * - The CALLER owns all data buffers.  "dev" pointers are CUDA device memory
+ *   on the plan's device (any allocator, e.g. PyTorch); "host" pointers are
+ *   ordinary host memory.  The PLAN owns everything it derives: sorted
+ *   visibility indices, kernel and deapodization tables, PSF spectra,
+ *   filters, work lists, workspaces and cuFFT plans.
+ * - Real arrays are float64 for MS_FP64 plans and float32 otherwise; complex
+ *   visibilities are interleaved (re, im) pairs of the same type.  Images are
+ *   N x N row-major; pixel (p, q) sits at l = (q - N/2) dl, m = (p - N/2) dl.
+ *   Wavelet coefficients are M planes of N x N in Mallat layout (see
+ *   ms_dictionary_synthesis).
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *   stream-ordered; results that come back to the host (ms_stats, counts)
+ *   are complete when the call returns.  A plan is not thread-safe: use it
+ *   from one host thread and one stream at a time.
+ * - Device-side waits inside kernels are bounded; a wait that runs out
+ *   returns MS_ERR_TIMEOUT.
+ */
+#ifndef MSTEP_H
+#define MSTEP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_ARG = 1,          /* invalid argument or unsupported size */
+  MS_ERR_CUDA = 2,         /* CUDA / cuFFT error */
+  MS_ERR_OOM = 3,          /* device allocation failed */
+  MS_ERR_NUMERIC = 4,      /* NaN / Inf seen, or a degenerate problem */
+  MS_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
+  MS_ERR_NOT_CONVERGED = 6,
+  MS_ERR_STATE = 7,        /* call out of order */
+  MS_ERR_UNSUPPORTED = 8
+} ms_status;
+
+typedef enum { MS_FP64 = 0, MS_FP32 = 1, MS_FP32_KAHAN = 2 } ms_precision;
+
+/* Baseline partitions of Sect. 3.1: L = {r <= ell + delta} (short baselines),
+ * H = {r >= ell - delta} (long baselines), ALL = every unflagged row. */
+typedef enum { MS_PART_L = 0, MS_PART_H = 1, MS_PART_ALL = 2 } ms_part;
+
+/* Minor-cycle problems: LOW = Eq. LowRes (Sect. 3.2) on V_L, FULL = Eq. FullRes
+ * (Sect. 3.3) on V_H, SINGLE = the LowRes problem on all rows (Sect. 5). */
+typedef enum { MS_STEP_LOW = 0, MS_STEP_FULL = 1, MS_STEP_SINGLE = 2 } ms_step;
+
+/* lambda rules: NORM2_2N is lambda_n = c ||i~_n||_2 2^n (Sect. 5, App. A.2);
+ * MAX_FIXED is lambda = c max|i~_1|, held for all cycles of a step. */
+typedef enum { MS_LAMBDA_NORM2_2N = 0, MS_LAMBDA_MAX_FIXED = 1 } ms_lambda_rule;
+
+typedef struct ms_plan ms_plan;
+
+typedef struct {
+  const double* u;        /* host [nchan * nvis] baseline u, wavelengths        */
+  const double* v;        /* host [nchan * nvis] baseline v, wavelengths        */
+  const uint8_t* flags;   /* host [nchan * nvis], nonzero = flagged; may be NULL */
+  int64_t nvis;           /* rows per channel, 1 .. 2^31-1                      */
+  int32_t nchan;          /* channels, >= 1                                     */
+  int32_t npix;           /* image side N: multiple of 16 and of 2^levels       */
+  double pixel_size;      /* dl in radians                                      */
+  double ell_px;          /* partition centre ell, pixel units of the N x N DFT */
+  double delta_px;        /* partition half width delta (> 0)                   */
+  int32_t kernel_width;   /* ES kernel support W in cells; 7                    */
+  int32_t oversample;     /* grid oversampling; 2                               */
+  double es_beta;         /* ES shape; <= 0 selects 2.30 * W                    */
+  int32_t levels;         /* wavelet levels J, 1..8                             */
+  int32_t n_bases;        /* dictionary size M, 1..8 (db1 .. dbM)               */
+  int32_t precision;      /* ms_precision                                       */
+  int32_t tile;           /* gridding tile side: 0 = default, or 16 / 32      */
+  int32_t chunk;          /* visibilities per work item: 0 = automatic          */
+  int32_t device;         /* CUDA device ordinal                                */
+} ms_plan_desc;
+
+typedef struct {
+  int32_t iterations;     /* prox steps taken in the last minor cycle         */
+  int32_t converged;      /* 1 if the relative-objective test stopped it      */
+  int32_t major_cycles;   /* major cycles run by a reconstruct call           */
+  int32_t total_iterations; /* prox steps over all minor cycles of the call   */
+  double objective;       /* F at the returned coefficients (FP64)            */
+  double lambda;          /* lambda of the last minor cycle                   */
+  double theta;           /* Lipschitz constant used (2 M max K^)             */
+  double sigma2;          /* sigma^2 used by step two (0 if none)             */
+  double eta2;            /* eta^2 used by step two (0 if none)               */
+  double elapsed_ms;      /* device time of the call (CUDA events)            */
+  double grid_ms;         /* of which: gridding + degridding kernels          */
+  double fft_ms;          /* of which: the Ng x Ng FFTs of the major cycles   */
+  double minor_ms;        /* of which: minor cycles                           */
+  int64_t gridded_vis;    /* visibilities degridded + gridded by the call     */
+  const double* objective_trace; /* plan-owned host array: F(beta_0..beta_k) of
+                             the last minor cycle, length iterations + 1;
+                             valid until the plan's next call                 */
+} ms_stats;
+
+typedef struct {
+  int32_t n_major;        /* major cycles per step (Sect. 5: 5)               */
+  int32_t fista_iters;    /* FISTA iterations per minor cycle (Sect. 5: 100)  */
+  double rel_tol;         /* stop when |F_k - F_k-1| <= rel_tol |F_k|; 0 = off */
+  int32_t lambda_rule;    /* ms_lambda_rule                                   */
+  double lambda_low;      /* c for step one (paper: 0.05)                     */
+  double lambda_full;     /* c for step two (paper: 0.05)                     */
+  double lambda_single;   /* c for the single-step method (paper: 0.01)       */
+  double sigma2;          /* <= 0: estimate on i~_H1 (Sect. 4.3)              */
+  double eta2;            /* <= 0: 1e-3 sigma^2 (Sect. 4.3)                   */
+} ms_recon_opts;
+
+/* ------------------------------------------------------------------ plan */
+
+/* Builds a plan (Sect. 3.1 partition + the gridding set-up the paper leaves
+ * open): classifies every row of every channel into L / H by
+ * r = |uv| N dl against ell +- delta (closed intervals), computes each row's
+ * ES footprint on the 2x oversampled grid (first cell floor(g - W/2) + 1,
+ * g = u Ng dl), sorts each partition by grid tile with a stable radix sort (so
+ * rows keep their original order inside a tile), splits tiles into work
+ * items, builds the deapodization table, the Daubechies filters db1..dbM and
+ * the cuFFT plans.  u, v, flags are copied; the caller may free them after
+ * the call.  Errors: MS_ERR_ARG (sizes, W != 7, oversample != 2, N not a
+ * multiple of 16 or 2^levels), MS_ERR_OOM, MS_ERR_CUDA. */
+ms_status ms_plan_create(const ms_plan_desc* desc, ms_plan** out);
+ms_status ms_plan_destroy(ms_plan* plan);
+const char* ms_last_error(const ms_plan* plan);
+
+/* Row counts of a partition (Sect. 3.1): out[0] = |V_L|, out[1] = |V_H|,
+ * out[2] = |V_L n V_H|, out[3] = unflagged rows, for channel chan. */
+ms_status ms_partition_counts(ms_plan* plan, int32_t chan, int64_t out[4]);
+
+/* The rows of partition `part` in the plan's sorted (tile) order, copied to
+ * host `rows` [count]; count = ms_partition_counts of that partition. */
+ms_status ms_partition_rows(ms_plan* plan, int32_t part, int32_t chan, int32_t* rows);
+
+/* ------------------------------------------------------ measurement operator */
+
+/* Degridding, A x (Sect. 2): image -> visibilities of the rows of `part`.
+ * image: dev N*N real.  vis_obs: dev complex [nvis] in original row order, or
+ * NULL.  vis_out: dev complex [nvis]; only the partition's rows are written,
+ * with vis_obs - A x (the residual visibilities) if vis_obs is given, else
+ * A x.  A = G F Z D with the ES kernel (W = 7, 2x oversampling). */
+ms_status ms_degrid(ms_plan* plan, int32_t part, int32_t chan, const void* image,
+                    const void* vis_obs, void* vis_out, void* stream);
+
+/* Gridding, A^H y / sum(w) (Sect. 2): the rows of `part` of vis (dev complex
+ * [nvis], original order) -> dirty image dev N*N real, natural weights. */
+ms_status ms_grid(ms_plan* plan, int32_t part, int32_t chan, const void* vis,
+                  void* dirty, void* stream);
+
+/* Major-cycle residual image i~ = F^H G^H (v - G F x) / sum(w) (Sect. 2) for
+ * the rows of `part`: degrid, subtract, grid, in one call.  model: dev N*N
+ * real; vis_obs: dev complex [nvis] original order; out: dev N*N real. */
+ms_status ms_residual_image(ms_plan* plan, int32_t part, int32_t chan,
+                            const void* vis_obs, const void* model, void* out,
+                            void* stream);
+
+/* PSF of a partition: A^H A applied to a unit impulse at (N/2, N/2), divided
+ * by sum(w) (peak ~1).  psf: dev N*N real. */
+ms_status ms_psf(ms_plan* plan, int32_t part, int32_t chan, void* psf, void* stream);
+
+/* ------------------------------------------------------------ dictionary */
+
+/* W alpha = sum_m Psi_m alpha_m (Sect. 4.3, App. A.1): M periodized
+ * orthonormal Daubechies (db1..dbM) syntheses with J levels.  alpha: dev
+ * [M][N][N] Mallat layout (after a level on an n x n block: [0,n/2)^2
+ * approximation, rows [0,n/2) x cols [n/2,n) low-y/high-x, rows [n/2,n) x
+ * cols [0,n/2) high-y/low-x, [n/2,n)^2 high/high).  x: dev N*N. */
+ms_status ms_dictionary_synthesis(ms_plan* plan, const void* alpha, void* x, void* stream);
+
+/* W^H x = [Psi_1^H x, ..., Psi_M^H x].  x: dev N*N; alpha: dev [M][N][N]. */
+ms_status ms_dictionary_analysis(ms_plan* plan, const void* x, void* alpha, void* stream);
+
+/* ----------------------------------------------------------- minor cycle */
+
+/* Noise variance estimate of Sect. 4.3: mean over all inside 5x5 windows of
+ * the population variance of image (dev N*N).  Result to host *sigma2. */
+ms_status ms_sigma2_hat(ms_plan* plan, const void* image, double* sigma2, void* stream);
+
+/* Lipschitz constant of the gradient (Sect. 3.4) for a step of a partition:
+ * closed form 2 M max K^ (K^ = |H^|^2, or |g_H H^|^2 + |g_L|^2 for FULL with
+ * the given sigma2, eta2), and, if power_iters > 0, 2 lambda_max by power
+ * iteration through W in FP64 reductions.  Results to host. */
+ms_status ms_lipschitz(ms_plan* plan, int32_t step, int32_t chan, double sigma2,
+                       double eta2, int32_t power_iters, double* theta_closed,
+                       double* theta_power, void* stream);
+
+/* One minor cycle: FISTA (Algorithm 1) on Eq. LowRes (LOW, SINGLE) or
+ * Eq. FullRes (FULL) with gradients Eq. GradL / Eq. GradH, step 1/theta with
+ * theta = 2 M max K^ (Sect. 3.4), threshold lambda/theta.  residual: dev N*N
+ * (i~_n); l_low: dev N*N (l_Ln), FULL only; sigma2, eta2: FULL only.
+ * beta_inout: dev [M][N][N] start point (NULL = zero) and, if not NULL, the
+ * result.  model_out: dev N*N, receives W beta.  Runs exactly max_iters prox
+ * steps unless rel_tol > 0 and |F_k - F_k-1| <= rel_tol |F_k| first.  The
+ * objective F is evaluated in FP64 at every prox output. */
+ms_status ms_minor_cycle(ms_plan* plan, int32_t step, int32_t chan,
+                         const void* residual, const void* l_low, double sigma2,
+                         double eta2, double lambda, int32_t max_iters,
+                         double rel_tol, void* beta_inout, void* model_out,
+                         ms_stats* stats, void* stream);
+
+/* ----------------------------------------------------------- reconstruct */
+
+/* The two-step method: step one (Eq. LowRes) on V_L for n_major cycles, final
+ * low-resolution image i^_L = i~_{L,N+1} + sum i_Ln; then step two (Eq.
+ * FullRes) on V_H with l_Ln = i^_L - sum_{j<n} i_j, final image
+ * i^ = i~_{H,N+1} + sum i_n.  vis: dev complex [nvis] original order.
+ * img_low_out, img_out: dev N*N; model_out (optional) receives sum i_n. */
+ms_status ms_reconstruct_two_step(ms_plan* plan, int32_t chan, const void* vis,
+                                  const ms_recon_opts* opts, void* img_low_out,
+                                  void* img_out, void* model_out, ms_stats* stats,
+                                  void* stream);
+
+/* The single-step baseline (Sect. 5): step one's problem on V_L u V_H. */
+ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vis,
+                                     const ms_recon_opts* opts, void* img_out,
+                                     void* model_out, ms_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSTEP_H */

@@ -1,0 +1,440 @@
+"""GB300 (sm_103a) implementation of the multi-step reconstruction of
+radio-interferometric images (Wang, Prunet, Mignot, Ferrari).
+
+A thin ctypes binding over ``libmstep.so`` (``include/mstep.h``): argument
+marshalling only, every step of the path runs in the library's CUDA kernels.
+Buffers are torch tensors on the plan's device; the calls are ordered on the
+current torch stream.  There is no CPU fallback: if the library cannot be
+loaded the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmstep.so")
+
+MS_OK, MS_ERR_ARG, MS_ERR_CUDA, MS_ERR_OOM, MS_ERR_NUMERIC = 0, 1, 2, 3, 4
+MS_ERR_TIMEOUT, MS_ERR_NOT_CONVERGED, MS_ERR_STATE, MS_ERR_UNSUPPORTED = 5, 6, 7, 8
+MS_FP64, MS_FP32, MS_FP32_KAHAN = 0, 1, 2
+MS_PART_L, MS_PART_H, MS_PART_ALL = 0, 1, 2
+MS_STEP_LOW, MS_STEP_FULL, MS_STEP_SINGLE = 0, 1, 2
+MS_LAMBDA_NORM2_2N, MS_LAMBDA_MAX_FIXED = 0, 1
+
+PRECISIONS = {"fp64": MS_FP64, "fp32": MS_FP32, "fp32_kahan": MS_FP32_KAHAN}
+PARTS = {"L": MS_PART_L, "H": MS_PART_H, "ALL": MS_PART_ALL}
+STEPS = {"low": MS_STEP_LOW, "full": MS_STEP_FULL, "single": MS_STEP_SINGLE}
+
+
+class MsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"mstep status {status}: {message}")
+        self.status = status
+
+
+class ms_plan_desc(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("nvis", ctypes.c_int64), ("nchan", ctypes.c_int32), ("npix", ctypes.c_int32),
+                ("pixel_size", ctypes.c_double), ("ell_px", ctypes.c_double),
+                ("delta_px", ctypes.c_double), ("kernel_width", ctypes.c_int32),
+                ("oversample", ctypes.c_int32), ("es_beta", ctypes.c_double),
+                ("levels", ctypes.c_int32), ("n_bases", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class ms_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("major_cycles", ctypes.c_int32), ("total_iterations", ctypes.c_int32),
+                ("objective", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("theta", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("eta2", ctypes.c_double), ("elapsed_ms", ctypes.c_double),
+                ("grid_ms", ctypes.c_double), ("fft_ms", ctypes.c_double),
+                ("minor_ms", ctypes.c_double), ("gridded_vis", ctypes.c_int64),
+                ("objective_trace", ctypes.POINTER(ctypes.c_double))]
+
+
+class ms_recon_opts(ctypes.Structure):
+    _fields_ = [("n_major", ctypes.c_int32), ("fista_iters", ctypes.c_int32),
+                ("rel_tol", ctypes.c_double), ("lambda_rule", ctypes.c_int32),
+                ("lambda_low", ctypes.c_double), ("lambda_full", ctypes.c_double),
+                ("lambda_single", ctypes.c_double), ("sigma2", ctypes.c_double),
+                ("eta2", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGNATURES = {
+    "ms_plan_create": [ctypes.POINTER(ms_plan_desc), ctypes.POINTER(_P)],
+    "ms_plan_destroy": [_P],
+    "ms_last_error": [_P],
+    "ms_partition_counts": [_P, _I32, ctypes.POINTER(_I64)],
+    "ms_partition_rows": [_P, _I32, _I32, _P],
+    "ms_degrid": [_P, _I32, _I32, _P, _P, _P, _P],
+    "ms_grid": [_P, _I32, _I32, _P, _P, _P],
+    "ms_residual_image": [_P, _I32, _I32, _P, _P, _P, _P],
+    "ms_psf": [_P, _I32, _I32, _P, _P],
+    "ms_dictionary_synthesis": [_P, _P, _P, _P],
+    "ms_dictionary_analysis": [_P, _P, _P, _P],
+    "ms_sigma2_hat": [_P, _P, ctypes.POINTER(_D), _P],
+    "ms_lipschitz": [_P, _I32, _I32, _D, _D, _I32, ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
+    "ms_minor_cycle": [_P, _I32, _I32, _P, _P, _D, _D, _D, _I32, _D, _P, _P,
+                       ctypes.POINTER(ms_stats), _P],
+    "ms_reconstruct_two_step": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P, _P,
+                                ctypes.POINTER(ms_stats), _P],
+    "ms_reconstruct_single_step": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P,
+                                   ctypes.POINTER(ms_stats), _P],
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmstep.so (built by ``_build.build``).  Raises if it is missing:
+    the package has no other implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2406_18356_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "ms_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> List[str]:
+    return list(_SIGNATURES)
+
+
+# ---------------------------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+@dataclass
+class Stats:
+    iterations: int
+    converged: bool
+    major_cycles: int
+    total_iterations: int
+    objective: float
+    lam: float
+    theta: float
+    sigma2: float
+    eta2: float
+    elapsed_ms: float
+    grid_ms: float
+    fft_ms: float
+    minor_ms: float
+    gridded_vis: int
+    trace: np.ndarray = field(default_factory=lambda: np.zeros(0))
+
+    @classmethod
+    def from_c(cls, s: ms_stats) -> "Stats":
+        n = s.iterations + 1 if s.objective_trace else 0
+        tr = np.array(s.objective_trace[:n]) if n else np.zeros(0)
+        return cls(s.iterations, bool(s.converged), s.major_cycles, s.total_iterations,
+                   s.objective, s.lambda_, s.theta, s.sigma2, s.eta2, s.elapsed_ms,
+                   s.grid_ms, s.fft_ms, s.minor_ms, s.gridded_vis, tr)
+
+
+@dataclass
+class ReconOptions:
+    n_major: int = 5
+    fista_iters: int = 100
+    rel_tol: float = 0.0
+    lambda_rule: str = "norm2_2n"      # or "max_fixed"
+    lambda_low: float = 0.05
+    lambda_full: float = 0.05
+    lambda_single: float = 0.01
+    sigma2: float = 0.0                # <= 0: estimate (Sect. 4.3)
+    eta2: float = 0.0                  # <= 0: 1e-3 sigma^2
+
+    def to_c(self) -> ms_recon_opts:
+        rule = {"norm2_2n": MS_LAMBDA_NORM2_2N, "max_fixed": MS_LAMBDA_MAX_FIXED}[self.lambda_rule]
+        return ms_recon_opts(self.n_major, self.fista_iters, self.rel_tol, rule, self.lambda_low,
+                             self.lambda_full, self.lambda_single, self.sigma2, self.eta2)
+
+
+class Plan:
+    """Owns an ``ms_plan``.  See ``include/mstep.h`` for the semantics."""
+
+    def __init__(self, u, v, npix: int, pixel_size: float, ell_px: float, delta_px: float,
+                 flags=None, precision: str = "fp64", levels: int = 4, n_bases: int = 8,
+                 kernel_width: int = 7, oversample: int = 2, es_beta: float = 0.0,
+                 tile: int = 0, chunk: int = 0, device: int = 0):
+        lib = load_library()
+        u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)))
+        v = np.ascontiguousarray(np.atleast_2d(np.asarray(v, dtype=np.float64)))
+        if u.shape != v.shape:
+            raise ValueError("u and v must have the same shape")
+        fl = None
+        if flags is not None:
+            fl = np.ascontiguousarray(np.atleast_2d(np.asarray(flags, dtype=np.uint8)))
+            if fl.shape != u.shape:
+                raise ValueError("flags must match u")
+        self.nchan, self.nvis = u.shape
+        self.npix = int(npix)
+        self.precision = precision
+        self.prec = PRECISIONS[precision]
+        self.levels, self.n_bases = levels, n_bases
+        self.device = device
+        d = ms_plan_desc(u.ctypes.data, v.ctypes.data, fl.ctypes.data if fl is not None else None,
+                         self.nvis, self.nchan, self.npix, pixel_size, ell_px, delta_px,
+                         kernel_width, oversample, es_beta, levels, n_bases, self.prec, tile,
+                         chunk, device)
+        h = _P()
+        st = lib.ms_plan_create(ctypes.byref(d), ctypes.byref(h))
+        if st != MS_OK:
+            raise MsError(st, "ms_plan_create failed (see stderr)")
+        self._h = h
+        self._lib = lib
+
+    # -- helpers -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ms_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != MS_OK:
+            msg = self._lib.ms_last_error(self._h)
+            raise MsError(st, msg.decode() if msg else "")
+
+    @property
+    def real_dtype(self):
+        torch = _torch()
+        return torch.float64 if self.prec == MS_FP64 else torch.float32
+
+    @property
+    def complex_dtype(self):
+        torch = _torch()
+        return torch.complex128 if self.prec == MS_FP64 else torch.complex64
+
+    def _dev(self):
+        return _torch().device("cuda", self.device)
+
+    def _need(self, t, dtype, numel, name):
+        if t is None:
+            raise ValueError(f"{name} is required")
+        if not t.is_cuda or t.device.index != self.device:
+            raise ValueError(f"{name} must be on cuda:{self.device}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous() or t.numel() != numel:
+            raise ValueError(f"{name} must be contiguous with {numel} elements")
+        return t.data_ptr()
+
+    def _image(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.npix, self.npix), dtype=self.real_dtype, device=self._dev())
+        return out
+
+    # -- ABI -----------------------------------------------------------------
+    def partition_counts(self, chan: int = 0):
+        out = (_I64 * 4)()
+        self._check(self._lib.ms_partition_counts(self._h, chan, out))
+        return {"L": out[0], "H": out[1], "LH": out[2], "ALL": out[3]}
+
+    def partition_rows(self, part: str, chan: int = 0) -> np.ndarray:
+        n = self.partition_counts(chan)[part]
+        rows = np.zeros(max(n, 1), dtype=np.int32)
+        self._check(self._lib.ms_partition_rows(self._h, PARTS[part], chan, rows.ctypes.data))
+        return rows[:n]
+
+    def degrid(self, part: str, image, vis_obs=None, out=None, chan: int = 0, stream=None):
+        torch = _torch()
+        n2 = self.npix * self.npix
+        if out is None:
+            out = torch.zeros(self.nvis, dtype=self.complex_dtype, device=self._dev())
+        self._check(self._lib.ms_degrid(
+            self._h, PARTS[part], chan, self._need(image, self.real_dtype, n2, "image"),
+            self._need(vis_obs, self.complex_dtype, self.nvis, "vis_obs") if vis_obs is not None else None,
+            self._need(out, self.complex_dtype, self.nvis, "vis_out"), _stream_handle(stream)))
+        return out
+
+    def grid(self, part: str, vis, out=None, chan: int = 0, stream=None):
+        out = self._image(out)
+        self._check(self._lib.ms_grid(
+            self._h, PARTS[part], chan, self._need(vis, self.complex_dtype, self.nvis, "vis"),
+            self._need(out, self.real_dtype, self.npix ** 2, "dirty"), _stream_handle(stream)))
+        return out
+
+    def residual_image(self, part: str, vis_obs, model, out=None, chan: int = 0, stream=None):
+        out = self._image(out)
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_residual_image(
+            self._h, PARTS[part], chan, self._need(vis_obs, self.complex_dtype, self.nvis, "vis_obs"),
+            self._need(model, self.real_dtype, n2, "model"),
+            self._need(out, self.real_dtype, n2, "out"), _stream_handle(stream)))
+        return out
+
+    def psf(self, part: str, chan: int = 0, out=None, stream=None):
+        out = self._image(out)
+        self._check(self._lib.ms_psf(self._h, PARTS[part], chan,
+                                     self._need(out, self.real_dtype, self.npix ** 2, "psf"),
+                                     _stream_handle(stream)))
+        return out
+
+    def dictionary_synthesis(self, alpha, out=None, stream=None):
+        out = self._image(out)
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_dictionary_synthesis(
+            self._h, self._need(alpha, self.real_dtype, self.n_bases * n2, "alpha"),
+            self._need(out, self.real_dtype, n2, "x"), _stream_handle(stream)))
+        return out
+
+    def dictionary_analysis(self, x, out=None, stream=None):
+        torch = _torch()
+        n2 = self.npix ** 2
+        if out is None:
+            out = torch.empty((self.n_bases, self.npix, self.npix), dtype=self.real_dtype,
+                              device=self._dev())
+        self._check(self._lib.ms_dictionary_analysis(
+            self._h, self._need(x, self.real_dtype, n2, "x"),
+            self._need(out, self.real_dtype, self.n_bases * n2, "alpha"), _stream_handle(stream)))
+        return out
+
+    def sigma2_hat(self, image, stream=None) -> float:
+        out = _D()
+        self._check(self._lib.ms_sigma2_hat(self._h, self._need(image, self.real_dtype,
+                                                                self.npix ** 2, "image"),
+                                            ctypes.byref(out), _stream_handle(stream)))
+        return out.value
+
+    def lipschitz(self, step: str, chan: int = 0, sigma2: float = 0.0, eta2: float = 0.0,
+                  power_iters: int = 0, stream=None):
+        c, p = _D(), _D()
+        self._check(self._lib.ms_lipschitz(self._h, STEPS[step], chan, sigma2, eta2, power_iters,
+                                           ctypes.byref(c), ctypes.byref(p),
+                                           _stream_handle(stream)))
+        return c.value, p.value
+
+    def minor_cycle(self, step: str, residual, lam: float, max_iters: int, l_low=None,
+                    sigma2: float = 0.0, eta2: float = 0.0, rel_tol: float = 0.0,
+                    beta=None, model_out=None, chan: int = 0, stream=None):
+        n2 = self.npix ** 2
+        model_out = self._image(model_out)
+        st = ms_stats()
+        self._check(self._lib.ms_minor_cycle(
+            self._h, STEPS[step], chan, self._need(residual, self.real_dtype, n2, "residual"),
+            self._need(l_low, self.real_dtype, n2, "l_low") if l_low is not None else None,
+            sigma2, eta2, lam, max_iters, rel_tol,
+            self._need(beta, self.real_dtype, self.n_bases * n2, "beta") if beta is not None else None,
+            self._need(model_out, self.real_dtype, n2, "model_out"), ctypes.byref(st),
+            _stream_handle(stream)))
+        return model_out, Stats.from_c(st)
+
+    def reconstruct_two_step(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
+                             low_out=None, out=None, model_out=None, stream=None):
+        opts = opts or ReconOptions()
+        low_out, out = self._image(low_out), self._image(out)
+        co = opts.to_c()
+        st = ms_stats()
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_reconstruct_two_step(
+            self._h, chan, self._need(vis, self.complex_dtype, self.nvis, "vis"), ctypes.byref(co),
+            self._need(low_out, self.real_dtype, n2, "img_low_out"),
+            self._need(out, self.real_dtype, n2, "img_out"),
+            self._need(model_out, self.real_dtype, n2, "model_out") if model_out is not None else None,
+            ctypes.byref(st), _stream_handle(stream)))
+        return low_out, out, Stats.from_c(st)
+
+    def reconstruct_single_step(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
+                                out=None, model_out=None, stream=None):
+        opts = opts or ReconOptions()
+        out = self._image(out)
+        co = opts.to_c()
+        st = ms_stats()
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_reconstruct_single_step(
+            self._h, chan, self._need(vis, self.complex_dtype, self.nvis, "vis"), ctypes.byref(co),
+            self._need(out, self.real_dtype, n2, "img_out"),
+            self._need(model_out, self.real_dtype, n2, "model_out") if model_out is not None else None,
+            ctypes.byref(st), _stream_handle(stream)))
+        return out, Stats.from_c(st)
+
+
+# module-level names matching the C ABI -------------------------------------
+def ms_plan_create(*args, **kw) -> Plan:
+    return Plan(*args, **kw)
+
+
+def ms_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def ms_partition_counts(plan: Plan, chan: int = 0):
+    return plan.partition_counts(chan)
+
+
+def ms_partition_rows(plan: Plan, part: str, chan: int = 0):
+    return plan.partition_rows(part, chan)
+
+
+def ms_degrid(plan: Plan, part, image, vis_obs=None, out=None, chan=0, stream=None):
+    return plan.degrid(part, image, vis_obs, out, chan, stream)
+
+
+def ms_grid(plan: Plan, part, vis, out=None, chan=0, stream=None):
+    return plan.grid(part, vis, out, chan, stream)
+
+
+def ms_residual_image(plan: Plan, part, vis_obs, model, out=None, chan=0, stream=None):
+    return plan.residual_image(part, vis_obs, model, out, chan, stream)
+
+
+def ms_psf(plan: Plan, part, chan=0, out=None, stream=None):
+    return plan.psf(part, chan, out, stream)
+
+
+def ms_dictionary_synthesis(plan: Plan, alpha, out=None, stream=None):
+    return plan.dictionary_synthesis(alpha, out, stream)
+
+
+def ms_dictionary_analysis(plan: Plan, x, out=None, stream=None):
+    return plan.dictionary_analysis(x, out, stream)
+
+
+def ms_sigma2_hat(plan: Plan, image, stream=None):
+    return plan.sigma2_hat(image, stream)
+
+
+def ms_lipschitz(plan: Plan, step, chan=0, sigma2=0.0, eta2=0.0, power_iters=0, stream=None):
+    return plan.lipschitz(step, chan, sigma2, eta2, power_iters, stream)
+
+
+def ms_minor_cycle(plan: Plan, step, residual, lam, max_iters, **kw):
+    return plan.minor_cycle(step, residual, lam, max_iters, **kw)
+
+
+def ms_reconstruct_two_step(plan: Plan, vis, opts=None, **kw):
+    return plan.reconstruct_two_step(vis, opts, **kw)
+
+
+def ms_reconstruct_single_step(plan: Plan, vis, opts=None, **kw):
+    return plan.reconstruct_single_step(vis, opts, **kw)

@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of libmstep.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+namespace ms {
+
+template <typename R> struct CplxOf;
+template <> struct CplxOf<float> { using T = float2; };
+template <> struct CplxOf<double> { using T = double2; };
+template <typename R> using C2 = typename CplxOf<R>::T;
+
+constexpr int kW = 7;          // ES kernel support in cells
+constexpr int kHalfW = 3;      // (W - 1) / 2
+constexpr int kMaxBases = 8;   // db1 .. db8
+constexpr int kMaxTaps = 16;   // db8 has 16 taps
+constexpr int kMaxLevels = 8;
+
+// One unit of (de)gridding work: `count` sorted rows starting at `start`
+// that all anchor in grid tile `tile`.
+struct WorkItem {
+  int32_t tile;
+  int32_t start;
+  int32_t count;
+  int32_t pad;
+};
+
+// Device-side state of a minor cycle, one per plan.  Read and written only by
+// the library's kernels; the host reads it back after a cycle.
+struct FistaCtl {
+  int32_t k;          // iteration index (coefficients B[k] are current)
+  int32_t done;       // stop flag (converged or iteration budget reached)
+  int32_t converged;
+  int32_t max_iters;
+  int32_t error;
+  int32_t pad[3];
+  double lam;         // lambda
+  double inv_theta;   // mu = 1/theta
+  double theta;
+  double c0;          // constant of the objective
+  double rel_tol;
+  double l1_cur;      // ||B[k]||_1
+  double xkx, bx;     // <x, K x>, <b, x> of B[k]
+  double F_prev, F_cur;
+  double sigma2, eta2;
+  double kmax;        // max K^ (unscaled)
+  double norm2, absmax;  // reductions of the residual image
+  double absmax_first;   // max |i~_1| of the current step
+};
+
+// ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1 (z = 2 t / W).
+__device__ __forceinline__ float es_phi(float z, float beta) {
+  float s = fmaxf(1.0f - z * z, 0.0f);
+  return expf(beta * (sqrtf(s) - 1.0f));
+}
+__device__ __forceinline__ double es_phi(double z, double beta) {
+  double s = fmax(1.0 - z * z, 0.0);
+  return exp(beta * (sqrt(s) - 1.0));
+}
+
+// -------------------------------------------------------------------------
+// launch wrappers (defined in the .cu files); all take the launch stream
+// -------------------------------------------------------------------------
+
+// plan_kernels.cu
+void launch_classify(const double* u, const double* v, const uint8_t* flags, int64_t n,
+                     int Ng, int npix, double dl, double ell, double delta, int tile,
+                     int ntx, uint32_t* cell, double2* frac, uint32_t* tile_id,
+                     uint8_t* member, cudaStream_t s);
+void launch_make_keys(const uint32_t* tile_id, const uint8_t* member, int64_t n,
+                      uint8_t mask, uint32_t sentinel, uint32_t* keys, int32_t* vals,
+                      cudaStream_t s);
+// stable LSD radix sort of (keys, vals) on the low `bits` bits of keys;
+// tmp buffers of n elements; returns the pointers holding the result
+void radix_sort(uint32_t** keys, int32_t** vals, uint32_t* ktmp, int32_t* vtmp, int64_t n,
+                int bits, int32_t* hist, int64_t hist_cap, cudaStream_t s);
+int64_t radix_hist_size(int64_t n);
+void launch_count_tiles(const uint32_t* keys, int64_t n, int32_t* counts, cudaStream_t s);
+void launch_exclusive_scan(const int32_t* in, int32_t* out, int n, cudaStream_t s);
+void launch_chunks_per_tile(const int32_t* counts, int ntiles, int chunk, int32_t* nchunks,
+                            cudaStream_t s);
+void launch_make_items(const int32_t* counts, const int32_t* tile_start,
+                       const int32_t* item_start, int ntiles, int chunk, WorkItem* items,
+                       cudaStream_t s);
+template <typename R>
+void launch_gather_geometry(const int32_t* idx, int64_t n, const uint32_t* cell_all,
+                            const double2* frac_all, uint32_t* cell, C2<R>* frac,
+                            cudaStream_t s);
+template <typename R>
+void launch_gather_vis(const int32_t* idx, int64_t n, const C2<R>* src, C2<R>* dst,
+                       cudaStream_t s);
+template <typename R>
+void launch_scatter_vis(const int32_t* idx, int64_t n, const C2<R>* src, C2<R>* dst,
+                        cudaStream_t s);
+void launch_deapodization(int npix, int ngrid, double beta, const double* nodes,
+                          const double* weights, int nq, double* psi, cudaStream_t s);
+
+// grid_kernels.cu
+template <typename R>
+void launch_pad(const R* image, const R* psi, int npix, int Ng, C2<R>* grid, cudaStream_t s);
+template <typename R>
+void launch_crop(const C2<R>* grid, const R* psi, int npix, int Ng, double scale, R* image,
+                 cudaStream_t s);
+template <typename R>
+void launch_degrid(const CUtensorMap* tmap, const C2<R>* grid, const WorkItem* items,
+                   int nitems, const uint32_t* cell, const C2<R>* frac, const C2<R>* obs,
+                   C2<R>* out, int Ng, int tile, int ntx, double beta, int32_t* err,
+                   cudaStream_t s);
+template <typename R, bool KAHAN>
+void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const C2<R>* frac,
+                 const C2<R>* vis, void* scratch, int Ng, int tile, int ntx, double beta,
+                 cudaStream_t s);
+template <typename R, bool KAHAN>
+void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int tile, int ntx,
+                 C2<R>* grid, cudaStream_t s);
+size_t grid_scratch_cell_bytes(int precision);
+
+// wavelet_kernels.cu
+void set_wavelet_filters(const double* h, const int* len, int nbases);   // host -> __constant__
+struct WaveletGeom {
+  int N, J, M;
+};
+// coef3 / B3 / Yh2 are DEVICE arrays of pointers; with a FistaCtl the kernels
+// pick buffer k % 3 (and k % 2) from it and skip all work once ctl->done is set
+template <typename R>
+void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
+                       const FistaCtl* ctl, cudaStream_t s);
+template <typename R>
+void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s);
+struct ProxArgs {
+  const void* ywork;      // y of the current coefficients (C2R output)
+  const void* b;          // b image of the quadratic objective
+};
+template <typename R>
+void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* tmp,
+                           WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
+                           cudaStream_t s);
+int analysis_prox_partials(WaveletGeom g);
+
+// spectral_kernels.cu
+int spectral_partials(int N);
+template <typename R>
+void launch_ifftshift_real(const R* in, R* out, int N, cudaStream_t s);
+template <typename R>
+void launch_real_part_spectrum(const C2<R>* in, R* out, int n, cudaStream_t s);
+template <typename R>
+void launch_filters(int N, double ell, double delta, const FistaCtl* ctl, R* gl2, R* gh2,
+                    cudaStream_t s);
+template <typename R>
+void launch_normal_spectrum(const R* Hhat, const R* gl2, const R* gh2, int N, int M, R* Ks,
+                            double* parts, FistaCtl* ctl, int32_t* ticket, cudaStream_t s);
+template <typename R>
+void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, const R* gl2,
+                       const R* gh2, int N, C2<R>* Bs, double* parts, FistaCtl* ctl,
+                       int32_t* ticket, cudaStream_t s);
+template <typename R>
+void launch_spec_mul(C2<R>* spec, const R* Ks, const C2<R>* Bs, int N, double* parts,
+                     FistaCtl* ctl, double* trace, int32_t* ticket, cudaStream_t s);
+template <typename R>
+void launch_spec_apply(C2<R>* spec, const R* Ks, int N, cudaStream_t s);
+template <typename R>
+void launch_image_norms(const R* img, int64_t n, double* parts, FistaCtl* ctl, int32_t* ticket,
+                        cudaStream_t s);
+template <typename R>
+void launch_sigma2_hat(const R* img, int N, double* parts, FistaCtl* ctl, int32_t* ticket,
+                       int set_eta, cudaStream_t s);
+void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, cudaStream_t s);
+template <typename R>
+void launch_axpby(const R* x, const R* y, R* out, double a, double b, int64_t n, cudaStream_t s);
+template <typename R>
+void launch_l1(const R* x, int64_t n, double* parts, double* out, int32_t* ticket,
+               cudaStream_t s);
+template <typename R>
+void launch_dot(const R* x, const R* y, int64_t n, double* parts, double* out, int32_t* ticket,
+                cudaStream_t s);
+template <typename R>
+void launch_normalize(R* x, int64_t n, const double* den, cudaStream_t s);
+template <typename R>
+void launch_hash_fill(R* x, int64_t n, uint64_t seed, cudaStream_t s);
+
+}  // namespace ms

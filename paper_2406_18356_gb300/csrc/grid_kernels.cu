@@ -1,0 +1,484 @@
+// Measurement operator kernels (Sect. 2: i~ = F^H G^H (v - G F x)):
+//   pad   : D Z   (deapodize, zero-pad N -> Ng, checkerboard so the FFT is centred)
+//   crop  : Z^H D^H (real part of the centred inverse FFT, deapodize, 1/sum w)
+//   degrid: G     (TMA-staged grid tile, W x W ES taps per visibility)
+//   grid  : G^H   (warp-private shared-memory sub-tiles, no global atomics)
+//   fold  : sums the per-work-item tiles (with their halos) into the grid.
+#include "common.cuh"
+
+namespace ms {
+
+namespace {
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ unsigned mbar_try_wait(uint64_t* bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(phase)
+      : "memory");
+  return ok;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// bounded wait on an mbarrier phase; false if it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+// ES weights of the W taps along one axis, from the centre offset f of the
+// footprint: tap i is at distance t = f + (W-1)/2 - i cells from the sample.
+// phi = exp(beta (sqrt(1 - z^2) - 1)) is evaluated as
+// exp(-beta z^2 / (1 + sqrt(1 - z^2))) so the centre taps keep full precision.
+template <typename R>
+__device__ __forceinline__ void es_weights(R f, R beta, R* w) {
+  const R c = (R)(4.0 / (kW * kW));
+#pragma unroll
+  for (int i = 0; i < kW; ++i) {
+    R t = f + (R)(kHalfW - i);
+    R z2 = t * t * c;
+    R s = (R)1 - z2;
+    s = s > (R)0 ? s : (R)0;
+    w[i] = exp(-beta * z2 / ((R)1 + sqrt(s)));
+  }
+}
+}  // namespace
+
+// ------------------------------------------------------------------ pad / crop
+template <typename R>
+__global__ void pad_kernel(const R* __restrict__ image, const R* __restrict__ psi, int npix,
+                           int Ng, C2<R>* __restrict__ grid) {
+  int64_t total = (int64_t)Ng * Ng;
+  const int h = npix / 2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int rr = (int)(k / Ng), cc = (int)(k % Ng);
+    int a = cc < h ? cc : (cc >= Ng - h ? cc - Ng : INT32_MAX);
+    int b = rr < h ? rr : (rr >= Ng - h ? rr - Ng : INT32_MAX);
+    C2<R> o;
+    o.x = (R)0;
+    o.y = (R)0;
+    if (a != INT32_MAX && b != INT32_MAX) {
+      int q = a + h, p = b + h;
+      R val = image[(int64_t)p * npix + q] / (psi[p] * psi[q]);
+      o.x = ((a + b) & 1) ? -val : val;
+    }
+    grid[k] = o;
+  }
+}
+
+template <typename R>
+__global__ void crop_kernel(const C2<R>* __restrict__ grid, const R* __restrict__ psi,
+                            int npix, int Ng, R scale, R* __restrict__ image) {
+  int64_t total = (int64_t)npix * npix;
+  const int h = npix / 2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(k / npix), q = (int)(k % npix);
+    int a = q - h, b = p - h;
+    int cc = a < 0 ? a + Ng : a;
+    int rr = b < 0 ? b + Ng : b;
+    R val = grid[(int64_t)rr * Ng + cc].x * scale / (psi[p] * psi[q]);
+    image[k] = ((a + b) & 1) ? -val : val;
+  }
+}
+
+template <typename R>
+void launch_pad(const R* image, const R* psi, int npix, int Ng, C2<R>* grid, cudaStream_t s) {
+  int64_t total = (int64_t)Ng * Ng;
+  int blocks = (int)((total + kThreads - 1) / kThreads);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  pad_kernel<R><<<blocks, kThreads, 0, s>>>(image, psi, npix, Ng, grid);
+}
+
+template <typename R>
+void launch_crop(const C2<R>* grid, const R* psi, int npix, int Ng, double scale, R* image,
+                 cudaStream_t s) {
+  int64_t total = (int64_t)npix * npix;
+  int blocks = (int)((total + kThreads - 1) / kThreads);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  crop_kernel<R><<<blocks, kThreads, 0, s>>>(grid, psi, npix, Ng, (R)scale, image);
+}
+
+// ------------------------------------------------------------------ degrid
+// One CTA per work item.  The (T + W - 1)^2 grid region that the item's
+// footprints cover is staged in shared memory by one TMA tensor copy (plain
+// loads with periodic wrap for tiles on the grid's last row/column), then each
+// thread interpolates visibilities: V = sum_j phi_v[j] sum_i phi_u[i] G[..].
+template <typename R, bool HAS_OBS>
+__global__ void __launch_bounds__(kThreads)
+    degrid_kernel(const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ grid,
+                  const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
+                  const C2<R>* __restrict__ frac, const C2<R>* __restrict__ obs,
+                  C2<R>* __restrict__ out, int Ng, int T, int ntx, R beta,
+                  int32_t* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  C2<R>* tile = reinterpret_cast<C2<R>*>(smem_raw);
+  const int S = T + kW - 1;
+  const WorkItem it = items[blockIdx.x];
+  const int tx = it.tile % ntx, ty = it.tile / ntx;
+  const int ox = tx * T, oy = ty * T;
+  const bool edge = (ox + S > Ng) || (oy + S > Ng);
+  bool ok = true;
+  if (!edge) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      mbar_expect_tx(&bar, (unsigned)(S * S * sizeof(C2<R>)));
+      tma_load_2d(tile, &tmap, 2 * ox, oy, &bar);
+    }
+    ok = mbar_wait_bounded(&bar, 0);
+    if (!ok) {
+      if (threadIdx.x == 0) atomicExch(err, 5);
+      mbar_wait_bounded(&bar, 0);   // give the copy in flight a second bounded chance
+      return;
+    }
+  } else {
+    for (int c = threadIdx.x; c < S * S; c += blockDim.x) {
+      int lv = c / S, lu = c - lv * S;
+      int gy = oy + lv, gx = ox + lu;
+      gy -= gy >= Ng ? Ng : 0;
+      gx -= gx >= Ng ? Ng : 0;
+      tile[c] = grid[(int64_t)gy * Ng + gx];
+    }
+    __syncthreads();
+  }
+  const int end = it.start + it.count;
+  for (int k = it.start + threadIdx.x; k < end; k += blockDim.x) {
+    uint32_t pc = cell[k];
+    int lu = (int)(pc & 0xffffu) - ox;
+    int lv = (int)(pc >> 16) - oy;
+    C2<R> f = frac[k];
+    R wu[kW], wv[kW];
+    es_weights<R>(f.x, beta, wu);
+    es_weights<R>(f.y, beta, wv);
+    R accr = 0, acci = 0;
+#pragma unroll
+    for (int j = 0; j < kW; ++j) {
+      const C2<R>* row = tile + (lv + j) * S + lu;
+      R rr = 0, ri = 0;
+#pragma unroll
+      for (int i = 0; i < kW; ++i) {
+        C2<R> g = row[i];
+        rr += wu[i] * g.x;
+        ri += wu[i] * g.y;
+      }
+      accr += wv[j] * rr;
+      acci += wv[j] * ri;
+    }
+    C2<R> o;
+    if (HAS_OBS) {
+      C2<R> v = obs[k];
+      o.x = v.x - accr;
+      o.y = v.y - acci;
+    } else {
+      o.x = accr;
+      o.y = acci;
+    }
+    out[k] = o;
+  }
+}
+
+template <typename R>
+void launch_degrid(const CUtensorMap* tmap, const C2<R>* grid, const WorkItem* items,
+                   int nitems, const uint32_t* cell, const C2<R>* frac, const C2<R>* obs,
+                   C2<R>* out, int Ng, int tile, int ntx, double beta, int32_t* err,
+                   cudaStream_t s) {
+  if (nitems <= 0) return;
+  const int S = tile + kW - 1;
+  size_t smem = (size_t)S * S * sizeof(C2<R>);
+  if (obs) {
+    auto k = degrid_kernel<R, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nitems, kThreads, smem, s>>>(*tmap, grid, items, cell, frac, obs, out, Ng, tile, ntx,
+                                     (R)beta, err);
+  } else {
+    auto k = degrid_kernel<R, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nitems, kThreads, smem, s>>>(*tmap, grid, items, cell, frac, obs, out, Ng, tile, ntx,
+                                     (R)beta, err);
+  }
+}
+
+// ------------------------------------------------------------------ grid
+// Scratch holds one (T + W - 1)^2 tile per work item: float2 for the plain
+// FP32 form, double2 for FP64 and for the compensated FP32 form.
+template <typename R, bool KAHAN> struct ScratchOf { using T = double2; };
+template <> struct ScratchOf<float, false> { using T = float2; };
+
+size_t grid_scratch_cell_bytes(int precision) { return precision == 1 ? 8 : 16; }
+
+template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_warps() {
+  return (KAHAN || sizeof(R) == 8) ? 4 : 8;
+}
+
+// A warp grids one visibility at a time: lane t < 32 takes tap t, lanes
+// 0..16 then take taps 32..48 (tap t = (i, j) = (t mod 7, t div 7)).  The 49
+// cells of one visibility are distinct, so a read-modify-write per lane needs
+// no atomics; __syncwarp orders successive visibilities.  Each warp owns its
+// sub-tile, so no two warps ever touch the same word; the compensated form
+// keeps a Kahan correction word per cell component.  At the end the warps'
+// tiles are summed in a fixed order into the item's scratch tile.
+template <typename R, bool KAHAN>
+__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
+    grid_kernel(const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
+                const C2<R>* __restrict__ frac, const C2<R>* __restrict__ vis,
+                typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int Ng, int T, int ntx,
+                R beta) {
+  using Acc = typename ScratchOf<R, KAHAN>::T;
+  constexpr int NW = grid_warps<R, KAHAN>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int S = T + kW - 1;
+  const int cells = S * S;
+  C2<R>* tiles = reinterpret_cast<C2<R>*>(smem_raw);                  // [NW][cells]
+  C2<R>* comps = tiles + (KAHAN ? NW * cells : 0);                     // [NW][cells]
+  R* stage_w = reinterpret_cast<R*>(tiles + (KAHAN ? 2 : 1) * NW * cells);  // [NW][32][14]
+  C2<R>* stage_v = reinterpret_cast<C2<R>*>(stage_w + NW * 32 * 2 * kW);     // [NW][32]
+  int* stage_c = reinterpret_cast<int*>(stage_v + NW * 32);                  // [NW][32]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const WorkItem it = items[blockIdx.x];
+  const int ox = (it.tile % ntx) * T, oy = (it.tile / ntx) * T;
+
+  for (int c = threadIdx.x; c < NW * cells; c += blockDim.x) {
+    C2<R> z;
+    z.x = (R)0;
+    z.y = (R)0;
+    tiles[c] = z;
+    if (KAHAN) comps[c] = z;
+  }
+  __syncthreads();
+
+  C2<R>* my = tiles + warp * cells;
+  C2<R>* myc = comps + warp * cells;
+  R* sw = stage_w + warp * 32 * 2 * kW;
+  C2<R>* sv = stage_v + warp * 32;
+  int* sc = stage_c + warp * 32;
+  const int i1 = lane % kW, j1 = lane / kW;
+  const int i2 = (lane + 32) % kW, j2 = (lane + 32) / kW;
+  const bool two = lane + 32 < kW * kW;
+
+  const int per = (it.count + NW - 1) / NW;
+  const int ws = it.start + warp * per;
+  int we = ws + per;
+  if (we > it.start + it.count) we = it.start + it.count;
+  for (int base = ws; base < we; base += 32) {
+    int k = base + lane;
+    if (k < we) {
+      uint32_t pc = cell[k];
+      int lu = (int)(pc & 0xffffu) - ox;
+      int lv = (int)(pc >> 16) - oy;
+      C2<R> f = frac[k];
+      es_weights<R>(f.x, beta, sw + lane * 2 * kW);
+      es_weights<R>(f.y, beta, sw + lane * 2 * kW + kW);
+      sv[lane] = vis[k];
+      sc[lane] = lv * S + lu;
+    }
+    __syncwarp();
+    int nb = we - base < 32 ? we - base : 32;
+    for (int sidx = 0; sidx < nb; ++sidx) {
+      const R* w = sw + sidx * 2 * kW;
+      const C2<R> val = sv[sidx];
+      const int c0 = sc[sidx];
+      {
+        R wt = w[i1] * w[kW + j1];
+        int c = c0 + j1 * S + i1;
+        C2<R> a = my[c];
+        if (KAHAN) {
+          C2<R> cp = myc[c];
+          R yr = wt * val.x - cp.x, yi = wt * val.y - cp.y;
+          R tr = a.x + yr, ti = a.y + yi;
+          cp.x = (tr - a.x) - yr;
+          cp.y = (ti - a.y) - yi;
+          a.x = tr;
+          a.y = ti;
+          myc[c] = cp;
+        } else {
+          a.x += wt * val.x;
+          a.y += wt * val.y;
+        }
+        my[c] = a;
+      }
+      if (two) {
+        R wt = w[i2] * w[kW + j2];
+        int c = c0 + j2 * S + i2;
+        C2<R> a = my[c];
+        if (KAHAN) {
+          C2<R> cp = myc[c];
+          R yr = wt * val.x - cp.x, yi = wt * val.y - cp.y;
+          R tr = a.x + yr, ti = a.y + yi;
+          cp.x = (tr - a.x) - yr;
+          cp.y = (ti - a.y) - yi;
+          a.x = tr;
+          a.y = ti;
+          myc[c] = cp;
+        } else {
+          a.x += wt * val.x;
+          a.y += wt * val.y;
+        }
+        my[c] = a;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  Acc* dst = scratch + (int64_t)blockIdx.x * cells;
+  for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+    Acc s;
+    s.x = 0;
+    s.y = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      C2<R> a = tiles[w * cells + c];
+      if (KAHAN) {
+        C2<R> cp = comps[w * cells + c];
+        s.x += (double)a.x - (double)cp.x;
+        s.y += (double)a.y - (double)cp.y;
+      } else {
+        s.x += a.x;
+        s.y += a.y;
+      }
+    }
+    dst[c] = s;
+  }
+}
+
+template <typename R, bool KAHAN>
+void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const C2<R>* frac,
+                 const C2<R>* vis, void* scratch, int Ng, int tile, int ntx, double beta,
+                 cudaStream_t s) {
+  if (nitems <= 0) return;
+  constexpr int NW = grid_warps<R, KAHAN>();
+  const int S = tile + kW - 1;
+  size_t smem = (size_t)NW * S * S * sizeof(C2<R>) * (KAHAN ? 2 : 1) +
+                (size_t)NW * 32 * (2 * kW * sizeof(R) + sizeof(C2<R>) + sizeof(int));
+  auto k = grid_kernel<R, KAHAN>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<nitems, 32 * NW, smem, s>>>(items, cell, frac, vis,
+                                 reinterpret_cast<typename ScratchOf<R, KAHAN>::T*>(scratch),
+                                 Ng, tile, ntx, (R)beta);
+}
+
+// Every grid cell sums, in a fixed order, the scratch tiles of all work items
+// of the (up to four) tiles whose footprint region covers it: its own tile
+// and, within W - 1 cells of a tile edge, the tiles to the left and above
+// (periodically).  Each cell is written once, so the grid needs no clearing.
+template <typename R, bool KAHAN>
+__global__ void fold_kernel(const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
+                            const int32_t* __restrict__ tile_items, int Ng, int T, int ntx,
+                            C2<R>* __restrict__ grid) {
+  using Acc = typename ScratchOf<R, KAHAN>::T;
+  const int S = T + kW - 1;
+  const int cells = S * S;
+  int64_t total = (int64_t)Ng * Ng;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int cv = (int)(k / Ng), cu = (int)(k % Ng);
+    int tx = cu / T, ty = cv / T, ou = cu - tx * T, ov = cv - ty * T;
+    Acc sum;
+    sum.x = 0;
+    sum.y = 0;
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      if (dy && ov >= kW - 1) break;
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        if (dx && ou >= kW - 1) break;
+        int stx = tx - dx, sty = ty - dy;
+        stx += stx < 0 ? ntx : 0;
+        sty += sty < 0 ? ntx : 0;
+        int t = sty * ntx + stx;
+        int off = (ov + dy * T) * S + (ou + dx * T);
+        int e = tile_items[t + 1];
+        for (int i = tile_items[t]; i < e; ++i) {
+          Acc a = scratch[(int64_t)i * cells + off];
+          sum.x += a.x;
+          sum.y += a.y;
+        }
+      }
+    }
+    C2<R> o;
+    o.x = (R)sum.x;
+    o.y = (R)sum.y;
+    grid[k] = o;
+  }
+}
+
+template <typename R, bool KAHAN>
+void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int tile, int ntx,
+                 C2<R>* grid, cudaStream_t s) {
+  int64_t total = (int64_t)Ng * Ng;
+  int blocks = (int)((total + kThreads - 1) / kThreads);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  fold_kernel<R, KAHAN><<<blocks, kThreads, 0, s>>>(
+      reinterpret_cast<const typename ScratchOf<R, KAHAN>::T*>(scratch), tile_items, Ng, tile,
+      ntx, grid);
+}
+
+// ---------------------------------------------------------------- instances
+template void launch_pad<float>(const float*, const float*, int, int, float2*, cudaStream_t);
+template void launch_pad<double>(const double*, const double*, int, int, double2*,
+                                 cudaStream_t);
+template void launch_crop<float>(const float2*, const float*, int, int, double, float*,
+                                 cudaStream_t);
+template void launch_crop<double>(const double2*, const double*, int, int, double, double*,
+                                  cudaStream_t);
+template void launch_degrid<float>(const CUtensorMap*, const float2*, const WorkItem*, int,
+                                   const uint32_t*, const float2*, const float2*, float2*, int,
+                                   int, int, double, int32_t*, cudaStream_t);
+template void launch_degrid<double>(const CUtensorMap*, const double2*, const WorkItem*, int,
+                                    const uint32_t*, const double2*, const double2*, double2*,
+                                    int, int, int, double, int32_t*, cudaStream_t);
+template void launch_grid<float, false>(const WorkItem*, int, const uint32_t*, const float2*,
+                                        const float2*, void*, int, int, int, double,
+                                        cudaStream_t);
+template void launch_grid<float, true>(const WorkItem*, int, const uint32_t*, const float2*,
+                                       const float2*, void*, int, int, int, double,
+                                       cudaStream_t);
+template void launch_grid<double, false>(const WorkItem*, int, const uint32_t*, const double2*,
+                                         const double2*, void*, int, int, int, double,
+                                         cudaStream_t);
+template void launch_fold<float, false>(const void*, const int32_t*, int, int, int, float2*,
+                                        cudaStream_t);
+template void launch_fold<float, true>(const void*, const int32_t*, int, int, int, float2*,
+                                       cudaStream_t);
+template void launch_fold<double, false>(const void*, const int32_t*, int, int, int, double2*,
+                                         cudaStream_t);
+
+}  // namespace ms

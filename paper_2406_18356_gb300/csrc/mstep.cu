@@ -1,0 +1,1225 @@
+// libmstep: plan object, C ABI and the orchestration of the method.
+//
+// Host code only sequences kernels: every step of the path (partitioning,
+// sorting, gridding, FFT stages through cuFFT, wavelets, FISTA, reductions)
+// runs on the device.  All work of a call is issued on a plan-owned stream
+// that is ordered after the caller's stream at entry, and the caller's stream
+// is ordered after it at exit.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mstep.h"
+
+using namespace ms;
+
+namespace {
+
+// ---------------------------------------------------------------- helpers
+struct Fail {
+  ms_status st;
+  std::string msg;
+};
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Fail{e == cudaErrorMemoryAllocation ? MS_ERR_OOM : MS_ERR_CUDA,
+               std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+void ckf(cufftResult r, const char* what) {
+  if (r != CUFFT_SUCCESS)
+    throw Fail{r == CUFFT_ALLOC_FAILED ? MS_ERR_OOM : MS_ERR_CUDA,
+               std::string(what) + ": cuFFT error " + std::to_string((int)r)};
+}
+
+void arg(bool ok, const char* what) {
+  if (!ok) throw Fail{MS_ERR_ARG, what};
+}
+
+template <typename T> T* dalloc(size_t n, const char* what) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  ck(cudaMalloc(&p, n * sizeof(T)), what);
+  return static_cast<T*>(p);
+}
+
+// Daubechies low-pass filter db_p (2p taps, sum sqrt 2): roots y_i of
+// P(y) = sum_{k<p} C(p-1+k, k) y^k by Durand-Kerner iteration in long double,
+// each mapped to the root z of z + 1/z = 2 - 4 y_i with |z| > 1, then
+// h ~ (1 + z)^p prod (z - z_i) in ascending powers of z.
+std::vector<double> daubechies(int p) {
+  typedef std::complex<long double> cx;
+  if (p == 1) return {std::sqrt(0.5), std::sqrt(0.5)};
+  const int deg = p - 1;
+  std::vector<long double> c(p);
+  for (int k = 0; k < p; ++k) {
+    long double b = 1;   // C(p-1+k, k)
+    for (int i = 1; i <= k; ++i) b = b * (p - 1 + i) / i;
+    c[k] = b;
+  }
+  auto P = [&](cx y) {
+    cx s = 0;
+    for (int k = deg; k >= 0; --k) s = s * y + c[k];
+    return s;
+  };
+  std::vector<cx> r(deg);
+  for (int i = 0; i < deg; ++i) r[i] = std::pow(cx(0.4L, 0.9L), i);
+  for (int it = 0; it < 2000; ++it) {
+    long double moved = 0;
+    for (int i = 0; i < deg; ++i) {
+      cx den = c[deg];
+      for (int j = 0; j < deg; ++j)
+        if (j != i) den *= (r[i] - r[j]);
+      cx d = P(r[i]) / den;
+      r[i] -= d;
+      moved = std::max(moved, std::abs(d));
+    }
+    if (moved < 1e-30L) break;
+  }
+  std::vector<cx> q(1, cx(1));   // ascending powers of z
+  for (int i = 0; i < deg; ++i) {
+    cx s = cx(1) - cx(2) * r[i];
+    cx disc = std::sqrt(s * s - cx(1));
+    cx z = s + disc;
+    if (std::abs(z) < 1) z = s - disc;
+    std::vector<cx> nq(q.size() + 1, cx(0));
+    for (size_t k = 0; k < q.size(); ++k) {
+      nq[k] -= z * q[k];
+      nq[k + 1] += q[k];
+    }
+    q.swap(nq);
+  }
+  std::vector<cx> h(q.size() + p, cx(0));
+  for (size_t k = 0; k < q.size(); ++k) {
+    long double b = 1;
+    for (int i = 0; i <= p; ++i) {
+      h[k + i] += b * q[k];
+      b = b * (p - i) / (i + 1);
+    }
+  }
+  long double sum = 0;
+  for (auto& v : h) sum += v.real();
+  std::vector<double> out(h.size());
+  for (size_t k = 0; k < h.size(); ++k)
+    out[k] = (double)(h[k].real() * std::sqrt((long double)2) / sum);
+  return out;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the three-term
+// recurrence of P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    long double z = std::cos(pi * (i + 0.75L) / (n + 0.5L));
+    long double dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      long double p0 = 1, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1);
+      long double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-19L) break;
+    }
+    x[i] = (double)z;
+    w[i] = (double)(2 / ((1 - z * z) * dp * dp));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+__global__ void set_ptrs_kernel(void** dst, void* a, void* b, void* c) {
+  dst[0] = a;
+  dst[1] = b;
+  dst[2] = c;
+}
+
+__global__ void init_ctl_kernel(FistaCtl* ctl, int max_iters, double rel_tol, double lam,
+                                int set_lam, double sigma2, double eta2, int set_noise) {
+  ctl->k = 0;
+  ctl->done = 0;
+  ctl->converged = 0;
+  ctl->max_iters = max_iters;
+  ctl->error = 0;
+  ctl->rel_tol = rel_tol;
+  if (set_lam) ctl->lam = lam;
+  if (set_noise) {
+    ctl->sigma2 = sigma2;
+    ctl->eta2 = eta2;
+  }
+  ctl->F_prev = NAN;
+  ctl->F_cur = NAN;
+}
+
+__global__ void set_eta_kernel(FistaCtl* ctl, double eta2) { ctl->eta2 = eta2; }
+
+__global__ void check_noise_kernel(FistaCtl* ctl) {
+  if (!(ctl->sigma2 > 0.0) || !(ctl->eta2 > 0.0) || !isfinite(ctl->sigma2) ||
+      !isfinite(ctl->eta2))
+    ctl->error = 4;
+}
+
+}  // namespace
+
+// ====================================================================== plan
+struct PartDev {
+  int64_t n = 0;
+  int32_t* idx = nullptr;
+  uint32_t* cell = nullptr;
+  void* frac = nullptr;
+  WorkItem* items = nullptr;
+  int nitems = 0;
+  int32_t* tile_items = nullptr;
+  void* Hhat = nullptr;
+  bool have_psf = false;
+};
+
+struct ChanDev {
+  PartDev part[3];
+  int64_t counts[4] = {0, 0, 0, 0};
+};
+
+struct ms_plan {
+  ms_plan_desc d{};
+  int dev = 0, N = 0, Ng = 0, T = 0, S = 0, ntx = 0, ntiles = 0, J = 0, M = 0, prec = 0;
+  int chunk = 0;
+  size_t rsz = 8;
+  double beta = 0;
+  std::vector<ChanDev> ch;
+  std::vector<void*> allocs;
+  cudaStream_t ps = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaEvent_t> tev;   // timing events
+  // tables / workspaces
+  void* psi = nullptr;
+  void* grid = nullptr;
+  void* scratch = nullptr;
+  int max_items = 0;
+  int64_t max_n = 0;
+  void *vis_a = nullptr, *vis_b = nullptr;
+  void* img[6] = {};
+  void *B[3] = {}, *Yh[2] = {}, *xwork = nullptr, *ywork = nullptr;
+  void *spec = nullptr, *spec2 = nullptr, *Ks = nullptr, *Bs = nullptr, *bimg = nullptr;
+  void *gl2 = nullptr, *gh2 = nullptr, *wtmp = nullptr;
+  void **B3_dev = nullptr, **Yh2_dev = nullptr, **api3_dev = nullptr;
+  FistaCtl* ctl = nullptr;
+  double* trace = nullptr;
+  double* parts = nullptr;     // reduction partials (one reduction at a time)
+  double* l1parts = nullptr;   // per-block |B_k+1| partials of the analysis levels
+  int32_t* tickets = nullptr;
+  double* scal = nullptr;
+  int32_t* err = nullptr;
+  int trace_cap = 0;
+  cufftHandle c2c = 0, r2c = 0, c2r = 0;
+  CUtensorMap tmap{};
+  std::string msg;
+  std::vector<double> htrace;
+  // captured FISTA passes
+  cudaGraphExec_t fista_exec = nullptr;
+  int fista_graph_step = -1;
+  int fista_graph_passes = 0;
+
+  template <typename T> T* alloc(size_t n, const char* what) {
+    T* p = dalloc<T>(n, what);
+    allocs.push_back(p);
+    return p;
+  }
+};
+
+namespace {
+
+constexpr int kPasses = 8;   // FISTA passes per captured graph launch
+
+struct Timer {
+  ms_plan* p;
+  std::vector<std::pair<int, int>> spans[3];   // grid, fft, minor
+  int used = 0;
+  explicit Timer(ms_plan* pl) : p(pl) {}
+  int mark() {
+    if (used >= (int)p->tev.size()) {
+      cudaEvent_t e;
+      ck(cudaEventCreate(&e), "event");
+      p->tev.push_back(e);
+    }
+    ck(cudaEventRecord(p->tev[used], p->ps), "event record");
+    return used++;
+  }
+  double total(int which) {
+    double t = 0;
+    for (auto& s : spans[which]) {
+      float ms = 0;
+      ck(cudaEventElapsedTime(&ms, p->tev[s.first], p->tev[s.second]), "event time");
+      t += ms;
+    }
+    return t;
+  }
+};
+
+struct Scope {
+  ms_plan* p;
+  cudaStream_t user;
+  int prev_dev = 0;
+  Scope(ms_plan* pl, void* stream) : p(pl), user((cudaStream_t)stream) {
+    cudaGetDevice(&prev_dev);
+    ck(cudaSetDevice(p->dev), "set device");
+    ck(cudaEventRecord(p->ev_in, user), "event record");
+    ck(cudaStreamWaitEvent(p->ps, p->ev_in, 0), "stream wait");
+  }
+  void finish() {
+    ck(cudaEventRecord(p->ev_out, p->ps), "event record");
+    ck(cudaStreamWaitEvent(user, p->ev_out, 0), "stream wait");
+    ck(cudaGetLastError(), "kernel launch");
+  }
+  ~Scope() { cudaSetDevice(prev_dev); }
+};
+
+template <typename F> ms_status guarded(ms_plan* p, F&& f) {
+  if (!p) return MS_ERR_ARG;
+  try {
+    p->msg.clear();
+    f();
+    return MS_OK;
+  } catch (const Fail& e) {
+    p->msg = e.msg;
+    return e.st;
+  } catch (const std::exception& e) {
+    p->msg = e.what();
+    return MS_ERR_CUDA;
+  } catch (...) {
+    p->msg = "unknown failure";
+    return MS_ERR_CUDA;
+  }
+}
+
+void check_device_error(ms_plan* p) {
+  int32_t e = 0;
+  ck(cudaMemcpyAsync(&e, p->err, sizeof(e), cudaMemcpyDeviceToHost, p->ps), "read error flag");
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  if (e) {
+    ck(cudaMemsetAsync(p->err, 0, sizeof(int32_t), p->ps), "clear error flag");
+    throw Fail{(ms_status)e, e == MS_ERR_TIMEOUT ? "a bounded device wait ran out"
+                                                 : "device-side error"};
+  }
+}
+
+PartDev& part_of(ms_plan* p, int part, int chan) {
+  arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+  arg(part >= 0 && part <= 2, "partition must be MS_PART_L, MS_PART_H or MS_PART_ALL");
+  return p->ch[chan].part[part];
+}
+
+// ------------------------------------------------------ measurement operator
+template <typename R> void fft_c2c(ms_plan* p, int dir) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecZ2Z(p->c2c, (cufftDoubleComplex*)p->grid, (cufftDoubleComplex*)p->grid, dir),
+        "Z2Z");
+  else
+    ckf(cufftExecC2C(p->c2c, (cufftComplex*)p->grid, (cufftComplex*)p->grid, dir), "C2C");
+}
+
+template <typename R> void fft_r2c(ms_plan* p, const void* in, void* out) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecD2Z(p->r2c, (cufftDoubleReal*)in, (cufftDoubleComplex*)out), "D2Z");
+  else
+    ckf(cufftExecR2C(p->r2c, (cufftReal*)in, (cufftComplex*)out), "R2C");
+}
+
+template <typename R> void fft_c2r(ms_plan* p, void* in, void* out) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecZ2D(p->c2r, (cufftDoubleComplex*)in, (cufftDoubleReal*)out), "Z2D");
+  else
+    ckf(cufftExecC2R(p->c2r, (cufftComplex*)in, (cufftReal*)out), "C2R");
+}
+
+// model grid = F Z D image (centred)
+template <typename R> void image_to_grid(ms_plan* p, const void* image, Timer* tm) {
+  launch_pad<R>((const R*)image, (const R*)p->psi, p->N, p->Ng, (C2<R>*)p->grid, p->ps);
+  int a = tm ? tm->mark() : 0;
+  fft_c2c<R>(p, CUFFT_FORWARD);
+  if (tm) tm->spans[1].push_back({a, tm->mark()});
+}
+
+// sorted visibilities -> model (or residual when obs given) with G
+template <typename R>
+void degrid_sorted(ms_plan* p, PartDev& pd, const void* obs_sorted, void* out_sorted, Timer* tm) {
+  int a = tm ? tm->mark() : 0;
+  launch_degrid<R>(&p->tmap, (const C2<R>*)p->grid, pd.items, pd.nitems, pd.cell,
+                   (const C2<R>*)pd.frac, (const C2<R>*)obs_sorted, (C2<R>*)out_sorted, p->Ng,
+                   p->T, p->ntx, p->beta, p->err, p->ps);
+  if (tm) tm->spans[0].push_back({a, tm->mark()});
+}
+
+// sorted visibilities -> image = Re(D Z^H F^H G^H y) / sum(w)
+template <typename R>
+void grid_sorted(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image, Timer* tm) {
+  int a = tm ? tm->mark() : 0;
+  if (p->prec == MS_FP32_KAHAN) {
+    launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
+                             (const float2*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx,
+                             p->beta, p->ps);
+    launch_fold<float, true>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
+                             p->ps);
+  } else {
+    launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
+                          (const C2<R>*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx, p->beta,
+                          p->ps);
+    launch_fold<R, false>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid,
+                          p->ps);
+  }
+  int b = tm ? tm->mark() : 0;
+  if (tm) tm->spans[0].push_back({a, b});
+  fft_c2c<R>(p, CUFFT_INVERSE);
+  if (tm) tm->spans[1].push_back({b, tm->mark()});
+  double sc = pd.n > 0 ? 1.0 / (double)pd.n : 0.0;
+  launch_crop<R>((const C2<R>*)p->grid, (const R*)p->psi, p->N, p->Ng, sc, (R*)image, p->ps);
+}
+
+// i~ = A^H (obs - A model) / sum(w), obs already sorted
+template <typename R>
+void residual_sorted(ms_plan* p, PartDev& pd, const void* obs_sorted, const void* model,
+                     void* out, Timer* tm) {
+  image_to_grid<R>(p, model, tm);
+  degrid_sorted<R>(p, pd, obs_sorted, p->vis_b, tm);
+  grid_sorted<R>(p, pd, p->vis_b, out, tm);
+}
+
+__global__ void impulse_kernel(void* img, int N, int is_double) {
+  int64_t c = (int64_t)(N / 2) * N + N / 2;
+  if (is_double)
+    static_cast<double*>(img)[c] = 1.0;
+  else
+    static_cast<float*>(img)[c] = 1.0f;
+}
+
+// PSF = A^H A delta / sum(w), delta the unit impulse at (N/2, N/2)
+template <typename R> void psf_image(ms_plan* p, PartDev& pd, void* out) {
+  const int N = p->N;
+  R* delta = (R*)p->img[5];
+  ck(cudaMemsetAsync(delta, 0, sizeof(R) * N * N, p->ps), "memset");
+  impulse_kernel<<<1, 1, 0, p->ps>>>(delta, N, sizeof(R) == 8);
+  image_to_grid<R>(p, delta, nullptr);
+  degrid_sorted<R>(p, pd, nullptr, p->vis_b, nullptr);
+  grid_sorted<R>(p, pd, p->vis_b, out, nullptr);
+}
+
+template <typename R> void ensure_psf(ms_plan* p, PartDev& pd) {
+  if (pd.have_psf) return;
+  const int N = p->N;
+  R* delta = (R*)p->img[5];
+  R* psf = (R*)p->img[4];
+  psf_image<R>(p, pd, psf);
+  launch_ifftshift_real<R>(psf, delta, N, p->ps);
+  fft_r2c<R>(p, delta, p->spec2);
+  launch_real_part_spectrum<R>((const C2<R>*)p->spec2, (R*)pd.Hhat, N * (N / 2 + 1), p->ps);
+  ck(cudaStreamSynchronize(p->ps), "psf");
+  pd.have_psf = true;
+}
+
+// ------------------------------------------------------------- minor cycle
+template <typename R> void record_fista_pass(ms_plan* p) {
+  WaveletGeom g{p->N, p->J, p->M};
+  launch_synthesis3<R>((const R* const*)p->B3_dev, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps);
+  fft_r2c<R>(p, p->xwork, p->spec);
+  launch_spec_mul<R>((C2<R>*)p->spec, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts,
+                     p->ctl, p->trace, p->tickets + 0, p->ps);
+  fft_c2r<R>(p, p->spec, p->ywork);
+  ProxArgs a{p->ywork, p->bimg};
+  launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
+                           p->ctl, p->tickets + 1, p->l1parts, p->ps);
+}
+
+template <typename R> void ensure_fista_graph(ms_plan* p) {
+  if (p->fista_exec) return;
+  cudaGraph_t graph;
+  ck(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p);
+  } catch (...) {
+    cudaStreamEndCapture(p->ps, &graph);
+    throw;
+  }
+  ck(cudaStreamEndCapture(p->ps, &graph), "end capture");
+  ck(cudaGraphInstantiate(&p->fista_exec, graph, 0), "graph instantiate");
+  cudaGraphDestroy(graph);
+}
+
+// Prepare K^, theta (once per step and channel) into the plan buffers.
+// step: LOW/SINGLE use the partition PSF only; FULL adds the filters built
+// from ctl->sigma2, ctl->eta2.
+template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, double ell,
+                                        double delta) {
+  ensure_psf<R>(p, pd);
+  if (step == MS_STEP_FULL) {
+    check_noise_kernel<<<1, 1, 0, p->ps>>>(p->ctl);
+    launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
+    launch_normal_spectrum<R>((const R*)pd.Hhat, (const R*)p->gl2, (const R*)p->gh2, p->N, p->M,
+                              (R*)p->Ks, p->parts, p->ctl, p->tickets + 2, p->ps);
+  } else {
+    launch_normal_spectrum<R>((const R*)pd.Hhat, nullptr, nullptr, p->N, p->M, (R*)p->Ks,
+                              p->parts, p->ctl, p->tickets + 2, p->ps);
+  }
+}
+
+// b, c0 from the residual (and l_low for FULL), then the FISTA loop.  The
+// result coefficients end in B[k % 3], W beta in xwork.
+template <typename R>
+void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const void* l_low,
+               const void* beta0, int max_iters, double rel_tol) {
+  const int N = p->N;
+  const int64_t npix2 = (int64_t)N * N;
+  const int64_t ncoef = (int64_t)p->M * npix2;
+  const int64_t nspec = (int64_t)N * (N / 2 + 1);
+  fft_r2c<R>(p, residual, p->spec);
+  if (step == MS_STEP_FULL) {
+    fft_r2c<R>(p, l_low, p->spec2);
+    launch_b_spectrum<R>((const C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)pd.Hhat,
+                         (const R*)p->gl2, (const R*)p->gh2, N, (C2<R>*)p->Bs, p->parts, p->ctl,
+                         p->tickets + 3, p->ps);
+  } else {
+    launch_b_spectrum<R>((const C2<R>*)p->spec, nullptr, (const R*)pd.Hhat, nullptr, nullptr, N,
+                         (C2<R>*)p->Bs, p->parts, p->ctl, p->tickets + 3, p->ps);
+  }
+  // the inverse real FFT overwrites its input: transform a copy of B^
+  ck(cudaMemcpyAsync(p->spec2, p->Bs, sizeof(C2<R>) * nspec, cudaMemcpyDeviceToDevice, p->ps),
+     "copy");
+  fft_c2r<R>(p, p->spec2, p->bimg);
+  // B[0] = start, B[2] = B[0] (its weight is zero for k < 2), y history zero
+  if (beta0)
+    ck(cudaMemcpyAsync(p->B[0], beta0, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
+       "copy");
+  else
+    ck(cudaMemsetAsync(p->B[0], 0, sizeof(R) * ncoef, p->ps), "memset");
+  ck(cudaMemcpyAsync(p->B[2], p->B[0], sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
+     "copy");
+  ck(cudaMemsetAsync(p->Yh[0], 0, sizeof(R) * npix2, p->ps), "memset");
+  launch_l1<R>((const R*)p->B[0], ncoef, p->parts, &p->ctl->l1_cur, p->tickets + 4, p->ps);
+  ensure_fista_graph<R>(p);
+  // max_iters prox steps plus one pass that only evaluates F at the result
+  const int passes = max_iters + 1;
+  int launched = 0;
+  while (launched < passes) {
+    ck(cudaGraphLaunch(p->fista_exec, p->ps), "graph launch");
+    launched += kPasses;
+    if (rel_tol > 0 && launched < passes && (launched / kPasses) % 4 == 0) {
+      int32_t done = 0;
+      ck(cudaMemcpyAsync(&done, &p->ctl->done, sizeof(done), cudaMemcpyDeviceToHost, p->ps),
+         "read done");
+      ck(cudaStreamSynchronize(p->ps), "synchronize");
+      if (done) break;
+    }
+  }
+}
+
+template <typename R> void fill_stats(ms_plan* p, ms_stats* st, bool copy_trace) {
+  FistaCtl h{};
+  ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  if (h.error) throw Fail{(ms_status)h.error, "non-finite objective or invalid noise levels"};
+  if (copy_trace) {
+    p->htrace.assign(h.k + 1, 0.0);
+    ck(cudaMemcpy(p->htrace.data(), p->trace, sizeof(double) * (h.k + 1),
+                  cudaMemcpyDeviceToHost),
+       "read trace");
+  }
+  if (st) {
+    st->iterations = h.k;
+    st->converged = h.converged;
+    st->objective = h.F_cur;
+    st->lambda = h.lam;
+    st->theta = h.theta;
+    st->sigma2 = h.sigma2;
+    st->eta2 = h.eta2;
+    st->objective_trace = p->htrace.data();
+  }
+}
+
+int step_part(int step) {
+  return step == MS_STEP_LOW ? MS_PART_L : (step == MS_STEP_FULL ? MS_PART_H : MS_PART_ALL);
+}
+
+// ------------------------------------------------------------- reconstruct
+// One step of the method on the partition of `step` (Sects. 3.2, 3.3): N_major
+// major cycles, each a residual image, a lambda, a minor cycle, a model update.
+// obs_sorted: the partition's visibilities in plan order (vis_a).
+template <typename R>
+void run_step(ms_plan* p, int step, int chan, const ms_recon_opts& o, const void* low_image,
+              void* image_out, void* model_out, ms_stats* st, Timer& tm) {
+  PartDev& pd = p->ch[chan].part[step_part(step)];
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N;
+  R* model = (R*)(model_out ? model_out : p->img[0]);
+  R* res = (R*)p->img[1];
+  R* l = (R*)p->img[2];
+  ck(cudaMemsetAsync(model, 0, sizeof(R) * n2, p->ps), "memset");
+  const double coef = step == MS_STEP_LOW ? o.lambda_low
+                      : step == MS_STEP_FULL ? o.lambda_full : o.lambda_single;
+  for (int n = 1; n <= o.n_major; ++n) {
+    residual_sorted<R>(p, pd, p->vis_a, model, res, &tm);
+    launch_image_norms<R>(res, n2, p->parts, p->ctl, p->tickets + 5, p->ps);
+    if (n == 1) {
+      init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, o.fista_iters, o.rel_tol, 0.0, 0,
+                                          o.sigma2, o.sigma2 > 0 && o.eta2 > 0 ? o.eta2
+                                                                               : 1e-3 * o.sigma2,
+                                          o.sigma2 > 0 ? 1 : 0);
+      if (step == MS_STEP_FULL && !(o.sigma2 > 0)) {
+        // sigma^2 estimated on i~_H1, eta^2 = 1e-3 sigma^2 unless given (Sect. 4.3)
+        launch_sigma2_hat<R>(res, N, p->parts, p->ctl, p->tickets + 6, o.eta2 > 0 ? 0 : 1, p->ps);
+        if (o.eta2 > 0) set_eta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, o.eta2);
+      }
+      build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px);
+    }
+    init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, o.fista_iters, o.rel_tol, 0.0, 0, 0, 0, 0);
+    launch_set_lambda(p->ctl, o.lambda_rule, coef, n, n == 1 ? 1 : 0, p->ps);
+    if (step == MS_STEP_FULL)
+      launch_axpby<R>((const R*)low_image, model, l, 1.0, -1.0, n2, p->ps);   // l = i^_L - sum i_j
+    int a = tm.mark();
+    run_fista<R>(p, step, pd, res, step == MS_STEP_FULL ? l : nullptr, nullptr, o.fista_iters,
+                 o.rel_tol);
+    tm.spans[2].push_back({a, tm.mark()});
+    launch_axpby<R>(model, (const R*)p->xwork, model, 1.0, 1.0, n2, p->ps);   // i^ += W beta
+    FistaCtl h{};
+    ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    if (h.error) throw Fail{(ms_status)h.error, "non-finite objective or invalid noise levels"};
+    if (st) {
+      st->total_iterations += h.k;
+      st->gridded_vis += 2 * pd.n;
+    }
+  }
+  residual_sorted<R>(p, pd, p->vis_a, model, res, &tm);   // i~_{N+1}
+  if (st) st->gridded_vis += 2 * pd.n;
+  launch_axpby<R>(res, model, (R*)image_out, 1.0, 1.0, n2, p->ps);
+  fill_stats<R>(p, st, true);
+  if (st) st->major_cycles += o.n_major;
+}
+
+void validate_opts(const ms_recon_opts* o) {
+  arg(o != nullptr, "options must not be NULL");
+  arg(o->n_major >= 1 && o->n_major <= 1000, "n_major must be 1..1000");
+  arg(o->fista_iters >= 1 && o->fista_iters <= 1000000, "fista_iters must be 1..1e6");
+  arg(o->lambda_rule == MS_LAMBDA_NORM2_2N || o->lambda_rule == MS_LAMBDA_MAX_FIXED,
+      "unknown lambda rule");
+  arg(o->rel_tol >= 0, "rel_tol must be >= 0");
+}
+
+void ensure_trace(ms_plan* p, int iters) {
+  if (iters + 2 <= p->trace_cap) return;
+  if (p->trace) {
+    cudaFree(p->trace);
+    auto it = std::find(p->allocs.begin(), p->allocs.end(), (void*)p->trace);
+    if (it != p->allocs.end()) p->allocs.erase(it);
+  }
+  p->trace_cap = std::max(iters + 2, 1024);
+  p->trace = p->alloc<double>(p->trace_cap, "trace");
+  if (p->fista_exec) {   // the captured passes point at the old trace
+    cudaGraphExecDestroy(p->fista_exec);
+    p->fista_exec = nullptr;
+  }
+}
+
+template <typename R>
+void two_step(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, void* low_out,
+              void* img_out, void* model_out, ms_stats* st, void* stream) {
+  Scope sc(p, stream);
+  Timer tm(p);
+  ensure_trace(p, o->fista_iters);
+  if (st) std::memset(st, 0, sizeof(*st));
+  int t0 = tm.mark();
+  ChanDev& c = p->ch[chan];
+  // step one on V_L
+  PartDev& pl = c.part[MS_PART_L];
+  launch_gather_vis<R>(pl.idx, pl.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+  run_step<R>(p, MS_STEP_LOW, chan, *o, nullptr, low_out, nullptr, st, tm);
+  // step two on V_H with i^_L
+  PartDev& ph = c.part[MS_PART_H];
+  launch_gather_vis<R>(ph.idx, ph.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+  run_step<R>(p, MS_STEP_FULL, chan, *o, low_out, img_out, model_out, st, tm);
+  int t1 = tm.mark();
+  check_device_error(p);
+  if (st) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, p->tev[t0], p->tev[t1]), "event time");
+    st->elapsed_ms = ms;
+    st->grid_ms = tm.total(0);
+    st->fft_ms = tm.total(1);
+    st->minor_ms = tm.total(2);
+  }
+  sc.finish();
+}
+
+template <typename R>
+void single_step(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, void* img_out,
+                 void* model_out, ms_stats* st, void* stream) {
+  Scope sc(p, stream);
+  Timer tm(p);
+  ensure_trace(p, o->fista_iters);
+  if (st) std::memset(st, 0, sizeof(*st));
+  int t0 = tm.mark();
+  PartDev& pa = p->ch[chan].part[MS_PART_ALL];
+  launch_gather_vis<R>(pa.idx, pa.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+  run_step<R>(p, MS_STEP_SINGLE, chan, *o, nullptr, img_out, model_out, st, tm);
+  int t1 = tm.mark();
+  check_device_error(p);
+  if (st) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, p->tev[t0], p->tev[t1]), "event time");
+    st->elapsed_ms = ms;
+    st->grid_ms = tm.total(0);
+    st->fft_ms = tm.total(1);
+    st->minor_ms = tm.total(2);
+  }
+  sc.finish();
+}
+
+// ------------------------------------------------------------- plan build
+template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
+  const int N = p->N, Ng = p->Ng;
+  const int64_t nvis = d->nvis;
+  cudaStream_t s = p->ps;
+  // Daubechies filters
+  {
+    std::vector<double> h(kMaxBases * kMaxTaps, 0.0);
+    std::vector<int> len(kMaxBases, 0);
+    for (int m = 0; m < p->M; ++m) {
+      std::vector<double> f = daubechies(m + 1);
+      len[m] = (int)f.size();
+      for (size_t k = 0; k < f.size(); ++k) h[m * kMaxTaps + k] = f[k];
+    }
+    set_wavelet_filters(h.data(), len.data(), p->M);
+    ck(cudaGetLastError(), "wavelet filters");
+  }
+  // deapodization table
+  {
+    std::vector<double> x, w;
+    gauss_legendre(96, x, w);
+    double* dx = dalloc<double>(x.size(), "gl");
+    double* dw = dalloc<double>(w.size(), "gl");
+    double* psi = dalloc<double>(N, "psi");
+    ck(cudaMemcpy(dx, x.data(), sizeof(double) * x.size(), cudaMemcpyHostToDevice), "copy");
+    ck(cudaMemcpy(dw, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice), "copy");
+    launch_deapodization(N, Ng, p->beta, dx, dw, (int)x.size(), psi, s);
+    std::vector<double> hp(N);
+    ck(cudaMemcpyAsync(hp.data(), psi, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "copy");
+    ck(cudaStreamSynchronize(s), "deapodization");
+    std::vector<R> hr(hp.begin(), hp.end());
+    p->psi = p->alloc<R>(N, "psi");
+    ck(cudaMemcpy(p->psi, hr.data(), sizeof(R) * N, cudaMemcpyHostToDevice), "copy");
+    cudaFree(dx);
+    cudaFree(dw);
+    cudaFree(psi);
+  }
+  // per channel: classify, sort, work items
+  double* du = dalloc<double>(nvis, "u");
+  double* dv = dalloc<double>(nvis, "v");
+  uint8_t* dfl = d->flags ? dalloc<uint8_t>(nvis, "flags") : nullptr;
+  uint32_t* cell_all = dalloc<uint32_t>(nvis, "cell");
+  double2* frac_all = dalloc<double2>(nvis, "frac");
+  uint32_t* tile_id = dalloc<uint32_t>(nvis, "tile");
+  uint8_t* member = dalloc<uint8_t>(nvis, "member");
+  uint32_t* keys = dalloc<uint32_t>(nvis, "keys");
+  int32_t* vals = dalloc<int32_t>(nvis, "vals");
+  uint32_t* ktmp = dalloc<uint32_t>(nvis, "keys");
+  int32_t* vtmp = dalloc<int32_t>(nvis, "vals");
+  int64_t hcap = radix_hist_size(nvis);
+  int32_t* hist = dalloc<int32_t>(hcap, "hist");
+  int32_t* counts = dalloc<int32_t>(p->ntiles + 1, "counts");
+  int32_t* tstart = dalloc<int32_t>(p->ntiles + 2, "tstart");
+  int32_t* nch = dalloc<int32_t>(p->ntiles + 1, "nchunks");
+  int bits = 0;
+  while ((1u << bits) <= (unsigned)p->ntiles) ++bits;
+  bits = ((bits + 7) / 8) * 8;
+  const uint8_t masks[3] = {4 | 1, 4 | 2, 4};
+  p->ch.resize(d->nchan);
+  for (int c = 0; c < d->nchan; ++c) {
+    ck(cudaMemcpy(du, d->u + (int64_t)c * nvis, sizeof(double) * nvis, cudaMemcpyHostToDevice),
+       "copy u");
+    ck(cudaMemcpy(dv, d->v + (int64_t)c * nvis, sizeof(double) * nvis, cudaMemcpyHostToDevice),
+       "copy v");
+    if (dfl)
+      ck(cudaMemcpy(dfl, d->flags + (int64_t)c * nvis, nvis, cudaMemcpyHostToDevice),
+         "copy flags");
+    launch_classify(du, dv, dfl, nvis, Ng, N, d->pixel_size, d->ell_px, d->delta_px, p->T,
+                    p->ntx, cell_all, frac_all, tile_id, member, s);
+    for (int pt = 0; pt < 3; ++pt) {
+      PartDev& pd = p->ch[c].part[pt];
+      launch_make_keys(tile_id, member, nvis, masks[pt], (uint32_t)p->ntiles, keys, vals, s);
+      uint32_t* k = keys;
+      int32_t* v = vals;
+      radix_sort(&k, &v, ktmp, vtmp, nvis, bits, hist, hcap, s);
+      ck(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (p->ntiles + 1), s), "memset");
+      launch_count_tiles(k, nvis, counts, s);
+      int32_t excluded = 0;
+      ck(cudaMemcpyAsync(&excluded, counts + p->ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                         s),
+         "copy");
+      ck(cudaStreamSynchronize(s), "sort");
+      pd.n = nvis - excluded;
+      launch_exclusive_scan(counts, tstart, p->ntiles, s);
+      launch_chunks_per_tile(counts, p->ntiles, p->chunk, nch, s);
+      pd.tile_items = p->alloc<int32_t>(p->ntiles + 1, "tile items");
+      launch_exclusive_scan(nch, pd.tile_items, p->ntiles, s);
+      int32_t nitems = 0;
+      ck(cudaMemcpyAsync(&nitems, pd.tile_items + p->ntiles, sizeof(int32_t),
+                         cudaMemcpyDeviceToHost, s),
+         "copy");
+      ck(cudaStreamSynchronize(s), "items");
+      pd.nitems = nitems;
+      pd.items = p->alloc<WorkItem>(std::max(nitems, 1), "items");
+      launch_make_items(counts, tstart, pd.tile_items, p->ntiles, p->chunk, pd.items, s);
+      pd.idx = p->alloc<int32_t>(std::max<int64_t>(pd.n, 1), "idx");
+      ck(cudaMemcpyAsync(pd.idx, v, sizeof(int32_t) * pd.n, cudaMemcpyDeviceToDevice, s), "copy");
+      pd.cell = p->alloc<uint32_t>(std::max<int64_t>(pd.n, 1), "cell");
+      pd.frac = p->alloc<C2<R>>(std::max<int64_t>(pd.n, 1), "frac");
+      launch_gather_geometry<R>(pd.idx, pd.n, cell_all, frac_all, pd.cell, (C2<R>*)pd.frac, s);
+      pd.Hhat = p->alloc<R>((size_t)N * (N / 2 + 1), "Hhat");
+      p->max_items = std::max(p->max_items, pd.nitems);
+      p->max_n = std::max(p->max_n, pd.n);
+      p->ch[c].counts[pt == 2 ? 3 : pt] = pd.n;
+    }
+    ChanDev& cd = p->ch[c];
+    cd.counts[2] = cd.counts[0] + cd.counts[1] - cd.counts[3];
+  }
+  ck(cudaStreamSynchronize(s), "plan");
+  for (void* q : {(void*)du, (void*)dv, (void*)dfl, (void*)cell_all, (void*)frac_all,
+                  (void*)tile_id, (void*)member, (void*)keys, (void*)vals, (void*)ktmp,
+                  (void*)vtmp, (void*)hist, (void*)counts, (void*)tstart, (void*)nch})
+    if (q) cudaFree(q);
+  // workspaces
+  const int64_t n2 = (int64_t)N * N;
+  const int64_t nspec = (int64_t)N * (N / 2 + 1);
+  const int64_t ncoef = (int64_t)p->M * n2;
+  p->grid = p->alloc<C2<R>>((size_t)Ng * Ng, "grid");
+  p->scratch = p->alloc<unsigned char>(
+      (size_t)std::max(p->max_items, 1) * p->S * p->S * grid_scratch_cell_bytes(p->prec),
+      "scratch");
+  p->vis_a = p->alloc<C2<R>>(std::max<int64_t>(p->max_n, 1), "vis");
+  p->vis_b = p->alloc<C2<R>>(std::max<int64_t>(p->max_n, 1), "vis");
+  for (auto& im : p->img) im = p->alloc<R>(n2, "image");
+  for (auto& b : p->B) b = p->alloc<R>(ncoef, "coefficients");
+  for (auto& y : p->Yh) y = p->alloc<R>(n2, "image");
+  p->xwork = p->alloc<R>(n2, "image");
+  p->ywork = p->alloc<R>(n2, "image");
+  p->bimg = p->alloc<R>(n2, "image");
+  p->spec = p->alloc<C2<R>>(nspec, "spectrum");
+  p->spec2 = p->alloc<C2<R>>(nspec, "spectrum");
+  p->Bs = p->alloc<C2<R>>(nspec, "spectrum");
+  p->Ks = p->alloc<R>(nspec, "spectrum");
+  p->gl2 = p->alloc<R>(nspec, "filter");
+  p->gh2 = p->alloc<R>(nspec, "filter");
+  p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
+  p->B3_dev = p->alloc<void*>(3, "ptrs");
+  p->Yh2_dev = p->alloc<void*>(2, "ptrs");
+  p->api3_dev = p->alloc<void*>(3, "ptrs");
+  p->ctl = p->alloc<FistaCtl>(1, "ctl");
+  p->parts = p->alloc<double>(4096, "partials");
+  p->l1parts = p->alloc<double>(analysis_prox_partials(WaveletGeom{N, p->J, p->M}), "partials");
+  p->tickets = p->alloc<int32_t>(16, "tickets");
+  p->scal = p->alloc<double>(16, "scalars");
+  p->err = p->alloc<int32_t>(1, "error flag");
+  ensure_trace(p, 1024);
+  ck(cudaMemset(p->tickets, 0, sizeof(int32_t) * 16), "memset");
+  ck(cudaMemset(p->err, 0, sizeof(int32_t)), "memset");
+  ck(cudaMemset(p->ctl, 0, sizeof(FistaCtl)), "memset");
+  set_ptrs_kernel<<<1, 1, 0, s>>>(p->B3_dev, p->B[0], p->B[1], p->B[2]);
+  set_ptrs_kernel<<<1, 1, 0, s>>>(p->Yh2_dev, p->Yh[0], p->Yh[1], nullptr);
+  // cuFFT plans
+  cufftType tc = sizeof(R) == 8 ? CUFFT_Z2Z : CUFFT_C2C;
+  cufftType tr = sizeof(R) == 8 ? CUFFT_D2Z : CUFFT_R2C;
+  cufftType ti = sizeof(R) == 8 ? CUFFT_Z2D : CUFFT_C2R;
+  ckf(cufftPlan2d(&p->c2c, Ng, Ng, tc), "plan C2C");
+  ckf(cufftPlan2d(&p->r2c, N, N, tr), "plan R2C");
+  ckf(cufftPlan2d(&p->c2r, N, N, ti), "plan C2R");
+  for (cufftHandle h : {p->c2c, p->r2c, p->c2r}) ckf(cufftSetStream(h, s), "set stream");
+  // TMA descriptor of the grid: {2 Ng scalars, Ng rows}, box {2 S, S}
+  {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    ck(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                        &q),
+       "driver entry point");
+    arg(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)2 * Ng, (cuuint64_t)Ng};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * Ng * sizeof(R)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * p->S), (cuuint32_t)p->S};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = ((EncodeTiledFn)fn)(
+        &p->tmap, sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+        2, p->grid, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Fail{MS_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
+  }
+  ck(cudaStreamSynchronize(s), "plan");
+  ck(cudaGetLastError(), "plan kernels");
+}
+
+template <typename R>
+void lipschitz(ms_plan* p, int step, int chan, double sigma2, double eta2, int power_iters,
+               double* closed, double* power) {
+  PartDev& pd = part_of(p, step_part(step), chan);
+  init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, 1, 0.0, 0.0, 0, sigma2, eta2, 1);
+  build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px);
+  FistaCtl h{};
+  ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  if (h.error) throw Fail{MS_ERR_NUMERIC, "invalid noise levels"};
+  if (closed) *closed = h.theta;
+  if (power) *power = 0.0;
+  if (power_iters <= 0) return;
+  const int64_t ncoef = (int64_t)p->M * p->N * p->N;
+  WaveletGeom g{p->N, p->J, p->M};
+  R* v = (R*)p->B[0];
+  R* w = (R*)p->B[1];
+  launch_hash_fill<R>(v, ncoef, 12345, p->ps);
+  set_ptrs_kernel<<<1, 1, 0, p->ps>>>(p->api3_dev, v, v, v);
+  double* sc = p->scal;
+  for (int it = 0; it < power_iters; ++it) {
+    launch_dot<R>(v, v, ncoef, p->parts, sc + 0, p->tickets + 7, p->ps);
+    launch_normalize<R>(v, ncoef, sc + 0, p->ps);
+    launch_synthesis3<R>((const R* const*)p->api3_dev, (R*)p->xwork, (R*)p->wtmp, g, nullptr,
+                         p->ps);
+    fft_r2c<R>(p, p->xwork, p->spec);
+    launch_spec_apply<R>((C2<R>*)p->spec, (const R*)p->Ks, p->N, p->ps);
+    fft_c2r<R>(p, p->spec, p->ywork);
+    launch_analysis<R>((const R*)p->ywork, w, (R*)p->wtmp, g, p->ps);
+    launch_dot<R>(v, w, ncoef, p->parts, sc + 1, p->tickets + 8, p->ps);
+    ck(cudaMemcpyAsync(v, w, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps), "copy");
+  }
+  double rho = 0;
+  ck(cudaMemcpyAsync(&rho, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, p->ps), "copy");
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  if (power) *power = 2.0 * rho;
+}
+
+template <typename R>
+void minor_cycle(ms_plan* p, int step, int chan, const void* residual, const void* l_low,
+                 double sigma2, double eta2, double lambda, int max_iters, double rel_tol,
+                 void* beta_inout, void* model_out, ms_stats* st) {
+  PartDev& pd = part_of(p, step_part(step), chan);
+  arg(residual != nullptr && model_out != nullptr, "residual and model_out are required");
+  arg(step != MS_STEP_FULL || l_low != nullptr, "FULL needs l_low");
+  arg(max_iters >= 1 && max_iters <= 1000000, "max_iters must be 1..1e6");
+  arg(lambda >= 0 && std::isfinite(lambda), "lambda must be finite and >= 0");
+  ensure_trace(p, max_iters);
+  init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, max_iters, rel_tol, lambda, 1, sigma2, eta2,
+                                      step == MS_STEP_FULL ? 1 : 0);
+  build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaEventRecord(e0, p->ps), "event");
+  run_fista<R>(p, step, pd, residual, l_low, beta_inout, max_iters, rel_tol);
+  ck(cudaEventRecord(e1, p->ps), "event");
+  const int64_t n2 = (int64_t)p->N * p->N;
+  ck(cudaMemcpyAsync(model_out, p->xwork, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps),
+     "copy");
+  fill_stats<R>(p, st, true);
+  if (beta_inout) {
+    int k = st ? st->iterations : 0;
+    if (!st) {
+      FistaCtl h{};
+      ck(cudaMemcpy(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost), "read ctl");
+      k = h.k;
+    }
+    ck(cudaMemcpyAsync(beta_inout, p->B[k % 3], sizeof(R) * p->M * n2, cudaMemcpyDeviceToDevice,
+                       p->ps),
+       "copy");
+  }
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  if (st) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    st->elapsed_ms = ms;
+    st->minor_ms = ms;
+    st->total_iterations = st->iterations;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+void destroy(ms_plan* p) {
+  if (!p) return;
+  cudaSetDevice(p->dev);
+  if (p->fista_exec) cudaGraphExecDestroy(p->fista_exec);
+  for (cufftHandle h : {p->c2c, p->r2c, p->c2r})
+    if (h) cufftDestroy(h);
+  for (void* a : p->allocs) cudaFree(a);
+  for (auto e : p->tev) cudaEventDestroy(e);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
+  if (p->ps) cudaStreamDestroy(p->ps);
+  delete p;
+}
+
+#define DISPATCH(p, ...)            \
+  do {                              \
+    if ((p)->prec == MS_FP64) {     \
+      typedef double R;             \
+      __VA_ARGS__;                  \
+    } else {                        \
+      typedef float R;              \
+      __VA_ARGS__;                  \
+    }                               \
+  } while (0)
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
+  if (!out) return MS_ERR_ARG;
+  *out = nullptr;
+  if (!d) return MS_ERR_ARG;
+  ms_plan* p = new (std::nothrow) ms_plan();
+  if (!p) return MS_ERR_OOM;
+  ms_status st = guarded(p, [&] {
+    arg(d->u && d->v, "u and v are required");
+    arg(d->nvis >= 1 && d->nvis < (int64_t)INT32_MAX, "nvis must be 1 .. 2^31-1");
+    arg(d->nchan >= 1, "nchan must be >= 1");
+    arg(d->kernel_width == 7, "only kernel_width = 7 is supported");
+    arg(d->oversample == 2, "only oversample = 2 is supported");
+    arg(d->n_bases >= 1 && d->n_bases <= kMaxBases, "n_bases must be 1..8");
+    arg(d->levels >= 1 && d->levels <= kMaxLevels, "levels must be 1..8");
+    arg(d->npix >= 16 && d->npix % 16 == 0 && d->npix <= 16384, "npix must be a multiple of 16");
+    arg(d->npix % (1 << d->levels) == 0 && (d->npix >> d->levels) >= 1,
+        "npix must be divisible by 2^levels");
+    arg(d->pixel_size > 0 && std::isfinite(d->pixel_size), "pixel_size must be > 0");
+    arg(d->delta_px > 0 && std::isfinite(d->ell_px), "delta must be > 0 and ell finite");
+    arg(d->precision >= MS_FP64 && d->precision <= MS_FP32_KAHAN, "unknown precision");
+    p->d = *d;
+    p->d.u = p->d.v = nullptr;
+    p->d.flags = nullptr;
+    p->dev = d->device;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    ck(cudaSetDevice(p->dev), "set device");
+    p->N = d->npix;
+    p->Ng = 2 * d->npix;
+    p->T = d->tile ? d->tile : (p->Ng % 32 == 0 ? 32 : 16);
+    arg(p->T == 16 || p->T == 32, "tile must be 16 or 32");
+    arg(p->Ng % p->T == 0, "grid side must be a multiple of the tile");
+    p->S = p->T + kW - 1;
+    p->ntx = p->Ng / p->T;
+    p->ntiles = p->ntx * p->ntx;
+    p->J = d->levels;
+    p->M = d->n_bases;
+    p->prec = d->precision;
+    p->rsz = p->prec == MS_FP64 ? 8 : 4;
+    p->beta = d->es_beta > 0 ? d->es_beta : 2.30 * kW;
+    if (d->chunk > 0) {
+      p->chunk = d->chunk;
+    } else {
+      int64_t c = (d->nvis + 152 * 8 - 1) / (152 * 8);
+      p->chunk = (int)std::min<int64_t>(std::max<int64_t>(c, 512), 8192);
+    }
+    ck(cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking), "stream");
+    ck(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming), "event");
+    ck(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming), "event");
+    DISPATCH(p, build_plan<R>(p, d));
+    cudaSetDevice(prev);
+  });
+  if (st != MS_OK) {
+    fprintf(stderr, "ms_plan_create: %s\n", p->msg.c_str());
+    destroy(p);
+    return st;
+  }
+  *out = p;
+  return MS_OK;
+}
+
+ms_status ms_plan_destroy(ms_plan* plan) {
+  if (!plan) return MS_ERR_ARG;
+  destroy(plan);
+  return MS_OK;
+}
+
+const char* ms_last_error(const ms_plan* plan) { return plan ? plan->msg.c_str() : "no plan"; }
+
+ms_status ms_partition_counts(ms_plan* p, int32_t chan, int64_t out[4]) {
+  return guarded(p, [&] {
+    arg(out != nullptr, "out is NULL");
+    arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+    for (int i = 0; i < 4; ++i) out[i] = p->ch[chan].counts[i];
+  });
+}
+
+ms_status ms_partition_rows(ms_plan* p, int32_t part, int32_t chan, int32_t* rows) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(rows != nullptr || pd.n == 0, "rows is NULL");
+    ck(cudaSetDevice(p->dev), "set device");
+    if (pd.n) ck(cudaMemcpy(rows, pd.idx, sizeof(int32_t) * pd.n, cudaMemcpyDeviceToHost), "copy");
+  });
+}
+
+ms_status ms_degrid(ms_plan* p, int32_t part, int32_t chan, const void* image,
+                    const void* vis_obs, void* vis_out, void* stream) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(image && vis_out, "image and vis_out are required");
+    Scope sc(p, stream);
+    DISPATCH(p, {
+      if (vis_obs)
+        launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis_obs, (C2<R>*)p->vis_a, p->ps);
+      image_to_grid<R>(p, image, nullptr);
+      degrid_sorted<R>(p, pd, vis_obs ? p->vis_a : nullptr, p->vis_b, nullptr);
+      launch_scatter_vis<R>(pd.idx, pd.n, (const C2<R>*)p->vis_b, (C2<R>*)vis_out, p->ps);
+    });
+    check_device_error(p);
+    sc.finish();
+  });
+}
+
+ms_status ms_grid(ms_plan* p, int32_t part, int32_t chan, const void* vis, void* dirty,
+                  void* stream) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(vis && dirty, "vis and dirty are required");
+    Scope sc(p, stream);
+    DISPATCH(p, {
+      launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+      grid_sorted<R>(p, pd, p->vis_a, dirty, nullptr);
+    });
+    sc.finish();
+  });
+}
+
+ms_status ms_residual_image(ms_plan* p, int32_t part, int32_t chan, const void* vis_obs,
+                            const void* model, void* out, void* stream) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(vis_obs && model && out, "vis_obs, model and out are required");
+    Scope sc(p, stream);
+    DISPATCH(p, {
+      launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis_obs, (C2<R>*)p->vis_a, p->ps);
+      residual_sorted<R>(p, pd, p->vis_a, model, out, nullptr);
+    });
+    check_device_error(p);
+    sc.finish();
+  });
+}
+
+ms_status ms_psf(ms_plan* p, int32_t part, int32_t chan, void* psf, void* stream) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(psf != nullptr, "psf is NULL");
+    Scope sc(p, stream);
+    DISPATCH(p, psf_image<R>(p, pd, psf));
+    check_device_error(p);
+    sc.finish();
+  });
+}
+
+ms_status ms_dictionary_synthesis(ms_plan* p, const void* alpha, void* x, void* stream) {
+  return guarded(p, [&] {
+    arg(alpha && x, "alpha and x are required");
+    Scope sc(p, stream);
+    WaveletGeom g{p->N, p->J, p->M};
+    DISPATCH(p, {
+      set_ptrs_kernel<<<1, 1, 0, p->ps>>>(p->api3_dev, (void*)alpha, (void*)alpha, (void*)alpha);
+      launch_synthesis3<R>((const R* const*)p->api3_dev, (R*)x, (R*)p->wtmp, g, nullptr, p->ps);
+    });
+    sc.finish();
+  });
+}
+
+ms_status ms_dictionary_analysis(ms_plan* p, const void* x, void* alpha, void* stream) {
+  return guarded(p, [&] {
+    arg(alpha && x, "alpha and x are required");
+    Scope sc(p, stream);
+    WaveletGeom g{p->N, p->J, p->M};
+    DISPATCH(p, launch_analysis<R>((const R*)x, (R*)alpha, (R*)p->wtmp, g, p->ps));
+    sc.finish();
+  });
+}
+
+ms_status ms_sigma2_hat(ms_plan* p, const void* image, double* sigma2, void* stream) {
+  return guarded(p, [&] {
+    arg(image && sigma2, "image and sigma2 are required");
+    Scope sc(p, stream);
+    DISPATCH(p, launch_sigma2_hat<R>((const R*)image, p->N, p->parts, p->ctl, p->tickets + 6, 1,
+                                     p->ps));
+    FistaCtl h{};
+    ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    *sigma2 = h.sigma2;
+    sc.finish();
+  });
+}
+
+ms_status ms_lipschitz(ms_plan* p, int32_t step, int32_t chan, double sigma2, double eta2,
+                       int32_t power_iters, double* theta_closed, double* theta_power,
+                       void* stream) {
+  return guarded(p, [&] {
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
+    arg(step != MS_STEP_FULL || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
+    Scope sc(p, stream);
+    DISPATCH(p, lipschitz<R>(p, step, chan, sigma2, eta2, power_iters, theta_closed,
+                             theta_power));
+    sc.finish();
+  });
+}
+
+ms_status ms_minor_cycle(ms_plan* p, int32_t step, int32_t chan, const void* residual,
+                         const void* l_low, double sigma2, double eta2, double lambda,
+                         int32_t max_iters, double rel_tol, void* beta_inout, void* model_out,
+                         ms_stats* st, void* stream) {
+  return guarded(p, [&] {
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
+    arg(step != MS_STEP_FULL || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
+    arg(rel_tol >= 0, "rel_tol must be >= 0");
+    if (st) std::memset(st, 0, sizeof(*st));
+    Scope sc(p, stream);
+    DISPATCH(p, minor_cycle<R>(p, step, chan, residual, l_low, sigma2, eta2, lambda, max_iters,
+                               rel_tol, beta_inout, model_out, st));
+    sc.finish();
+  });
+}
+
+ms_status ms_reconstruct_two_step(ms_plan* p, int32_t chan, const void* vis,
+                                  const ms_recon_opts* o, void* low_out, void* img_out,
+                                  void* model_out, ms_stats* st, void* stream) {
+  return guarded(p, [&] {
+    validate_opts(o);
+    arg(vis && low_out && img_out, "vis, img_low_out and img_out are required");
+    arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+    arg(p->ch[chan].part[MS_PART_L].n > 0 && p->ch[chan].part[MS_PART_H].n > 0,
+        "both partitions need visibilities");
+    DISPATCH(p, two_step<R>(p, chan, vis, o, low_out, img_out, model_out, st, stream));
+  });
+}
+
+ms_status ms_reconstruct_single_step(ms_plan* p, int32_t chan, const void* vis,
+                                     const ms_recon_opts* o, void* img_out, void* model_out,
+                                     ms_stats* st, void* stream) {
+  return guarded(p, [&] {
+    validate_opts(o);
+    arg(vis && img_out, "vis and img_out are required");
+    arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+    arg(p->ch[chan].part[MS_PART_ALL].n > 0, "no visibilities");
+    DISPATCH(p, single_step<R>(p, chan, vis, o, img_out, model_out, st, stream));
+  });
+}
+
+}  // extern "C"

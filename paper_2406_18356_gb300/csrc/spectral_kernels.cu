@@ -1,0 +1,512 @@
+// Fourier-domain pieces of the minor cycle and the FP64 reductions.
+//
+// Both problems are quadratic in x = W alpha (Sect. 3.2, 3.3):
+//   f(alpha) = <x, K x> - 2 <b, x> + c0,
+//   LOW / SINGLE (Eq. LowRes):  K^ = |H^|^2,              B^ = H^ I^,
+//                               c0 = ||i~||^2
+//   FULL (Eq. FullRes):         K^ = g_H^2 |H^|^2 + g_L^2, B^ = g_H^2 H^ I^ + g_L^2 L^,
+//                               c0 = ||G_H i~||^2 + ||G_L l||^2
+// with H^ the (real) PSF spectrum and I^, L^ the spectra of i~ and l_L, so the
+// gradient of Eqs. GradL / GradH is 2 W^H (K x - b) and the Lipschitz constant
+// of Sect. 3.4 is 2 M max K^.  Inner products use Parseval on the rfft
+// half-plane (columns 0 and N/2 once, the others twice).  All reductions are
+// FP64, per-block partials summed by the last block in a fixed order.
+#include "common.cuh"
+
+namespace ms {
+
+namespace {
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// block reduction of NV doubles (sum or max per slot); result in thread 0
+template <int NV>
+__device__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV]) {
+  __shared__ double red[NV][kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = is_max[i] ? warp_max(v[i]) : warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) red[i][warp] = v[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = is_max[i] ? -INFINITY : 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s = is_max[i] ? fmax(s, red[i][w]) : s + red[i][w];
+      v[i] = s;
+    }
+  }
+}
+
+// write this block's partials; returns true in thread 0 of the last block,
+// which then sees every block's partials
+template <int NV>
+__device__ bool publish_partials(const double (&v)[NV], double* parts, int32_t* ticket) {
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) parts[(int64_t)i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    int prior = atomicAdd(ticket, 1);
+    last = (prior == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  return last && threadIdx.x == 0;
+}
+
+template <int NV>
+__device__ void gather_partials(double (&out)[NV], const double* parts, const bool (&is_max)[NV],
+                                int32_t* ticket) {
+  __threadfence();
+  const volatile double* vp = parts;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double s = is_max[i] ? -INFINITY : 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      double x = vp[(int64_t)i * gridDim.x + b];
+      s = is_max[i] ? fmax(s, x) : s + x;
+    }
+    out[i] = s;
+  }
+  *ticket = 0;
+}
+
+__device__ __forceinline__ double half_plane_weight(int col, int N) {
+  return (col == 0 || col == N / 2) ? 1.0 : 2.0;
+}
+
+int nparts_for(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > 152 * 4) b = 152 * 4;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+}  // namespace
+
+int spectral_partials(int N) { return nparts_for((int64_t)N * (N / 2 + 1)); }
+
+// ------------------------------------------------------------- PSF spectrum
+template <typename R>
+__global__ void ifftshift_kernel(const R* __restrict__ in, R* __restrict__ out, int N) {
+  int64_t total = (int64_t)N * N;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(k / N), q = (int)(k % N);
+    int sp = p + N / 2, sq = q + N / 2;
+    sp -= sp >= N ? N : 0;
+    sq -= sq >= N ? N : 0;
+    out[k] = in[(int64_t)sp * N + sq];
+  }
+}
+
+template <typename R>
+void launch_ifftshift_real(const R* in, R* out, int N, cudaStream_t s) {
+  ifftshift_kernel<R><<<nparts_for((int64_t)N * N), kThreads, 0, s>>>(in, out, N);
+}
+
+template <typename R>
+__global__ void real_part_kernel(const C2<R>* __restrict__ in, R* __restrict__ out, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    out[k] = in[k].x;
+}
+
+template <typename R>
+void launch_real_part_spectrum(const C2<R>* in, R* out, int n, cudaStream_t s) {
+  real_part_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(in, out, n);
+}
+
+// ------------------------------------------------------------- filters
+// Sect. 3.3: |g_H|^2 = 1/sigma^2 above ell + delta, 0 below ell - delta;
+// |g_L|^2 = 1/eta^2 below, 0 above; in the band g_L = a (1 - s), g_H = a (1 + s),
+// s = sin(pi (r - ell) / (2 delta)), a = 1/sqrt(eta^2 (1-s)^2 + sigma^2 (1+s)^2).
+// r = sqrt(kx^2 + ky^2) on the rfft half-plane, pixel units.  Squares stored.
+template <typename R>
+__global__ void filters_kernel(int N, double ell, double delta, const FistaCtl* __restrict__ ctl,
+                               R* __restrict__ gl2, R* __restrict__ gh2) {
+  const int nc = N / 2 + 1;
+  const int64_t total = (int64_t)N * nc;
+  const double s2 = ctl->sigma2, e2 = ctl->eta2;
+  const double pi = 3.141592653589793238462643383279502884;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int row = (int)(k / nc), col = (int)(k % nc);
+    double ky = row < N / 2 ? row : row - N;
+    double r = sqrt(ky * ky + (double)col * col);
+    double l2, h2;
+    if (r > ell + delta) {
+      l2 = 0.0;
+      h2 = 1.0 / s2;
+    } else if (r < ell - delta) {
+      l2 = 1.0 / e2;
+      h2 = 0.0;
+    } else {
+      double sn = sin(pi * (r - ell) / (2.0 * delta));
+      double a2 = 1.0 / (e2 * (1.0 - sn) * (1.0 - sn) + s2 * (1.0 + sn) * (1.0 + sn));
+      l2 = a2 * (1.0 - sn) * (1.0 - sn);
+      h2 = a2 * (1.0 + sn) * (1.0 + sn);
+    }
+    gl2[k] = (R)l2;
+    gh2[k] = (R)h2;
+  }
+}
+
+template <typename R>
+void launch_filters(int N, double ell, double delta, const FistaCtl* ctl, R* gl2, R* gh2,
+                    cudaStream_t s) {
+  filters_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(N, ell, delta, ctl, gl2, gh2);
+}
+
+// ------------------------------------------------------------- K^ and theta
+template <typename R>
+__global__ void normal_spectrum_kernel(const R* __restrict__ Hhat, const R* __restrict__ gl2,
+                                       const R* __restrict__ gh2, int N, int M,
+                                       R* __restrict__ Ks, double* __restrict__ parts,
+                                       FistaCtl* __restrict__ ctl, int32_t* ticket) {
+  const int64_t total = (int64_t)N * (N / 2 + 1);
+  const double inv = 1.0 / ((double)N * N);
+  double v[1] = {0.0};
+  const bool mx[1] = {true};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double h = (double)Hhat[k];
+    double kk = h * h;
+    if (gl2) kk = (double)gh2[k] * kk + (double)gl2[k];
+    Ks[k] = (R)(kk * inv);
+    v[0] = fmax(v[0], kk);
+  }
+  block_reduce<1>(v, mx);
+  if (publish_partials<1>(v, parts, ticket)) {
+    double o[1];
+    gather_partials<1>(o, parts, mx, ticket);
+    ctl->kmax = o[0];
+    ctl->theta = 2.0 * M * o[0];
+    ctl->inv_theta = o[0] > 0 ? 1.0 / (2.0 * M * o[0]) : 0.0;
+  }
+}
+
+template <typename R>
+void launch_normal_spectrum(const R* Hhat, const R* gl2, const R* gh2, int N, int M, R* Ks,
+                            double* parts, FistaCtl* ctl, int32_t* ticket, cudaStream_t s) {
+  normal_spectrum_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(Hhat, gl2, gh2, N, M, Ks,
+                                                                      parts, ctl, ticket);
+}
+
+// ------------------------------------------------------------- b and c0
+template <typename R>
+__global__ void b_spectrum_kernel(const C2<R>* __restrict__ Ihat, const C2<R>* __restrict__ Lhat,
+                                  const R* __restrict__ Hhat, const R* __restrict__ gl2,
+                                  const R* __restrict__ gh2, int N, C2<R>* __restrict__ Bs,
+                                  double* __restrict__ parts, FistaCtl* __restrict__ ctl,
+                                  int32_t* ticket) {
+  const int nc = N / 2 + 1;
+  const int64_t total = (int64_t)N * nc;
+  const double inv = 1.0 / ((double)N * N);
+  double v[1] = {0.0};
+  const bool mx[1] = {false};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double w = half_plane_weight((int)(k % nc), N);
+    C2<R> I = Ihat[k];
+    double h = (double)Hhat[k];
+    double br, bi, c;
+    if (gl2) {
+      C2<R> Lv = Lhat[k];
+      double gh = (double)gh2[k], gl = (double)gl2[k];
+      br = gh * h * I.x + gl * Lv.x;
+      bi = gh * h * I.y + gl * Lv.y;
+      c = gh * ((double)I.x * I.x + (double)I.y * I.y) + gl * ((double)Lv.x * Lv.x + (double)Lv.y * Lv.y);
+    } else {
+      br = h * I.x;
+      bi = h * I.y;
+      c = (double)I.x * I.x + (double)I.y * I.y;
+    }
+    C2<R> o;
+    o.x = (R)(br * inv);
+    o.y = (R)(bi * inv);
+    Bs[k] = o;
+    v[0] += w * c;
+  }
+  block_reduce<1>(v, mx);
+  if (publish_partials<1>(v, parts, ticket)) {
+    double o[1];
+    gather_partials<1>(o, parts, mx, ticket);
+    ctl->c0 = o[0] * inv;
+  }
+}
+
+template <typename R>
+void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, const R* gl2,
+                       const R* gh2, int N, C2<R>* Bs, double* parts, FistaCtl* ctl,
+                       int32_t* ticket, cudaStream_t s) {
+  b_spectrum_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(Ihat, Lhat, Hhat, gl2, gh2, N,
+                                                                 Bs, parts, ctl, ticket);
+}
+
+// ------------------------------------------------------------- y = K x
+// Per iteration: <x, K x> and <b, x> of the current coefficients from the
+// spectrum X^ (Parseval), then X^ <- K^/N^2 X^ for the inverse FFT.  The last
+// block assembles F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it
+// to the trace and raises `done` on convergence or at the iteration budget.
+template <typename R>
+__global__ void spec_mul_kernel(C2<R>* __restrict__ spec, const R* __restrict__ Ks,
+                                const C2<R>* __restrict__ Bs, int N,
+                                double* __restrict__ parts, FistaCtl* __restrict__ ctl,
+                                double* __restrict__ trace, int32_t* ticket) {
+  if (ctl->done) return;
+  const int nc = N / 2 + 1;
+  const int64_t total = (int64_t)N * nc;
+  double v[2] = {0.0, 0.0};
+  const bool mx[2] = {false, false};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double w = half_plane_weight((int)(k % nc), N);
+    C2<R> X = spec[k];
+    R kk = Ks[k];
+    C2<R> B = Bs[k];
+    v[0] += w * (double)kk * ((double)X.x * X.x + (double)X.y * X.y);
+    v[1] += w * ((double)B.x * X.x + (double)B.y * X.y);
+    X.x *= kk;
+    X.y *= kk;
+    spec[k] = X;
+  }
+  block_reduce<2>(v, mx);
+  if (publish_partials<2>(v, parts, ticket)) {
+    double o[2];
+    gather_partials<2>(o, parts, mx, ticket);
+    const int k = ctl->k;
+    double F = o[0] - 2.0 * o[1] + ctl->c0 + ctl->lam * ctl->l1_cur;
+    ctl->xkx = o[0];
+    ctl->bx = o[1];
+    ctl->F_prev = ctl->F_cur;
+    ctl->F_cur = F;
+    trace[k] = F;
+    if (!isfinite(F)) {
+      ctl->error = 4;
+      ctl->done = 1;
+    } else if (k >= 1 && ctl->rel_tol > 0.0 && fabs(F - ctl->F_prev) <= ctl->rel_tol * fabs(F)) {
+      ctl->converged = 1;
+      ctl->done = 1;
+    } else if (k >= ctl->max_iters) {
+      ctl->done = 1;
+    }
+    __threadfence();
+  }
+}
+
+template <typename R>
+void launch_spec_mul(C2<R>* spec, const R* Ks, const C2<R>* Bs, int N, double* parts,
+                     FistaCtl* ctl, double* trace, int32_t* ticket, cudaStream_t s) {
+  spec_mul_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(spec, Ks, Bs, N, parts, ctl,
+                                                               trace, ticket);
+}
+
+template <typename R>
+__global__ void spec_apply_kernel(C2<R>* __restrict__ spec, const R* __restrict__ Ks, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    C2<R> X = spec[k];
+    R kk = Ks[k];
+    X.x *= kk;
+    X.y *= kk;
+    spec[k] = X;
+  }
+}
+
+template <typename R>
+void launch_spec_apply(C2<R>* spec, const R* Ks, int N, cudaStream_t s) {
+  int64_t n = (int64_t)N * (N / 2 + 1);
+  spec_apply_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(spec, Ks, n);
+}
+
+// ------------------------------------------------------------- image stats
+// ||x||_2^2 and max |x| of an image -> ctl->norm2, ctl->absmax
+template <typename R>
+__global__ void image_norms_kernel(const R* __restrict__ img, int64_t n, double* parts,
+                                   FistaCtl* ctl, int32_t* ticket) {
+  double v[2] = {0.0, 0.0};
+  const bool mx[2] = {false, true};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double x = (double)img[k];
+    v[0] += x * x;
+    v[1] = fmax(v[1], fabs(x));
+  }
+  block_reduce<2>(v, mx);
+  if (publish_partials<2>(v, parts, ticket)) {
+    double o[2];
+    gather_partials<2>(o, parts, mx, ticket);
+    ctl->norm2 = o[0];
+    ctl->absmax = o[1];
+  }
+}
+
+template <typename R>
+void launch_image_norms(const R* img, int64_t n, double* parts, FistaCtl* ctl, int32_t* ticket,
+                        cudaStream_t s) {
+  image_norms_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(img, n, parts, ctl, ticket);
+}
+
+// Sect. 4.3: mean over all inside 5x5 windows of the population variance.
+template <typename R>
+__global__ void sigma2_kernel(const R* __restrict__ img, int N, double* parts, FistaCtl* ctl,
+                              int32_t* ticket, int set_eta) {
+  const int nw = N - 4;
+  const int64_t total = (int64_t)nw * nw;
+  double v[1] = {0.0};
+  const bool mx[1] = {false};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(k / nw), q = (int)(k % nw);
+    double s = 0.0, s2 = 0.0;
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) {
+        double x = (double)img[(int64_t)(p + a) * N + q + b];
+        s += x;
+        s2 += x * x;
+      }
+    double mean = s / 25.0;
+    double var = s2 / 25.0 - mean * mean;
+    v[0] += var > 0.0 ? var : 0.0;
+  }
+  block_reduce<1>(v, mx);
+  if (publish_partials<1>(v, parts, ticket)) {
+    double o[1];
+    gather_partials<1>(o, parts, mx, ticket);
+    double s2 = o[0] / (double)total;
+    ctl->sigma2 = s2;
+    if (set_eta) ctl->eta2 = 1e-3 * s2;
+  }
+}
+
+template <typename R>
+void launch_sigma2_hat(const R* img, int N, double* parts, FistaCtl* ctl, int32_t* ticket,
+                       int set_eta, cudaStream_t s) {
+  sigma2_kernel<R><<<nparts_for((int64_t)(N - 4) * (N - 4)), kThreads, 0, s>>>(
+      img, N, parts, ctl, ticket, set_eta);
+}
+
+// lambda of major cycle n (1-based): rule 0: c ||i~_n||_2 2^n; rule 1: c max|i~_1|
+__global__ void set_lambda_kernel(FistaCtl* ctl, int rule, double coef, int n, int first) {
+  if (first) ctl->absmax_first = ctl->absmax;
+  if (rule == 0)
+    ctl->lam = coef * sqrt(ctl->norm2) * ldexp(1.0, n);
+  else
+    ctl->lam = coef * ctl->absmax_first;
+}
+
+// ------------------------------------------------------------- small vector ops
+template <typename R>
+__global__ void axpby_kernel(const R* __restrict__ x, const R* __restrict__ y, R* __restrict__ o,
+                             R a, R b, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    o[k] = a * x[k] + (y ? b * y[k] : (R)0);
+}
+
+template <typename R>
+void launch_axpby(const R* x, const R* y, R* out, double a, double b, int64_t n, cudaStream_t s) {
+  axpby_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(x, y, out, (R)a, (R)b, n);
+}
+
+// sum |x| (OP 0) or <x, y> (OP 1) in FP64 -> *out
+template <typename R, int OP>
+__global__ void reduce_kernel(const R* __restrict__ x, const R* __restrict__ y, int64_t n,
+                              double* parts, double* out, int32_t* ticket) {
+  double v[1] = {0.0};
+  const bool mx[1] = {false};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[0] += OP == 0 ? fabs((double)x[k]) : (double)x[k] * (double)y[k];
+  block_reduce<1>(v, mx);
+  if (publish_partials<1>(v, parts, ticket)) {
+    double o[1];
+    gather_partials<1>(o, parts, mx, ticket);
+    *out = o[0];
+  }
+}
+
+template <typename R>
+void launch_l1(const R* x, int64_t n, double* parts, double* out, int32_t* ticket,
+               cudaStream_t s) {
+  reduce_kernel<R, 0><<<nparts_for(n), kThreads, 0, s>>>(x, nullptr, n, parts, out, ticket);
+}
+
+template <typename R>
+void launch_dot(const R* x, const R* y, int64_t n, double* parts, double* out, int32_t* ticket,
+                cudaStream_t s) {
+  reduce_kernel<R, 1><<<nparts_for(n), kThreads, 0, s>>>(x, y, n, parts, out, ticket);
+}
+
+// x <- x / sqrt(*den)
+template <typename R>
+__global__ void normalize_kernel(R* __restrict__ x, int64_t n, const double* __restrict__ den) {
+  const double sc = 1.0 / sqrt(*den);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    x[k] = (R)((double)x[k] * sc);
+}
+
+template <typename R>
+void launch_normalize(R* x, int64_t n, const double* den, cudaStream_t s) {
+  normalize_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(x, n, den);
+}
+
+// deterministic pseudo-random start vector in [-1, 1] (splitmix64 of the index)
+template <typename R>
+__global__ void hash_fill_kernel(R* __restrict__ x, int64_t n, uint64_t seed) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(k + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[k] = (R)((double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+
+template <typename R>
+void launch_hash_fill(R* x, int64_t n, uint64_t seed, cudaStream_t s) {
+  hash_fill_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(x, n, seed);
+}
+
+void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, cudaStream_t s) {
+  set_lambda_kernel<<<1, 1, 0, s>>>(ctl, rule, coef, n, first);
+}
+
+#define MS_INST(R)                                                                               \
+  template void launch_ifftshift_real<R>(const R*, R*, int, cudaStream_t);                       \
+  template void launch_real_part_spectrum<R>(const C2<R>*, R*, int, cudaStream_t);               \
+  template void launch_filters<R>(int, double, double, const FistaCtl*, R*, R*, cudaStream_t);   \
+  template void launch_normal_spectrum<R>(const R*, const R*, const R*, int, int, R*, double*,   \
+                                          FistaCtl*, int32_t*, cudaStream_t);                    \
+  template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
+                                     int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
+  template void launch_spec_mul<R>(C2<R>*, const R*, const C2<R>*, int, double*, FistaCtl*,      \
+                                   double*, int32_t*, cudaStream_t);                             \
+  template void launch_spec_apply<R>(C2<R>*, const R*, int, cudaStream_t);                       \
+  template void launch_image_norms<R>(const R*, int64_t, double*, FistaCtl*, int32_t*,           \
+                                      cudaStream_t);                                             \
+  template void launch_sigma2_hat<R>(const R*, int, double*, FistaCtl*, int32_t*, int,           \
+                                     cudaStream_t);                                              \
+  template void launch_axpby<R>(const R*, const R*, R*, double, double, int64_t, cudaStream_t);  \
+  template void launch_l1<R>(const R*, int64_t, double*, double*, int32_t*, cudaStream_t);       \
+  template void launch_dot<R>(const R*, const R*, int64_t, double*, double*, int32_t*,           \
+                              cudaStream_t);                                                     \
+  template void launch_normalize<R>(R*, int64_t, const double*, cudaStream_t);                   \
+  template void launch_hash_fill<R>(R*, int64_t, uint64_t, cudaStream_t);
+
+MS_INST(float)
+MS_INST(double)
+
+}  // namespace ms

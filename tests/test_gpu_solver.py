@@ -1,0 +1,173 @@
+"""Parity of the CUDA minor cycle and the two-step / single-step
+reconstructions with the FP64 oracle, through the C ABI (GPU)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gridding as og
+from oracle import imaging as oi
+from oracle import solver as osv
+from oracle.wavelets import Dictionary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ms():
+    import torch
+    import paper_2406_18356_gb300 as pkg
+    from paper_2406_18356_gb300 import _build
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _build.build()
+    pkg.load_library()
+    return pkg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def cuda(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _setup(ms, precision="fp64", N=32, J=3, M=8, seed=4):
+    w = synth.tiny(npix=N, n_ant=12, n_dumps=10, seed=seed)
+    plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px, precision=precision,
+                   levels=J, n_bases=M)
+    return w, plan
+
+
+def _oracle_problem(w, kind, J, M, lam, part, res, l_low=None, s2=None, e2=None):
+    u, v = w.u[0], w.v[0]
+    in_l, in_h = og.partition(u, v, w.npix, w.pixel_size, w.ell_px, w.delta_px)
+    mask = {"L": in_l, "H": in_h, "ALL": np.ones_like(in_l)}[part]
+    A = og.GriddedOperator(u[mask], v[mask], w.npix, w.pixel_size)
+    Hhat = osv.psf_spectrum(A.psf())
+    W = Dictionary(w.npix, M, J)
+    if kind == "low":
+        return osv.Problem("low", W, Hhat, res, lam)
+    gl, gh = osv.filter_responses(w.npix, w.ell_px, w.delta_px, s2, e2)
+    return osv.Problem("full", W, Hhat, res, lam, gl=gl, gh=gh, l_low=l_low)
+
+
+@pytest.mark.parametrize("step,part", [("low", "L"), ("single", "ALL"), ("full", "H")])
+def test_lipschitz_closed_form_matches_oracle(ms, step, part):
+    w, plan = _setup(ms)
+    res = np.zeros((32, 32))
+    s2, e2 = 2.0e-3, 2.0e-6
+    prob = _oracle_problem(w, "full" if step == "full" else "low", 3, 8, 0.0, part, res,
+                           l_low=res, s2=s2, e2=e2)
+    closed, power = plan.lipschitz(step, sigma2=s2, eta2=e2, power_iters=300)
+    assert abs(closed - prob.lipschitz_closed_form()) <= 1e-10 * closed
+    # the power iteration approaches the closed form from below
+    assert power <= closed * (1 + 1e-9)
+    assert power >= 0.97 * closed
+    plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
+@pytest.mark.parametrize("step,part", [("low", "L"), ("single", "ALL"), ("full", "H")])
+def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
+    """Objective trace F(beta_0..beta_K) and the model W beta_K of one minor
+    cycle (Algorithm 1 with Eqs. GradL / GradH) against the oracle."""
+    J, M, iters = 3, 8, 30
+    w, plan = _setup(ms, precision, J=J, M=M)
+    u, v = w.u[0], w.v[0]
+    in_l, in_h = og.partition(u, v, 32, w.pixel_size, w.ell_px, w.delta_px)
+    mask = {"L": in_l, "H": in_h, "ALL": np.ones_like(in_l)}[part]
+    A = og.GriddedOperator(u[mask], v[mask], 32, w.pixel_size)
+    res = A.dirty(w.vis[0][mask])
+    lam = 0.05 * np.linalg.norm(res) * 2
+    rng = np.random.default_rng(0)
+    l_low = 0.5 * res + 0.01 * rng.standard_normal(res.shape)
+    s2 = osv.sigma2_hat(res)
+    e2 = 1e-3 * s2
+    prob = _oracle_problem(w, "full" if step == "full" else "low", J, M, lam, part, res,
+                           l_low=l_low, s2=s2, e2=e2)
+    ref = osv.fista(prob, iters)
+    model, st = plan.minor_cycle(step, cuda(res).to(plan.real_dtype), lam, iters,
+                                 l_low=cuda(l_low).to(plan.real_dtype) if step == "full" else None,
+                                 sigma2=s2, eta2=e2)
+    assert st.iterations == iters
+    np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
+    assert rel(model.cpu().numpy(), prob.W.synth(ref.beta)) <= 10 * tol
+    assert abs(st.theta - prob.lipschitz_closed_form()) <= 1e-6 * st.theta
+    plan.close()
+
+
+def test_minor_cycle_relative_tolerance_stop_and_warm_start(ms):
+    J, M = 3, 8
+    w, plan = _setup(ms, J=J, M=M)
+    u, v = w.u[0], w.v[0]
+    A = og.GriddedOperator(u, v, 32, w.pixel_size)
+    res = A.dirty(w.vis[0])
+    lam = 0.02 * np.linalg.norm(res) * 2
+    prob = _oracle_problem(w, "low", J, M, lam, "ALL", res)
+    ref = osv.fista(prob, 500, rel_tol=1e-5)
+    model, st = plan.minor_cycle("single", cuda(res), lam, 500, rel_tol=1e-5)
+    assert st.converged and st.iterations == ref.iterations
+    np.testing.assert_allclose(st.trace, ref.objective, rtol=1e-9)
+    # warm start from a given beta: the oracle from the same start
+    beta0 = np.random.default_rng(1).standard_normal((M, 32, 32)) * 1e-3
+    ref2 = osv.fista(prob, 12, beta0=beta0)
+    b = cuda(beta0)
+    _, st2 = plan.minor_cycle("single", cuda(res), lam, 12, beta=b)
+    np.testing.assert_allclose(st2.trace, ref2.objective, rtol=1e-9)
+    np.testing.assert_allclose(b.cpu().numpy(), ref2.beta, atol=1e-10)
+    plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-4), ("fp32_kahan", 1e-4)])
+def test_two_step_and_single_step_small(ms, precision, tol):
+    w, plan = _setup(ms, precision, seed=9)
+    u, v, vis = w.u[0], w.v[0], w.vis[0]
+    opts = ms.ReconOptions(n_major=3, fista_iters=25)
+    ro = oi.ReconOptions(n_major=3, fista_iters=25, levels=3)
+    tv = cuda(vis).to(plan.complex_dtype)
+    low, img, st = plan.reconstruct_two_step(tv, opts)
+    o_low, o_full = oi.reconstruct_two_step(vis, u, v, 32, w.pixel_size, w.ell_px, w.delta_px, ro)
+    assert rel(low.cpu().numpy(), o_low.image) <= tol
+    assert rel(img.cpu().numpy(), o_full.image) <= tol
+    assert abs(st.sigma2 - o_full.sigma2) <= 1e-6 * o_full.sigma2 * (1 if precision == "fp64" else 100)
+    assert st.total_iterations == 2 * 3 * 25
+    single, st1 = plan.reconstruct_single_step(tv, opts)
+    o_single = oi.reconstruct_single_step(vis, u, v, 32, w.pixel_size, ro)
+    assert rel(single.cpu().numpy(), o_single.image) <= tol
+    plan.close()
+
+
+@pytest.mark.slow
+def test_small_fp64_workload_end_to_end(ms):
+    """The 128-pixel, 31,744-row workload: two-step and single-step FISTA,
+    200 iterations x 5 major cycles, lambda = 1e-3 max|dirty| (held), FP64,
+    against the oracle: final images within 1e-4 relative L2."""
+    w = synth.small_fp64()
+    u, v, vis = w.u[0], w.v[0], w.vis[0]
+    plan = ms.Plan(u, v, 128, w.pixel_size, w.ell_px, w.delta_px, precision="fp64")
+    opts = ms.ReconOptions(n_major=5, fista_iters=200, lambda_rule="max_fixed",
+                           lambda_low=1e-3, lambda_full=1e-3, lambda_single=1e-3)
+    ro = oi.ReconOptions(n_major=5, fista_iters=200, lambda_rule="max_fixed",
+                         lambda_low=1e-3, lambda_full=1e-3, lambda_single=1e-3)
+    tv = cuda(vis)
+    low, img, st = plan.reconstruct_two_step(tv, opts)
+    o_low, o_full = oi.reconstruct_two_step(vis, u, v, 128, w.pixel_size, w.ell_px, w.delta_px, ro)
+    e_low, e_img = rel(low.cpu().numpy(), o_low.image), rel(img.cpu().numpy(), o_full.image)
+    single, _ = plan.reconstruct_single_step(tv, opts)
+    o_single = oi.reconstruct_single_step(vis, u, v, 128, w.pixel_size, ro)
+    e_single = rel(single.cpu().numpy(), o_single.image)
+    print(f"small fp64 end to end: low {e_low:.2e} full {e_img:.2e} single {e_single:.2e}")
+    assert e_low <= 1e-4 and e_img <= 1e-4 and e_single <= 1e-4
+    plan.close()
+
+
+def test_two_step_needs_both_partitions(ms):
+    w = synth.tiny(npix=32, n_ant=8, n_dumps=6, seed=5)
+    # ell - delta above every baseline: V_H is empty
+    plan = ms.Plan(w.u[0], w.v[0], 32, w.pixel_size, 40.0, 2.0)
+    assert plan.partition_counts()["H"] == 0
+    with pytest.raises(ms.MsError) as e:
+        plan.reconstruct_two_step(cuda(w.vis[0]))
+    assert e.value.status == ms.MS_ERR_ARG
+    plan.close()
