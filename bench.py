@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the two-step reconstruction on the 1024-pixel, 9.27M-row
+SKA-Mid-like workload (FP32 operator, FP64 reductions, 5 major cycles x 100
+FISTA iterations per step, split at 10 % of max |uv|).
+
+One step = one complete two-step reconstruction (every row of the hot path:
+degrid + residual, grid + adjoint FFT, PSF / filters / K^, step size,
+lambda and sigma estimates, FISTA minor cycles, image updates) over the
+workload's visibilities, already resident in HBM.
+
+value  = visibilities passed through a degrid + grid pair per second of
+         degrid + grid kernel time (FFT excluded, timed separately), summed
+         over all ranks / the slowest rank's kernel time.
+e2e    = the same visibilities per second of wall time of the public call
+         with host buffers: pinned host -> device copy of the visibilities,
+         the reconstruction, device -> host copy of both images.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun, one rank per GPU): every rank reconstructs its own
+independent observation (its own sky seed); no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "vis/s grid+degrid, FISTA iters/s, time-to-ε: chosen vs plain form on 1 GB300"
+UNIT = "vis/s"
+L2_FLUSH_BYTES = 256 << 20
+N_MAJOR, FISTA_ITERS = 5, 100
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-rows", type=int, default=1_000_000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_kahan", "fp64"])
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_vis_rate(w, rows: int):
+    """Oracle degrid + grid (FFT time measured separately and removed) on the
+    first `rows` rows of the workload, single host thread."""
+    import numpy as np
+    from oracle.gridding import GriddedOperator
+    rows = min(rows, w.nvis)
+    A = GriddedOperator(w.u[0][:rows], w.v[0][:rows], w.npix, w.pixel_size)
+    x = np.zeros((w.npix, w.npix))
+    x[w.npix // 2, w.npix // 2] = 1.0
+    t0 = time.perf_counter()
+    A.forward(x)
+    t1 = time.perf_counter()
+    A.adjoint(w.vis[0][:rows])
+    t2 = time.perf_counter()
+    g = np.zeros((A.ngrid, A.ngrid), complex)
+    t3 = time.perf_counter()
+    np.fft.fft2(g)
+    np.fft.ifft2(g)
+    t4 = time.perf_counter()
+    t = (t2 - t0) - (t4 - t3)
+    return rows / t, t, rows
+
+
+def cpu_cores_used():
+    return 1
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import synth
+    w = synth.ska_mid_like(device="cpu" if not _cuda_ok() else "cuda")
+    for _ in range(max(args.warmup, 0)):
+        oracle_vis_rate(w, min(args.cpu_sample_rows // 4, w.nvis))
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, t, rows = oracle_vis_rate(w, args.cpu_sample_rows)
+        rates.append(r)
+        secs.append(t)
+    value = sum(args.cpu_sample_rows for _ in rates) / sum(secs)
+    sample = (f"oracle degrid+grid of the first {args.cpu_sample_rows} rows of the "
+              f"{w.name} workload per step, FFT time removed")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def workload_config(w, precision):
+    return {"workload": w.name, "npix": w.npix, "nvis": int(w.nvis),
+            "partition": f"ell = 10% of max|uv| ({w.ell_px:.1f} px), delta = {w.delta_px} px",
+            "n_major": N_MAJOR, "fista_iters": FISTA_ITERS, "precision": precision,
+            "lambda": "0.05 ||i~_n||_2 2^n (both steps)", "wavelets": "db1-db8, 4 levels",
+            "es_kernel": "W=7, 2x oversampling",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    if rank == 0:
+        from paper_2406_18356_gb300 import _build
+        _build.build()
+    if pg:
+        pg.barrier()
+    import paper_2406_18356_gb300 as ms
+    ms.load_library()
+
+    w = synth.ska_mid_like(seed=rank, device=str(dev))
+    plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
+                   precision=args.precision, device=local_rank)
+    opts = ms.ReconOptions(n_major=N_MAJOR, fista_iters=FISTA_ITERS)
+    vis = torch.from_numpy(w.vis[0]).to(dev).to(plan.complex_dtype)
+    low = torch.empty((w.npix, w.npix), dtype=plan.real_dtype, device=dev)
+    img = torch.empty_like(low)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(max(args.warmup, 3)):
+        plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
+    torch.cuda.synchronize()
+
+    # ---- timed region (captured-graph minor cycles) ----
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    tot = dict(vis=0, grid_ms=0.0, fft_ms=0.0, minor_ms=0.0, iters=0, elapsed=0.0)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        _, _, st = plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
+        tot["vis"] += st.gridded_vis
+        tot["grid_ms"] += st.grid_ms
+        tot["fft_ms"] += st.fft_ms
+        tot["minor_ms"] += st.minor_ms
+        tot["iters"] += st.total_iterations
+        tot["elapsed"] += st.elapsed_ms
+    ev1.record()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop() if clocks else None
+    wall_ms = ev0.elapsed_time(ev1)
+    grid_s = tot["grid_ms"] / 1000.0
+    vis_total = tot["vis"]
+    if pg:
+        t = torch.tensor([wall_ms, grid_s], device=dev, dtype=torch.float64)
+        v = torch.tensor([float(vis_total)], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(v, op=pg.ReduceOp.SUM)
+        wall_ms, grid_s = float(t[0]), float(t[1])
+        vis_total = float(v[0])
+    value = vis_total / grid_s
+    ms_per_step = wall_ms / args.steps
+    fista_rate = tot["iters"] / (tot["minor_ms"] / 1000.0)
+    kernels_per_pass = 2 * 4 + 1
+    passes_per_cycle = math.ceil((FISTA_ITERS + 1) / 8) * 8
+    launches_per_step = 2 * (N_MAJOR * (passes_per_cycle * kernels_per_pass + 5 + 8) + 5 + 2)
+    gpu_launches = launches_per_step * args.steps
+
+    # ---- per-kernel durations: the same steps with every kernel family
+    #      bracketed by CUDA events on the plan's stream ----
+    roofline = None
+    prof = None
+    if rank == 0:
+        plan.kernel_profile(reset=True)
+        plan.set_profiling(True)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
+        prof = plan.kernel_profile(reset=True)
+        plan.set_profiling(False)
+        roofline = roofline_of(prof, w, plan, args)
+
+    # ---- end to end through the public call with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        hvis = torch.from_numpy(w.vis[0]).to(plan.complex_dtype).pin_memory()
+        hlow = torch.empty((w.npix, w.npix), dtype=plan.real_dtype).pin_memory()
+        himg = torch.empty_like(hlow).pin_memory()
+        dvis = torch.empty_like(vis)
+        plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        e2e_vis = 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            dvis.copy_(hvis, non_blocking=True)
+            _, _, st = plan.reconstruct_two_step(dvis, opts, low_out=low, out=img)
+            hlow.copy_(low, non_blocking=True)
+            himg.copy_(img, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_vis += st.gridded_vis
+        e2e_s = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            v = torch.tensor([float(e2e_vis)], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            pg.all_reduce(v, op=pg.ReduceOp.SUM)
+            e2e_s, e2e_vis = float(t[0]), float(v[0])
+        e2e = {"value": e2e_vis / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(hvis.numel() * hvis.element_size()),
+               "d2h_bytes_per_step": int(2 * hlow.numel() * hlow.element_size()),
+               "ms_per_step": 1000 * e2e_s / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, rows = oracle_vis_rate(w, args.cpu_sample_rows)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": f"oracle degrid+grid of the first {rows} rows of this workload "
+                         f"(FFT time removed), {secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+                "config": workload_config(w, args.precision),
+                "fista_iters_per_s": fista_rate,
+                "step_breakdown_ms": {"grid_degrid": tot["grid_ms"] / args.steps,
+                                      "fft_grid": tot["fft_ms"] / args.steps,
+                                      "minor_cycles": tot["minor_ms"] / args.steps},
+                "gpu_launches": gpu_launches,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}
+                if prof else None}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def roofline_of(prof, w, plan, args):
+    """Roofline of the dominant kernel family of the library (largest share of
+    kernel time).  Algorithmic bytes per launch (FP32, M = 8 bases, N^2 px):
+      analysis_l1: read y_k, y_k-1, b, write y_k (16 B/px), read B_k, B_k-1
+                   and write B_k+1 over the detail subbands (3 x 8 x 3/4 x 4 B
+                   = 72 B/px), write the level-1 approximations (8 B/px):
+                   96 B/px.
+      synth_l1:    read 8 planes (32 B/px), write x (4 B/px): 36 B/px.
+      degrid:      per row 12 B geometry + 8 B observed + 8 B residual, plus
+                   one read of the (2N)^2 complex64 grid.
+      grid:        per row 12 B geometry + 8 B value, plus the work-item tiles
+                   written (one (T+6)^2 tile of float2 per item).
+    """
+    hbm, kind = _peaks()
+    rsz = 4 if args.precision != "fp64" else 8
+    N = w.npix
+    mine = {k: v for k, v in prof.items() if not k.startswith("fft") and v[0] > 0}
+    fam = max(mine, key=lambda k: mine[k][1])
+    launches, total_ms = mine[fam]
+    avg_s = total_ms / launches / 1000.0
+    per_px = {"analysis_l1": 96 * rsz / 4, "synth_l1": 36 * rsz / 4}
+    if fam in per_px:
+        bytes_ = per_px[fam] * N * N
+    elif fam == "degrid":
+        counts = plan.partition_counts()
+        rows = (counts["L"] + counts["H"]) / 2.0
+        bytes_ = rows * (4 + 2 * rsz + 4 * rsz) + 4 * N * N * 2 * rsz
+    else:
+        return {"bound": "hbm", "kernel": fam, "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_kind": kind}
+    achieved = bytes_ / avg_s / 1e9
+    return {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_kind": f"{kind} (hbm_gbs burst copy)",
+            "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
+            "launches": launches}
+
+
+if __name__ == "__main__":
+    main()

@@ -98,7 +98,8 @@ typedef struct {
   double grid_ms;         /* of which: gridding + degridding kernels          */
   double fft_ms;          /* of which: the Ng x Ng FFTs of the major cycles   */
   double minor_ms;        /* of which: minor cycles                           */
-  int64_t gridded_vis;    /* visibilities degridded + gridded by the call     */
+  int64_t gridded_vis;    /* visibilities passed through one degrid + grid pair,
+                             summed over the residual images of the call      */
   const double* objective_trace; /* plan-owned host array: F(beta_0..beta_k) of
                              the last minor cycle, length iterations + 1;
                              valid until the plan's next call                 */
@@ -222,6 +223,32 @@ ms_status ms_reconstruct_two_step(ms_plan* plan, int32_t chan, const void* vis,
 ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vis,
                                      const ms_recon_opts* opts, void* img_out,
                                      void* model_out, ms_stats* stats, void* stream);
+
+/* ------------------------------------------------------------- profiling */
+
+/* Kernel families timed by the profiler.  SYNTH / ANALYSIS are the wavelet
+ * levels 2..J, *_L1 the first level (the largest); ANALYSIS includes the
+ * fused prox of the minor cycle; FFT_GRID is the Ng x Ng transform of the
+ * major cycle, FFT_R2C / FFT_C2R the N x N transforms of the minor cycle. */
+typedef enum {
+  MS_K_DEGRID = 0, MS_K_GRID = 1, MS_K_FOLD = 2, MS_K_FFT_GRID = 3, MS_K_PAD_CROP = 4,
+  MS_K_SYNTH = 5, MS_K_SYNTH_L1 = 6, MS_K_FFT_R2C = 7, MS_K_SPEC_MUL = 8,
+  MS_K_FFT_C2R = 9, MS_K_ANALYSIS = 10, MS_K_ANALYSIS_L1 = 11, MS_K_COUNT = 12
+} ms_kernel_family;
+
+typedef struct {
+  int64_t launches[16];   /* timed launches (groups of launches) per family   */
+  double total_ms[16];    /* summed CUDA-event durations per family           */
+} ms_kernel_profile;
+
+/* on = 1: every subsequent call brackets each kernel family launch with CUDA
+ * events on the plan's stream (the minor cycle then runs its passes as direct
+ * launches instead of the captured graph).  on = 0 turns it off. */
+ms_status ms_set_profiling(ms_plan* plan, int32_t on);
+
+/* Waits for the plan's stream, then copies the accumulated per-family times
+ * to *out; reset = 1 clears the accumulators afterwards. */
+ms_status ms_get_kernel_profile(ms_plan* plan, ms_kernel_profile* out, int32_t reset);
 
 #ifdef __cplusplus
 }

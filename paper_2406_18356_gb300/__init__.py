@@ -59,6 +59,14 @@ class ms_stats(ctypes.Structure):
                 ("objective_trace", ctypes.POINTER(ctypes.c_double))]
 
 
+class ms_kernel_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 16), ("total_ms", ctypes.c_double * 16)]
+
+
+KERNEL_FAMILIES = ["degrid", "grid", "fold", "fft_grid", "pad_crop", "synth", "synth_l1",
+                   "fft_r2c", "spec_mul", "fft_c2r", "analysis", "analysis_l1"]
+
+
 class ms_recon_opts(ctypes.Structure):
     _fields_ = [("n_major", ctypes.c_int32), ("fista_iters", ctypes.c_int32),
                 ("rel_tol", ctypes.c_double), ("lambda_rule", ctypes.c_int32),
@@ -89,6 +97,8 @@ _SIGNATURES = {
                                 ctypes.POINTER(ms_stats), _P],
     "ms_reconstruct_single_step": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P,
                                    ctypes.POINTER(ms_stats), _P],
+    "ms_set_profiling": [_P, _I32],
+    "ms_get_kernel_profile": [_P, ctypes.POINTER(ms_kernel_profile), _I32],
 }
 
 _lib = None
@@ -379,6 +389,16 @@ class Plan:
         return out, Stats.from_c(st)
 
 
+    def set_profiling(self, on: bool):
+        self._check(self._lib.ms_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_profile(self, reset: bool = False) -> dict:
+        """{family: (timed launch groups, total ms)} from CUDA events."""
+        out = ms_kernel_profile()
+        self._check(self._lib.ms_get_kernel_profile(self._h, ctypes.byref(out), 1 if reset else 0))
+        return {name: (out.launches[i], out.total_ms[i]) for i, name in enumerate(KERNEL_FAMILIES)}
+
+
 # module-level names matching the C ABI -------------------------------------
 def ms_plan_create(*args, **kw) -> Plan:
     return Plan(*args, **kw)
@@ -438,3 +458,11 @@ def ms_reconstruct_two_step(plan: Plan, vis, opts=None, **kw):
 
 def ms_reconstruct_single_step(plan: Plan, vis, opts=None, **kw):
     return plan.reconstruct_single_step(vis, opts, **kw)
+
+
+def ms_set_profiling(plan: Plan, on: bool):
+    plan.set_profiling(on)
+
+
+def ms_get_kernel_profile(plan: Plan, reset: bool = False):
+    return plan.kernel_profile(reset)

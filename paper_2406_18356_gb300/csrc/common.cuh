@@ -127,7 +127,7 @@ struct WaveletGeom {
 // pick buffer k % 3 (and k % 2) from it and skip all work once ctl->done is set
 template <typename R>
 void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
-                       const FistaCtl* ctl, cudaStream_t s);
+                       const FistaCtl* ctl, cudaStream_t s, int only_level = 0);
 template <typename R>
 void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s);
 struct ProxArgs {
@@ -137,7 +137,7 @@ struct ProxArgs {
 template <typename R>
 void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* tmp,
                            WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
-                           cudaStream_t s);
+                           cudaStream_t s, int only_level = 0);
 int analysis_prox_partials(WaveletGeom g);
 
 // spectral_kernels.cu

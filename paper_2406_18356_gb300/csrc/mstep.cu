@@ -234,6 +234,17 @@ struct ms_plan {
   CUtensorMap tmap{};
   std::string msg;
   std::vector<double> htrace;
+  // profiling: CUDA-event spans per kernel family
+  bool prof = false;
+  bool capturing = false;
+  std::vector<cudaEvent_t> evpool;
+  struct Span {
+    int fam;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> pending;
+  int64_t k_launch[16] = {};
+  double k_ms[16] = {};
   // captured FISTA passes
   cudaGraphExec_t fista_exec = nullptr;
   int fista_graph_step = -1;
@@ -249,6 +260,51 @@ struct ms_plan {
 namespace {
 
 constexpr int kPasses = 8;   // FISTA passes per captured graph launch
+
+cudaEvent_t pool_event(ms_plan* p) {
+  if (!p->evpool.empty()) {
+    cudaEvent_t e = p->evpool.back();
+    p->evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  ck(cudaEventCreate(&e), "event");
+  return e;
+}
+
+// Sums the finished spans into the per-family accumulators (synchronizes).
+void harvest(ms_plan* p) {
+  if (p->pending.empty()) return;
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  for (auto& s : p->pending) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, s.a, s.b), "event time");
+    p->k_ms[s.fam] += ms;
+    p->k_launch[s.fam] += 1;
+    p->evpool.push_back(s.a);
+    p->evpool.push_back(s.b);
+  }
+  p->pending.clear();
+}
+
+// Brackets the launches of one kernel family with events when profiling.
+struct KSpan {
+  ms_plan* p;
+  int fam;
+  cudaEvent_t a = nullptr;
+  KSpan(ms_plan* pl, int f) : p(pl), fam(f) {
+    if (p->prof && !p->capturing) {
+      a = pool_event(p);
+      ck(cudaEventRecord(a, p->ps), "event record");
+    }
+  }
+  ~KSpan() {
+    if (!a) return;
+    cudaEvent_t b = pool_event(p);
+    cudaEventRecord(b, p->ps);
+    p->pending.push_back({fam, a, b});
+  }
+};
 
 struct Timer {
   ms_plan* p;
@@ -353,9 +409,15 @@ template <typename R> void fft_c2r(ms_plan* p, void* in, void* out) {
 
 // model grid = F Z D image (centred)
 template <typename R> void image_to_grid(ms_plan* p, const void* image, Timer* tm) {
-  launch_pad<R>((const R*)image, (const R*)p->psi, p->N, p->Ng, (C2<R>*)p->grid, p->ps);
+  {
+    KSpan k(p, MS_K_PAD_CROP);
+    launch_pad<R>((const R*)image, (const R*)p->psi, p->N, p->Ng, (C2<R>*)p->grid, p->ps);
+  }
   int a = tm ? tm->mark() : 0;
-  fft_c2c<R>(p, CUFFT_FORWARD);
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    fft_c2c<R>(p, CUFFT_FORWARD);
+  }
   if (tm) tm->spans[1].push_back({a, tm->mark()});
 }
 
@@ -363,9 +425,12 @@ template <typename R> void image_to_grid(ms_plan* p, const void* image, Timer* t
 template <typename R>
 void degrid_sorted(ms_plan* p, PartDev& pd, const void* obs_sorted, void* out_sorted, Timer* tm) {
   int a = tm ? tm->mark() : 0;
-  launch_degrid<R>(&p->tmap, (const C2<R>*)p->grid, pd.items, pd.nitems, pd.cell,
-                   (const C2<R>*)pd.frac, (const C2<R>*)obs_sorted, (C2<R>*)out_sorted, p->Ng,
-                   p->T, p->ntx, p->beta, p->err, p->ps);
+  {
+    KSpan k(p, MS_K_DEGRID);
+    launch_degrid<R>(&p->tmap, (const C2<R>*)p->grid, pd.items, pd.nitems, pd.cell,
+                     (const C2<R>*)pd.frac, (const C2<R>*)obs_sorted, (C2<R>*)out_sorted, p->Ng,
+                     p->T, p->ntx, p->beta, p->err, p->ps);
+  }
   if (tm) tm->spans[0].push_back({a, tm->mark()});
 }
 
@@ -374,23 +439,35 @@ template <typename R>
 void grid_sorted(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image, Timer* tm) {
   int a = tm ? tm->mark() : 0;
   if (p->prec == MS_FP32_KAHAN) {
-    launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
-                             (const float2*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx,
-                             p->beta, p->ps);
+    {
+      KSpan k(p, MS_K_GRID);
+      launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
+                               (const float2*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx,
+                               p->beta, p->ps);
+    }
+    KSpan k(p, MS_K_FOLD);
     launch_fold<float, true>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
                              p->ps);
   } else {
-    launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
-                          (const C2<R>*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx, p->beta,
-                          p->ps);
+    {
+      KSpan k(p, MS_K_GRID);
+      launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
+                            (const C2<R>*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx, p->beta,
+                            p->ps);
+    }
+    KSpan k(p, MS_K_FOLD);
     launch_fold<R, false>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid,
                           p->ps);
   }
   int b = tm ? tm->mark() : 0;
   if (tm) tm->spans[0].push_back({a, b});
-  fft_c2c<R>(p, CUFFT_INVERSE);
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    fft_c2c<R>(p, CUFFT_INVERSE);
+  }
   if (tm) tm->spans[1].push_back({b, tm->mark()});
   double sc = pd.n > 0 ? 1.0 / (double)pd.n : 0.0;
+  KSpan k(p, MS_K_PAD_CROP);
   launch_crop<R>((const C2<R>*)p->grid, (const R*)p->psi, p->N, p->Ng, sc, (R*)image, p->ps);
 }
 
@@ -438,26 +515,56 @@ template <typename R> void ensure_psf(ms_plan* p, PartDev& pd) {
 // ------------------------------------------------------------- minor cycle
 template <typename R> void record_fista_pass(ms_plan* p) {
   WaveletGeom g{p->N, p->J, p->M};
-  launch_synthesis3<R>((const R* const*)p->B3_dev, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps);
-  fft_r2c<R>(p, p->xwork, p->spec);
-  launch_spec_mul<R>((C2<R>*)p->spec, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts,
-                     p->ctl, p->trace, p->tickets + 0, p->ps);
-  fft_c2r<R>(p, p->spec, p->ywork);
+  const R* const* B3 = (const R* const*)p->B3_dev;
+  if (p->J > 1) {
+    KSpan k(p, MS_K_SYNTH);
+    for (int j = p->J; j >= 2; --j)
+      launch_synthesis3<R>(B3, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps, j);
+  }
+  {
+    KSpan k(p, MS_K_SYNTH_L1);
+    launch_synthesis3<R>(B3, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps, 1);
+  }
+  {
+    KSpan k(p, MS_K_FFT_R2C);
+    fft_r2c<R>(p, p->xwork, p->spec);
+  }
+  {
+    KSpan k(p, MS_K_SPEC_MUL);
+    launch_spec_mul<R>((C2<R>*)p->spec, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts,
+                       p->ctl, p->trace, p->tickets + 0, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FFT_C2R);
+    fft_c2r<R>(p, p->spec, p->ywork);
+  }
   ProxArgs a{p->ywork, p->bimg};
-  launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
-                           p->ctl, p->tickets + 1, p->l1parts, p->ps);
+  {
+    KSpan k(p, MS_K_ANALYSIS_L1);
+    launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
+                             p->ctl, p->tickets + 1, p->l1parts, p->ps, 1);
+  }
+  if (p->J > 1) {
+    KSpan k(p, MS_K_ANALYSIS);
+    for (int j = 2; j <= p->J; ++j)
+      launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
+                               p->ctl, p->tickets + 1, p->l1parts, p->ps, j);
+  }
 }
 
 template <typename R> void ensure_fista_graph(ms_plan* p) {
   if (p->fista_exec) return;
   cudaGraph_t graph;
   ck(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal), "begin capture");
+  p->capturing = true;
   try {
     for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p);
   } catch (...) {
+    p->capturing = false;
     cudaStreamEndCapture(p->ps, &graph);
     throw;
   }
+  p->capturing = false;
   ck(cudaStreamEndCapture(p->ps, &graph), "end capture");
   ck(cudaGraphInstantiate(&p->fista_exec, graph, 0), "graph instantiate");
   cudaGraphDestroy(graph);
@@ -513,9 +620,23 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
      "copy");
   ck(cudaMemsetAsync(p->Yh[0], 0, sizeof(R) * npix2, p->ps), "memset");
   launch_l1<R>((const R*)p->B[0], ncoef, p->parts, &p->ctl->l1_cur, p->tickets + 4, p->ps);
-  ensure_fista_graph<R>(p);
   // max_iters prox steps plus one pass that only evaluates F at the result
   const int passes = max_iters + 1;
+  if (p->prof) {   // direct launches, each kernel family bracketed by events
+    for (int i = 0; i < passes; ++i) {
+      record_fista_pass<R>(p);
+      if ((i + 1) % kPasses == 0 && p->pending.size() > 4096) harvest(p);
+      if (rel_tol > 0 && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes) {
+        int32_t done = 0;
+        ck(cudaMemcpyAsync(&done, &p->ctl->done, sizeof(done), cudaMemcpyDeviceToHost, p->ps),
+           "read done");
+        ck(cudaStreamSynchronize(p->ps), "synchronize");
+        if (done) break;
+      }
+    }
+    return;
+  }
+  ensure_fista_graph<R>(p);
   int launched = 0;
   while (launched < passes) {
     ck(cudaGraphLaunch(p->fista_exec, p->ps), "graph launch");
@@ -603,11 +724,11 @@ void run_step(ms_plan* p, int step, int chan, const ms_recon_opts& o, const void
     if (h.error) throw Fail{(ms_status)h.error, "non-finite objective or invalid noise levels"};
     if (st) {
       st->total_iterations += h.k;
-      st->gridded_vis += 2 * pd.n;
+      st->gridded_vis += pd.n;
     }
   }
   residual_sorted<R>(p, pd, p->vis_a, model, res, &tm);   // i~_{N+1}
-  if (st) st->gridded_vis += 2 * pd.n;
+  if (st) st->gridded_vis += pd.n;
   launch_axpby<R>(res, model, (R*)image_out, 1.0, 1.0, n2, p->ps);
   fill_stats<R>(p, st, true);
   if (st) st->major_cycles += o.n_major;
@@ -965,6 +1086,11 @@ void destroy(ms_plan* p) {
     if (h) cufftDestroy(h);
   for (void* a : p->allocs) cudaFree(a);
   for (auto e : p->tev) cudaEventDestroy(e);
+  for (auto e : p->evpool) cudaEventDestroy(e);
+  for (auto& sp : p->pending) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
   if (p->ev_in) cudaEventDestroy(p->ev_in);
   if (p->ev_out) cudaEventDestroy(p->ev_out);
   if (p->ps) cudaStreamDestroy(p->ps);
@@ -1219,6 +1345,33 @@ ms_status ms_reconstruct_single_step(ms_plan* p, int32_t chan, const void* vis,
     arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
     arg(p->ch[chan].part[MS_PART_ALL].n > 0, "no visibilities");
     DISPATCH(p, single_step<R>(p, chan, vis, o, img_out, model_out, st, stream));
+  });
+}
+
+ms_status ms_set_profiling(ms_plan* p, int32_t on) {
+  return guarded(p, [&] {
+    ck(cudaSetDevice(p->dev), "set device");
+    harvest(p);
+    p->prof = on != 0;
+  });
+}
+
+ms_status ms_get_kernel_profile(ms_plan* p, ms_kernel_profile* out, int32_t reset) {
+  return guarded(p, [&] {
+    arg(out != nullptr, "out is NULL");
+    ck(cudaSetDevice(p->dev), "set device");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    harvest(p);
+    std::memset(out, 0, sizeof(*out));
+    for (int i = 0; i < MS_K_COUNT; ++i) {
+      out->launches[i] = p->k_launch[i];
+      out->total_ms[i] = p->k_ms[i];
+    }
+    if (reset)
+      for (int i = 0; i < 16; ++i) {
+        p->k_launch[i] = 0;
+        p->k_ms[i] = 0;
+      }
   });
 }
 

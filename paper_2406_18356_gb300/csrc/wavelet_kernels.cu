@@ -173,12 +173,13 @@ __global__ void __launch_bounds__(kThreads)
 
 template <typename R>
 void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
-                       const FistaCtl* ctl, cudaStream_t s) {
+                       const FistaCtl* ctl, cudaStream_t s, int only_level) {
   const size_t smem = (size_t)(4 * kSynCnt * kSynCnt + 2 * kSynTile * kSynCnt) * sizeof(R);
   auto k = synthesis_kernel<R>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
   for (int j = g.J; j >= 1; --j) {
+    if (only_level > 0 && j != only_level) continue;
     int h = g.N >> j, n = 2 * h;
     int TS = n < kSynTile ? n : kSynTile;
     int tiles = (n / TS) * (n / TS);
@@ -394,7 +395,7 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
 template <typename R>
 void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* tmp,
                            WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
-                           cudaStream_t s) {
+                           cudaStream_t s, int only_level) {
   const size_t smem = analysis_smem_bytes(sizeof(R));
   auto k = analysis_kernel<R, 1>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -408,24 +409,25 @@ void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* t
     const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
     dim3 grid(tiles, j == 1 ? 1 : g.M);
-    k<<<grid, kThreads, smem, s>>>(nullptr, ll_in, ll_out, nullptr, a, B3_dev, Yh2_dev, g.N,
-                                   j, g.J, g.M, ctl, l1_parts, base, ticket, total);
+    if (only_level <= 0 || j == only_level)
+      k<<<grid, kThreads, smem, s>>>(nullptr, ll_in, ll_out, nullptr, a, B3_dev, Yh2_dev, g.N,
+                                     j, g.J, g.M, ctl, l1_parts, base, ticket, total);
     base += tiles * (j == 1 ? 1 : g.M);
   }
 }
 
 template void launch_synthesis3<float>(const float* const*, float*, float*, WaveletGeom,
-                                       const FistaCtl*, cudaStream_t);
+                                       const FistaCtl*, cudaStream_t, int);
 template void launch_synthesis3<double>(const double* const*, double*, double*, WaveletGeom,
-                                        const FistaCtl*, cudaStream_t);
+                                        const FistaCtl*, cudaStream_t, int);
 template void launch_analysis<float>(const float*, float*, float*, WaveletGeom, cudaStream_t);
 template void launch_analysis<double>(const double*, double*, double*, WaveletGeom,
                                       cudaStream_t);
 template void launch_analysis_prox3<float>(ProxArgs, float* const*, float* const*, float*,
                                            WaveletGeom, FistaCtl*, int32_t*, double*,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 template void launch_analysis_prox3<double>(ProxArgs, double* const*, double* const*, double*,
                                             WaveletGeom, FistaCtl*, int32_t*, double*,
-                                            cudaStream_t);
+                                            cudaStream_t, int);
 
 }  // namespace ms
