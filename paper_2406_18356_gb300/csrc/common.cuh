@@ -130,15 +130,14 @@ void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
                        const FistaCtl* ctl, cudaStream_t s, int only_level = 0);
 template <typename R>
 void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s);
-struct ProxArgs {
-  const void* ywork;      // y of the current coefficients (C2R output)
-  const void* b;          // b image of the quadratic objective
-};
+// gradient image 2 (K W alpha_k - b) of the current pass (inverse FFT output)
+// and an optional TMA descriptor of it (nullptr: plain loads)
 template <typename R>
-void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* tmp,
+void launch_analysis_prox3(const R* grad, const CUtensorMap* grad_map, R* const* B3_dev, R* tmp,
                            WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
                            cudaStream_t s, int only_level = 0);
 int analysis_prox_partials(WaveletGeom g);
+void analysis_window_box(unsigned* cols, unsigned* rows);
 
 // spectral_kernels.cu
 int spectral_partials(int N);
@@ -157,8 +156,9 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
                        const R* gh2, int N, C2<R>* Bs, double* parts, FistaCtl* ctl,
                        int32_t* ticket, cudaStream_t s);
 template <typename R>
-void launch_spec_mul(C2<R>* spec, const R* Ks, const C2<R>* Bs, int N, double* parts,
-                     FistaCtl* ctl, double* trace, int32_t* ticket, cudaStream_t s);
+void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
+                     double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
+                     cudaStream_t s);
 template <typename R>
 void launch_spec_apply(C2<R>* spec, const R* Ks, int N, cudaStream_t s);
 template <typename R>

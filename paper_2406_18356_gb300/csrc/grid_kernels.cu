@@ -144,21 +144,37 @@ __global__ void __launch_bounds__(kThreads)
                   const C2<R>* __restrict__ frac, const C2<R>* __restrict__ obs,
                   C2<R>* __restrict__ out, int Ng, int T, int ntx, R beta,
                   int32_t* __restrict__ err) {
+  // the tile sits at a 128-byte-aligned shared address (TMA destination rule),
+  // the mbarrier and a flag after it, all in the dynamic allocation
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  C2<R>* tile = reinterpret_cast<C2<R>*>(smem_raw);
+  const unsigned pad = (128u - (smem_addr(smem_raw) & 127u)) & 127u;
+  C2<R>* tile = reinterpret_cast<C2<R>*>(smem_raw + pad);
   const int S = T + kW - 1;
+  uint64_t& bar = *reinterpret_cast<uint64_t*>(tile + S * S);
+  int& use_tma = *reinterpret_cast<int*>(&bar + 1);
   const WorkItem it = items[blockIdx.x];
   const int tx = it.tile % ntx, ty = it.tile / ntx;
   const int ox = tx * T, oy = ty * T;
-  const bool edge = (ox + S > Ng) || (oy + S > Ng);
+  bool edge = (ox + S > Ng) || (oy + S > Ng);
   bool ok = true;
   if (!edge) {
     if (threadIdx.x == 0) {
-      mbar_init(&bar, 1);
-      fence_mbar_init();
+      // alignment rules of the copy, checked before it is issued
+      const bool aligned = (smem_addr(tile) & 127u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(&tmap) & 63u) == 0 &&
+                           ((2 * ox * (int)sizeof(R)) & 15) == 0;
+      use_tma = aligned ? 1 : 0;
+      if (aligned) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+      } else {
+        atomicExch(err, 8);
+      }
     }
     __syncthreads();
+    edge = use_tma == 0;
+  }
+  if (!edge) {
     if (threadIdx.x == 0) {
       mbar_expect_tx(&bar, (unsigned)(S * S * sizeof(C2<R>)));
       tma_load_2d(tile, &tmap, 2 * ox, oy, &bar);
@@ -222,7 +238,8 @@ void launch_degrid(const CUtensorMap* tmap, const C2<R>* grid, const WorkItem* i
                    cudaStream_t s) {
   if (nitems <= 0) return;
   const int S = tile + kW - 1;
-  size_t smem = (size_t)S * S * sizeof(C2<R>);
+  // tile + alignment slack + mbarrier + flag
+  size_t smem = (size_t)S * S * sizeof(C2<R>) + 128 + sizeof(uint64_t) + sizeof(int) + 4;
   if (obs) {
     auto k = degrid_kernel<R, true>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -218,10 +218,13 @@ struct ms_plan {
   int64_t max_n = 0;
   void *vis_a = nullptr, *vis_b = nullptr;
   void* img[6] = {};
-  void *B[3] = {}, *Yh[2] = {}, *xwork = nullptr, *ywork = nullptr;
-  void *spec = nullptr, *spec2 = nullptr, *Ks = nullptr, *Bs = nullptr, *bimg = nullptr;
+  void *B[3] = {}, *xwork = nullptr, *ywork = nullptr;
+  void *F[2] = {};   // FISTA spectra X^_k / X^_{k-1} (ping-pong by pass parity)
+  void *spec = nullptr, *spec2 = nullptr, *Ks = nullptr, *Bs = nullptr;
   void *gl2 = nullptr, *gh2 = nullptr, *wtmp = nullptr;
-  void **B3_dev = nullptr, **Yh2_dev = nullptr, **api3_dev = nullptr;
+  void **B3_dev = nullptr, **api3_dev = nullptr;
+  CUtensorMap grad_map{};   // TMA descriptor of the gradient image (ywork)
+  bool have_grad_map = false;
   FistaCtl* ctl = nullptr;
   double* trace = nullptr;
   double* parts = nullptr;     // reduction partials (one reduction at a time)
@@ -513,8 +516,13 @@ template <typename R> void ensure_psf(ms_plan* p, PartDev& pd) {
 }
 
 // ------------------------------------------------------------- minor cycle
-template <typename R> void record_fista_pass(ms_plan* p) {
+// One FISTA pass.  Pass i of a minor cycle has iteration index k = i, so the
+// two spectrum buffers alternate with the pass parity: F[k % 2] receives
+// X^_k, F[(k+1) % 2] holds X^_{k-1} and then the gradient spectrum.
+template <typename R> void record_fista_pass(ms_plan* p, int parity) {
   WaveletGeom g{p->N, p->J, p->M};
+  C2<R>* Fk = (C2<R>*)p->F[parity];
+  C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
   const R* const* B3 = (const R* const*)p->B3_dev;
   if (p->J > 1) {
     KSpan k(p, MS_K_SYNTH);
@@ -527,28 +535,29 @@ template <typename R> void record_fista_pass(ms_plan* p) {
   }
   {
     KSpan k(p, MS_K_FFT_R2C);
-    fft_r2c<R>(p, p->xwork, p->spec);
+    fft_r2c<R>(p, p->xwork, Fk);
   }
   {
     KSpan k(p, MS_K_SPEC_MUL);
-    launch_spec_mul<R>((C2<R>*)p->spec, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts,
-                       p->ctl, p->trace, p->tickets + 0, p->ps);
+    launch_spec_mul<R>(Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts, p->ctl,
+                       p->trace, p->tickets + 0, p->ps);
   }
   {
     KSpan k(p, MS_K_FFT_C2R);
-    fft_c2r<R>(p, p->spec, p->ywork);
+    fft_c2r<R>(p, Fo, p->ywork);   // gradient image 2 (K W alpha_k - b)
   }
-  ProxArgs a{p->ywork, p->bimg};
+  const R* grad = (const R*)p->ywork;
+  const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
   {
     KSpan k(p, MS_K_ANALYSIS_L1);
-    launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
-                             p->ctl, p->tickets + 1, p->l1parts, p->ps, 1);
+    launch_analysis_prox3<R>(grad, gmap, (R* const*)p->B3_dev, (R*)p->wtmp, g, p->ctl,
+                             p->tickets + 1, p->l1parts, p->ps, 1);
   }
   if (p->J > 1) {
     KSpan k(p, MS_K_ANALYSIS);
     for (int j = 2; j <= p->J; ++j)
-      launch_analysis_prox3<R>(a, (R* const*)p->B3_dev, (R* const*)p->Yh2_dev, (R*)p->wtmp, g,
-                               p->ctl, p->tickets + 1, p->l1parts, p->ps, j);
+      launch_analysis_prox3<R>(grad, gmap, (R* const*)p->B3_dev, (R*)p->wtmp, g, p->ctl,
+                               p->tickets + 1, p->l1parts, p->ps, j);
   }
 }
 
@@ -558,7 +567,7 @@ template <typename R> void ensure_fista_graph(ms_plan* p) {
   ck(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal), "begin capture");
   p->capturing = true;
   try {
-    for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p);
+    for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p, i & 1);
   } catch (...) {
     p->capturing = false;
     cudaStreamEndCapture(p->ps, &graph);
@@ -606,11 +615,8 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     launch_b_spectrum<R>((const C2<R>*)p->spec, nullptr, (const R*)pd.Hhat, nullptr, nullptr, N,
                          (C2<R>*)p->Bs, p->parts, p->ctl, p->tickets + 3, p->ps);
   }
-  // the inverse real FFT overwrites its input: transform a copy of B^
-  ck(cudaMemcpyAsync(p->spec2, p->Bs, sizeof(C2<R>) * nspec, cudaMemcpyDeviceToDevice, p->ps),
-     "copy");
-  fft_c2r<R>(p, p->spec2, p->bimg);
-  // B[0] = start, B[2] = B[0] (its weight is zero for k < 2), y history zero
+  // B[0] = start, B[2] = B[0] and X^_{-1} = 0 (their weight is zero for k < 2)
+  ck(cudaMemsetAsync(p->F[1], 0, sizeof(C2<R>) * nspec, p->ps), "memset");
   if (beta0)
     ck(cudaMemcpyAsync(p->B[0], beta0, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
        "copy");
@@ -618,13 +624,12 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     ck(cudaMemsetAsync(p->B[0], 0, sizeof(R) * ncoef, p->ps), "memset");
   ck(cudaMemcpyAsync(p->B[2], p->B[0], sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
      "copy");
-  ck(cudaMemsetAsync(p->Yh[0], 0, sizeof(R) * npix2, p->ps), "memset");
   launch_l1<R>((const R*)p->B[0], ncoef, p->parts, &p->ctl->l1_cur, p->tickets + 4, p->ps);
   // max_iters prox steps plus one pass that only evaluates F at the result
   const int passes = max_iters + 1;
   if (p->prof) {   // direct launches, each kernel family bracketed by events
     for (int i = 0; i < passes; ++i) {
-      record_fista_pass<R>(p);
+      record_fista_pass<R>(p, i & 1);
       if ((i + 1) % kPasses == 0 && p->pending.size() > 4096) harvest(p);
       if (rel_tol > 0 && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes) {
         int32_t done = 0;
@@ -937,10 +942,9 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->vis_b = p->alloc<C2<R>>(std::max<int64_t>(p->max_n, 1), "vis");
   for (auto& im : p->img) im = p->alloc<R>(n2, "image");
   for (auto& b : p->B) b = p->alloc<R>(ncoef, "coefficients");
-  for (auto& y : p->Yh) y = p->alloc<R>(n2, "image");
   p->xwork = p->alloc<R>(n2, "image");
   p->ywork = p->alloc<R>(n2, "image");
-  p->bimg = p->alloc<R>(n2, "image");
+  for (auto& f : p->F) f = p->alloc<C2<R>>(nspec, "spectrum");
   p->spec = p->alloc<C2<R>>(nspec, "spectrum");
   p->spec2 = p->alloc<C2<R>>(nspec, "spectrum");
   p->Bs = p->alloc<C2<R>>(nspec, "spectrum");
@@ -949,7 +953,6 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->gh2 = p->alloc<R>(nspec, "filter");
   p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
   p->B3_dev = p->alloc<void*>(3, "ptrs");
-  p->Yh2_dev = p->alloc<void*>(2, "ptrs");
   p->api3_dev = p->alloc<void*>(3, "ptrs");
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
   p->parts = p->alloc<double>(4096, "partials");
@@ -962,7 +965,6 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   ck(cudaMemset(p->err, 0, sizeof(int32_t)), "memset");
   ck(cudaMemset(p->ctl, 0, sizeof(FistaCtl)), "memset");
   set_ptrs_kernel<<<1, 1, 0, s>>>(p->B3_dev, p->B[0], p->B[1], p->B[2]);
-  set_ptrs_kernel<<<1, 1, 0, s>>>(p->Yh2_dev, p->Yh[0], p->Yh[1], nullptr);
   // cuFFT plans
   cufftType tc = sizeof(R) == 8 ? CUFFT_Z2Z : CUFFT_C2C;
   cufftType tr = sizeof(R) == 8 ? CUFFT_D2Z : CUFFT_R2C;
@@ -989,6 +991,22 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) throw Fail{MS_ERR_CUDA, "cuTensorMapEncodeTiled failed"};
+    // gradient image of the minor cycle: {N, N}, box = the analysis input
+    // window {80, 78}; only images at least one window wide use it
+    unsigned bc = 0, br = 0;
+    analysis_window_box(&bc, &br);
+    if ((unsigned)N >= bc) {
+      cuuint64_t gd[2] = {(cuuint64_t)N, (cuuint64_t)N};
+      cuuint64_t gs[1] = {(cuuint64_t)N * sizeof(R)};
+      cuuint32_t gb[2] = {bc, br};
+      r = ((EncodeTiledFn)fn)(
+          &p->grad_map,
+          sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+          p->ywork, gd, gs, gb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) throw Fail{MS_ERR_CUDA, "cuTensorMapEncodeTiled failed (gradient)"};
+      p->have_grad_map = true;
+    }
   }
   ck(cudaStreamSynchronize(s), "plan");
   ck(cudaGetLastError(), "plan kernels");

@@ -49,8 +49,7 @@ __device__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV]) {
   }
 }
 
-// write this block's partials; returns true in thread 0 of the last block,
-// which then sees every block's partials
+// write this block's partials; returns true in every thread of the last block
 template <int NV>
 __device__ bool publish_partials(const double (&v)[NV], double* parts, int32_t* ticket) {
   __shared__ int last;
@@ -62,24 +61,30 @@ __device__ bool publish_partials(const double (&v)[NV], double* parts, int32_t* 
     last = (prior == (int)gridDim.x - 1);
   }
   __syncthreads();
-  return last && threadIdx.x == 0;
+  return last != 0;
 }
 
+// the last block combines all partials: thread t takes blocks t, t+256, ...
+// then a fixed shuffle tree; the result is valid in thread 0
 template <int NV>
 __device__ void gather_partials(double (&out)[NV], const double* parts, const bool (&is_max)[NV],
                                 int32_t* ticket) {
   __threadfence();
   const volatile double* vp = parts;
+  double v[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double s = is_max[i] ? -INFINITY : 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
       double x = vp[(int64_t)i * gridDim.x + b];
       s = is_max[i] ? fmax(s, x) : s + x;
     }
-    out[i] = s;
+    v[i] = s;
   }
-  *ticket = 0;
+  block_reduce<NV>(v, is_max);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = v[i];
+  if (threadIdx.x == 0) *ticket = 0;
 }
 
 __device__ __forceinline__ double half_plane_weight(int col, int N) {
@@ -189,9 +194,11 @@ __global__ void normal_spectrum_kernel(const R* __restrict__ Hhat, const R* __re
   if (publish_partials<1>(v, parts, ticket)) {
     double o[1];
     gather_partials<1>(o, parts, mx, ticket);
-    ctl->kmax = o[0];
-    ctl->theta = 2.0 * M * o[0];
-    ctl->inv_theta = o[0] > 0 ? 1.0 / (2.0 * M * o[0]) : 0.0;
+    if (threadIdx.x == 0) {
+      ctl->kmax = o[0];
+      ctl->theta = 2.0 * M * o[0];
+      ctl->inv_theta = o[0] > 0 ? 1.0 / (2.0 * M * o[0]) : 0.0;
+    }
   }
 }
 
@@ -241,7 +248,9 @@ __global__ void b_spectrum_kernel(const C2<R>* __restrict__ Ihat, const C2<R>* _
   if (publish_partials<1>(v, parts, ticket)) {
     double o[1];
     gather_partials<1>(o, parts, mx, ticket);
-    ctl->c0 = o[0] * inv;
+    if (threadIdx.x == 0) {
+      ctl->c0 = o[0] * inv;
+    }
   }
 }
 
@@ -253,61 +262,85 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
                                                                  Bs, parts, ctl, ticket);
 }
 
-// ------------------------------------------------------------- y = K x
-// Per iteration: <x, K x> and <b, x> of the current coefficients from the
-// spectrum X^ (Parseval), then X^ <- K^/N^2 X^ for the inverse FFT.  The last
-// block assembles F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it
-// to the trace and raises `done` on convergence or at the iteration budget.
+// ------------------------------------------------------------- FISTA spectrum
+// One pass of the minor cycle in the Fourier domain.  X^_k = rfft(W B_k) gives
+// <x_k, K x_k> and <b, x_k> (Parseval) for the objective of B_k; FISTA's
+// extrapolation alpha_k = B_k + t_k (B_k - B_{k-1}) is linear, so its gradient
+// image 2 (K W alpha_k - b) is the inverse transform of
+//   S^ = 2 (K^/N^2 ((1 + t_k) X^_k - t_k X^_{k-1}) - B^/N^2),
+// which this kernel writes over X^_{k-1} (no longer needed).  The last block
+// assembles F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it to
+// the trace and raises `done` on convergence or at the iteration budget.
 template <typename R>
-__global__ void spec_mul_kernel(C2<R>* __restrict__ spec, const R* __restrict__ Ks,
-                                const C2<R>* __restrict__ Bs, int N,
+__global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict__ Xprev,
+                                const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, int N,
                                 double* __restrict__ parts, FistaCtl* __restrict__ ctl,
                                 double* __restrict__ trace, int32_t* ticket) {
   if (ctl->done) return;
   const int nc = N / 2 + 1;
   const int64_t total = (int64_t)N * nc;
-  double v[2] = {0.0, 0.0};
-  const bool mx[2] = {false, false};
+  const int kit = ctl->k;
+  const R t = (R)(kit >= 2 ? (double)(kit - 1) / (double)(kit + 2) : 0.0);
+  const R a = (R)1 + t;
+  const float inv_nc = 1.0f / (float)nc;
+  // per-thread compensated sums in the working precision, combined in FP64
+  R s0 = 0, c0 = 0, s1 = 0, c1 = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const double w = half_plane_weight((int)(k % nc), N);
-    C2<R> X = spec[k];
+    // column of the half-plane (exact: the quotient stays 0.5/nc from an integer)
+    const int row = __float2int_rz(((float)k + 0.5f) * inv_nc);
+    const int col = (int)(k - (int64_t)row * nc);
+    const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
+    C2<R> X = Xk[k];
+    C2<R> P = Xprev[k];
     R kk = Ks[k];
     C2<R> B = Bs[k];
-    v[0] += w * (double)kk * ((double)X.x * X.x + (double)X.y * X.y);
-    v[1] += w * ((double)B.x * X.x + (double)B.y * X.y);
-    X.x *= kk;
-    X.y *= kk;
-    spec[k] = X;
+    R y0 = w * kk * (X.x * X.x + X.y * X.y) - c0;
+    R t0 = s0 + y0;
+    c0 = (t0 - s0) - y0;
+    s0 = t0;
+    R y1 = w * (B.x * X.x + B.y * X.y) - c1;
+    R t1 = s1 + y1;
+    c1 = (t1 - s1) - y1;
+    s1 = t1;
+    C2<R> S;
+    S.x = (R)2 * (kk * (a * X.x - t * P.x) - B.x);
+    S.y = (R)2 * (kk * (a * X.y - t * P.y) - B.y);
+    Xprev[k] = S;
   }
+  double v[2] = {(double)s0 - (double)c0, (double)s1 - (double)c1};
+  const bool mx[2] = {false, false};
   block_reduce<2>(v, mx);
   if (publish_partials<2>(v, parts, ticket)) {
     double o[2];
     gather_partials<2>(o, parts, mx, ticket);
-    const int k = ctl->k;
-    double F = o[0] - 2.0 * o[1] + ctl->c0 + ctl->lam * ctl->l1_cur;
-    ctl->xkx = o[0];
-    ctl->bx = o[1];
-    ctl->F_prev = ctl->F_cur;
-    ctl->F_cur = F;
-    trace[k] = F;
-    if (!isfinite(F)) {
-      ctl->error = 4;
-      ctl->done = 1;
-    } else if (k >= 1 && ctl->rel_tol > 0.0 && fabs(F - ctl->F_prev) <= ctl->rel_tol * fabs(F)) {
-      ctl->converged = 1;
-      ctl->done = 1;
-    } else if (k >= ctl->max_iters) {
-      ctl->done = 1;
+    if (threadIdx.x == 0) {
+      const int k = ctl->k;
+      double F = o[0] - 2.0 * o[1] + ctl->c0 + ctl->lam * ctl->l1_cur;
+      ctl->xkx = o[0];
+      ctl->bx = o[1];
+      ctl->F_prev = ctl->F_cur;
+      ctl->F_cur = F;
+      trace[k] = F;
+      if (!isfinite(F)) {
+        ctl->error = 4;
+        ctl->done = 1;
+      } else if (k >= 1 && ctl->rel_tol > 0.0 && fabs(F - ctl->F_prev) <= ctl->rel_tol * fabs(F)) {
+        ctl->converged = 1;
+        ctl->done = 1;
+      } else if (k >= ctl->max_iters) {
+        ctl->done = 1;
+      }
+      __threadfence();
     }
-    __threadfence();
   }
 }
 
 template <typename R>
-void launch_spec_mul(C2<R>* spec, const R* Ks, const C2<R>* Bs, int N, double* parts,
-                     FistaCtl* ctl, double* trace, int32_t* ticket, cudaStream_t s) {
-  spec_mul_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(spec, Ks, Bs, N, parts, ctl,
+void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
+                     double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
+                     cudaStream_t s) {
+  spec_mul_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(Xk, Xprev, Ks, Bs, N, parts, ctl,
                                                                trace, ticket);
 }
 
@@ -346,8 +379,10 @@ __global__ void image_norms_kernel(const R* __restrict__ img, int64_t n, double*
   if (publish_partials<2>(v, parts, ticket)) {
     double o[2];
     gather_partials<2>(o, parts, mx, ticket);
-    ctl->norm2 = o[0];
-    ctl->absmax = o[1];
+    if (threadIdx.x == 0) {
+      ctl->norm2 = o[0];
+      ctl->absmax = o[1];
+    }
   }
 }
 
@@ -383,9 +418,11 @@ __global__ void sigma2_kernel(const R* __restrict__ img, int N, double* parts, F
   if (publish_partials<1>(v, parts, ticket)) {
     double o[1];
     gather_partials<1>(o, parts, mx, ticket);
-    double s2 = o[0] / (double)total;
-    ctl->sigma2 = s2;
-    if (set_eta) ctl->eta2 = 1e-3 * s2;
+    if (threadIdx.x == 0) {
+      double s2 = o[0] / (double)total;
+      ctl->sigma2 = s2;
+      if (set_eta) ctl->eta2 = 1e-3 * s2;
+    }
   }
 }
 
@@ -432,7 +469,9 @@ __global__ void reduce_kernel(const R* __restrict__ x, const R* __restrict__ y, 
   if (publish_partials<1>(v, parts, ticket)) {
     double o[1];
     gather_partials<1>(o, parts, mx, ticket);
-    *out = o[0];
+    if (threadIdx.x == 0) {
+      *out = o[0];
+    }
   }
 }
 
@@ -492,7 +531,8 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                           FistaCtl*, int32_t*, cudaStream_t);                    \
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
-  template void launch_spec_mul<R>(C2<R>*, const R*, const C2<R>*, int, double*, FistaCtl*,      \
+  template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
+                                   FistaCtl*,                                                    \
                                    double*, int32_t*, cudaStream_t);                             \
   template void launch_spec_apply<R>(C2<R>*, const R*, int, cudaStream_t);                       \
   template void launch_image_norms<R>(const R*, int64_t, double*, FistaCtl*, int32_t*,           \

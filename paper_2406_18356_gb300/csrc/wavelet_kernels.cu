@@ -3,18 +3,26 @@
 // closed-form Lipschitz constant of Sect. 3.4 assumes orthogonal bases with
 // circular boundaries).
 //
-// One analysis level on an n x n block X is Y = T X T^T (rows filtered along x
-// first, then columns along y), T the periodized analysis matrix:
+// One analysis level on an n x n block X is Y = T X T^T, T the periodized
+// analysis matrix:
 //   a_i = sum_k h_k x[(2i + k) mod n],  d_i = sum_k g_k x[(2i + k) mod n],
 //   g_k = (-1)^k h_{L-1-k}.
 // Mallat layout: [0,h)^2 approximation, rows [0,h) x cols [h,n) low-y/high-x,
 // rows [h,n) x cols [0,h) high-y/low-x, [h,n)^2 high/high, h = n/2.
 // Synthesis is the transpose X = T^T Y T.
 //
+// Both directions are register-blocked: a thread slides over 8 outputs of one
+// row or column with its inputs held in registers, and each basis is a
+// separate template instance so the filter taps are compile-time constant-bank
+// operands.  Global traffic goes through shared memory in whole rows:
+// cp.async prefetches (the coefficient tiles of the FISTA state, the next
+// basis's subband windows) overlap the filtering, and results leave as
+// 16-byte vector stores.
+//
 // The analysis kernel of the minor cycle also does FISTA's step (Algorithm 1):
-// it builds the gradient image 2((1+t) y_k - t y_{k-1} - b) on the fly, and at
-// each coefficient forms alpha = B_k + t (B_k - B_{k-1}) and writes
-// B_{k+1} = soft(alpha - g / theta, lambda / theta), so the gradient
+// it builds the gradient image 2((1+t) y_k - t y_{k-1} - b) while staging its
+// input tile, and at each coefficient forms alpha = B_k + t (B_k - B_{k-1})
+// and writes B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient
 // coefficients never reach global memory.
 #include "common.cuh"
 
@@ -24,14 +32,11 @@ __constant__ double c_hd[kMaxBases][kMaxTaps];
 __constant__ double c_gd[kMaxBases][kMaxTaps];
 __constant__ float c_hf[kMaxBases][kMaxTaps];
 __constant__ float c_gf[kMaxBases][kMaxTaps];
-__constant__ int c_len[kMaxBases];
 
 void set_wavelet_filters(const double* h, const int* len, int nbases) {
   double hd[kMaxBases][kMaxTaps] = {}, gd[kMaxBases][kMaxTaps] = {};
   float hf[kMaxBases][kMaxTaps] = {}, gf[kMaxBases][kMaxTaps] = {};
-  int l[kMaxBases] = {};
   for (int m = 0; m < nbases; ++m) {
-    l[m] = len[m];
     for (int k = 0; k < len[m]; ++k) {
       hd[m][k] = h[m * kMaxTaps + k];
       gd[m][k] = ((k & 1) ? -1.0 : 1.0) * h[m * kMaxTaps + len[m] - 1 - k];
@@ -43,7 +48,6 @@ void set_wavelet_filters(const double* h, const int* len, int nbases) {
   cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
   cudaMemcpyToSymbol(c_hf, hf, sizeof(hf));
   cudaMemcpyToSymbol(c_gf, gf, sizeof(gf));
-  cudaMemcpyToSymbol(c_len, l, sizeof(l));
 }
 
 namespace {
@@ -54,18 +58,141 @@ template <> __device__ __forceinline__ float fg<float>(int m, int k) { return c_
 template <> __device__ __forceinline__ double fh<double>(int m, int k) { return c_hd[m][k]; }
 template <> __device__ __forceinline__ double fg<double>(int m, int k) { return c_gd[m][k]; }
 
-constexpr int kSynTile = 64;                      // synthesis output tile side
-constexpr int kSynCnt = kSynTile / 2 + kMaxTaps / 2 - 1;   // subband positions needed
-constexpr int kAnaTile = 32;                      // analysis output tile side (per subband)
-constexpr int kAnaCnt = 2 * kAnaTile + kMaxTaps - 2;       // input positions needed
 constexpr int kThreads = 256;
+constexpr int kP = 8;                             // outputs per thread and direction
+// analysis: output tile of 32 x 32 per subband; input tile 2*32 + 16 - 2
+constexpr int kAT = 32;
+constexpr int kAIn = 2 * kAT + kMaxTaps - 2;      // 78
+constexpr int kAInS = kAIn + 2;                   // 80: rows of the TMA box
+constexpr int kYS = kAIn + 1;                     // odd row stride of ylo / yhi
+constexpr int kGS = kAT + 4;                      // 16-byte aligned row stride of the outputs
+// region sizes rounded up to 4 elements so every region starts 16-byte aligned
+constexpr int kAnaInSz = (kAIn * kAInS + 3) / 4 * 4;
+constexpr int kAnaYSz = (kAT * kYS + 3) / 4 * 4;
+// synthesis: output tile 64 x 64; subband positions 64/2 + 16/2 - 1
+constexpr int kST = 64;
+constexpr int kSIn = kST / 2 + kMaxTaps / 2 - 1;  // 39
+constexpr int kSInS = kSIn + 2;                   // odd row stride (41)
+constexpr int kSubSz = 4 * kSIn * kSInS;          // one staged basis (four windows)
+
+// Tile sides: large levels use big tiles (less halo), small levels smaller
+// ones so that they still spread over the SMs.
+__host__ __device__ __forceinline__ int syn_tile(int n) {   // synthesis output side
+  return n >= 512 ? 64 : (n >= 256 ? 32 : (n >= 16 ? 16 : n));
+}
+__host__ __device__ __forceinline__ int ana_tile(int h) {   // analysis subband side
+  return h >= 256 ? 32 : (h >= 16 ? 16 : h);
+}
 
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
 }
+// periodic index for i in [-n, 2n)
+__device__ __forceinline__ int wrapc(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
 
-// deterministic block sum of a double (all threads of the block call it)
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)),
+               "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+      "l"((unsigned long long)map), "r"(x), "r"(y),
+      "r"((unsigned)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ unsigned saddr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// first 128-byte-aligned shared address at or after p
+__device__ __forceinline__ unsigned char* smem_align128(unsigned char* p) {
+  const unsigned pad = (128u - (saddr(p) & 127u)) & 127u;
+  return p + pad;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(saddr(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 8 decimated outputs from 2*8 + L - 2 inputs held in registers
+template <typename R, int MB>
+__device__ __forceinline__ void fir_down8(const R* x, R* lo, R* hi) {
+  constexpr int L = 2 * (MB + 1);
+#pragma unroll
+  for (int j = 0; j < kP; ++j) {
+    R a = 0, d = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      a += fh<R>(MB, k) * x[2 * j + k];
+      d += fg<R>(MB, k) * x[2 * j + k];
+    }
+    lo[j] = a;
+    hi[j] = d;
+  }
+}
+
+// 8 upsampled outputs r = 0..7 from L/2 + 3 low and high inputs:
+// out[r] = sum_{k = r mod 2, step 2} h_k lo[(r - k)/2 + L/2 - 1] + g_k hi[...]
+template <typename R, int MB>
+__device__ __forceinline__ void fir_up8(const R* lo, const R* hi, R* out) {
+  constexpr int L = 2 * (MB + 1);
+#pragma unroll
+  for (int r = 0; r < kP; ++r) {
+    R s = 0;
+#pragma unroll
+    for (int k = (r & 1); k < L; k += 2) {
+      const int i = (r - k) / 2 + L / 2 - 1;
+      s += fh<R>(MB, k) * lo[i] + fg<R>(MB, k) * hi[i];
+    }
+    out[r] = s;
+  }
+}
+
+// deterministic block sum (fixed shuffle tree); result valid in thread 0
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -73,115 +200,223 @@ __device__ double block_sum(double v, double* red) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double s = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-  return s;   // valid in thread 0
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
 }
+
+// per-thread compensated sum of |x| in the working precision (Kahan), so the
+// FP64 unit only sees one value per thread
+template <typename R> struct KSum {
+  R s = 0, c = 0;
+  __device__ __forceinline__ void add(R v) {
+    R y = v - c;
+    R t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename R> struct Vec;
+template <> struct Vec<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec<double> { using T = double2; static constexpr int N = 2; };
 }  // namespace
 
 // ------------------------------------------------------------------ synthesis
-// Level j (h = N >> j subband side, n = 2h output side).  Approximation
-// input: level J reads the top-left block of each coefficient plane, other
-// levels read the LL buffer written by the level above.  Level 1 sums the M
-// bases into x; other levels write LL_{j-1} per basis.
+// Level j: subbands of side h = N >> j -> output side n = 2h.  Level J reads
+// its approximation from the coefficient planes, lower levels from the LL
+// buffer written by the level above.  Level 1 sums the M bases into x, with
+// the next basis's windows prefetched by cp.async while the current one is
+// filtered.
 template <typename R>
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N, int h, int r0,
+                                            int c0, int cnt, R* sub) {
+  const int base_r = r0 / 2 - (kMaxTaps / 2 - 1), base_c = c0 / 2 - (kMaxTaps / 2 - 1);
+  // positions lie in [-7, h + cnt): one conditional wrap when h >= cnt, 7
+  const bool cheap = h >= cnt && h >= kMaxTaps / 2 - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int a = warp; a < cnt; a += kThreads / 32) {
+    const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
+    for (int b = lane; b < cnt; b += 32) {
+      const int ix = cheap ? wrapc(base_c + b, h) : wrap(base_c + b, h);
+      R* d = sub + a * kSInS + b;
+      cp_async<sizeof(R)>(d, llp ? llp + (int64_t)iy * h + ix : plane + (int64_t)iy * N + ix);
+      cp_async<sizeof(R)>(d + kSIn * kSInS, plane + (int64_t)iy * N + h + ix);
+      cp_async<sizeof(R)>(d + 2 * kSIn * kSInS, plane + (int64_t)(h + iy) * N + ix);
+      cp_async<sizeof(R)>(d + 3 * kSIn * kSInS, plane + (int64_t)(h + iy) * N + h + ix);
+    }
+  }
+}
+
+template <typename R, int MB>
+__device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, int c0,
+                                            const R* sub, R* zlo, R* zhi, R (&acc)[2][kP],
+                                            bool sum_bases, R* ll_out, int n) {
+  constexpr int L = 2 * (MB + 1);
+  constexpr int NI = L / 2 + 3;
+  const int tid = threadIdx.x;
+  // columns (y): units (b, pair, seg); pair 0 -> zlo from (approximation,
+  // high-y/low-x), pair 1 -> zhi from (low-y/high-x, high/high)
+  const int nseg = TS / kP > 0 ? TS / kP : 1;
+  const int units_a = cnt * 2 * nseg;
+  for (int u = tid; u < units_a; u += kThreads) {
+    int rest = u / cnt;
+    int b = u - rest * cnt;
+    int pair = rest & 1, seg = rest >> 1;
+    const R* s0 = sub + (pair ? 1 : 0) * kSIn * kSInS;
+    const R* s1 = sub + (pair ? 3 : 2) * kSIn * kSInS;
+    const int first = 4 * seg + 8 - L / 2;
+    R lo[NI], hi[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      lo[i] = s0[(first + i) * kSInS + b];
+      hi[i] = s1[(first + i) * kSInS + b];
+    }
+    R out[kP];
+    fir_up8<R, MB>(lo, hi, out);
+    R* z = pair ? zhi : zlo;
+#pragma unroll
+    for (int r = 0; r < kP; ++r) z[(kP * seg + r) * kSInS + b] = out[r];
+  }
+  __syncthreads();
+  // rows (x): units (r, seg), a warp takes consecutive rows of one segment
+  for (int q = 0; q < 2; ++q) {
+    int u = tid + q * kThreads;
+    int r = u & (TS - 1), seg = u >> lts;
+    if (seg >= nseg) continue;
+    const int first = 4 * seg + 8 - L / 2;
+    R lo[NI], hi[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      lo[i] = zlo[r * kSInS + first + i];
+      hi[i] = zhi[r * kSInS + first + i];
+    }
+    R out[kP];
+    fir_up8<R, MB>(lo, hi, out);
+    if (sum_bases) {
+#pragma unroll
+      for (int cc = 0; cc < kP; ++cc) acc[q][cc] += out[cc];
+    } else {
+      R* dst = ll_out + (int64_t)(r0 + r) * n + c0 + kP * seg;
+#pragma unroll
+      for (int cc = 0; cc < kP; ++cc)
+        if (kP * seg + cc < TS) dst[cc] = out[cc];
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2)
     synthesis_kernel(const R* const* __restrict__ coef3, const R* __restrict__ ll_in,
                      R* __restrict__ ll_out, R* __restrict__ x, int N, int j, int J, int M,
                      const FistaCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sA = reinterpret_cast<R*>(smem_raw);      // [cnt][cnt] approximation
-  R* sBx = sA + kSynCnt * kSynCnt;             // low-y / high-x
-  R* sBy = sBx + kSynCnt * kSynCnt;            // high-y / low-x
-  R* sD = sBy + kSynCnt * kSynCnt;             // high / high
-  R* zlo = sD + kSynCnt * kSynCnt;             // [TS][cnt]
-  R* zhi = zlo + kSynTile * kSynCnt;
-
+  R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][kSIn][kSInS]
+  R* zlo = subs + 2 * kSubSz;                         // [kST][kSInS]
+  R* zhi = zlo + kST * kSInS;
   const R* coef = coef3[ctl ? (ctl->k % 3) : 0];
   const int h = N >> j, n = 2 * h;
-  const int TS = n < kSynTile ? n : kSynTile;
+  const int TS = syn_tile(n);
+  const int lts = 31 - __clz(TS);
   const int cnt = TS / 2 + kMaxTaps / 2 - 1;
   const int tiles_x = n / TS;
   const int r0 = (blockIdx.x / tiles_x) * TS, c0 = (blockIdx.x % tiles_x) * TS;
-  const int i0 = r0 / 2 - (kMaxTaps / 2 - 1), j0 = c0 / 2 - (kMaxTaps / 2 - 1);
   const bool sum_bases = (j == 1);
   const int m_lo = sum_bases ? 0 : blockIdx.y, m_hi = sum_bases ? M : blockIdx.y + 1;
-  constexpr int kPer = (kSynTile * kSynTile) / kThreads;   // outputs per thread (16)
-  R acc[kPer];
+  R acc[2][kP];
 #pragma unroll
-  for (int q = 0; q < kPer; ++q) acc[q] = (R)0;
-
-  for (int m = m_lo; m < m_hi; ++m) {
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int cc = 0; cc < kP; ++cc) acc[q][cc] = (R)0;
+  auto stage = [&](int m) {
     const R* plane = coef + (int64_t)m * N * N;
     const R* llp = (j == J) ? nullptr : ll_in + (int64_t)m * h * h;
-    const int L = c_len[m];
-    for (int e = threadIdx.x; e < cnt * cnt; e += blockDim.x) {
-      int a = e / cnt, b = e - a * cnt;
-      int iy = wrap(i0 + a, h), ix = wrap(j0 + b, h);
-      sA[a * kSynCnt + b] = llp ? llp[(int64_t)iy * h + ix] : plane[(int64_t)iy * N + ix];
-      sBx[a * kSynCnt + b] = plane[(int64_t)iy * N + h + ix];
-      sBy[a * kSynCnt + b] = plane[(int64_t)(h + iy) * N + ix];
-      sD[a * kSynCnt + b] = plane[(int64_t)(h + iy) * N + h + ix];
+    synth_stage<R>(plane, llp, N, h, r0, c0, cnt, subs + (m & 1) * kSubSz);
+    cp_async_commit();
+  };
+  stage(m_lo);
+  for (int m = m_lo; m < m_hi; ++m) {
+    if (m + 1 < m_hi) {
+      stage(m + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
-    // columns (y): z[r][b] = sum_k h_k S[(r - k)/2] ...   (k = r mod 2, r mod 2 + 2, ...)
-    for (int e = threadIdx.x; e < TS * cnt; e += blockDim.x) {
-      int r = e / cnt, b = e - r * cnt;
-      R lo = 0, hi = 0;
-      for (int k = r & 1; k < L; k += 2) {
-        int a = ((r - k) >> 1) + (kMaxTaps / 2 - 1);
-        R hk = fh<R>(m, k), gk = fg<R>(m, k);
-        lo += hk * sA[a * kSynCnt + b] + gk * sBy[a * kSynCnt + b];
-        hi += hk * sBx[a * kSynCnt + b] + gk * sD[a * kSynCnt + b];
-      }
-      zlo[r * kSynCnt + b] = lo;
-      zhi[r * kSynCnt + b] = hi;
-    }
-    __syncthreads();
-    // rows (x)
-#pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      int e = threadIdx.x + q * kThreads;
-      if (e < TS * TS) {
-        int r = e / TS, c = e - r * TS;
-        R s = 0;
-        for (int k = c & 1; k < L; k += 2) {
-          int b = ((c - k) >> 1) + (kMaxTaps / 2 - 1);
-          s += fh<R>(m, k) * zlo[r * kSynCnt + b] + fg<R>(m, k) * zhi[r * kSynCnt + b];
-        }
-        if (sum_bases) {
-          acc[q] += s;
-        } else {
-          ll_out[(int64_t)m * n * n + (int64_t)(r0 + r) * n + c0 + c] = s;
-        }
-      }
+    const R* sub = subs + (m & 1) * kSubSz;
+    R* llo = sum_bases ? nullptr : ll_out + (int64_t)m * n * n;
+    switch (m) {
+#define MS_SYN(MBV)                                                                    \
+  case MBV:                                                                            \
+    synth_basis<R, MBV>(TS, lts, cnt, r0, c0, sub, zlo, zhi, acc, sum_bases, llo, n);  \
+    break;
+      MS_SYN(0) MS_SYN(1) MS_SYN(2) MS_SYN(3) MS_SYN(4) MS_SYN(5) MS_SYN(6) MS_SYN(7)
+#undef MS_SYN
     }
     __syncthreads();
   }
   if (sum_bases) {
+    const int nseg = TS / kP > 0 ? TS / kP : 1;
+    for (int q = 0; q < 2; ++q) {
+      int u = threadIdx.x + q * kThreads;
+      int r = u & (TS - 1), seg = u >> lts;
+      if (seg >= nseg) continue;
+      R* dst = x + (int64_t)(r0 + r) * N + c0 + kP * seg;
+      if (TS % kP == 0) {
+        using V = typename Vec<R>::T;
+        constexpr int NV = Vec<R>::N;
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      int e = threadIdx.x + q * kThreads;
-      if (e < TS * TS) {
-        int r = e / TS, c = e - r * TS;
-        x[(int64_t)(r0 + r) * N + c0 + c] = acc[q];
+        for (int cc = 0; cc < kP; cc += NV) {
+          V v;
+          if (NV == 4) {
+            reinterpret_cast<R*>(&v)[0] = acc[q][cc];
+            reinterpret_cast<R*>(&v)[1] = acc[q][cc + 1];
+            reinterpret_cast<R*>(&v)[2] = acc[q][cc + (NV > 2 ? 2 : 0)];
+            reinterpret_cast<R*>(&v)[3] = acc[q][cc + (NV > 2 ? 3 : 0)];
+          } else {
+            reinterpret_cast<R*>(&v)[0] = acc[q][cc];
+            reinterpret_cast<R*>(&v)[1] = acc[q][cc + 1];
+          }
+          *reinterpret_cast<V*>(dst + cc) = v;
+        }
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < kP; ++cc)
+          if (kP * seg + cc < TS) dst[cc] = acc[q][cc];
       }
     }
   }
 }
 
+namespace {
+size_t synthesis_smem_bytes(size_t rsz) {
+  return (size_t)(2 * kSubSz + 2 * kST * kSInS) * rsz;
+}
+// input tile (the four output subbands alias it), ylo / yhi, prefetched
+// B_k and B_{k-1} detail tiles
+size_t analysis_smem_bytes(size_t rsz) {
+  // + alignment slack, block-sum scratch, mbarrier and flags
+  return (size_t)(kAnaInSz + 2 * kAnaYSz + 2 * 3 * kAT * kAT) * rsz + 128 +
+         (kThreads / 32) * sizeof(double) + sizeof(uint64_t) + 2 * sizeof(int);
+}
+}  // namespace
+
 template <typename R>
 void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
                        const FistaCtl* ctl, cudaStream_t s, int only_level) {
-  const size_t smem = (size_t)(4 * kSynCnt * kSynCnt + 2 * kSynTile * kSynCnt) * sizeof(R);
+  const size_t smem = synthesis_smem_bytes(sizeof(R));
   auto k = synthesis_kernel<R>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
   for (int j = g.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
     int h = g.N >> j, n = 2 * h;
-    int TS = n < kSynTile ? n : kSynTile;
+    int TS = syn_tile(n);
     int tiles = (n / TS) * (n / TS);
     const R* ll_in = (j == g.J) ? nullptr : tmp + ((j + 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
@@ -191,162 +426,297 @@ void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
 }
 
 // ------------------------------------------------------------------ analysis
-// Level j on an n x n input (n = N >> (j-1)), output subbands of side h = n/2.
-// MODE 0: plain analysis (W^H x), input x (level 1) or LL_{j-1}; outputs to
-//         coefficient planes, approximation to the LL buffer for j < J.
-// MODE 1: FISTA step; level 1 input is the gradient image built from
-//         y_k, y_{k-1}, b; detail (and level-J approximation) outputs go
+// Filtering of one basis on the staged input tile: columns (y) into
+// ylo / yhi, then rows (x) into the four subbands gout[0..3] =
+// (approximation, low-y/high-x, high-y/low-x, high/high), 32 x kGS each.
+// TOe (a power of two, 8..32) outputs per subband side, lt = log2(TOe).
+template <typename R, int MB>
+__device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R* gout, int TOe,
+                                                int lt) {
+  constexpr int L = 2 * (MB + 1);
+  constexpr int NI = 2 * kP + L - 2;
+  const int tid = threadIdx.x;
+  const int nparts = TOe >> 3;
+  const int cols = 2 * TOe + L - 2;
+  for (int u = tid; u < nparts * cols; u += kThreads) {
+    int part = u / cols;
+    int col = u - part * cols;
+    R xin[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) xin[i] = sIn[(2 * kP * part + i) * kAInS + col];
+    R lo[kP], hi[kP];
+    fir_down8<R, MB>(xin, lo, hi);
+#pragma unroll
+    for (int r = 0; r < kP; ++r) {
+      ylo[(kP * part + r) * kYS + col] = lo[r];
+      yhi[(kP * part + r) * kYS + col] = hi[r];
+    }
+  }
+  __syncthreads();
+  // rows: unit = (row r, segment, source); a warp takes consecutive rows of
+  // one segment
+  const int lp = lt - 3;   // log2(nparts)
+  const int r = tid & (TOe - 1), seg = (tid >> lt) & (nparts - 1), src = tid >> (lt + lp);
+  const bool active = src < 2;
+  R xin[NI];
+  if (active) {
+    const R* yrow = (src ? yhi : ylo) + r * kYS + 2 * kP * seg;
+#pragma unroll
+    for (int i = 0; i < NI; ++i) xin[i] = yrow[i];
+  }
+  __syncthreads();   // the outputs overwrite the input tile
+  if (!active) return;
+  R lo[kP], hi[kP];
+  fir_down8<R, MB>(xin, lo, hi);
+  R* o_lo = gout + (src ? 2 : 0) * kAT * kGS + r * kGS + kP * seg;
+  R* o_hi = gout + (src ? 3 : 1) * kAT * kGS + r * kGS + kP * seg;
+  using V = typename Vec<R>::T;
+  constexpr int NV = Vec<R>::N;
+#pragma unroll
+  for (int q = 0; q < kP; q += NV) {
+    *reinterpret_cast<V*>(o_lo + q) = *reinterpret_cast<const V*>(lo + q);
+    *reinterpret_cast<V*>(o_hi + q) = *reinterpret_cast<const V*>(hi + q);
+  }
+}
+
+// Level j on an n x n input (n = N >> (j-1)), subbands of side h = n/2; one
+// block per (output tile, basis).
+// MODE 0: plain analysis (W^H x); input x (level 1) or LL_{j-1}.
+// MODE 1: FISTA step; level 1 input is the gradient image
+//         2 (K W alpha_k - b); detail (and level-J approximation) outputs go
 //         through the prox into B_{k+1}.
+// Level 1 stages its 78 x 78 input window by one TMA tensor copy when the
+// window does not wrap around the image (plain loads otherwise).
 template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads)
-    analysis_kernel(const R* __restrict__ x_in, const R* __restrict__ ll_in,
-                    R* __restrict__ ll_out, R* __restrict__ out_plain, ProxArgs pa,
-                    R* const* __restrict__ B3, R* const* __restrict__ Yh2, int N, int j,
-                    int J, int M, FistaCtl* __restrict__ ctl, double* __restrict__ l1_parts,
+__global__ void __launch_bounds__(kThreads, 2)
+    analysis_kernel(const __grid_constant__ CUtensorMap xmap, const R* __restrict__ x_in,
+                    int use_tma, const R* __restrict__ ll_in, R* __restrict__ ll_out,
+                    R* __restrict__ out_plain, R* const* __restrict__ B3, int N, int j, int J,
+                    int M, FistaCtl* __restrict__ ctl, double* __restrict__ l1_parts,
                     int part_base, int32_t* __restrict__ ticket, int total_parts) {
   if (MODE == 1 && ctl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kThreads / 32];
-  R* sIn = reinterpret_cast<R*>(smem_raw);     // [kAnaCnt][kAnaCnt]
-  R* slo = sIn + kAnaCnt * kAnaCnt;            // [kAnaCnt][TO]
-  R* shi = slo + kAnaCnt * kAnaTile;
+  // every shared array lives in the dynamic allocation, the tile at a
+  // 128-byte-aligned shared address (the TMA destination rule)
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = smem_align128(smem_raw);
+  R* sIn = reinterpret_cast<R*>(base);         // [kAIn][kAInS]; later gout [4][kAT][kGS]
+  R* ylo = sIn + kAnaInSz;                      // [kAT][kYS]
+  R* yhi = ylo + kAnaYSz;
+  R* sCur = yhi + kAnaYSz;                     // [3][kAT][kAT] details of B_k (16-B aligned)
+  R* sPrev = sCur + 3 * kAT * kAT;              // [3][kAT][kAT] details of B_{k-1}
+  double* red = reinterpret_cast<double*>(sPrev + 3 * kAT * kAT);   // [8]
+  uint64_t* bar_p = reinterpret_cast<uint64_t*>(red + kThreads / 32);
+  int* flags = reinterpret_cast<int*>(bar_p + 1);                   // [0] last, [1] use TMA
+  uint64_t& bar = *bar_p;
+  int& last = flags[0];
+  R* gout = sIn;
 
   const int n = N >> (j - 1), h = n / 2;
-  const int TO = h < kAnaTile ? h : kAnaTile;
-  const int cnt = 2 * TO + kMaxTaps - 2;
+  const int TO = ana_tile(h);
+  const int TOe = TO < kP ? kP : TO;             // outputs computed per side
+  const int lt = 31 - __clz(TOe);
+  const int lto = 31 - __clz(TO);
+  const int ext = 2 * TOe + kMaxTaps - 2;        // staged input window side
   const int tiles_x = h / TO;
   const int o0y = (blockIdx.x / tiles_x) * TO, o0x = (blockIdx.x % tiles_x) * TO;
   const int p0y = 2 * o0y, p0x = 2 * o0x;
-  const bool level1 = (j == 1);
-  const int m_lo = level1 ? 0 : blockIdx.y, m_hi = level1 ? M : blockIdx.y + 1;
+  const int m = blockIdx.y;
+  constexpr int NV = Vec<R>::N;
+  constexpr int LNV = NV == 4 ? 2 : 1;
+  using V = typename Vec<R>::T;
+  const bool vec = (TO % NV) == 0;
+  // cp.async prefetch of the FISTA state tiles: 16-byte rows and destination
+  const bool pre = vec && (saddr(sCur) & 15u) == 0;
+  const int64_t plane = (int64_t)m * N * N;
+  // coefficient-plane offset of (subband s = 1..3, row, col) of this tile
+  auto coef_off = [&](int s, int row, int col) -> int64_t {
+    int rr = (s >= 2 ? h : 0) + o0y + row;
+    int cc = (s & 1 ? h : 0) + o0x + col;
+    return plane + (int64_t)rr * N + cc;
+  };
+
+  // level 1: one TMA copy of the input window if it lies inside the image.
+  // The copy is issued only after checking its alignment rules (128-byte
+  // shared destination, 64-byte descriptor, 16-byte start column); a
+  // violation is recorded in ctl->error (MS_ERR_UNSUPPORTED) and plain loads
+  // are used.
+  bool tma = use_tma && j == 1 && TO == kAT && p0x + kAInS <= n && p0y + kAIn <= n;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      const bool aligned = (saddr(sIn) & 127u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(&xmap) & 63u) == 0 &&
+                           ((p0x * (int)sizeof(R)) & 15) == 0;
+      flags[1] = aligned ? 1 : 0;
+      if (aligned)
+        mbar_init(&bar, 1);
+      else if (ctl)
+        atomicExch(&ctl->error, 8);
+    }
+    __syncthreads();
+    tma = flags[1] != 0;
+    if (tma && threadIdx.x == 0) {
+      mbar_expect_tx(&bar, (unsigned)(kAIn * kAInS * sizeof(R)));
+      tma_load_2d(sIn, &xmap, p0x, p0y, &bar);
+    }
+  }
+
+  if (!tma) {
+    // stage the input window with periodic wrap, asynchronously (first
+    // cp.async group)
+    const R* src = (j == 1) ? x_in : ll_in + (int64_t)m * n * n;
+    const bool cheap = n >= ext;   // positions lie in [0, n + ext)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = warp; a < ext; a += kThreads / 32) {
+      const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
+      const R* row = src + (int64_t)py * n;
+      for (int b = lane; b < ext; b += 32) {
+        const int px = cheap ? wrapc(p0x + b, n) : wrap(p0x + b, n);
+        cp_async<sizeof(R)>(sIn + a * kAInS + b, row + px);
+      }
+    }
+    cp_async_commit();
+  }
 
   R t = 0, mu = 0, thr = 0;
   const R* cur = nullptr;
   const R* prev = nullptr;
   R* next = nullptr;
-  const R* ykm = nullptr;
-  R* ysave = nullptr;
+  const int lpr = lto - LNV;   // log2(vectors per tile row)
   if (MODE == 1) {
     const int k = ctl->k;
-    ykm = Yh2[k % 2];
-    ysave = Yh2[(k + 1) % 2];
-    double td = k >= 2 ? (double)(k - 1) / (double)(k + 2) : 0.0;
-    t = (R)td;
+    t = (R)(k >= 2 ? (double)(k - 1) / (double)(k + 2) : 0.0);
     mu = (R)ctl->inv_theta;
     thr = (R)(ctl->lam * ctl->inv_theta);
     cur = B3[k % 3];
     prev = B3[(k + 2) % 3];
     next = B3[(k + 1) % 3];
+    if (pre) {   // prefetch the detail tiles of B_k and B_{k-1} (next group)
+      const int per_sub = 1 << (lto + lpr);
+      for (int e = threadIdx.x; e < 3 * per_sub; e += kThreads) {
+        int s = 1 + (e >> (lto + lpr));
+        int rem = e & (per_sub - 1);
+        int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
+        int64_t g = coef_off(s, row, c4);
+        int so = ((s - 1) * kAT + row) * kAT + c4;
+        cp_async<16>(sCur + so, cur + g);
+        cp_async<16>(sPrev + so, prev + g);
+      }
+      cp_async_commit();
+    }
   }
-  double l1 = 0.0;
 
-  // level 1: the input is shared by all bases, load it once
-  auto load_input = [&](int m) {
-    for (int e = threadIdx.x; e < cnt * cnt; e += blockDim.x) {
-      int a = e / cnt, b = e - a * cnt;
-      int py = wrap(p0y + a, n), px = wrap(p0x + b, n);
-      int64_t p = (int64_t)py * n + px;
-      R v;
-      if (level1) {
-        if (MODE == 1) {
-          const R* yk = static_cast<const R*>(pa.ywork);
-          const R* bb = static_cast<const R*>(pa.b);
-          R yc = yk[p];
-          v = (R)2 * (((R)1 + t) * yc - t * ykm[p] - bb[p]);
-          if (a < 2 * TO && b < 2 * TO) ysave[p] = yc;
-        } else {
-          v = x_in[p];
-        }
-      } else {
-        v = ll_in[(int64_t)m * n * n + p];
-      }
-      sIn[a * kAnaCnt + b] = v;
+  if (tma) {
+    // wait (bounded) for the input window; on time-out flag the error and
+    // skip the update of this tile
+    if (!mbar_wait_bounded(&bar, 0)) {
+      if (threadIdx.x == 0 && ctl) atomicExch(&ctl->error, 5);
+      mbar_wait_bounded(&bar, 0);
+      if (MODE == 1 && pre) cp_async_wait<0>();
+      return;
     }
-  };
-  if (level1) {
-    load_input(0);
-    __syncthreads();
+  } else if (MODE == 1 && pre) {
+    cp_async_wait<1>();   // the window; the prefetch may still be in flight
+  } else {
+    cp_async_wait<0>();
   }
-  for (int m = m_lo; m < m_hi; ++m) {
-    if (!level1) {
-      load_input(m);
-      __syncthreads();
-    }
-    const int L = c_len[m];
-    const int rows = 2 * TO + L - 2;
-    // rows: filter along x
-    for (int e = threadIdx.x; e < rows * TO; e += blockDim.x) {
-      int a = e / TO, c = e - a * TO;
-      R lo = 0, hi = 0;
-      const R* src = sIn + a * kAnaCnt + 2 * c;
-      for (int k = 0; k < L; ++k) {
-        R v = src[k];
-        lo += fh<R>(m, k) * v;
-        hi += fg<R>(m, k) * v;
-      }
-      slo[a * kAnaTile + c] = lo;
-      shi[a * kAnaTile + c] = hi;
-    }
-    __syncthreads();
-    // columns: filter along y, four subbands
-    R* plane_out = (MODE == 1 ? next : out_plain) + (int64_t)m * N * N;
-    const R* plane_cur = MODE == 1 ? cur + (int64_t)m * N * N : nullptr;
-    const R* plane_prev = MODE == 1 ? prev + (int64_t)m * N * N : nullptr;
-    for (int e = threadIdx.x; e < TO * TO; e += blockDim.x) {
-      int r = e / TO, c = e - r * TO;
-      R ll = 0, lh = 0, hl = 0, hh = 0;
-      for (int k = 0; k < L; ++k) {
-        R hk = fh<R>(m, k), gk = fg<R>(m, k);
-        R vl = slo[(2 * r + k) * kAnaTile + c], vh = shi[(2 * r + k) * kAnaTile + c];
-        ll += hk * vl;
-        lh += hk * vh;
-        hl += gk * vl;
-        hh += gk * vh;
-      }
-      const int oy = o0y + r, ox = o0x + c;
-      // (value, row, col) of the three detail subbands, plus the approximation
-      R vals[4] = {lh, hl, hh, ll};
-      int rows_[4] = {oy, h + oy, h + oy, oy};
-      int cols_[4] = {h + ox, ox, h + ox, ox};
-      const int nsub = (j == J) ? 4 : 3;
-      for (int sb = 0; sb < nsub; ++sb) {
-        int64_t idx = (int64_t)rows_[sb] * N + cols_[sb];
-        if (MODE == 1) {
-          R bc = plane_cur[idx], bp = plane_prev[idx];
-          R alpha = bc + t * (bc - bp);
-          R z = alpha - mu * vals[sb];
-          R az = fabs(z) - thr;
-          R nb = az > (R)0 ? copysign(az, z) : (R)0;
-          plane_out[idx] = nb;
-          l1 += fabs((double)nb);
+  __syncthreads();
+  switch (m) {
+#define MS_ANA(MBV)                                          \
+  case MBV:                                                  \
+    analysis_filter<R, MBV>(sIn, ylo, yhi, gout, TOe, lt);   \
+    break;
+    MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
+#undef MS_ANA
+  }
+  if (MODE == 1 && pre) cp_async_wait<0>();
+  __syncthreads();
+
+  // write / update the tile's coefficients
+  KSum<R> l1;
+  auto prox = [&](R g, R bc, R bp) -> R {
+    R alpha = bc + t * (bc - bp);
+    R z = alpha - mu * g;
+    R az = fabs(z) - thr;
+    R nb = az > (R)0 ? copysign(az, z) : (R)0;
+    l1.add(fabs(nb));
+    return nb;
+  };
+  if (vec) {
+    const int s_first = (j == J) ? 0 : 1;
+    const int lsub = lto + lpr;   // log2(vectors per subband tile)
+    const int items = (4 - s_first) << lsub;
+    for (int e = threadIdx.x; e < items; e += kThreads) {
+      int s = s_first + (e >> lsub);
+      int rem = e & ((1 << lsub) - 1);
+      int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
+      V gv = *reinterpret_cast<const V*>(gout + (s * kAT + row) * kGS + c4);
+      int64_t off = s ? coef_off(s, row, c4) : plane + (int64_t)(o0y + row) * N + o0x + c4;
+      if (MODE == 0) {
+        *reinterpret_cast<V*>(out_plain + off) = gv;
+      } else {
+        V cv, pv;
+        if (s && pre) {
+          int so = ((s - 1) * kAT + row) * kAT + c4;
+          cv = *reinterpret_cast<const V*>(sCur + so);
+          pv = *reinterpret_cast<const V*>(sPrev + so);
         } else {
-          plane_out[idx] = vals[sb];
+          cv = *reinterpret_cast<const V*>(cur + off);
+          pv = *reinterpret_cast<const V*>(prev + off);
         }
+        V nv;
+        R* np = reinterpret_cast<R*>(&nv);
+        const R* gp = reinterpret_cast<const R*>(&gv);
+        const R* cp = reinterpret_cast<const R*>(&cv);
+        const R* pp = reinterpret_cast<const R*>(&pv);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) np[q] = prox(gp[q], cp[q], pp[q]);
+        *reinterpret_cast<V*>(next + off) = nv;
       }
-      if (j < J) ll_out[(int64_t)m * h * h + (int64_t)oy * h + ox] = ll;
     }
-    __syncthreads();
+    if (j < J) {   // approximation feeds the next level
+      for (int e = threadIdx.x; e < (1 << lsub); e += kThreads) {
+        int row = e >> lpr, c4 = (e & ((1 << lpr) - 1)) << LNV;
+        *reinterpret_cast<V*>(ll_out + (int64_t)m * h * h + (int64_t)(o0y + row) * h + o0x + c4) =
+            *reinterpret_cast<const V*>(gout + row * kGS + c4);
+      }
+    }
+  } else {   // tiny levels: scalar path
+    const int s_first = (j == J) ? 0 : 1;
+    for (int e = threadIdx.x; e < 4 * TO * TO; e += kThreads) {
+      int s = e / (TO * TO);
+      int row = (e / TO) % TO, col = e % TO;
+      R gval = gout[(s * kAT + row) * kGS + col];
+      if (s == 0 && j < J) {
+        ll_out[(int64_t)m * h * h + (int64_t)(o0y + row) * h + o0x + col] = gval;
+        continue;
+      }
+      if (s < s_first) continue;
+      int64_t off = s ? coef_off(s, row, col) : plane + (int64_t)(o0y + row) * N + o0x + col;
+      if (MODE == 0)
+        out_plain[off] = gval;
+      else
+        next[off] = prox(gval, cur[off], prev[off]);
+    }
   }
 
   if (MODE == 1) {
-    double bsum = block_sum(l1, red);
+    double bsum = block_sum(l1.value(), red);
     const int pid = part_base + blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
       l1_parts[pid] = bsum;
       __threadfence();
+      last = 0;
+      if (j == J) last = (atomicAdd(ticket, 1) == (int)(gridDim.x * gridDim.y) - 1);
     }
-    if (j == J) {
-      __shared__ int last;
+    __syncthreads();
+    if (j == J && last) {
+      // the last block of the last level sums every level's partials
+      __threadfence();
+      const volatile double* vp = l1_parts;
+      double s = 0.0;
+      for (int i = threadIdx.x; i < total_parts; i += kThreads) s += vp[i];
+      s = block_sum(s, red);
       if (threadIdx.x == 0) {
-        int prior = atomicAdd(ticket, 1);
-        last = (prior == (int)(gridDim.x * gridDim.y) - 1);
-      }
-      __syncthreads();
-      if (last && threadIdx.x == 0) {
-        __threadfence();
-        double s = 0;
-        const volatile double* vp = l1_parts;
-        for (int i = 0; i < total_parts; ++i) s += vp[i];
         ctl->l1_cur = s;
         ctl->k = ctl->k + 1;
         *ticket = 0;
@@ -356,19 +726,13 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
-namespace {
-size_t analysis_smem_bytes(size_t rsz) {
-  return (size_t)(kAnaCnt * kAnaCnt + 2 * kAnaCnt * kAnaTile) * rsz;
-}
-}  // namespace
-
 int analysis_prox_partials(WaveletGeom g) {
   int total = 0;
   for (int j = 1; j <= g.J; ++j) {
     int h = g.N >> j;
-    int TO = h < kAnaTile ? h : kAnaTile;
+    int TO = ana_tile(h);
     int tiles = (h / TO) * (h / TO);
-    total += tiles * (j == 1 ? 1 : g.M);
+    total += tiles * g.M;
   }
   return total;
 }
@@ -379,21 +743,27 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
   auto k = analysis_kernel<R, 0>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
-  ProxArgs none{};
+  CUtensorMap none{};
   for (int j = 1; j <= g.J; ++j) {
     int h = g.N >> j;
-    int TO = h < kAnaTile ? h : kAnaTile;
+    int TO = ana_tile(h);
     int tiles = (h / TO) * (h / TO);
     const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
-    dim3 grid(tiles, j == 1 ? 1 : g.M);
-    k<<<grid, kThreads, smem, s>>>(x, ll_in, ll_out, coef, none, nullptr, nullptr, g.N, j,
-                                   g.J, g.M, nullptr, nullptr, 0, nullptr, 0);
+    dim3 grid(tiles, g.M);
+    k<<<grid, kThreads, smem, s>>>(none, x, 0, ll_in, ll_out, coef, nullptr, g.N, j, g.J, g.M,
+                                   nullptr, nullptr, 0, nullptr, 0);
   }
 }
 
+// TMA box of the level-1 input window: {80 columns, 78 rows}
+void analysis_window_box(unsigned* cols, unsigned* rows) {
+  *cols = kAInS;
+  *rows = kAIn;
+}
+
 template <typename R>
-void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* tmp,
+void launch_analysis_prox3(const R* grad, const CUtensorMap* grad_map, R* const* B3_dev, R* tmp,
                            WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
                            cudaStream_t s, int only_level) {
   const size_t smem = analysis_smem_bytes(sizeof(R));
@@ -404,15 +774,16 @@ void launch_analysis_prox3(ProxArgs a, R* const* B3_dev, R* const* Yh2_dev, R* t
   int base = 0;
   for (int j = 1; j <= g.J; ++j) {
     int h = g.N >> j;
-    int TO = h < kAnaTile ? h : kAnaTile;
+    int TO = ana_tile(h);
     int tiles = (h / TO) * (h / TO);
     const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
-    dim3 grid(tiles, j == 1 ? 1 : g.M);
+    dim3 grid(tiles, g.M);
     if (only_level <= 0 || j == only_level)
-      k<<<grid, kThreads, smem, s>>>(nullptr, ll_in, ll_out, nullptr, a, B3_dev, Yh2_dev, g.N,
-                                     j, g.J, g.M, ctl, l1_parts, base, ticket, total);
-    base += tiles * (j == 1 ? 1 : g.M);
+      k<<<grid, kThreads, smem, s>>>(grad_map ? *grad_map : CUtensorMap{}, grad,
+                                     grad_map ? 1 : 0, ll_in, ll_out, nullptr, B3_dev, g.N, j,
+                                     g.J, g.M, ctl, l1_parts, base, ticket, total);
+    base += tiles * g.M;
   }
 }
 
@@ -423,11 +794,11 @@ template void launch_synthesis3<double>(const double* const*, double*, double*, 
 template void launch_analysis<float>(const float*, float*, float*, WaveletGeom, cudaStream_t);
 template void launch_analysis<double>(const double*, double*, double*, WaveletGeom,
                                       cudaStream_t);
-template void launch_analysis_prox3<float>(ProxArgs, float* const*, float* const*, float*,
-                                           WaveletGeom, FistaCtl*, int32_t*, double*,
+template void launch_analysis_prox3<float>(const float*, const CUtensorMap*, float* const*,
+                                           float*, WaveletGeom, FistaCtl*, int32_t*, double*,
                                            cudaStream_t, int);
-template void launch_analysis_prox3<double>(ProxArgs, double* const*, double* const*, double*,
-                                            WaveletGeom, FistaCtl*, int32_t*, double*,
+template void launch_analysis_prox3<double>(const double*, const CUtensorMap*, double* const*,
+                                            double*, WaveletGeom, FistaCtl*, int32_t*, double*,
                                             cudaStream_t, int);
 
 }  // namespace ms
