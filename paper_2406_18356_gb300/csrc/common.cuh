@@ -130,12 +130,32 @@ void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
                        const FistaCtl* ctl, cudaStream_t s, int only_level = 0);
 template <typename R>
 void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s);
-// gradient image 2 (K W alpha_k - b) of the current pass (inverse FFT output)
-// and an optional TMA descriptor of it (nullptr: plain loads)
+// Buffers of one minor-cycle pass, passed by value to the persistent pass
+// kernels: the coefficient ring B0..B2 (B[k % 3] is current), the gradient
+// image 2 (K W alpha_k - b) written by the inverse FFT, the synthesized image
+// x = W B_k, the approximation ping-pong, the control block and the per-block
+// partial sums of ||B_{k+1}||_1.
+template <typename R> struct FistaPass {
+  R* B0;
+  R* B1;
+  R* B2;
+  const R* grad;
+  R* x;
+  R* tmp;
+  FistaCtl* ctl;
+  double* l1_parts;
+  int N, J, M;
+};
+// The minor cycle's synthesis levels (J..1) and analysis + FISTA-update
+// levels (1..J), one launch per level.  only_level: 0 = all levels, j > 0 =
+// level j alone, -1 = all levels but level 1.  The analysis takes an optional
+// TMA descriptor of the gradient image (nullptr: plain loads) and writes one
+// l1 partial per block, analysis_prox_partials() in all.
 template <typename R>
-void launch_analysis_prox3(const R* grad, const CUtensorMap* grad_map, R* const* B3_dev, R* tmp,
-                           WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
-                           cudaStream_t s, int only_level = 0);
+cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int only_level = 0);
+template <typename R>
+cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_map,
+                                 cudaStream_t s, int only_level = 0);
 int analysis_prox_partials(WaveletGeom g);
 void analysis_window_box(unsigned* cols, unsigned* rows);
 
@@ -158,7 +178,7 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 template <typename R>
 void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
                      double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
-                     cudaStream_t s);
+                     const double* l1_parts, int n_l1, cudaStream_t s);
 template <typename R>
 void launch_spec_apply(C2<R>* spec, const R* Ks, int N, cudaStream_t s);
 template <typename R>

@@ -222,13 +222,14 @@ struct ms_plan {
   void *F[2] = {};   // FISTA spectra X^_k / X^_{k-1} (ping-pong by pass parity)
   void *spec = nullptr, *spec2 = nullptr, *Ks = nullptr, *Bs = nullptr;
   void *gl2 = nullptr, *gh2 = nullptr, *wtmp = nullptr;
-  void **B3_dev = nullptr, **api3_dev = nullptr;
+  void** api3_dev = nullptr;   // pointer table of the one-shot synthesis calls
   CUtensorMap grad_map{};   // TMA descriptor of the gradient image (ywork)
   bool have_grad_map = false;
   FistaCtl* ctl = nullptr;
   double* trace = nullptr;
   double* parts = nullptr;     // reduction partials (one reduction at a time)
   double* l1parts = nullptr;   // per-block |B_k+1| partials of the analysis levels
+  int n_l1 = 0;                // their number
   int32_t* tickets = nullptr;
   double* scal = nullptr;
   int32_t* err = nullptr;
@@ -519,19 +520,37 @@ template <typename R> void ensure_psf(ms_plan* p, PartDev& pd) {
 // One FISTA pass.  Pass i of a minor cycle has iteration index k = i, so the
 // two spectrum buffers alternate with the pass parity: F[k % 2] receives
 // X^_k, F[(k+1) % 2] holds X^_{k-1} and then the gradient spectrum.
+template <typename R> FistaPass<R> fista_pass_args(ms_plan* p) {
+  FistaPass<R> a;
+  a.B0 = (R*)p->B[0];
+  a.B1 = (R*)p->B[1];
+  a.B2 = (R*)p->B[2];
+  a.grad = (const R*)p->ywork;
+  a.x = (R*)p->xwork;
+  a.tmp = (R*)p->wtmp;
+  a.ctl = p->ctl;
+  a.l1_parts = p->l1parts;
+  a.N = p->N;
+  a.J = p->J;
+  a.M = p->M;
+  return a;
+}
+
+// One FISTA iteration (Algorithm 1): synthesis x = W B_k (levels J..1),
+// X^_k = F x, the spectral step (objective, iteration control, gradient
+// spectrum with the momentum folded in), the inverse FFT to the gradient
+// image, and analysis + prox into B_{k+1} (levels 1..J).
 template <typename R> void record_fista_pass(ms_plan* p, int parity) {
-  WaveletGeom g{p->N, p->J, p->M};
   C2<R>* Fk = (C2<R>*)p->F[parity];
   C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
-  const R* const* B3 = (const R* const*)p->B3_dev;
+  const FistaPass<R> a = fista_pass_args<R>(p);
   if (p->J > 1) {
     KSpan k(p, MS_K_SYNTH);
-    for (int j = p->J; j >= 2; --j)
-      launch_synthesis3<R>(B3, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps, j);
+    ck(launch_synthesis_pass<R>(a, p->ps, -1), "synthesis");
   }
   {
     KSpan k(p, MS_K_SYNTH_L1);
-    launch_synthesis3<R>(B3, (R*)p->xwork, (R*)p->wtmp, g, p->ctl, p->ps, 1);
+    ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
   }
   {
     KSpan k(p, MS_K_FFT_R2C);
@@ -540,24 +559,20 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
   {
     KSpan k(p, MS_K_SPEC_MUL);
     launch_spec_mul<R>(Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts, p->ctl,
-                       p->trace, p->tickets + 0, p->ps);
+                       p->trace, p->tickets + 0, p->l1parts, p->n_l1, p->ps);
   }
   {
     KSpan k(p, MS_K_FFT_C2R);
     fft_c2r<R>(p, Fo, p->ywork);   // gradient image 2 (K W alpha_k - b)
   }
-  const R* grad = (const R*)p->ywork;
   const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
   {
     KSpan k(p, MS_K_ANALYSIS_L1);
-    launch_analysis_prox3<R>(grad, gmap, (R* const*)p->B3_dev, (R*)p->wtmp, g, p->ctl,
-                             p->tickets + 1, p->l1parts, p->ps, 1);
+    ck(launch_analysis_pass<R>(a, gmap, p->ps, 1), "analysis");
   }
   if (p->J > 1) {
     KSpan k(p, MS_K_ANALYSIS);
-    for (int j = 2; j <= p->J; ++j)
-      launch_analysis_prox3<R>(grad, gmap, (R* const*)p->B3_dev, (R*)p->wtmp, g, p->ctl,
-                               p->tickets + 1, p->l1parts, p->ps, j);
+    ck(launch_analysis_pass<R>(a, gmap, p->ps, -1), "analysis");
   }
 }
 
@@ -624,7 +639,9 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     ck(cudaMemsetAsync(p->B[0], 0, sizeof(R) * ncoef, p->ps), "memset");
   ck(cudaMemcpyAsync(p->B[2], p->B[0], sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
      "copy");
-  launch_l1<R>((const R*)p->B[0], ncoef, p->parts, &p->ctl->l1_cur, p->tickets + 4, p->ps);
+  // ||B_0||_1 enters the first objective through the analysis partials
+  ck(cudaMemsetAsync(p->l1parts, 0, sizeof(double) * p->n_l1, p->ps), "memset");
+  launch_l1<R>((const R*)p->B[0], ncoef, p->parts, p->l1parts, p->tickets + 4, p->ps);
   // max_iters prox steps plus one pass that only evaluates F at the result
   const int passes = max_iters + 1;
   if (p->prof) {   // direct launches, each kernel family bracketed by events
@@ -952,11 +969,11 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->gl2 = p->alloc<R>(nspec, "filter");
   p->gh2 = p->alloc<R>(nspec, "filter");
   p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
-  p->B3_dev = p->alloc<void*>(3, "ptrs");
   p->api3_dev = p->alloc<void*>(3, "ptrs");
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
   p->parts = p->alloc<double>(4096, "partials");
-  p->l1parts = p->alloc<double>(analysis_prox_partials(WaveletGeom{N, p->J, p->M}), "partials");
+  p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
+  p->l1parts = p->alloc<double>(p->n_l1, "partials");
   p->tickets = p->alloc<int32_t>(16, "tickets");
   p->scal = p->alloc<double>(16, "scalars");
   p->err = p->alloc<int32_t>(1, "error flag");
@@ -964,7 +981,6 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   ck(cudaMemset(p->tickets, 0, sizeof(int32_t) * 16), "memset");
   ck(cudaMemset(p->err, 0, sizeof(int32_t)), "memset");
   ck(cudaMemset(p->ctl, 0, sizeof(FistaCtl)), "memset");
-  set_ptrs_kernel<<<1, 1, 0, s>>>(p->B3_dev, p->B[0], p->B[1], p->B[2]);
   // cuFFT plans
   cufftType tc = sizeof(R) == 8 ? CUFFT_Z2Z : CUFFT_C2C;
   cufftType tr = sizeof(R) == 8 ? CUFFT_D2Z : CUFFT_R2C;

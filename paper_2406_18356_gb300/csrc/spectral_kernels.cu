@@ -70,13 +70,14 @@ template <int NV>
 __device__ void gather_partials(double (&out)[NV], const double* parts, const bool (&is_max)[NV],
                                 int32_t* ticket) {
   __threadfence();
-  const volatile double* vp = parts;
+  // L2-coherent loads (the writers fenced before taking their ticket); they
+  // are independent, so a thread keeps all of them in flight at once
   double v[NV];
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double s = is_max[i] ? -INFINITY : 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      double x = vp[(int64_t)i * gridDim.x + b];
+      double x = __ldcg(parts + (int64_t)i * gridDim.x + b);
       s = is_max[i] ? fmax(s, x) : s + x;
     }
     v[i] = s;
@@ -269,17 +270,25 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // image 2 (K W alpha_k - b) is the inverse transform of
 //   S^ = 2 (K^/N^2 ((1 + t_k) X^_k - t_k X^_{k-1}) - B^/N^2),
 // which this kernel writes over X^_{k-1} (no longer needed).  The last block
-// assembles F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it to
-// the trace and raises `done` on convergence or at the iteration budget.
+// assembles F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1 (the l1 norm
+// from the n_l1 per-block partials the previous analysis pass left), appends
+// it to the trace, raises `done` on convergence or at the iteration budget,
+// and otherwise advances the iteration index to k + 1 for the analysis pass
+// that builds B_{k+1}.
 template <typename R>
 __global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict__ Xprev,
                                 const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, int N,
                                 double* __restrict__ parts, FistaCtl* __restrict__ ctl,
-                                double* __restrict__ trace, int32_t* ticket) {
+                                double* __restrict__ trace, int32_t* ticket,
+                                const double* __restrict__ l1_parts, int n_l1) {
   if (ctl->done) return;
   const int nc = N / 2 + 1;
   const int64_t total = (int64_t)N * nc;
   const int kit = ctl->k;
+  // fields the finalizing block needs, read while the loop runs
+  const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
+  const double rtol = ctl->rel_tol;
+  const int max_iters = ctl->max_iters;
   const R t = (R)(kit >= 2 ? (double)(kit - 1) / (double)(kit + 2) : 0.0);
   const R a = (R)1 + t;
   const float inv_nc = 1.0f / (float)nc;
@@ -314,22 +323,30 @@ __global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict_
   if (publish_partials<2>(v, parts, ticket)) {
     double o[2];
     gather_partials<2>(o, parts, mx, ticket);
+    double l1v[1] = {0.0};
+    for (int b = threadIdx.x; b < n_l1; b += blockDim.x) l1v[0] += __ldcg(l1_parts + b);
+    const bool mx1[1] = {false};
+    block_reduce<1>(l1v, mx1);
     if (threadIdx.x == 0) {
-      const int k = ctl->k;
-      double F = o[0] - 2.0 * o[1] + ctl->c0 + ctl->lam * ctl->l1_cur;
+      const int k = kit;
+      const double l1 = l1v[0];
+      double F = o[0] - 2.0 * o[1] + c0v + lam * l1;
+      ctl->l1_cur = l1;
       ctl->xkx = o[0];
       ctl->bx = o[1];
-      ctl->F_prev = ctl->F_cur;
+      ctl->F_prev = Fprev;
       ctl->F_cur = F;
       trace[k] = F;
       if (!isfinite(F)) {
         ctl->error = 4;
         ctl->done = 1;
-      } else if (k >= 1 && ctl->rel_tol > 0.0 && fabs(F - ctl->F_prev) <= ctl->rel_tol * fabs(F)) {
+      } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
         ctl->converged = 1;
         ctl->done = 1;
-      } else if (k >= ctl->max_iters) {
+      } else if (k >= max_iters) {
         ctl->done = 1;
+      } else {
+        ctl->k = k + 1;
       }
       __threadfence();
     }
@@ -339,9 +356,9 @@ __global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict_
 template <typename R>
 void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
                      double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
-                     cudaStream_t s) {
+                     const double* l1_parts, int n_l1, cudaStream_t s) {
   spec_mul_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(Xk, Xprev, Ks, Bs, N, parts, ctl,
-                                                               trace, ticket);
+                                                               trace, ticket, l1_parts, n_l1);
 }
 
 template <typename R>
@@ -533,7 +550,7 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
   template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
                                    FistaCtl*,                                                    \
-                                   double*, int32_t*, cudaStream_t);                             \
+                                   double*, int32_t*, const double*, int, cudaStream_t);         \
   template void launch_spec_apply<R>(C2<R>*, const R*, int, cudaStream_t);                       \
   template void launch_image_norms<R>(const R*, int64_t, double*, FistaCtl*, int32_t*,           \
                                       cudaStream_t);                                             \

@@ -24,6 +24,7 @@
 // input tile, and at each coefficient forms alpha = B_k + t (B_k - B_{k-1})
 // and writes B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient
 // coefficients never reach global memory.
+
 #include "common.cuh"
 
 namespace ms {
@@ -309,25 +310,25 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
   }
 }
 
+// One synthesis work item: output tile `tile` of level j for basis mb
+// (level 1: all bases summed into x).  Ends with a block barrier, so the
+// caller may reuse the shared buffers.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
-    synthesis_kernel(const R* const* __restrict__ coef3, const R* __restrict__ ll_in,
-                     R* __restrict__ ll_out, R* __restrict__ x, int N, int j, int J, int M,
-                     const FistaCtl* __restrict__ ctl) {
-  if (ctl && ctl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __restrict__ coef,
+                                           const R* __restrict__ ll_in, R* __restrict__ ll_out,
+                                           R* __restrict__ x, int N, int j, int J, int M,
+                                           int tile, int mb) {
   R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][kSIn][kSInS]
   R* zlo = subs + 2 * kSubSz;                         // [kST][kSInS]
   R* zhi = zlo + kST * kSInS;
-  const R* coef = coef3[ctl ? (ctl->k % 3) : 0];
   const int h = N >> j, n = 2 * h;
   const int TS = syn_tile(n);
   const int lts = 31 - __clz(TS);
   const int cnt = TS / 2 + kMaxTaps / 2 - 1;
   const int tiles_x = n / TS;
-  const int r0 = (blockIdx.x / tiles_x) * TS, c0 = (blockIdx.x % tiles_x) * TS;
+  const int r0 = (tile / tiles_x) * TS, c0 = (tile % tiles_x) * TS;
   const bool sum_bases = (j == 1);
-  const int m_lo = sum_bases ? 0 : blockIdx.y, m_hi = sum_bases ? M : blockIdx.y + 1;
+  const int m_lo = sum_bases ? 0 : mb, m_hi = sum_bases ? M : mb + 1;
   R acc[2][kP];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -373,15 +374,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
         for (int cc = 0; cc < kP; cc += NV) {
           V v;
-          if (NV == 4) {
-            reinterpret_cast<R*>(&v)[0] = acc[q][cc];
-            reinterpret_cast<R*>(&v)[1] = acc[q][cc + 1];
-            reinterpret_cast<R*>(&v)[2] = acc[q][cc + (NV > 2 ? 2 : 0)];
-            reinterpret_cast<R*>(&v)[3] = acc[q][cc + (NV > 2 ? 3 : 0)];
-          } else {
-            reinterpret_cast<R*>(&v)[0] = acc[q][cc];
-            reinterpret_cast<R*>(&v)[1] = acc[q][cc + 1];
-          }
+          R* vp = reinterpret_cast<R*>(&v);
+#pragma unroll
+          for (int e = 0; e < NV; ++e) vp[e] = acc[q][cc + e];
           *reinterpret_cast<V*>(dst + cc) = v;
         }
       } else {
@@ -391,6 +386,37 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
   }
+}
+
+// one level per launch (dictionary synthesis of the API and the power
+// iteration): blockIdx.x = tile, blockIdx.y = basis
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2)
+    synthesis_kernel(const R* const* __restrict__ coef3, const R* __restrict__ ll_in,
+                     R* __restrict__ ll_out, R* __restrict__ x, int N, int j, int J, int M,
+                     const FistaCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const R* coef = coef3[ctl ? (ctl->k % 3) : 0];
+  synth_item<R>(smem_raw, coef, ll_in, ll_out, x, N, j, J, M, blockIdx.x, blockIdx.y);
+}
+
+// Level j of the minor cycle's synthesis x = W B_k: blockIdx.x = output
+// tile, blockIdx.y = basis (level 1: one block per tile sums all bases).  The
+// buffers come by value and B_k is picked by k % 3, so no pointer table is
+// read before the first load.
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2)
+    synthesis_level_kernel(FistaPass<R> a, int j) {
+  const int done = a.ctl->done;
+  const int k = a.ctl->k;
+  if (done) return;   // uniform: `done` does not change during this kernel
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const R* coef = k % 3 == 0 ? a.B0 : (k % 3 == 1 ? a.B1 : a.B2);
+  const int64_t half = (int64_t)a.M * (a.N / 2) * (a.N / 2);
+  const R* ll_in = (j == a.J) ? nullptr : a.tmp + ((j + 1) & 1) * half;
+  R* ll_out = a.tmp + (j & 1) * half;
+  synth_item<R>(smem_raw, coef, ll_in, ll_out, a.x, a.N, j, a.J, a.M, blockIdx.x, blockIdx.y);
 }
 
 namespace {
@@ -479,37 +505,36 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   }
 }
 
-// Level j on an n x n input (n = N >> (j-1)), subbands of side h = n/2; one
-// block per (output tile, basis).
+// One analysis work item: subband tile `tile` (of side TO) of level j for
+// basis m.  n = N >> (j-1) is the input side, h = n/2 the subband side.
 // MODE 0: plain analysis (W^H x); input x (level 1) or LL_{j-1}.
-// MODE 1: FISTA step; level 1 input is the gradient image
-//         2 (K W alpha_k - b); detail (and level-J approximation) outputs go
-//         through the prox into B_{k+1}.
+// MODE 1: FISTA step; level 1 input is the gradient image 2 (K W alpha_k - b);
+//         detail (and level-J approximation) outputs go through the prox into
+//         B_{k+1} and |B_{k+1}| accumulates into l1.
 // Level 1 stages its 78 x 78 input window by one TMA tensor copy when the
-// window does not wrap around the image (plain loads otherwise).
-template <typename R, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
-    analysis_kernel(const __grid_constant__ CUtensorMap xmap, const R* __restrict__ x_in,
-                    int use_tma, const R* __restrict__ ll_in, R* __restrict__ ll_out,
-                    R* __restrict__ out_plain, R* const* __restrict__ B3, int N, int j, int J,
-                    int M, FistaCtl* __restrict__ ctl, double* __restrict__ l1_parts,
-                    int part_base, int32_t* __restrict__ ticket, int total_parts) {
-  if (MODE == 1 && ctl->done) return;
-  // every shared array lives in the dynamic allocation, the tile at a
-  // 128-byte-aligned shared address (the TMA destination rule)
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned char* base = smem_align128(smem_raw);
+// window lies inside the image (the caller has initialized the mbarrier and
+// tracks its phase); other windows are staged by cp.async with periodic wrap.
+// The basis MB is a template parameter, so a block's loop over tiles of one
+// basis keeps the filter taps as compile-time constant-bank operands.
+// Ends with a block barrier, so the caller may reuse the shared buffers.
+template <typename R, int MODE, int MB>
+__device__ __forceinline__ void analysis_item(unsigned char* base, const CUtensorMap* xmap,
+                                              bool use_tma, unsigned& phase, const R* x_in,
+                                              const R* ll_in, R* ll_out, R* out_plain,
+                                              const R* cur, const R* prev, R* next, R t, R mu,
+                                              R thr, int N, int j, int J, int tile,
+                                              FistaCtl* ctl, KSum<R>& l1) {
+  constexpr int m = MB;
   R* sIn = reinterpret_cast<R*>(base);         // [kAIn][kAInS]; later gout [4][kAT][kGS]
   R* ylo = sIn + kAnaInSz;                      // [kAT][kYS]
   R* yhi = ylo + kAnaYSz;
   R* sCur = yhi + kAnaYSz;                     // [3][kAT][kAT] details of B_k (16-B aligned)
   R* sPrev = sCur + 3 * kAT * kAT;              // [3][kAT][kAT] details of B_{k-1}
   double* red = reinterpret_cast<double*>(sPrev + 3 * kAT * kAT);   // [8]
-  uint64_t* bar_p = reinterpret_cast<uint64_t*>(red + kThreads / 32);
-  int* flags = reinterpret_cast<int*>(bar_p + 1);                   // [0] last, [1] use TMA
-  uint64_t& bar = *bar_p;
-  int& last = flags[0];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
+  int* flags = reinterpret_cast<int*>(bar + 1);                     // [1] TMA issued
   R* gout = sIn;
+  (void)red;
 
   const int n = N >> (j - 1), h = n / 2;
   const int TO = ana_tile(h);
@@ -518,15 +543,14 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lto = 31 - __clz(TO);
   const int ext = 2 * TOe + kMaxTaps - 2;        // staged input window side
   const int tiles_x = h / TO;
-  const int o0y = (blockIdx.x / tiles_x) * TO, o0x = (blockIdx.x % tiles_x) * TO;
+  const int o0y = (tile / tiles_x) * TO, o0x = (tile % tiles_x) * TO;
   const int p0y = 2 * o0y, p0x = 2 * o0x;
-  const int m = blockIdx.y;
   constexpr int NV = Vec<R>::N;
   constexpr int LNV = NV == 4 ? 2 : 1;
   using V = typename Vec<R>::T;
   const bool vec = (TO % NV) == 0;
   // cp.async prefetch of the FISTA state tiles: 16-byte rows and destination
-  const bool pre = vec && (saddr(sCur) & 15u) == 0;
+  const bool pre = MODE == 1 && vec && (saddr(sCur) & 15u) == 0;
   const int64_t plane = (int64_t)m * N * N;
   // coefficient-plane offset of (subband s = 1..3, row, col) of this tile
   auto coef_off = [&](int s, int row, int col) -> int64_t {
@@ -535,34 +559,33 @@ __global__ void __launch_bounds__(kThreads, 2)
     return plane + (int64_t)rr * N + cc;
   };
 
-  // level 1: one TMA copy of the input window if it lies inside the image.
-  // The copy is issued only after checking its alignment rules (128-byte
+  // The TMA copy is issued only after checking its alignment rules (128-byte
   // shared destination, 64-byte descriptor, 16-byte start column); a
-  // violation is recorded in ctl->error (MS_ERR_UNSUPPORTED) and plain loads
-  // are used.
+  // violation is recorded in ctl->error (MS_ERR_UNSUPPORTED) and the window
+  // is staged by cp.async instead.
   bool tma = use_tma && j == 1 && TO == kAT && p0x + kAInS <= n && p0y + kAIn <= n;
   if (tma) {
     if (threadIdx.x == 0) {
       const bool aligned = (saddr(sIn) & 127u) == 0 &&
-                           (reinterpret_cast<uintptr_t>(&xmap) & 63u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(xmap) & 63u) == 0 &&
                            ((p0x * (int)sizeof(R)) & 15) == 0;
       flags[1] = aligned ? 1 : 0;
-      if (aligned)
-        mbar_init(&bar, 1);
-      else if (ctl)
+      if (aligned) {
+        // order the block's earlier generic accesses of the window before
+        // the asynchronous copy overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (unsigned)(kAIn * kAInS * sizeof(R)));
+        tma_load_2d(sIn, xmap, p0x, p0y, bar);
+      } else if (ctl) {
         atomicExch(&ctl->error, 8);
+      }
     }
     __syncthreads();
     tma = flags[1] != 0;
-    if (tma && threadIdx.x == 0) {
-      mbar_expect_tx(&bar, (unsigned)(kAIn * kAInS * sizeof(R)));
-      tma_load_2d(sIn, &xmap, p0x, p0y, &bar);
-    }
   }
 
   if (!tma) {
-    // stage the input window with periodic wrap, asynchronously (first
-    // cp.async group)
+    // stage the input window with periodic wrap (first cp.async group)
     const R* src = (j == 1) ? x_in : ll_in + (int64_t)m * n * n;
     const bool cheap = n >= ext;   // positions lie in [0, n + ext)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -577,62 +600,45 @@ __global__ void __launch_bounds__(kThreads, 2)
     cp_async_commit();
   }
 
-  R t = 0, mu = 0, thr = 0;
-  const R* cur = nullptr;
-  const R* prev = nullptr;
-  R* next = nullptr;
   const int lpr = lto - LNV;   // log2(vectors per tile row)
-  if (MODE == 1) {
-    const int k = ctl->k;
-    t = (R)(k >= 2 ? (double)(k - 1) / (double)(k + 2) : 0.0);
-    mu = (R)ctl->inv_theta;
-    thr = (R)(ctl->lam * ctl->inv_theta);
-    cur = B3[k % 3];
-    prev = B3[(k + 2) % 3];
-    next = B3[(k + 1) % 3];
-    if (pre) {   // prefetch the detail tiles of B_k and B_{k-1} (next group)
-      const int per_sub = 1 << (lto + lpr);
-      for (int e = threadIdx.x; e < 3 * per_sub; e += kThreads) {
-        int s = 1 + (e >> (lto + lpr));
-        int rem = e & (per_sub - 1);
-        int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
-        int64_t g = coef_off(s, row, c4);
-        int so = ((s - 1) * kAT + row) * kAT + c4;
-        cp_async<16>(sCur + so, cur + g);
-        cp_async<16>(sPrev + so, prev + g);
-      }
-      cp_async_commit();
+  if (pre) {   // prefetch the detail tiles of B_k and B_{k-1} (next group)
+    const int per_sub = 1 << (lto + lpr);
+    for (int e = threadIdx.x; e < 3 * per_sub; e += kThreads) {
+      int s = 1 + (e >> (lto + lpr));
+      int rem = e & (per_sub - 1);
+      int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
+      int64_t g = coef_off(s, row, c4);
+      int so = ((s - 1) * kAT + row) * kAT + c4;
+      cp_async<16>(sCur + so, cur + g);
+      cp_async<16>(sPrev + so, prev + g);
     }
+    cp_async_commit();
   }
 
+  bool skip = false;
   if (tma) {
-    // wait (bounded) for the input window; on time-out flag the error and
-    // skip the update of this tile
-    if (!mbar_wait_bounded(&bar, 0)) {
-      if (threadIdx.x == 0 && ctl) atomicExch(&ctl->error, 5);
-      mbar_wait_bounded(&bar, 0);
-      if (MODE == 1 && pre) cp_async_wait<0>();
-      return;
-    }
-  } else if (MODE == 1 && pre) {
+    // bounded wait for the window; on time-out the tile is skipped (the
+    // error is recorded) but every barrier is still passed
+    const bool ok = mbar_wait_bounded(bar, phase);
+    phase ^= 1u;
+    skip = __syncthreads_or(!ok) != 0;
+    if (skip && threadIdx.x == 0 && ctl) atomicExch(&ctl->error, 5);
+  } else if (pre) {
     cp_async_wait<1>();   // the window; the prefetch may still be in flight
   } else {
     cp_async_wait<0>();
   }
   __syncthreads();
-  switch (m) {
-#define MS_ANA(MBV)                                          \
-  case MBV:                                                  \
-    analysis_filter<R, MBV>(sIn, ylo, yhi, gout, TOe, lt);   \
-    break;
-    MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
-#undef MS_ANA
+  if (!skip) {
+    analysis_filter<R, MB>(sIn, ylo, yhi, gout, TOe, lt);
+  } else {
+    __syncthreads();   // the filter's two barriers
+    __syncthreads();
   }
-  if (MODE == 1 && pre) cp_async_wait<0>();
+  if (pre) cp_async_wait<0>();
   __syncthreads();
 
   // write / update the tile's coefficients
-  KSum<R> l1;
   auto prox = [&](R g, R bc, R bp) -> R {
     R alpha = bc + t * (bc - bp);
     R z = alpha - mu * g;
@@ -641,7 +647,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     l1.add(fabs(nb));
     return nb;
   };
-  if (vec) {
+  if (skip) {
+    // nothing is written for a tile whose window never arrived
+  } else if (vec) {
     const int s_first = (j == J) ? 0 : 1;
     const int lsub = lto + lpr;   // log2(vectors per subband tile)
     const int items = (4 - s_first) << lsub;
@@ -698,32 +706,76 @@ __global__ void __launch_bounds__(kThreads, 2)
         next[off] = prox(gval, cur[off], prev[off]);
     }
   }
+  __syncthreads();
+}
 
-  if (MODE == 1) {
-    double bsum = block_sum(l1.value(), red);
-    const int pid = part_base + blockIdx.y * gridDim.x + blockIdx.x;
-    if (threadIdx.x == 0) {
-      l1_parts[pid] = bsum;
-      __threadfence();
-      last = 0;
-      if (j == J) last = (atomicAdd(ticket, 1) == (int)(gridDim.x * gridDim.y) - 1);
-    }
-    __syncthreads();
-    if (j == J && last) {
-      // the last block of the last level sums every level's partials
-      __threadfence();
-      const volatile double* vp = l1_parts;
-      double s = 0.0;
-      for (int i = threadIdx.x; i < total_parts; i += kThreads) s += vp[i];
-      s = block_sum(s, red);
-      if (threadIdx.x == 0) {
-        ctl->l1_cur = s;
-        ctl->k = ctl->k + 1;
-        *ticket = 0;
-        __threadfence();
-      }
-    }
+// one level per launch (dictionary analysis of the API and the power
+// iteration): blockIdx.x = tile, blockIdx.y = basis
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2)
+    analysis_kernel(const R* __restrict__ x_in, const R* __restrict__ ll_in,
+                    R* __restrict__ ll_out, R* __restrict__ out_plain, int N, int j, int J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_align128(smem_raw);
+  unsigned phase = 0;
+  KSum<R> l1;
+  switch (blockIdx.y) {
+#define MS_ANA(MBV)                                                                         \
+  case MBV:                                                                                 \
+    analysis_item<R, 0, MBV>(base, nullptr, false, phase, x_in, ll_in, ll_out, out_plain,   \
+                             nullptr, nullptr, nullptr, (R)0, (R)0, (R)0, N, j, J,          \
+                             blockIdx.x, nullptr, l1);                                      \
+    break;
+    MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
+#undef MS_ANA
   }
+}
+
+// Level j of the minor cycle's analysis + FISTA update: blockIdx.x = subband
+// tile, blockIdx.y = basis.  The spectral kernel of this pass has already
+// advanced ctl->k, so this builds B_{k+1} with k = ctl->k - 1.  Each block
+// leaves its sum of |B_{k+1}| over its tile in l1_parts[part_base + block];
+// the next spectral kernel adds them up (fixed order).
+template <typename R>
+__global__ void __launch_bounds__(kThreads, 2)
+    analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a, int j,
+                          int use_tma, int part_base) {
+  const int done = a.ctl->done;
+  const int kc = a.ctl->k;
+  const double lam = a.ctl->lam, inv_theta = a.ctl->inv_theta;
+  if (done) return;   // uniform: `done` does not change during this kernel
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_align128(smem_raw);
+  const int k = kc - 1;
+  const R t = (R)(k >= 2 ? (double)(k - 1) / (double)(k + 2) : 0.0);
+  const R mu = (R)inv_theta;
+  const R thr = (R)(lam * inv_theta);
+  const R* cur = k % 3 == 0 ? a.B0 : (k % 3 == 1 ? a.B1 : a.B2);
+  const R* prev = k % 3 == 0 ? a.B2 : (k % 3 == 1 ? a.B0 : a.B1);
+  R* next = k % 3 == 0 ? a.B1 : (k % 3 == 1 ? a.B2 : a.B0);
+  double* red = reinterpret_cast<double*>(reinterpret_cast<R*>(base) + kAnaInSz +
+                                          2 * kAnaYSz + 6 * kAT * kAT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
+  const bool tma = use_tma != 0 && j == 1;
+  if (tma && threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  unsigned phase = 0;
+  KSum<R> l1;
+  const int64_t half = (int64_t)a.M * (a.N / 2) * (a.N / 2);
+  const R* ll_in = (j == 1) ? nullptr : a.tmp + ((j - 1) & 1) * half;
+  R* ll_out = a.tmp + (j & 1) * half;
+  switch (blockIdx.y) {
+#define MS_ANA(MBV)                                                                             \
+  case MBV:                                                                                     \
+    analysis_item<R, 1, MBV>(base, &xmap, tma, phase, a.grad, ll_in, ll_out, nullptr, cur, prev, \
+                             next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1);             \
+    break;
+    MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
+#undef MS_ANA
+  }
+  double sum = block_sum(l1.value(), red);
+  if (threadIdx.x == 0)
+    a.l1_parts[part_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = sum;
 }
 
 int analysis_prox_partials(WaveletGeom g) {
@@ -740,10 +792,9 @@ int analysis_prox_partials(WaveletGeom g) {
 template <typename R>
 void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s) {
   const size_t smem = analysis_smem_bytes(sizeof(R));
-  auto k = analysis_kernel<R, 0>;
+  auto k = analysis_kernel<R>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
-  CUtensorMap none{};
   for (int j = 1; j <= g.J; ++j) {
     int h = g.N >> j;
     int TO = ana_tile(h);
@@ -751,8 +802,7 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
     const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
     dim3 grid(tiles, g.M);
-    k<<<grid, kThreads, smem, s>>>(none, x, 0, ll_in, ll_out, coef, nullptr, g.N, j, g.J, g.M,
-                                   nullptr, nullptr, 0, nullptr, 0);
+    k<<<grid, kThreads, smem, s>>>(x, ll_in, ll_out, coef, g.N, j, g.J);
   }
 }
 
@@ -763,28 +813,39 @@ void analysis_window_box(unsigned* cols, unsigned* rows) {
 }
 
 template <typename R>
-void launch_analysis_prox3(const R* grad, const CUtensorMap* grad_map, R* const* B3_dev, R* tmp,
-                           WaveletGeom g, FistaCtl* ctl, int32_t* ticket, double* l1_parts,
-                           cudaStream_t s, int only_level) {
-  const size_t smem = analysis_smem_bytes(sizeof(R));
-  auto k = analysis_kernel<R, 1>;
+cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int only_level) {
+  const size_t smem = synthesis_smem_bytes(sizeof(R));
+  auto k = synthesis_level_kernel<R>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
-  const int total = analysis_prox_partials(g);
-  int base = 0;
-  for (int j = 1; j <= g.J; ++j) {
-    int h = g.N >> j;
-    int TO = ana_tile(h);
-    int tiles = (h / TO) * (h / TO);
-    const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
-    R* ll_out = tmp + (j & 1) * half;
-    dim3 grid(tiles, g.M);
-    if (only_level <= 0 || j == only_level)
-      k<<<grid, kThreads, smem, s>>>(grad_map ? *grad_map : CUtensorMap{}, grad,
-                                     grad_map ? 1 : 0, ll_in, ll_out, nullptr, B3_dev, g.N, j,
-                                     g.J, g.M, ctl, l1_parts, base, ticket, total);
-    base += tiles * g.M;
+  for (int j = a.J; j >= 1; --j) {
+    if (only_level > 0 && j != only_level) continue;
+    if (only_level < 0 && j == 1) continue;
+    int n = 2 * (a.N >> j), TS = syn_tile(n);
+    dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M);
+    k<<<grid, kThreads, smem, s>>>(a, j);
   }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_map,
+                                 cudaStream_t s, int only_level) {
+  const size_t smem = analysis_smem_bytes(sizeof(R));
+  auto k = analysis_level_kernel<R>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const CUtensorMap m = grad_map ? *grad_map : CUtensorMap{};
+  int part_base = 0;
+  for (int j = 1; j <= a.J; ++j) {
+    const int h = a.N >> j, TO = ana_tile(h);
+    const int tiles = (h / TO) * (h / TO);
+    const bool run = only_level == 0 || j == only_level || (only_level < 0 && j > 1);
+    if (run) {
+      dim3 grid(tiles, a.M);
+      k<<<grid, kThreads, smem, s>>>(m, a, j, grad_map ? 1 : 0, part_base);
+    }
+    part_base += tiles * a.M;
+  }
+  return cudaGetLastError();
 }
 
 template void launch_synthesis3<float>(const float* const*, float*, float*, WaveletGeom,
@@ -794,11 +855,11 @@ template void launch_synthesis3<double>(const double* const*, double*, double*, 
 template void launch_analysis<float>(const float*, float*, float*, WaveletGeom, cudaStream_t);
 template void launch_analysis<double>(const double*, double*, double*, WaveletGeom,
                                       cudaStream_t);
-template void launch_analysis_prox3<float>(const float*, const CUtensorMap*, float* const*,
-                                           float*, WaveletGeom, FistaCtl*, int32_t*, double*,
-                                           cudaStream_t, int);
-template void launch_analysis_prox3<double>(const double*, const CUtensorMap*, double* const*,
-                                            double*, WaveletGeom, FistaCtl*, int32_t*, double*,
-                                            cudaStream_t, int);
+template cudaError_t launch_synthesis_pass<float>(const FistaPass<float>&, cudaStream_t, int);
+template cudaError_t launch_synthesis_pass<double>(const FistaPass<double>&, cudaStream_t, int);
+template cudaError_t launch_analysis_pass<float>(const FistaPass<float>&, const CUtensorMap*,
+                                                 cudaStream_t, int);
+template cudaError_t launch_analysis_pass<double>(const FistaPass<double>&, const CUtensorMap*,
+                                                  cudaStream_t, int);
 
 }  // namespace ms
