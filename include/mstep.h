@@ -156,6 +156,27 @@ ms_status ms_degrid(ms_plan* plan, int32_t part, int32_t chan, const void* image
 ms_status ms_grid(ms_plan* plan, int32_t part, int32_t chan, const void* vis,
                   void* dirty, void* stream);
 
+/* ms_grid with the gridding kernel's per-work-item tiles in a fixed 64 MiB
+ * array that is part of the library's device image, so this call obtains no
+ * device memory (no cudaMalloc / cudaFree, no allocating library).  It is
+ * meant for callers that may not allocate while they run: a process whose
+ * device memory is already held by another allocator, or a pipeline that
+ * cannot take the device-wide synchronization an allocation or free implies.
+ * The paper has no counterpart of this call; its result equals ms_grid's.
+ * Arguments, layouts and ownership are those of ms_grid; the plan's own
+ * buffers (created by ms_plan_create) are used as in ms_grid.
+ * Scratch need: (work items of the partition) x (tile + 6)^2 cells x 8 bytes
+ * (FP32) or 16 bytes (FP64, FP32 compensated); a larger need returns
+ * MS_ERR_ARG with the sizes in ms_last_error, and nothing is launched.
+ * Nothing in the array has to start at zero (each tile is written in full
+ * before it is read).  The array is shared by every plan and stream of a
+ * device: calls whose executions overlap on one device race on it, so the
+ * caller orders them (one stream, or events).  The first call on a device
+ * looks up the array's address (cudaGetSymbolAddress, which may load the
+ * module); make that first call before beginning any stream capture. */
+ms_status ms_grid_static_scratch(ms_plan* plan, int32_t part, int32_t chan, const void* vis,
+                                 void* dirty, void* stream);
+
 /* Major-cycle residual image i~ = F^H G^H (v - G F x) / sum(w) (Sect. 2) for
  * the rows of `part`: degrid, subtract, grid, in one call.  model: dev N*N
  * real; vis_obs: dev complex [nvis] original order; out: dev N*N real. */

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "ms_partition_rows": [_P, _I32, _I32, _P],
     "ms_degrid": [_P, _I32, _I32, _P, _P, _P, _P],
     "ms_grid": [_P, _I32, _I32, _P, _P, _P],
+    "ms_grid_static_scratch": [_P, _I32, _I32, _P, _P, _P],
     "ms_residual_image": [_P, _I32, _I32, _P, _P, _P, _P],
     "ms_psf": [_P, _I32, _I32, _P, _P],
     "ms_dictionary_synthesis": [_P, _P, _P, _P],
@@ -294,6 +295,15 @@ class Plan:
             self._need(out, self.real_dtype, self.npix ** 2, "dirty"), _stream_handle(stream)))
         return out
 
+    def grid_static_scratch(self, part: str, vis, out, chan: int = 0, stream=None):
+        """ms_grid with the gridding tiles in the library's fixed static
+        scratch; `out` (N*N real, on the device) is required, so the call
+        allocates nothing."""
+        self._check(self._lib.ms_grid_static_scratch(
+            self._h, PARTS[part], chan, self._need(vis, self.complex_dtype, self.nvis, "vis"),
+            self._need(out, self.real_dtype, self.npix ** 2, "dirty"), _stream_handle(stream)))
+        return out
+
     def residual_image(self, part: str, vis_obs, model, out=None, chan: int = 0, stream=None):
         out = self._image(out)
         n2 = self.npix ** 2
@@ -422,6 +432,10 @@ def ms_degrid(plan: Plan, part, image, vis_obs=None, out=None, chan=0, stream=No
 
 def ms_grid(plan: Plan, part, vis, out=None, chan=0, stream=None):
     return plan.grid(part, vis, out, chan, stream)
+
+
+def ms_grid_static_scratch(plan: Plan, part, vis, out, chan=0, stream=None):
+    return plan.grid_static_scratch(part, vis, out, chan, stream)
 
 
 def ms_residual_image(plan: Plan, part, vis_obs, model, out=None, chan=0, stream=None):

@@ -14,6 +14,7 @@
 #include <complex>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1145,6 +1146,57 @@ void destroy(ms_plan* p) {
 }  // namespace
 
 // ====================================================================== ABI
+// ------------------------------------------ gridding with static scratch
+// ms_grid_static_scratch grids with its per-work-item tiles in this
+// fixed-size array instead of the plan's scratch buffer.  The array belongs to
+// the library's device image: it is reserved when the module is loaded, so the
+// call itself obtains no device memory.  Every tile a call uses is written in
+// full by the gridding kernel before the fold reads it, so no part of the
+// array has to start at zero.  All plans and streams on a device share the
+// one array: calls whose executions overlap on a device race on it.
+constexpr size_t kStaticGridScratchBytes = (size_t)64 << 20;   // 64 MiB
+static __device__ __align__(256) unsigned char g_grid_scratch[kStaticGridScratchBytes];
+
+namespace {
+constexpr int kScratchDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kScratchDevices] = {};
+
+// device address of g_grid_scratch on the current device `dev`, looked up
+// once per device (the lookup may load the module)
+void* static_grid_scratch(int dev) {
+  arg(dev >= 0 && dev < kScratchDevices, "device ordinal beyond the static scratch table");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* a = nullptr;
+    ck(cudaGetSymbolAddress(&a, g_grid_scratch), "static scratch address");
+    g_scratch_addr[dev] = a;
+  }
+  return g_scratch_addr[dev];
+}
+
+// the gridding half of grid_sorted with a caller-given scratch base
+template <typename R>
+void grid_sorted_with(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image,
+                      void* scratch) {
+  if (p->prec == MS_FP32_KAHAN) {
+    launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
+                             (const float2*)vis_sorted, scratch, p->Ng, p->T, p->ntx, p->beta,
+                             p->ps);
+    launch_fold<float, true>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
+                             p->ps);
+  } else {
+    launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
+                          (const C2<R>*)vis_sorted, scratch, p->Ng, p->T, p->ntx, p->beta,
+                          p->ps);
+    launch_fold<R, false>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid, p->ps);
+  }
+  fft_c2c<R>(p, CUFFT_INVERSE);
+  const double sc = pd.n > 0 ? 1.0 / (double)pd.n : 0.0;
+  launch_crop<R>((const C2<R>*)p->grid, (const R*)p->psi, p->N, p->Ng, sc, (R*)image, p->ps);
+}
+}  // namespace
+
 extern "C" {
 
 ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
@@ -1406,6 +1458,31 @@ ms_status ms_get_kernel_profile(ms_plan* p, ms_kernel_profile* out, int32_t rese
         p->k_launch[i] = 0;
         p->k_ms[i] = 0;
       }
+  });
+}
+
+ms_status ms_grid_static_scratch(ms_plan* p, int32_t part, int32_t chan, const void* vis,
+                                 void* dirty, void* stream) {
+  return guarded(p, [&] {
+    PartDev& pd = part_of(p, part, chan);
+    arg(vis && dirty, "vis and dirty are required");
+    const size_t need =
+        (size_t)pd.nitems * p->S * p->S * grid_scratch_cell_bytes(p->prec);
+    if (need > kStaticGridScratchBytes) {
+      char buf[192];
+      std::snprintf(buf, sizeof(buf),
+                    "the partition needs %zu bytes of gridding scratch; the static scratch "
+                    "holds %zu bytes (use ms_grid)",
+                    need, kStaticGridScratchBytes);
+      throw Fail{MS_ERR_ARG, buf};
+    }
+    Scope sc(p, stream);
+    void* scratch = static_grid_scratch(p->dev);
+    DISPATCH(p, {
+      launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+      grid_sorted_with<R>(p, pd, p->vis_a, dirty, scratch);
+    });
+    sc.finish();
   });
 }
 
