@@ -50,12 +50,30 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-rows", type=int, default=1_000_000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_kahan", "fp64"])
+    ap.add_argument("--no-time-to-eps", action="store_true")
+    # smaller schedules for profiler captures only (a bench line needs the defaults)
+    ap.add_argument("--n-major", type=int, default=N_MAJOR)
+    ap.add_argument("--fista-iters", type=int, default=FISTA_ITERS)
+    ap.add_argument("--eps", type=float, default=1e-6)
     return ap.parse_args()
 
 
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def reduce_over_ranks(pg, device, maxes, sums):
+    """Max over ranks of `maxes` (times) and sum over ranks of `sums`
+    (work units); identity without a process group."""
+    if pg is None:
+        return list(maxes), list(sums)
+    import torch
+    t = torch.tensor([float(x) for x in maxes], device=device, dtype=torch.float64)
+    v = torch.tensor([float(x) for x in sums], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    pg.all_reduce(v, op=pg.ReduceOp.SUM)
+    return t.tolist(), v.tolist()
 
 
 # ---------------------------------------------------------------------------
@@ -124,10 +142,10 @@ def _cuda_ok():
         return False
 
 
-def workload_config(w, precision):
+def workload_config(w, precision, n_major=N_MAJOR, fista_iters=FISTA_ITERS):
     return {"workload": w.name, "npix": w.npix, "nvis": int(w.nvis),
             "partition": f"ell = 10% of max|uv| ({w.ell_px:.1f} px), delta = {w.delta_px} px",
-            "n_major": N_MAJOR, "fista_iters": FISTA_ITERS, "precision": precision,
+            "n_major": n_major, "fista_iters": fista_iters, "precision": precision,
             "lambda": "0.05 ||i~_n||_2 2^n (both steps)", "wavelets": "db1-db8, 4 levels",
             "es_kernel": "W=7, 2x oversampling",
             "l2": "flushed between timed steps (256 MiB write)"}
@@ -212,7 +230,7 @@ def main():
     w = synth.ska_mid_like(seed=rank, device=str(dev))
     plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
                    precision=args.precision, device=local_rank)
-    opts = ms.ReconOptions(n_major=N_MAJOR, fista_iters=FISTA_ITERS)
+    opts = ms.ReconOptions(n_major=args.n_major, fista_iters=args.fista_iters)
     vis = torch.from_numpy(w.vis[0]).to(dev).to(plan.complex_dtype)
     low = torch.empty((w.npix, w.npix), dtype=plan.real_dtype, device=dev)
     img = torch.empty_like(low)
@@ -252,19 +270,14 @@ def main():
     wall_ms = ev0.elapsed_time(ev1)
     grid_s = tot["grid_ms"] / 1000.0
     vis_total = tot["vis"]
-    if pg:
-        t = torch.tensor([wall_ms, grid_s], device=dev, dtype=torch.float64)
-        v = torch.tensor([float(vis_total)], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        pg.all_reduce(v, op=pg.ReduceOp.SUM)
-        wall_ms, grid_s = float(t[0]), float(t[1])
-        vis_total = float(v[0])
+    (wall_ms, grid_s), (vis_total,) = reduce_over_ranks(pg, dev, [wall_ms, grid_s],
+                                                        [vis_total])
     value = vis_total / grid_s
     ms_per_step = wall_ms / args.steps
     fista_rate = tot["iters"] / (tot["minor_ms"] / 1000.0)
     kernels_per_pass = 2 * 4 + 1
-    passes_per_cycle = math.ceil((FISTA_ITERS + 1) / 8) * 8
-    launches_per_step = 2 * (N_MAJOR * (passes_per_cycle * kernels_per_pass + 5 + 8) + 5 + 2)
+    passes_per_cycle = math.ceil((args.fista_iters + 1) / 8) * 8
+    launches_per_step = 2 * (args.n_major * (passes_per_cycle * kernels_per_pass + 5 + 8) + 5 + 2)
     gpu_launches = launches_per_step * args.steps
 
     # ---- per-kernel durations: the same steps with every kernel family
@@ -303,16 +316,15 @@ def main():
             torch.cuda.synchronize()
             e2e_vis += st.gridded_vis
         e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            v = torch.tensor([float(e2e_vis)], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            pg.all_reduce(v, op=pg.ReduceOp.SUM)
-            e2e_s, e2e_vis = float(t[0]), float(v[0])
+        (e2e_s,), (e2e_vis,) = reduce_over_ranks(pg, dev, [e2e_s], [e2e_vis])
         e2e = {"value": e2e_vis / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(hvis.numel() * hvis.element_size()),
                "d2h_bytes_per_step": int(2 * hlow.numel() * hlow.element_size()),
                "ms_per_step": 1000 * e2e_s / args.steps}
+
+    tte = None
+    if rank == 0 and not args.no_time_to_eps:
+        tte = time_to_eps(ms, w, dev, args.eps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -326,13 +338,14 @@ def main():
                 "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
-                "config": workload_config(w, args.precision),
+                "config": workload_config(w, args.precision, args.n_major, args.fista_iters),
                 "fista_iters_per_s": fista_rate,
                 "step_breakdown_ms": {"grid_degrid": tot["grid_ms"] / args.steps,
                                       "fft_grid": tot["fft_ms"] / args.steps,
                                       "minor_cycles": tot["minor_ms"] / args.steps},
                 "gpu_launches": gpu_launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "time_to_eps": tte,
                 "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}
                 if prof else None}
         print(json.dumps(line), flush=True)
@@ -340,6 +353,44 @@ def main():
     if pg:
         pg.barrier()
         pg.destroy_process_group()
+
+
+def time_to_eps(ms, w, dev, eps, max_iters=1000):
+    """Wall time of the two-step reconstruction of the same workload (one
+    major cycle per step) with every minor cycle run until
+    |F_k - F_k-1| <= eps |F_k| (at most max_iters iterations): the chosen
+    form (FP32 data, Kahan-compensated gridding, FP64 reductions) against the
+    plain FP64 form, both on this GPU, plus the relative L2 difference of
+    their final images."""
+    import torch
+    out, imgs = {}, {}
+    for form in ("fp32_kahan", "fp64"):
+        plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
+                       precision=form, device=dev.index or 0)
+        vis = torch.from_numpy(w.vis[0]).to(dev).to(plan.complex_dtype)
+        low = torch.empty((w.npix, w.npix), dtype=plan.real_dtype, device=dev)
+        img = torch.empty_like(low)
+        plan.reconstruct_two_step(vis, ms.ReconOptions(n_major=1, fista_iters=16),
+                                  low_out=low, out=img)   # warm: plans, graph
+        opts = ms.ReconOptions(n_major=1, fista_iters=max_iters, rel_tol=eps)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, st = plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
+        e1.record()
+        torch.cuda.synchronize()
+        out[form] = {"ms": e0.elapsed_time(e1), "fista_iterations": st.total_iterations,
+                     "last_cycle_converged": bool(st.converged),
+                     "objective": st.objective}
+        imgs[form] = img.double().cpu()
+        plan.close()
+        del vis
+    diff = float((imgs["fp32_kahan"] - imgs["fp64"]).norm() / imgs["fp64"].norm())
+    return {"eps": eps, "max_iters": max_iters,
+            "workload": f"{w.name}, two-step, 1 major cycle per step",
+            "chosen": out["fp32_kahan"], "plain": out["fp64"],
+            "speedup": out["fp64"]["ms"] / out["fp32_kahan"]["ms"],
+            "image_rel_l2_chosen_vs_plain": diff}
 
 
 def _peaks():
@@ -352,41 +403,78 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def family_bytes(fam, N, M, J, rsz, plan):
+    """Algorithmic HBM bytes of one span of a kernel family (what the
+    operation must move at least once; per minor-cycle pass for the FISTA
+    families, per call for the operator families).  rsz = bytes of a real.
+
+      analysis_l1  read the gradient image, read B_k and B_k-1 and write B_k+1
+                   over the level-1 detail subbands (3 M (N/2)^2 each), write
+                   the level-1 approximations: (1 + 9 M/4 + M/4) N^2 rsz.
+      analysis     levels 2..J: read LL_j-1, the prox traffic of the detail
+                   subbands, write LL_j (level J: the approximation goes
+                   through the prox as well).
+      synth_l1     read the level-1 details and approximations of all bases
+                   (M N^2 values), write x: (M + 1) N^2 rsz.
+      synth        levels J..2: read details + approximation input, write
+                   LL_j-1.
+      spec_mul     per half-plane element read X_k, X_k-1, B (complex) and
+                   K (real), write S (complex): 9 rsz.
+      degrid       per row: packed cell (4 B) + offsets (2 rsz) + observed and
+                   residual value (2 x 2 rsz), plus one read of the (2N)^2
+                   complex grid.
+    """
+    q = lambda j: (N >> j) ** 2   # subband side^2 at level j
+    if fam == "analysis_l1":
+        return (N * N + 9 * M * q(1) + M * q(1)) * rsz
+    if fam == "analysis":
+        b = 0
+        for j in range(2, J + 1):
+            b += M * q(j - 1) + 9 * M * q(j) + (M * q(j) if j < J else 3 * M * q(j))
+        return b * rsz
+    if fam == "synth_l1":
+        return (M * N * N + N * N) * rsz
+    if fam == "synth":
+        b = 0
+        for j in range(2, J + 1):
+            b += 3 * M * q(j) + M * q(j) + M * q(j - 1)
+        return b * rsz
+    if fam == "spec_mul":
+        return 9 * rsz * N * (N // 2 + 1)
+    if fam == "degrid":
+        counts = plan.partition_counts()
+        rows = (counts["L"] + counts["H"]) / 2.0
+        return rows * (4 + 2 * rsz + 4 * rsz) + 4 * N * N * 2 * rsz
+    return None
+
+
 def roofline_of(prof, w, plan, args):
     """Roofline of the dominant kernel family of the library (largest share of
-    kernel time).  Algorithmic bytes per launch (FP32, M = 8 bases, N^2 px):
-      analysis_l1: read the gradient image (4 B/px), read B_k, B_k-1
-                   and write B_k+1 over the detail subbands (3 x 8 x 3/4 x 4 B
-                   = 72 B/px), write the level-1 approximations (8 B/px):
-                   84 B/px.
-      synth_l1:    read 8 planes (32 B/px), write x (4 B/px): 36 B/px.
-      degrid:      per row 12 B geometry + 8 B observed + 8 B residual, plus
-                   one read of the (2N)^2 complex64 grid.
-      grid:        per row 12 B geometry + 8 B value, plus the work-item tiles
-                   written (one (T+6)^2 tile of float2 per item).
-    """
+    kernel time, cuFFT excluded): algorithmic bytes of one span (family_bytes)
+    over the span's average CUDA-event duration, against the measured HBM
+    copy bandwidth."""
     hbm, kind = _peaks()
     rsz = 4 if args.precision != "fp64" else 8
-    N = w.npix
+    N, M, J = w.npix, 8, 4
     mine = {k: v for k, v in prof.items() if not k.startswith("fft") and v[0] > 0}
     fam = max(mine, key=lambda k: mine[k][1])
     launches, total_ms = mine[fam]
     avg_s = total_ms / launches / 1000.0
-    per_px = {"analysis_l1": 84 * rsz / 4, "synth_l1": 36 * rsz / 4}
-    if fam in per_px:
-        bytes_ = per_px[fam] * N * N
-    elif fam == "degrid":
-        counts = plan.partition_counts()
-        rows = (counts["L"] + counts["H"]) / 2.0
-        bytes_ = rows * (4 + 2 * rsz + 4 * rsz) + 4 * N * N * 2 * rsz
-    else:
+    bytes_ = family_bytes(fam, N, M, J, rsz, plan)
+    others = {}
+    for k, (n, t) in mine.items():
+        b = family_bytes(k, N, M, J, rsz, plan)
+        if b:
+            others[k] = round(b / (t / n / 1000.0) / 1e9 / hbm, 4)
+    if bytes_ is None:
         return {"bound": "hbm", "kernel": fam, "achieved": None, "peak": hbm, "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_kind": kind}
+                "frac": None, "traffic": None, "peak_kind": kind, "frac_by_family": others}
     achieved = bytes_ / avg_s / 1e9
     return {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None, "peak_kind": f"{kind} (hbm_gbs burst copy)",
+            "frac": achieved / hbm, "traffic": None,
+            "peak_kind": f"{kind} (hbm_gbs burst copy)",
             "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
-            "launches": launches}
+            "launches": launches, "frac_by_family": others}
 
 
 if __name__ == "__main__":

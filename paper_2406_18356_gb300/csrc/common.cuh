@@ -28,6 +28,29 @@ struct WorkItem {
   int32_t pad;
 };
 
+// One job of the batched (multi-channel, multi-partition) operator: the
+// plan's sorted geometry of one (channel, partition) pair, the caller's
+// buffers of this call, and the job's place among all jobs' work items.
+template <typename R> struct BatchJob {
+  const WorkItem* items;      // the job's work items
+  const uint32_t* cell;       // sorted packed anchor cells
+  const C2<R>* frac;          // sorted sub-cell offsets
+  const int32_t* idx;         // sorted position -> original row
+  const int32_t* tile_items;  // first work item of each tile (and the total)
+  C2<R>* sorted_in;           // gridding input / observed values, plan order
+  C2<R>* sorted_out;          // degridding output, plan order
+  C2<R>* grid;                // the job's Ng^2 grid
+  const C2<R>* user_in;       // caller's visibilities (original order) or null
+  C2<R>* user_out;            // caller's output visibilities (original order)
+  const R* image_in;          // degridding: the caller's image
+  R* image_out;               // gridding: the caller's dirty image
+  int64_t n;                  // rows of the job
+  int64_t item_base;          // index of the job's first item over all jobs
+  int32_t nitems;
+  int32_t pad;
+  double inv_n;               // 1 / n (dirty-image scale; 0 when n = 0)
+};
+
 // Device-side state of a minor cycle, one per plan.  Read and written only by
 // the library's kernels; the host reads it back after a cycle.
 struct FistaCtl {
@@ -49,7 +72,52 @@ struct FistaCtl {
   double kmax;        // max K^ (unscaled)
   double norm2, absmax;  // reductions of the residual image
   double absmax_first;   // max |i~_1| of the current step
+  // per-iteration scalars, computed once by the spectral kernel's final
+  // block so no thread of the pass kernels spends FP64 work on them:
+  // momentum t_k = (k-1)/(k+2) (0 for k < 2) in slot k & 1, step mu = 1/theta
+  // and threshold lambda/theta, in FP32 and FP64
+  float tf[2];
+  float muf, thrf;
+  double td[2];
+  double mud, thrd;
 };
+
+template <typename R> __device__ __forceinline__ R ctl_t(const FistaCtl* c, int slot);
+template <> __device__ __forceinline__ float ctl_t<float>(const FistaCtl* c, int slot) {
+  return c->tf[slot];
+}
+template <> __device__ __forceinline__ double ctl_t<double>(const FistaCtl* c, int slot) {
+  return c->td[slot];
+}
+template <typename R> __device__ __forceinline__ R ctl_mu(const FistaCtl* c) {
+  return sizeof(R) == 8 ? (R)c->mud : (R)c->muf;
+}
+template <typename R> __device__ __forceinline__ R ctl_thr(const FistaCtl* c) {
+  return sizeof(R) == 8 ? (R)c->thrd : (R)c->thrf;
+}
+
+// Error-free sum of two working-precision numbers: a + b = s + e exactly.
+template <typename R> __device__ __forceinline__ void two_sum(R a, R b, R& s, R& e) {
+  s = a + b;
+  R bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of per-lane compensated values hi + lo in the working precision
+// (pairwise, each addition error-free up to the lo terms), converted to FP64
+// once per warp; the result is valid in lane 0.
+template <typename R> __device__ __forceinline__ double warp_sum_comp(R hi, R lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    R h2 = __shfl_down_sync(0xffffffffu, hi, o);
+    R l2 = __shfl_down_sync(0xffffffffu, lo, o);
+    R s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = lo + l2 + e;
+  }
+  return (double)hi + (double)lo;
+}
 
 // ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1 (z = 2 t / W).
 __device__ __forceinline__ float es_phi(float z, float beta) {
@@ -59,6 +127,33 @@ __device__ __forceinline__ float es_phi(float z, float beta) {
 __device__ __forceinline__ double es_phi(double z, double beta) {
   double s = fmax(1.0 - z * z, 0.0);
   return exp(beta * (sqrt(s) - 1.0));
+}
+
+// Programmatic dependent launch.  A kernel launched with
+// launch_pdl may be scheduled while the preceding kernel of its stream is
+// still running; it must call pdl_wait() before touching anything that
+// kernel writes (pdl_wait returns once the predecessor has completed and its
+// memory is visible; without the launch attribute it returns at once).
+// pdl_trigger() lets the next kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // -------------------------------------------------------------------------
@@ -117,6 +212,30 @@ template <typename R, bool KAHAN>
 void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int tile, int ntx,
                  C2<R>* grid, cudaStream_t s);
 size_t grid_scratch_cell_bytes(int precision);
+// batched form (all launches take the device job table)
+template <typename R>
+void launch_job_of(const BatchJob<R>* jobs, int njobs, int max_items, int32_t* job_of,
+                   cudaStream_t s);
+template <typename R>
+void launch_batch_gather(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s);
+template <typename R>
+void launch_batch_scatter(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s);
+template <typename R, bool KAHAN>
+void launch_grid_batch(const BatchJob<R>* jobs, const int32_t* job_of, int total_items,
+                       void* scratch, int tile, int ntx, double beta, cudaStream_t s);
+template <typename R, bool KAHAN>
+void launch_fold_batch(const BatchJob<R>* jobs, int njobs, const void* scratch, int Ng,
+                       int tile, int ntx, cudaStream_t s);
+template <typename R>
+void launch_degrid_batch(const CUtensorMap* tmap, const BatchJob<R>* jobs,
+                         const int32_t* job_of, int total_items, bool has_obs, int Ng, int tile,
+                         int ntx, double beta, int32_t* err, cudaStream_t s);
+template <typename R>
+void launch_pad_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
+                      cudaStream_t s);
+template <typename R>
+void launch_crop_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
+                       cudaStream_t s);
 
 // wavelet_kernels.cu
 void set_wavelet_filters(const double* h, const int* len, int nbases);   // host -> __constant__

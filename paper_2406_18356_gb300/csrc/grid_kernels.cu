@@ -137,13 +137,16 @@ void launch_crop(const C2<R>* grid, const R* psi, int npix, int Ng, double scale
 // footprints cover is staged in shared memory by one TMA tensor copy (plain
 // loads with periodic wrap for tiles on the grid's last row/column), then each
 // thread interpolates visibilities: V = sum_j phi_v[j] sum_i phi_u[i] G[..].
+// One degridding work item `it` of a grid whose TMA descriptor row of the
+// grid's first row is tma_y0 (0 for one grid; job * Ng for stacked grids).
 template <typename R, bool HAS_OBS>
-__global__ void __launch_bounds__(kThreads)
-    degrid_kernel(const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ grid,
-                  const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
-                  const C2<R>* __restrict__ frac, const C2<R>* __restrict__ obs,
-                  C2<R>* __restrict__ out, int Ng, int T, int ntx, R beta,
-                  int32_t* __restrict__ err) {
+__device__ __forceinline__ void degrid_item(const CUtensorMap* tmap, int tma_y0,
+                                            const C2<R>* __restrict__ grid, const WorkItem it,
+                                            const uint32_t* __restrict__ cell,
+                                            const C2<R>* __restrict__ frac,
+                                            const C2<R>* __restrict__ obs,
+                                            C2<R>* __restrict__ out, int Ng, int T, int ntx,
+                                            R beta, int32_t* __restrict__ err) {
   // the tile sits at a 128-byte-aligned shared address (TMA destination rule),
   // the mbarrier and a flag after it, all in the dynamic allocation
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -152,7 +155,6 @@ __global__ void __launch_bounds__(kThreads)
   const int S = T + kW - 1;
   uint64_t& bar = *reinterpret_cast<uint64_t*>(tile + S * S);
   int& use_tma = *reinterpret_cast<int*>(&bar + 1);
-  const WorkItem it = items[blockIdx.x];
   const int tx = it.tile % ntx, ty = it.tile / ntx;
   const int ox = tx * T, oy = ty * T;
   bool edge = (ox + S > Ng) || (oy + S > Ng);
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kThreads)
     if (threadIdx.x == 0) {
       // alignment rules of the copy, checked before it is issued
       const bool aligned = (smem_addr(tile) & 127u) == 0 &&
-                           (reinterpret_cast<uintptr_t>(&tmap) & 63u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(tmap) & 63u) == 0 &&
                            ((2 * ox * (int)sizeof(R)) & 15) == 0;
       use_tma = aligned ? 1 : 0;
       if (aligned) {
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kThreads)
   if (!edge) {
     if (threadIdx.x == 0) {
       mbar_expect_tx(&bar, (unsigned)(S * S * sizeof(C2<R>)));
-      tma_load_2d(tile, &tmap, 2 * ox, oy, &bar);
+      tma_load_2d(tile, tmap, 2 * ox, tma_y0 + oy, &bar);
     }
     ok = mbar_wait_bounded(&bar, 0);
     if (!ok) {
@@ -231,6 +233,32 @@ __global__ void __launch_bounds__(kThreads)
   }
 }
 
+
+template <typename R, bool HAS_OBS>
+__global__ void __launch_bounds__(kThreads)
+    degrid_kernel(const __grid_constant__ CUtensorMap tmap, const C2<R>* __restrict__ grid,
+                  const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
+                  const C2<R>* __restrict__ frac, const C2<R>* __restrict__ obs,
+                  C2<R>* __restrict__ out, int Ng, int T, int ntx, R beta,
+                  int32_t* __restrict__ err) {
+  degrid_item<R, HAS_OBS>(&tmap, 0, grid, items[blockIdx.x], cell, frac, obs, out, Ng, T, ntx,
+                          beta, err);
+}
+
+// Stacked form: one block per work item of all jobs; job_of[item] names the
+// job, whose grid is row block job * Ng of the stacked TMA descriptor.
+template <typename R, bool HAS_OBS>
+__global__ void __launch_bounds__(kThreads)
+    degrid_batch_kernel(const __grid_constant__ CUtensorMap tmap,
+                        const BatchJob<R>* __restrict__ jobs, const int32_t* __restrict__ job_of,
+                        int Ng, int T, int ntx, R beta, int32_t* __restrict__ err) {
+  const int j = job_of[blockIdx.x];
+  const BatchJob<R> jb = jobs[j];
+  const WorkItem it = jb.items[blockIdx.x - jb.item_base];
+  degrid_item<R, HAS_OBS>(&tmap, j * Ng, jb.grid, it, jb.cell, jb.frac, jb.sorted_in,
+                          jb.sorted_out, Ng, T, ntx, beta, err);
+}
+
 template <typename R>
 void launch_degrid(const CUtensorMap* tmap, const C2<R>* grid, const WorkItem* items,
                    int nitems, const uint32_t* cell, const C2<R>* frac, const C2<R>* obs,
@@ -272,12 +300,13 @@ template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_warps()
 // sub-tile, so no two warps ever touch the same word; the compensated form
 // keeps a Kahan correction word per cell component.  At the end the warps'
 // tiles are summed in a fixed order into the item's scratch tile.
+// One gridding work item `it`; its tile goes to scratch tile `scratch_tile`.
 template <typename R, bool KAHAN>
-__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
-    grid_kernel(const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
-                const C2<R>* __restrict__ frac, const C2<R>* __restrict__ vis,
-                typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int Ng, int T, int ntx,
-                R beta) {
+__device__ __forceinline__ void grid_item(const WorkItem it, const uint32_t* __restrict__ cell,
+                                          const C2<R>* __restrict__ frac,
+                                          const C2<R>* __restrict__ vis,
+                                          typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
+                                          int64_t scratch_tile, int T, int ntx, R beta) {
   using Acc = typename ScratchOf<R, KAHAN>::T;
   constexpr int NW = grid_warps<R, KAHAN>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -290,7 +319,6 @@ __global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
   int* stage_c = reinterpret_cast<int*>(stage_v + NW * 32);                  // [NW][32]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const WorkItem it = items[blockIdx.x];
   const int ox = (it.tile % ntx) * T, oy = (it.tile / ntx) * T;
 
   for (int c = threadIdx.x; c < NW * cells; c += blockDim.x) {
@@ -375,7 +403,7 @@ __global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
     }
   }
   __syncthreads();
-  Acc* dst = scratch + (int64_t)blockIdx.x * cells;
+  Acc* dst = scratch + scratch_tile * cells;
   for (int c = threadIdx.x; c < cells; c += blockDim.x) {
     Acc s;
     s.x = 0;
@@ -396,6 +424,28 @@ __global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
   }
 }
 
+
+template <typename R, bool KAHAN>
+__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
+    grid_kernel(const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
+                const C2<R>* __restrict__ frac, const C2<R>* __restrict__ vis,
+                typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int Ng, int T, int ntx,
+                R beta) {
+  grid_item<R, KAHAN>(items[blockIdx.x], cell, frac, vis, scratch, blockIdx.x, T, ntx, beta);
+}
+
+// Stacked form: one block per work item of all jobs (scratch tile = the
+// item's index over all jobs).
+template <typename R, bool KAHAN>
+__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
+    grid_batch_kernel(const BatchJob<R>* __restrict__ jobs, const int32_t* __restrict__ job_of,
+                      typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int T, int ntx,
+                      R beta) {
+  const BatchJob<R> jb = jobs[job_of[blockIdx.x]];
+  grid_item<R, KAHAN>(jb.items[blockIdx.x - jb.item_base], jb.cell, jb.frac, jb.sorted_in,
+                      scratch, blockIdx.x, T, ntx, beta);
+}
+
 template <typename R, bool KAHAN>
 void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const C2<R>* frac,
                  const C2<R>* vis, void* scratch, int Ng, int tile, int ntx, double beta,
@@ -412,14 +462,10 @@ void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const 
                                  Ng, tile, ntx, (R)beta);
 }
 
-// Every grid cell sums, in a fixed order, the scratch tiles of all work items
-// of the (up to four) tiles whose footprint region covers it: its own tile
-// and, within W - 1 cells of a tile edge, the tiles to the left and above
-// (periodically).  Each cell is written once, so the grid needs no clearing.
 template <typename R, bool KAHAN>
-__global__ void fold_kernel(const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
-                            const int32_t* __restrict__ tile_items, int Ng, int T, int ntx,
-                            C2<R>* __restrict__ grid) {
+__device__ __forceinline__ void fold_cells(const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
+                                           const int32_t* __restrict__ tile_items, int Ng, int T,
+                                           int ntx, C2<R>* __restrict__ grid) {
   using Acc = typename ScratchOf<R, KAHAN>::T;
   const int S = T + kW - 1;
   const int cells = S * S;
@@ -457,6 +503,28 @@ __global__ void fold_kernel(const typename ScratchOf<R, KAHAN>::T* __restrict__ 
   }
 }
 
+// Every grid cell sums, in a fixed order, the scratch tiles of all work items
+// of the (up to four) tiles whose footprint region covers it: its own tile
+// and, within W - 1 cells of a tile edge, the tiles to the left and above
+// (periodically).  Each cell is written once, so the grid needs no clearing.
+template <typename R, bool KAHAN>
+__global__ void fold_kernel(const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
+                            const int32_t* __restrict__ tile_items, int Ng, int T, int ntx,
+                            C2<R>* __restrict__ grid) {
+  fold_cells<R, KAHAN>(scratch, tile_items, Ng, T, ntx, grid);
+}
+
+// stacked form: blockIdx.y = job (its tiles start at its first item)
+template <typename R, bool KAHAN>
+__global__ void fold_batch_kernel(const BatchJob<R>* __restrict__ jobs,
+                                  const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
+                                  int Ng, int T, int ntx) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  const int S = T + kW - 1;
+  fold_cells<R, KAHAN>(scratch + jb.item_base * (int64_t)(S * S), jb.tile_items, Ng, T, ntx,
+                       jb.grid);
+}
+
 template <typename R, bool KAHAN>
 void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int tile, int ntx,
                  C2<R>* grid, cudaStream_t s) {
@@ -469,6 +537,176 @@ void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int til
 }
 
 // ---------------------------------------------------------------- instances
+// ------------------------------------------------------------ batched form
+// Every job's rows / cells are walked by blockIdx.x, x-stride; blockIdx.y = job.
+template <typename R>
+__global__ void job_of_kernel(const BatchJob<R>* __restrict__ jobs, int32_t* __restrict__ job_of) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < jb.nitems; i += gridDim.x * blockDim.x)
+    job_of[jb.item_base + i] = (int32_t)blockIdx.y;
+}
+
+template <typename R>
+__global__ void batch_gather_kernel(const BatchJob<R>* __restrict__ jobs) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < jb.n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    jb.sorted_in[k] = jb.user_in[jb.idx[k]];
+}
+
+template <typename R>
+__global__ void batch_scatter_kernel(const BatchJob<R>* __restrict__ jobs) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < jb.n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    jb.user_out[jb.idx[k]] = jb.sorted_out[k];
+}
+
+template <typename R>
+__global__ void pad_batch_kernel(const BatchJob<R>* __restrict__ jobs, const R* __restrict__ psi,
+                                 int npix, int Ng) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  int64_t total = (int64_t)Ng * Ng;
+  const int h = npix / 2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int rr = (int)(k / Ng), cc = (int)(k % Ng);
+    int a = cc < h ? cc : (cc >= Ng - h ? cc - Ng : INT32_MAX);
+    int b = rr < h ? rr : (rr >= Ng - h ? rr - Ng : INT32_MAX);
+    C2<R> o;
+    o.x = (R)0;
+    o.y = (R)0;
+    if (a != INT32_MAX && b != INT32_MAX) {
+      int q = a + h, p = b + h;
+      R val = jb.image_in[(int64_t)p * npix + q] / (psi[p] * psi[q]);
+      o.x = ((a + b) & 1) ? -val : val;
+    }
+    jb.grid[k] = o;
+  }
+}
+
+template <typename R>
+__global__ void crop_batch_kernel(const BatchJob<R>* __restrict__ jobs, const R* __restrict__ psi,
+                                  int npix, int Ng) {
+  const BatchJob<R> jb = jobs[blockIdx.y];
+  const R scale = (R)jb.inv_n;
+  int64_t total = (int64_t)npix * npix;
+  const int h = npix / 2;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(k / npix), q = (int)(k % npix);
+    int a = q - h, b = p - h;
+    int cc = a < 0 ? a + Ng : a;
+    int rr = b < 0 ? b + Ng : b;
+    R val = jb.grid[(int64_t)rr * Ng + cc].x * scale / (psi[p] * psi[q]);
+    jb.image_out[k] = ((a + b) & 1) ? -val : val;
+  }
+}
+
+namespace {
+int blocks_for(int64_t n, int cap) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : (int)b;
+}
+}  // namespace
+
+template <typename R>
+void launch_job_of(const BatchJob<R>* jobs, int njobs, int max_items, int32_t* job_of,
+                   cudaStream_t s) {
+  job_of_kernel<R><<<dim3(blocks_for(max_items, 152), njobs), kThreads, 0, s>>>(jobs, job_of);
+}
+
+template <typename R>
+void launch_batch_gather(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s) {
+  batch_gather_kernel<R><<<dim3(blocks_for(max_n, 152 * 4), njobs), kThreads, 0, s>>>(jobs);
+}
+
+template <typename R>
+void launch_batch_scatter(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s) {
+  batch_scatter_kernel<R><<<dim3(blocks_for(max_n, 152 * 4), njobs), kThreads, 0, s>>>(jobs);
+}
+
+template <typename R, bool KAHAN>
+void launch_grid_batch(const BatchJob<R>* jobs, const int32_t* job_of, int total_items,
+                       void* scratch, int tile, int ntx, double beta, cudaStream_t s) {
+  if (total_items <= 0) return;
+  constexpr int NW = grid_warps<R, KAHAN>();
+  const int S = tile + kW - 1;
+  size_t smem = (size_t)NW * S * S * sizeof(C2<R>) * (KAHAN ? 2 : 1) +
+                (size_t)NW * 32 * (2 * kW * sizeof(R) + sizeof(C2<R>) + sizeof(int));
+  auto k = grid_batch_kernel<R, KAHAN>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<total_items, 32 * NW, smem, s>>>(
+      jobs, job_of, reinterpret_cast<typename ScratchOf<R, KAHAN>::T*>(scratch), tile, ntx,
+      (R)beta);
+}
+
+template <typename R, bool KAHAN>
+void launch_fold_batch(const BatchJob<R>* jobs, int njobs, const void* scratch, int Ng,
+                       int tile, int ntx, cudaStream_t s) {
+  fold_batch_kernel<R, KAHAN><<<dim3(blocks_for((int64_t)Ng * Ng, 152 * 8), njobs), kThreads, 0,
+                                s>>>(
+      jobs, reinterpret_cast<const typename ScratchOf<R, KAHAN>::T*>(scratch), Ng, tile, ntx);
+}
+
+template <typename R>
+void launch_degrid_batch(const CUtensorMap* tmap, const BatchJob<R>* jobs,
+                         const int32_t* job_of, int total_items, bool has_obs, int Ng, int tile,
+                         int ntx, double beta, int32_t* err, cudaStream_t s) {
+  if (total_items <= 0) return;
+  const int S = tile + kW - 1;
+  size_t smem = (size_t)S * S * sizeof(C2<R>) + 128 + sizeof(uint64_t) + sizeof(int) + 4;
+  if (has_obs) {
+    auto k = degrid_batch_kernel<R, true>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total_items, kThreads, smem, s>>>(*tmap, jobs, job_of, Ng, tile, ntx, (R)beta, err);
+  } else {
+    auto k = degrid_batch_kernel<R, false>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<total_items, kThreads, smem, s>>>(*tmap, jobs, job_of, Ng, tile, ntx, (R)beta, err);
+  }
+}
+
+template <typename R>
+void launch_pad_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
+                      cudaStream_t s) {
+  pad_batch_kernel<R><<<dim3(blocks_for((int64_t)Ng * Ng, 152 * 8), njobs), kThreads, 0, s>>>(
+      jobs, psi, npix, Ng);
+}
+
+template <typename R>
+void launch_crop_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
+                       cudaStream_t s) {
+  crop_batch_kernel<R><<<dim3(blocks_for((int64_t)npix * npix, 152 * 8), njobs), kThreads, 0,
+                         s>>>(jobs, psi, npix, Ng);
+}
+
+#define MS_BATCH_INST(R)                                                                         \
+  template void launch_job_of<R>(const BatchJob<R>*, int, int, int32_t*, cudaStream_t);         \
+  template void launch_batch_gather<R>(const BatchJob<R>*, int, int64_t, cudaStream_t);         \
+  template void launch_batch_scatter<R>(const BatchJob<R>*, int, int64_t, cudaStream_t);        \
+  template void launch_degrid_batch<R>(const CUtensorMap*, const BatchJob<R>*, const int32_t*,  \
+                                       int, bool, int, int, int, double, int32_t*,             \
+                                       cudaStream_t);                                           \
+  template void launch_pad_batch<R>(const BatchJob<R>*, int, const R*, int, int, cudaStream_t); \
+  template void launch_crop_batch<R>(const BatchJob<R>*, int, const R*, int, int, cudaStream_t);
+MS_BATCH_INST(float)
+MS_BATCH_INST(double)
+#undef MS_BATCH_INST
+template void launch_grid_batch<float, false>(const BatchJob<float>*, const int32_t*, int, void*,
+                                              int, int, double, cudaStream_t);
+template void launch_grid_batch<float, true>(const BatchJob<float>*, const int32_t*, int, void*,
+                                             int, int, double, cudaStream_t);
+template void launch_grid_batch<double, false>(const BatchJob<double>*, const int32_t*, int,
+                                               void*, int, int, double, cudaStream_t);
+template void launch_fold_batch<float, false>(const BatchJob<float>*, int, const void*, int, int,
+                                              int, cudaStream_t);
+template void launch_fold_batch<float, true>(const BatchJob<float>*, int, const void*, int, int,
+                                             int, cudaStream_t);
+template void launch_fold_batch<double, false>(const BatchJob<double>*, int, const void*, int,
+                                               int, int, cudaStream_t);
+
 template void launch_pad<float>(const float*, const float*, int, int, float2*, cudaStream_t);
 template void launch_pad<double>(const double*, const double*, int, int, double2*,
                                  cudaStream_t);

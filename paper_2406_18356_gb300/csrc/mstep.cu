@@ -170,6 +170,8 @@ __global__ void init_ctl_kernel(FistaCtl* ctl, int max_iters, double rel_tol, do
   }
   ctl->F_prev = NAN;
   ctl->F_cur = NAN;
+  ctl->tf[0] = ctl->tf[1] = 0.0f;   // t_0 = t_1 = 0
+  ctl->td[0] = ctl->td[1] = 0.0;
 }
 
 __global__ void set_eta_kernel(FistaCtl* ctl, double eta2) { ctl->eta2 = eta2; }

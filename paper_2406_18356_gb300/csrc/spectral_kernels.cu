@@ -74,13 +74,21 @@ __device__ void gather_partials(double (&out)[NV], const double* parts, const bo
   // are independent, so a thread keeps all of them in flight at once
   double v[NV];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    double s = is_max[i] ? -INFINITY : 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-      double x = __ldcg(parts + (int64_t)i * gridDim.x + b);
-      s = is_max[i] ? fmax(s, x) : s + x;
+  for (int i = 0; i < NV; ++i) v[i] = is_max[i] ? -INFINITY : 0.0;
+  const int G = (int)gridDim.x;
+  for (int b0 = threadIdx.x; b0 < G; b0 += 4 * blockDim.x) {
+    double x[NV][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int b = b0 + u * blockDim.x;
+#pragma unroll
+      for (int i = 0; i < NV; ++i)
+        x[i][u] = b < G ? __ldcg(parts + (int64_t)i * G + b) : (is_max[i] ? -INFINITY : 0.0);
     }
-    v[i] = s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < NV; ++i) v[i] = is_max[i] ? fmax(v[i], x[i][u]) : v[i] + x[i][u];
   }
   block_reduce<NV>(v, is_max);
 #pragma unroll
@@ -276,11 +284,13 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // and otherwise advances the iteration index to k + 1 for the analysis pass
 // that builds B_{k+1}.
 template <typename R>
-__global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict__ Xprev,
+__global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict__ Xprev,
                                 const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, int N,
                                 double* __restrict__ parts, FistaCtl* __restrict__ ctl,
                                 double* __restrict__ trace, int32_t* ticket,
                                 const double* __restrict__ l1_parts, int n_l1) {
+  pdl_wait();
+  pdl_trigger();
   if (ctl->done) return;
   const int nc = N / 2 + 1;
   const int64_t total = (int64_t)N * nc;
@@ -289,47 +299,82 @@ __global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict_
   const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
   const double rtol = ctl->rel_tol;
   const int max_iters = ctl->max_iters;
-  const R t = (R)(kit >= 2 ? (double)(kit - 1) / (double)(kit + 2) : 0.0);
+  const R t = ctl_t<R>(ctl, kit & 1);
+  const double inv_theta = ctl->inv_theta;
   const R a = (R)1 + t;
   const float inv_nc = 1.0f / (float)nc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // this thread's share of the l1 partials of the previous analysis pass
+  double l1s = 0.0;
+  for (int64_t i = first; i < n_l1; i += stride) l1s += __ldcg(l1_parts + i);
   // per-thread compensated sums in the working precision, combined in FP64
   R s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    // column of the half-plane (exact: the quotient stays 0.5/nc from an integer)
-    const int row = __float2int_rz(((float)k + 0.5f) * inv_nc);
-    const int col = (int)(k - (int64_t)row * nc);
-    const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
-    C2<R> X = Xk[k];
-    C2<R> P = Xprev[k];
-    R kk = Ks[k];
-    C2<R> B = Bs[k];
-    R y0 = w * kk * (X.x * X.x + X.y * X.y) - c0;
-    R t0 = s0 + y0;
-    c0 = (t0 - s0) - y0;
-    s0 = t0;
-    R y1 = w * (B.x * X.x + B.y * X.y) - c1;
-    R t1 = s1 + y1;
-    c1 = (t1 - s1) - y1;
-    s1 = t1;
-    C2<R> S;
-    S.x = (R)2 * (kk * (a * X.x - t * P.x) - B.x);
-    S.y = (R)2 * (kk * (a * X.y - t * P.y) - B.y);
-    Xprev[k] = S;
+  constexpr int U = 2;   // elements per thread and round, loads issued together
+  for (int64_t k0 = first; k0 < total; k0 += U * stride) {
+    C2<R> X[U], P[U], B[U];
+    R kk[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = k0 + u * stride;
+      if (k < total) {
+        X[u] = Xk[k];
+        P[u] = Xprev[k];
+        kk[u] = Ks[k];
+        B[u] = Bs[k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t k = k0 + u * stride;
+      if (k >= total) break;
+      // column of the half-plane (exact: the quotient stays 0.5/nc from an integer)
+      const int row = __float2int_rz(((float)k + 0.5f) * inv_nc);
+      const int col = (int)(k - (int64_t)row * nc);
+      const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
+      R y0 = w * kk[u] * (X[u].x * X[u].x + X[u].y * X[u].y) - c0;
+      R t0 = s0 + y0;
+      c0 = (t0 - s0) - y0;
+      s0 = t0;
+      R y1 = w * (B[u].x * X[u].x + B[u].y * X[u].y) - c1;
+      R t1 = s1 + y1;
+      c1 = (t1 - s1) - y1;
+      s1 = t1;
+      C2<R> S;
+      S.x = (R)2 * (kk[u] * (a * X[u].x - t * P[u].x) - B[u].x);
+      S.y = (R)2 * (kk[u] * (a * X[u].y - t * P[u].y) - B[u].y);
+      Xprev[k] = S;
+    }
   }
-  double v[2] = {(double)s0 - (double)c0, (double)s1 - (double)c1};
-  const bool mx[2] = {false, false};
-  block_reduce<2>(v, mx);
-  if (publish_partials<2>(v, parts, ticket)) {
-    double o[2];
-    gather_partials<2>(o, parts, mx, ticket);
-    double l1v[1] = {0.0};
-    for (int b = threadIdx.x; b < n_l1; b += blockDim.x) l1v[0] += __ldcg(l1_parts + b);
-    const bool mx1[1] = {false};
-    block_reduce<1>(l1v, mx1);
+  // block sums: the working-precision pairs (s, -c) are combined error-free
+  // within each warp and reach FP64 once per warp; the l1 partials (FP64)
+  // only exist in the first blocks
+  __shared__ double red3[3][kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double w0 = warp_sum_comp<R>(s0, -c0);
+  double w1 = warp_sum_comp<R>(s1, -c1);
+  double w2 = 0.0;
+  if ((int64_t)blockIdx.x * blockDim.x < n_l1) w2 = warp_sum(l1s);
+  if (lane == 0) {
+    red3[0][warp] = w0;
+    red3[1][warp] = w1;
+    red3[2][warp] = w2;
+  }
+  __syncthreads();
+  double v[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kThreads / 32; ++q) {
+      v[0] += red3[0][q];
+      v[1] += red3[1][q];
+      v[2] += red3[2][q];
+    }
+  const bool mx[3] = {false, false, false};
+  if (publish_partials<3>(v, parts, ticket)) {
+    double o[3];
+    gather_partials<3>(o, parts, mx, ticket);
     if (threadIdx.x == 0) {
       const int k = kit;
-      const double l1 = l1v[0];
+      const double l1 = o[2];
       double F = o[0] - 2.0 * o[1] + c0v + lam * l1;
       ctl->l1_cur = l1;
       ctl->xkx = o[0];
@@ -347,7 +392,14 @@ __global__ void spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict_
         ctl->done = 1;
       } else {
         ctl->k = k + 1;
+        const double tn = k + 1 >= 2 ? (double)k / (double)(k + 3) : 0.0;   // t_{k+1}
+        ctl->td[(k + 1) & 1] = tn;
+        ctl->tf[(k + 1) & 1] = (float)tn;
       }
+      ctl->mud = inv_theta;
+      ctl->thrd = lam * inv_theta;
+      ctl->muf = (float)inv_theta;
+      ctl->thrf = (float)(lam * inv_theta);
       __threadfence();
     }
   }
@@ -357,8 +409,8 @@ template <typename R>
 void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
                      double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
                      const double* l1_parts, int n_l1, cudaStream_t s) {
-  spec_mul_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(Xk, Xprev, Ks, Bs, N, parts, ctl,
-                                                               trace, ticket, l1_parts, n_l1);
+  launch_pdl(spec_mul_kernel<R>, dim3(spectral_partials(N)), dim3(kThreads), 0, s, Xk, Xprev, Ks,
+             Bs, N, parts, ctl, trace, ticket, l1_parts, n_l1);
 }
 
 template <typename R>

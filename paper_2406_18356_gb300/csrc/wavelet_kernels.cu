@@ -193,22 +193,6 @@ __device__ __forceinline__ void fir_up8(const R* lo, const R* hi, R* out) {
   }
 }
 
-// deterministic block sum (fixed shuffle tree); result valid in thread 0
-__device__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double s = 0;
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
-  __syncthreads();
-  return s;
-}
-
 // per-thread compensated sum of |x| in the working precision (Kahan), so the
 // FP64 unit only sees one value per thread
 template <typename R> struct KSum {
@@ -408,6 +392,8 @@ __global__ void __launch_bounds__(kThreads, 2)
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 2)
     synthesis_level_kernel(FistaPass<R> a, int j) {
+  pdl_wait();
+  pdl_trigger();
   const int done = a.ctl->done;
   const int k = a.ctl->k;
   if (done) return;   // uniform: `done` does not change during this kernel
@@ -740,16 +726,17 @@ template <typename R>
 __global__ void __launch_bounds__(kThreads, 2)
     analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a, int j,
                           int use_tma, int part_base) {
+  pdl_wait();
+  pdl_trigger();
   const int done = a.ctl->done;
   const int kc = a.ctl->k;
-  const double lam = a.ctl->lam, inv_theta = a.ctl->inv_theta;
   if (done) return;   // uniform: `done` does not change during this kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_align128(smem_raw);
   const int k = kc - 1;
-  const R t = (R)(k >= 2 ? (double)(k - 1) / (double)(k + 2) : 0.0);
-  const R mu = (R)inv_theta;
-  const R thr = (R)(lam * inv_theta);
+  const R t = ctl_t<R>(a.ctl, k & 1);   // momentum t_k
+  const R mu = ctl_mu<R>(a.ctl);        // 1 / theta
+  const R thr = ctl_thr<R>(a.ctl);      // lambda / theta
   const R* cur = k % 3 == 0 ? a.B0 : (k % 3 == 1 ? a.B1 : a.B2);
   const R* prev = k % 3 == 0 ? a.B2 : (k % 3 == 1 ? a.B0 : a.B1);
   R* next = k % 3 == 0 ? a.B1 : (k % 3 == 1 ? a.B2 : a.B0);
@@ -773,9 +760,16 @@ __global__ void __launch_bounds__(kThreads, 2)
     MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
 #undef MS_ANA
   }
-  double sum = block_sum(l1.value(), red);
-  if (threadIdx.x == 0)
+  // block sum of |B_{k+1}|: error-free working-precision warp sums, FP64
+  // once per warp
+  const double ws = warp_sum_comp<R>(l1.s, -l1.c);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
     a.l1_parts[part_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = sum;
+  }
 }
 
 int analysis_prox_partials(WaveletGeom g) {
@@ -822,9 +816,10 @@ cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int onl
     if (only_level < 0 && j == 1) continue;
     int n = 2 * (a.N >> j), TS = syn_tile(n);
     dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M);
-    k<<<grid, kThreads, smem, s>>>(a, j);
+    cudaError_t e = launch_pdl(k, grid, dim3(kThreads), smem, s, a, j);
+    if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <typename R>
@@ -841,11 +836,13 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
     const bool run = only_level == 0 || j == only_level || (only_level < 0 && j > 1);
     if (run) {
       dim3 grid(tiles, a.M);
-      k<<<grid, kThreads, smem, s>>>(m, a, j, grad_map ? 1 : 0, part_base);
+      cudaError_t e = launch_pdl(k, grid, dim3(kThreads), smem, s, m, a, j, grad_map ? 1 : 0,
+                                 part_base);
+      if (e != cudaSuccess) return e;
     }
     part_base += tiles * a.M;
   }
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template void launch_synthesis3<float>(const float* const*, float*, float*, WaveletGeom,
