@@ -73,8 +73,9 @@ constexpr int kAnaYSz = (kAT * kYS + 3) / 4 * 4;
 // synthesis: output tile 64 x 64; subband positions 64/2 + 16/2 - 1
 constexpr int kST = 64;
 constexpr int kSIn = kST / 2 + kMaxTaps / 2 - 1;  // 39
-constexpr int kSInS = kSIn + 2;                   // odd row stride (41)
-constexpr int kSubSz = 4 * kSIn * kSInS;          // one staged basis (four windows)
+constexpr int kSubS = 44;                         // staged row stride: 16-byte rows, >= 40 + 1
+constexpr int kSInS = kSIn + 2;                   // odd row stride of zlo / zhi (41)
+constexpr int kSubSz = 4 * kSIn * kSubS;          // one staged basis (four windows)
 
 // Tile sides: large levels use big tiles (less halo), small levels smaller
 // ones so that they still spread over the SMs.
@@ -217,22 +218,51 @@ template <> struct Vec<double> { using T = double2; static constexpr int N = 2; 
 // buffer written by the level above.  Level 1 sums the M bases into x, with
 // the next basis's windows prefetched by cp.async while the current one is
 // filtered.
+// Stages the four subband windows of one basis: rows from r0/2 - 7, columns
+// from c0/2 - 8 (one column before the filter's first, so that in the image's
+// interior each window row starts on a 16-byte boundary and is copied in
+// whole 16-byte chunks); rows always, columns near the edges, wrap
+// periodically.  Window element (a, b) of subband s is at
+// sub[s][a][b] with b = column - (c0/2 - 8).
 template <typename R>
 __device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N, int h, int r0,
                                             int c0, int cnt, R* sub) {
-  const int base_r = r0 / 2 - (kMaxTaps / 2 - 1), base_c = c0 / 2 - (kMaxTaps / 2 - 1);
-  // positions lie in [-7, h + cnt): one conditional wrap when h >= cnt, 7
-  const bool cheap = h >= cnt && h >= kMaxTaps / 2 - 1;
+  const int base_r = r0 / 2 - (kMaxTaps / 2 - 1), base_c = c0 / 2 - kMaxTaps / 2;
+  const int ncol = cnt + 1;
+  constexpr int V = 16 / (int)sizeof(R);
+  const int nch = (ncol + V - 1) / V;
+  // rows lie in [-7, h), columns in [-8, h): one conditional wrap when h >= 8
+  const bool cheap = h >= kMaxTaps / 2;
+  if (base_c >= 0 && base_c + nch * V <= h) {
+    const int per_sub = cnt * nch;
+    for (int e = threadIdx.x; e < 4 * per_sub; e += kThreads) {
+      const int sb = e / per_sub, rem = e - sb * per_sub;
+      const int a = rem / nch, c = rem - a * nch;
+      const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
+      const int ix = base_c + c * V;
+      const R* src;
+      if (sb == 0)
+        src = llp ? llp + (int64_t)iy * h + ix : plane + (int64_t)iy * N + ix;
+      else if (sb == 1)
+        src = plane + (int64_t)iy * N + h + ix;
+      else if (sb == 2)
+        src = plane + (int64_t)(h + iy) * N + ix;
+      else
+        src = plane + (int64_t)(h + iy) * N + h + ix;
+      cp_async<16>(sub + (sb * kSIn + a) * kSubS + c * V, src);
+    }
+    return;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int a = warp; a < cnt; a += kThreads / 32) {
     const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
-    for (int b = lane; b < cnt; b += 32) {
+    for (int b = lane; b < ncol; b += 32) {
       const int ix = cheap ? wrapc(base_c + b, h) : wrap(base_c + b, h);
-      R* d = sub + a * kSInS + b;
+      R* d = sub + a * kSubS + b;
       cp_async<sizeof(R)>(d, llp ? llp + (int64_t)iy * h + ix : plane + (int64_t)iy * N + ix);
-      cp_async<sizeof(R)>(d + kSIn * kSInS, plane + (int64_t)iy * N + h + ix);
-      cp_async<sizeof(R)>(d + 2 * kSIn * kSInS, plane + (int64_t)(h + iy) * N + ix);
-      cp_async<sizeof(R)>(d + 3 * kSIn * kSInS, plane + (int64_t)(h + iy) * N + h + ix);
+      cp_async<sizeof(R)>(d + kSIn * kSubS, plane + (int64_t)iy * N + h + ix);
+      cp_async<sizeof(R)>(d + 2 * kSIn * kSubS, plane + (int64_t)(h + iy) * N + ix);
+      cp_async<sizeof(R)>(d + 3 * kSIn * kSubS, plane + (int64_t)(h + iy) * N + h + ix);
     }
   }
 }
@@ -252,14 +282,15 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
     int rest = u / cnt;
     int b = u - rest * cnt;
     int pair = rest & 1, seg = rest >> 1;
-    const R* s0 = sub + (pair ? 1 : 0) * kSIn * kSInS;
-    const R* s1 = sub + (pair ? 3 : 2) * kSIn * kSInS;
+    // window column b + 1 is filter column b (the window starts one early)
+    const R* s0 = sub + (pair ? 1 : 0) * kSIn * kSubS + 1;
+    const R* s1 = sub + (pair ? 3 : 2) * kSIn * kSubS + 1;
     const int first = 4 * seg + 8 - L / 2;
     R lo[NI], hi[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-      lo[i] = s0[(first + i) * kSInS + b];
-      hi[i] = s1[(first + i) * kSInS + b];
+      lo[i] = s0[(first + i) * kSubS + b];
+      hi[i] = s1[(first + i) * kSubS + b];
     }
     R out[kP];
     fir_up8<R, MB>(lo, hi, out);
@@ -302,7 +333,7 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
                                            const R* __restrict__ ll_in, R* __restrict__ ll_out,
                                            R* __restrict__ x, int N, int j, int J, int M,
                                            int tile, int mb) {
-  R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][kSIn][kSInS]
+  R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][kSIn][kSubS]
   R* zlo = subs + 2 * kSubSz;                         // [kST][kSInS]
   R* zhi = zlo + kST * kSInS;
   const int h = N >> j, n = 2 * h;
@@ -574,13 +605,25 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
     // stage the input window with periodic wrap (first cp.async group)
     const R* src = (j == 1) ? x_in : ll_in + (int64_t)m * n * n;
     const bool cheap = n >= ext;   // positions lie in [0, n + ext)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int a = warp; a < ext; a += kThreads / 32) {
-      const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
-      const R* row = src + (int64_t)py * n;
-      for (int b = lane; b < ext; b += 32) {
-        const int px = cheap ? wrapc(p0x + b, n) : wrap(p0x + b, n);
-        cp_async<sizeof(R)>(sIn + a * kAInS + b, row + px);
+    constexpr int V = 16 / (int)sizeof(R);
+    const int nch = (ext + V - 1) / V;
+    if (p0x + nch * V <= n && (n % V) == 0) {
+      // the window's columns need no wrap: whole 16-byte chunks per row
+      // (p0x = 2 o0x is a multiple of 16), rows wrap
+      for (int e = threadIdx.x; e < ext * nch; e += kThreads) {
+        const int a = e / nch, c = e - a * nch;
+        const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
+        cp_async<16>(sIn + a * kAInS + c * V, src + (int64_t)py * n + p0x + c * V);
+      }
+    } else {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int a = warp; a < ext; a += kThreads / 32) {
+        const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
+        const R* row = src + (int64_t)py * n;
+        for (int b = lane; b < ext; b += 32) {
+          const int px = cheap ? wrapc(p0x + b, n) : wrap(p0x + b, n);
+          cp_async<sizeof(R)>(sIn + a * kAInS + b, row + px);
+        }
       }
     }
     cp_async_commit();
