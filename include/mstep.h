@@ -177,6 +177,40 @@ ms_status ms_grid(ms_plan* plan, int32_t part, int32_t chan, const void* vis,
 ms_status ms_grid_static_scratch(ms_plan* plan, int32_t part, int32_t chan, const void* vis,
                                  void* dirty, void* stream);
 
+/* ----------------------------------------------------------- batched form */
+
+/* Gridding of several (channel, partition) jobs at once: the work items of
+ * all jobs go through one gridding launch and one fold launch, the grids
+ * through one batched inverse FFT and one crop.  chans, parts, vis, dirty are
+ * HOST arrays of njobs entries; vis[j] is a dev complex [nvis] array of
+ * channel chans[j] in original row order, dirty[j] a dev N*N real image that
+ * receives A^H y / sum(w) of the rows of parts[j] (as ms_grid would).  The
+ * plan grows its batch workspaces (grids, tiles, rows) when a call needs more
+ * than an earlier one; later calls of the same or smaller size allocate
+ * nothing.  Errors: MS_ERR_ARG (a NULL array or entry, channel or partition
+ * out of range), MS_ERR_OOM, MS_ERR_CUDA. */
+ms_status ms_grid_batch(ms_plan* plan, int32_t njobs, const int32_t* chans,
+                        const int32_t* parts, const void* const* vis, void* const* dirty,
+                        void* stream);
+
+/* Degridding of several jobs at once (one pad, one batched FFT, one
+ * degridding launch over all jobs' work items): images[j] (dev N*N real) ->
+ * vis_out[j] (dev complex [nvis], only the rows of parts[j] written) = A x,
+ * or vis_obs[j] - A x when vis_obs is not NULL.  Host arrays as in
+ * ms_grid_batch; vis_obs may be NULL as a whole. */
+ms_status ms_degrid_batch(ms_plan* plan, int32_t njobs, const int32_t* chans,
+                          const int32_t* parts, const void* const* images,
+                          const void* const* vis_obs, void* const* vis_out, void* stream);
+
+/* Autotuner of the gridding layout: builds a plan from *desc for every grid
+ * tile side T in {16, 32} (dividing 2N) and work-item size in {512, 1024,
+ * 2048, 4096, 8192} rows, times `reps` degrid + grid pairs of channel chan's
+ * full row set on this GPU (CUDA events, after one untimed pair) and returns
+ * the fastest tile and chunk (to be put into desc->tile, desc->chunk) and its
+ * time per pair in ms.  desc is not modified. */
+ms_status ms_plan_autotune(const ms_plan_desc* desc, int32_t chan, int32_t reps,
+                           int32_t* best_tile, int32_t* best_chunk, double* best_ms);
+
 /* Major-cycle residual image i~ = F^H G^H (v - G F x) / sum(w) (Sect. 2) for
  * the rows of `part`: degrid, subtract, grid, in one call.  model: dev N*N
  * real; vis_obs: dev complex [nvis] original order; out: dev N*N real. */

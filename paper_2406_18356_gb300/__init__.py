@@ -86,6 +86,12 @@ _SIGNATURES = {
     "ms_degrid": [_P, _I32, _I32, _P, _P, _P, _P],
     "ms_grid": [_P, _I32, _I32, _P, _P, _P],
     "ms_grid_static_scratch": [_P, _I32, _I32, _P, _P, _P],
+    "ms_grid_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                      ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "ms_degrid_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                        ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "ms_plan_autotune": [ctypes.POINTER(ms_plan_desc), _I32, _I32, ctypes.POINTER(_I32),
+                         ctypes.POINTER(_I32), ctypes.POINTER(_D)],
     "ms_residual_image": [_P, _I32, _I32, _P, _P, _P, _P],
     "ms_psf": [_P, _I32, _I32, _P, _P],
     "ms_dictionary_synthesis": [_P, _P, _P, _P],
@@ -304,6 +310,42 @@ class Plan:
             self._need(out, self.real_dtype, self.npix ** 2, "dirty"), _stream_handle(stream)))
         return out
 
+    def _jobs(self, jobs):
+        n = len(jobs)
+        chans = (_I32 * n)(*[int(c) for c, _ in jobs])
+        parts = (_I32 * n)(*[PARTS[p] for _, p in jobs])
+        return n, chans, parts
+
+    def grid_batch(self, jobs, vis, outs=None, stream=None):
+        """jobs: [(chan, part)], vis: one dev complex [nvis] tensor per job
+        (that channel's visibilities), outs: dirty images (allocated if None)."""
+        n, chans, parts = self._jobs(jobs)
+        if outs is None:
+            outs = [self._image() for _ in range(n)]
+        vp = (_P * n)(*[self._need(v, self.complex_dtype, self.nvis, "vis") for v in vis])
+        op = (_P * n)(*[self._need(o, self.real_dtype, self.npix ** 2, "dirty") for o in outs])
+        self._check(self._lib.ms_grid_batch(self._h, n, chans, parts, vp, op,
+                                            _stream_handle(stream)))
+        return outs
+
+    def degrid_batch(self, jobs, images, vis_obs=None, outs=None, stream=None):
+        """jobs: [(chan, part)], images: one dev N*N real tensor per job;
+        vis_obs: None or one dev complex [nvis] tensor per job."""
+        torch = _torch()
+        n, chans, parts = self._jobs(jobs)
+        if outs is None:
+            outs = [torch.zeros(self.nvis, dtype=self.complex_dtype, device=self._dev())
+                    for _ in range(n)]
+        ip = (_P * n)(*[self._need(x, self.real_dtype, self.npix ** 2, "image") for x in images])
+        op = (_P * n)(*[self._need(o, self.complex_dtype, self.nvis, "vis_out") for o in outs])
+        ob = None
+        if vis_obs is not None:
+            ob = (_P * n)(*[self._need(v, self.complex_dtype, self.nvis, "vis_obs")
+                            for v in vis_obs])
+        self._check(self._lib.ms_degrid_batch(self._h, n, chans, parts, ip, ob, op,
+                                              _stream_handle(stream)))
+        return outs
+
     def residual_image(self, part: str, vis_obs, model, out=None, chan: int = 0, stream=None):
         out = self._image(out)
         n2 = self.npix ** 2
@@ -436,6 +478,36 @@ def ms_grid(plan: Plan, part, vis, out=None, chan=0, stream=None):
 
 def ms_grid_static_scratch(plan: Plan, part, vis, out, chan=0, stream=None):
     return plan.grid_static_scratch(part, vis, out, chan, stream)
+
+
+def ms_grid_batch(plan: Plan, jobs, vis, outs=None, stream=None):
+    return plan.grid_batch(jobs, vis, outs, stream)
+
+
+def ms_degrid_batch(plan: Plan, jobs, images, vis_obs=None, outs=None, stream=None):
+    return plan.degrid_batch(jobs, images, vis_obs, outs, stream)
+
+
+def ms_plan_autotune(u, v, npix: int, pixel_size: float, ell_px: float, delta_px: float,
+                     flags=None, precision: str = "fp32", levels: int = 4, n_bases: int = 8,
+                     chan: int = 0, reps: int = 3, device: int = 0):
+    """Fastest (tile, chunk) of the gridding layout for these rows on this GPU,
+    and its degrid + grid time in ms (see ms_plan_autotune in mstep.h)."""
+    lib = load_library()
+    u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)))
+    v = np.ascontiguousarray(np.atleast_2d(np.asarray(v, dtype=np.float64)))
+    fl = None
+    if flags is not None:
+        fl = np.ascontiguousarray(np.atleast_2d(np.asarray(flags, dtype=np.uint8)))
+    d = ms_plan_desc(u.ctypes.data, v.ctypes.data, fl.ctypes.data if fl is not None else None,
+                     u.shape[1], u.shape[0], int(npix), pixel_size, ell_px, delta_px, 7, 2, 0.0,
+                     levels, n_bases, PRECISIONS[precision], 0, 0, device)
+    t, c, ms_ = _I32(), _I32(), _D()
+    st = lib.ms_plan_autotune(ctypes.byref(d), chan, reps, ctypes.byref(t), ctypes.byref(c),
+                              ctypes.byref(ms_))
+    if st != MS_OK:
+        raise MsError(st, "ms_plan_autotune failed")
+    return int(t.value), int(c.value), float(ms_.value)
 
 
 def ms_residual_image(plan: Plan, part, vis_obs, model, out=None, chan=0, stream=None):

@@ -262,6 +262,21 @@ struct ms_plan {
     allocs.push_back(p);
     return p;
   }
+  // batched form: workspaces grown on demand, freed with the plan
+  struct Batch {
+    int cap_jobs = 0;
+    int64_t cap_items = 0, cap_rows = 0;
+    void* jobs = nullptr;       // BatchJob<R>[cap_jobs]
+    int32_t* job_of = nullptr;  // [cap_items]
+    void* grids = nullptr;      // cap_jobs Ng^2 complex
+    void* scratch = nullptr;    // cap_items tiles
+    void* rows_a = nullptr;     // cap_rows complex (inputs in plan order)
+    void* rows_b = nullptr;     // cap_rows complex (outputs in plan order)
+    cufftHandle fft = 0;
+    int fft_jobs = 0;
+    CUtensorMap tmap{};
+    int tmap_jobs = 0;
+  } batch;
 };
 
 namespace {
@@ -1122,6 +1137,10 @@ void destroy(ms_plan* p) {
   for (cufftHandle h : {p->c2c, p->r2c, p->c2r})
     if (h) cufftDestroy(h);
   for (void* a : p->allocs) cudaFree(a);
+  if (p->batch.fft) cufftDestroy(p->batch.fft);
+  for (void* a : {p->batch.jobs, (void*)p->batch.job_of, p->batch.grids, p->batch.scratch,
+                  p->batch.rows_a, p->batch.rows_b})
+    if (a) cudaFree(a);
   for (auto e : p->tev) cudaEventDestroy(e);
   for (auto e : p->evpool) cudaEventDestroy(e);
   for (auto& sp : p->pending) {
@@ -1144,6 +1163,213 @@ void destroy(ms_plan* p) {
       __VA_ARGS__;                  \
     }                               \
   } while (0)
+
+// ------------------------------------------------------------ batched form
+// All (channel, partition) jobs of one call share one gridding launch, one
+// fold launch, one batched FFT and one crop (or one pad, one batched FFT, one
+// degridding launch): the work items of all jobs form one launch, the job
+// table says whose item a block holds.
+
+struct BatchShape {
+  int njobs = 0;
+  int64_t items = 0, rows = 0, max_n = 0;
+  int max_items = 0;
+};
+
+template <typename R>
+BatchShape batch_jobs(ms_plan* p, int njobs, const int32_t* chans, const int32_t* parts,
+                      std::vector<BatchJob<R>>& jobs) {
+  arg(njobs > 0, "njobs must be positive");
+  arg(chans && parts, "chans and parts are required");
+  BatchShape sh;
+  sh.njobs = njobs;
+  jobs.assign(njobs, BatchJob<R>{});
+  for (int j = 0; j < njobs; ++j) {
+    PartDev& pd = part_of(p, parts[j], chans[j]);
+    BatchJob<R>& b = jobs[j];
+    b.items = pd.items;
+    b.cell = pd.cell;
+    b.frac = (const C2<R>*)pd.frac;
+    b.idx = pd.idx;
+    b.tile_items = pd.tile_items;
+    b.n = pd.n;
+    b.nitems = pd.nitems;
+    b.item_base = sh.items;
+    b.inv_n = pd.n > 0 ? 1.0 / (double)pd.n : 0.0;
+    b.sorted_in = (C2<R>*)(intptr_t)sh.rows;    // offsets for now, pointers below
+    sh.items += pd.nitems;
+    sh.rows += pd.n;
+    sh.max_n = std::max(sh.max_n, pd.n);
+    sh.max_items = std::max(sh.max_items, pd.nitems);
+  }
+  arg(sh.items < (int64_t)1 << 31, "too many work items for one launch");
+  return sh;
+}
+
+// grow the batch workspaces to hold `sh` (allocates only when it grows)
+template <typename R> void batch_reserve(ms_plan* p, const BatchShape& sh) {
+  auto& B = p->batch;
+  const int Ng = p->Ng;
+  auto grow = [&](void*& ptr, size_t bytes, const char* what) {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    ptr = dalloc<unsigned char>(bytes, what);
+  };
+  if (sh.njobs > B.cap_jobs) {
+    grow(B.jobs, sizeof(BatchJob<R>) * sh.njobs, "batch jobs");
+    grow(B.grids, sizeof(C2<R>) * (size_t)Ng * Ng * sh.njobs, "batch grids");
+    B.cap_jobs = sh.njobs;
+    B.tmap_jobs = 0;   // the stacked-grid descriptor names the old buffer
+    if (B.fft) cufftDestroy(B.fft);
+    B.fft = 0;
+    B.fft_jobs = 0;
+  }
+  if (sh.items > B.cap_items) {
+    void* jo = B.job_of;
+    grow(jo, sizeof(int32_t) * std::max<int64_t>(sh.items, 1), "batch items");
+    B.job_of = (int32_t*)jo;
+    grow(B.scratch,
+         (size_t)std::max<int64_t>(sh.items, 1) * p->S * p->S * grid_scratch_cell_bytes(p->prec),
+         "batch scratch");
+    B.cap_items = sh.items;
+  }
+  if (sh.rows > B.cap_rows) {
+    grow(B.rows_a, sizeof(C2<R>) * std::max<int64_t>(sh.rows, 1), "batch rows");
+    grow(B.rows_b, sizeof(C2<R>) * std::max<int64_t>(sh.rows, 1), "batch rows");
+    B.cap_rows = sh.rows;
+  }
+  if (B.fft_jobs != sh.njobs) {
+    if (B.fft) cufftDestroy(B.fft);
+    B.fft = 0;
+    int n[2] = {Ng, Ng};
+    ckf(cufftPlanMany(&B.fft, 2, n, nullptr, 1, Ng * Ng, nullptr, 1, Ng * Ng,
+                      sizeof(R) == 8 ? CUFFT_Z2Z : CUFFT_C2C, sh.njobs),
+        "batched FFT plan");
+    ckf(cufftSetStream(B.fft, p->ps), "set stream");
+    B.fft_jobs = sh.njobs;
+  }
+  if (B.tmap_jobs != sh.njobs) {
+    // the jobs' grids stacked: {2 Ng scalars, njobs Ng rows}, box {2 S, S}
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    ck(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                        &q),
+       "driver entry point");
+    arg(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)2 * Ng, (cuuint64_t)Ng * sh.njobs};
+    cuuint64_t strides[1] = {(cuuint64_t)2 * Ng * sizeof(R)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * p->S), (cuuint32_t)p->S};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = ((EncodeTiledFn)fn)(
+        &B.tmap, sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+        2, B.grids, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Fail{MS_ERR_CUDA, "cuTensorMapEncodeTiled failed (batch)"};
+    B.tmap_jobs = sh.njobs;
+  }
+}
+
+// fill the workspace pointers of the jobs, upload the table, map items to jobs
+template <typename R>
+void batch_upload(ms_plan* p, const BatchShape& sh, std::vector<BatchJob<R>>& jobs) {
+  auto& B = p->batch;
+  const int64_t ng2 = (int64_t)p->Ng * p->Ng;
+  for (int j = 0; j < sh.njobs; ++j) {
+    const int64_t off = (int64_t)(intptr_t)jobs[j].sorted_in;
+    jobs[j].sorted_in = (C2<R>*)B.rows_a + off;
+    jobs[j].sorted_out = (C2<R>*)B.rows_b + off;
+    jobs[j].grid = (C2<R>*)B.grids + j * ng2;
+  }
+  ck(cudaMemcpyAsync(B.jobs, jobs.data(), sizeof(BatchJob<R>) * sh.njobs,
+                     cudaMemcpyHostToDevice, p->ps),
+     "job table");
+  launch_job_of<R>((const BatchJob<R>*)B.jobs, sh.njobs, sh.max_items, B.job_of, p->ps);
+}
+
+template <typename R> void batch_fft(ms_plan* p, int dir) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecZ2Z(p->batch.fft, (cufftDoubleComplex*)p->batch.grids,
+                     (cufftDoubleComplex*)p->batch.grids, dir),
+        "batched Z2Z");
+  else
+    ckf(cufftExecC2C(p->batch.fft, (cufftComplex*)p->batch.grids,
+                     (cufftComplex*)p->batch.grids, dir),
+        "batched C2C");
+}
+
+template <typename R>
+void grid_batch(ms_plan* p, int njobs, const int32_t* chans, const int32_t* parts,
+                const void* const* vis, void* const* dirty) {
+  arg(vis && dirty, "vis and dirty are required");
+  std::vector<BatchJob<R>> jobs;
+  BatchShape sh = batch_jobs<R>(p, njobs, chans, parts, jobs);
+  for (int j = 0; j < njobs; ++j) {
+    arg(vis[j] && dirty[j], "a job's vis or dirty pointer is NULL");
+    jobs[j].user_in = (const C2<R>*)vis[j];
+    jobs[j].image_out = (R*)dirty[j];
+  }
+  batch_reserve<R>(p, sh);
+  batch_upload<R>(p, sh, jobs);
+  const BatchJob<R>* jd = (const BatchJob<R>*)p->batch.jobs;
+  launch_batch_gather<R>(jd, njobs, sh.max_n, p->ps);
+  {
+    KSpan k(p, MS_K_GRID);
+    if (p->prec == MS_FP32_KAHAN)
+      launch_grid_batch<float, true>((const BatchJob<float>*)jd, p->batch.job_of, (int)sh.items,
+                                     p->batch.scratch, p->T, p->ntx, p->beta, p->ps);
+    else
+      launch_grid_batch<R, false>(jd, p->batch.job_of, (int)sh.items, p->batch.scratch, p->T,
+                                  p->ntx, p->beta, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FOLD);
+    if (p->prec == MS_FP32_KAHAN)
+      launch_fold_batch<float, true>((const BatchJob<float>*)jd, njobs, p->batch.scratch, p->Ng,
+                                     p->T, p->ntx, p->ps);
+    else
+      launch_fold_batch<R, false>(jd, njobs, p->batch.scratch, p->Ng, p->T, p->ntx, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    batch_fft<R>(p, CUFFT_INVERSE);
+  }
+  KSpan k(p, MS_K_PAD_CROP);
+  launch_crop_batch<R>(jd, njobs, (const R*)p->psi, p->N, p->Ng, p->ps);
+}
+
+template <typename R>
+void degrid_batch(ms_plan* p, int njobs, const int32_t* chans, const int32_t* parts,
+                  const void* const* images, const void* const* vis_obs, void* const* vis_out) {
+  arg(images && vis_out, "images and vis_out are required");
+  std::vector<BatchJob<R>> jobs;
+  BatchShape sh = batch_jobs<R>(p, njobs, chans, parts, jobs);
+  for (int j = 0; j < njobs; ++j) {
+    arg(images[j] && vis_out[j], "a job's image or vis_out pointer is NULL");
+    arg(!vis_obs || vis_obs[j], "a job's vis_obs pointer is NULL");
+    jobs[j].image_in = (const R*)images[j];
+    jobs[j].user_in = vis_obs ? (const C2<R>*)vis_obs[j] : nullptr;
+    jobs[j].user_out = (C2<R>*)vis_out[j];
+  }
+  batch_reserve<R>(p, sh);
+  batch_upload<R>(p, sh, jobs);
+  const BatchJob<R>* jd = (const BatchJob<R>*)p->batch.jobs;
+  if (vis_obs) launch_batch_gather<R>(jd, njobs, sh.max_n, p->ps);
+  {
+    KSpan k(p, MS_K_PAD_CROP);
+    launch_pad_batch<R>(jd, njobs, (const R*)p->psi, p->N, p->Ng, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    batch_fft<R>(p, CUFFT_FORWARD);
+  }
+  {
+    KSpan k(p, MS_K_DEGRID);
+    launch_degrid_batch<R>(&p->batch.tmap, jd, p->batch.job_of, (int)sh.items, vis_obs != nullptr,
+                           p->Ng, p->T, p->ntx, p->beta, p->err, p->ps);
+  }
+  launch_batch_scatter<R>(jd, njobs, sh.max_n, p->ps);
+}
 
 }  // namespace
 
@@ -1486,6 +1712,97 @@ ms_status ms_grid_static_scratch(ms_plan* p, int32_t part, int32_t chan, const v
     });
     sc.finish();
   });
+}
+
+ms_status ms_grid_batch(ms_plan* p, int32_t njobs, const int32_t* chans, const int32_t* parts,
+                        const void* const* vis, void* const* dirty, void* stream) {
+  return guarded(p, [&] {
+    Scope sc(p, stream);
+    DISPATCH(p, grid_batch<R>(p, njobs, chans, parts, vis, dirty));
+    sc.finish();
+  });
+}
+
+ms_status ms_degrid_batch(ms_plan* p, int32_t njobs, const int32_t* chans, const int32_t* parts,
+                          const void* const* images, const void* const* vis_obs,
+                          void* const* vis_out, void* stream) {
+  return guarded(p, [&] {
+    Scope sc(p, stream);
+    DISPATCH(p, degrid_batch<R>(p, njobs, chans, parts, images, vis_obs, vis_out));
+    check_device_error(p);
+    sc.finish();
+  });
+}
+
+ms_status ms_plan_autotune(const ms_plan_desc* desc, int32_t chan, int32_t reps,
+                           int32_t* best_tile, int32_t* best_chunk, double* best_ms) {
+  if (!desc || !best_tile || !best_chunk || chan < 0 || chan >= desc->nchan || reps < 1)
+    return MS_ERR_ARG;
+  const int tiles[2] = {16, 32};
+  const int chunks[5] = {512, 1024, 2048, 4096, 8192};
+  double best = 1e300;
+  int bt = 0, bc = 0;
+  void* vis = nullptr;
+  void* img = nullptr;
+  void* out = nullptr;
+  ms_status st = MS_OK;
+  for (int ti = 0; ti < 2 && st == MS_OK; ++ti) {
+    if ((2 * desc->npix) % tiles[ti]) continue;
+    for (int ci = 0; ci < 5 && st == MS_OK; ++ci) {
+      ms_plan_desc d = *desc;
+      d.tile = tiles[ti];
+      d.chunk = chunks[ci];
+      ms_plan* q = nullptr;
+      st = ms_plan_create(&d, &q);
+      if (st != MS_OK) break;
+      const size_t rsz = q->rsz;
+      if (!vis) {
+        if (cudaMalloc(&vis, 2 * rsz * std::max<int64_t>(desc->nvis, 1)) != cudaSuccess ||
+            cudaMalloc(&out, 2 * rsz * std::max<int64_t>(desc->nvis, 1)) != cudaSuccess ||
+            cudaMalloc(&img, rsz * desc->npix * desc->npix) != cudaSuccess) {
+          ms_plan_destroy(q);
+          st = MS_ERR_OOM;
+          break;
+        }
+        if (rsz == 8) {
+          launch_hash_fill<double>((double*)vis, 2 * desc->nvis, 7, q->ps);
+          launch_hash_fill<double>((double*)img, (int64_t)desc->npix * desc->npix, 8, q->ps);
+        } else {
+          launch_hash_fill<float>((float*)vis, 2 * desc->nvis, 7, q->ps);
+          launch_hash_fill<float>((float*)img, (int64_t)desc->npix * desc->npix, 8, q->ps);
+        }
+        cudaStreamSynchronize(q->ps);
+      }
+      // one untimed pair, then `reps` timed degrid + grid pairs
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      for (int r = 0; r <= reps && st == MS_OK; ++r) {
+        if (r == 1) cudaEventRecord(e0, q->ps);
+        st = ms_degrid(q, MS_PART_ALL, chan, img, nullptr, out, q->ps);
+        if (st == MS_OK) st = ms_grid(q, MS_PART_ALL, chan, vis, img, q->ps);
+      }
+      cudaEventRecord(e1, q->ps);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ms_plan_destroy(q);
+      if (st == MS_OK && ms / reps < best) {
+        best = ms / reps;
+        bt = tiles[ti];
+        bc = chunks[ci];
+      }
+    }
+  }
+  for (void* a : {vis, img, out})
+    if (a) cudaFree(a);
+  if (st != MS_OK) return st;
+  *best_tile = bt;
+  *best_chunk = bc;
+  if (best_ms) *best_ms = best;
+  return MS_OK;
 }
 
 }  // extern "C"
