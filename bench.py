@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--n-major", type=int, default=N_MAJOR)
     ap.add_argument("--fista-iters", type=int, default=FISTA_ITERS)
     ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-channels", type=int, default=64)
     return ap.parse_args()
 
 
@@ -325,6 +327,11 @@ def main():
     tte = None
     if rank == 0 and not args.no_time_to_eps:
         tte = time_to_eps(ms, w, dev, args.eps)
+    plan.close()
+
+    batched = None
+    if rank == 0 and not args.no_batched:
+        batched = batched_leg(ms, dev, args.batched_channels, args.precision)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -345,11 +352,10 @@ def main():
                                       "minor_cycles": tot["minor_ms"] / args.steps},
                 "gpu_launches": gpu_launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "time_to_eps": tte,
+                "time_to_eps": tte, "batched": batched,
                 "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}
                 if prof else None}
         print(json.dumps(line), flush=True)
-    plan.close()
     if pg:
         pg.barrier()
         pg.destroy_process_group()
@@ -391,6 +397,70 @@ def time_to_eps(ms, w, dev, eps, max_iters=1000):
             "chosen": out["fp32_kahan"], "plain": out["fp64"],
             "speedup": out["fp64"]["ms"] / out["fp32_kahan"]["ms"],
             "image_rel_l2_chosen_vs_plain": diff}
+
+
+def batched_leg(ms, dev, nchan, precision, steps=3):
+    """The batched form on nchan channels x 1024^2 (the layout of the main
+    workload, uv scaled per channel over 350-1050 MHz, U(0, 0.5) random
+    flagging per channel): one degrid + grid pass over both partitions of
+    every channel, as one batched call pair against one call pair per
+    (channel, partition) job.  Visibility values are random (the operator's
+    time does not depend on them)."""
+    import torch
+    import synth
+    t0 = time.perf_counter()
+    w = synth.multi_channel(npix=1024, nchan=nchan, seed=11)
+    gen_s = time.perf_counter() - t0
+    plan = ms.Plan(w.u, w.v, w.npix, w.pixel_size, w.ell_px, w.delta_px, flags=w.flags,
+                   precision=precision, device=dev.index or 0)
+    del w.u, w.v
+    g = torch.Generator(device=dev).manual_seed(3)
+    jobs = [(c, p) for c in range(nchan) for p in ("L", "H")]
+    vis = {c: torch.randn(plan.nvis, dtype=plan.complex_dtype, device=dev, generator=g)
+           for c in range(nchan)}
+    imgs = [torch.randn((w.npix, w.npix), dtype=plan.real_dtype, device=dev, generator=g)
+            for _ in jobs]
+    vin = [vis[c] for c, _ in jobs]
+    vout = [torch.zeros(plan.nvis, dtype=plan.complex_dtype, device=dev) for _ in jobs]
+    dirty = [torch.empty((w.npix, w.npix), dtype=plan.real_dtype, device=dev) for _ in jobs]
+    rows = sum(plan.partition_counts(c)[p] for c, p in jobs)
+
+    def batched_pass():
+        plan.degrid_batch(jobs, imgs, vis_obs=vin, outs=vout)
+        plan.grid_batch(jobs, vout, outs=dirty)
+
+    def per_job_pass():
+        for (c, p), x, vo, o, d in zip(jobs, imgs, vin, vout, dirty):
+            plan.degrid(p, x, vo, out=o, chan=c)
+            plan.grid(p, o, out=d, chan=c)
+
+    out = {"workload": f"{nchan} channels x 1024^2, 350-1050 MHz, U(0,0.5) flagging, "
+                       f"L and H partitions of every channel ({len(jobs)} jobs)",
+           "rows_per_pass": int(rows), "precision": precision,
+           "host_uv_generation_s": round(gen_s, 1)}
+    for name, fn in (("batched", batched_pass), ("per_job", per_job_pass)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_ = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_pass": ms_, "vis_per_s": rows / (ms_ / 1000.0)}
+    # kernel time of the batched degrid + grid launches (FFT, pad, crop excluded)
+    plan.kernel_profile(reset=True)
+    plan.set_profiling(True)
+    batched_pass()
+    prof = plan.kernel_profile(reset=True)
+    plan.set_profiling(False)
+    kms = sum(prof[k][1] for k in ("degrid", "grid", "fold"))
+    out["batched"]["kernel_ms_grid_degrid"] = kms
+    out["batched"]["kernel_vis_per_s"] = rows / (kms / 1000.0)
+    out["speedup_batched_vs_per_job"] = out["per_job"]["ms_per_pass"] / out["batched"]["ms_per_pass"]
+    plan.close()
+    return out
 
 
 def _peaks():

@@ -104,9 +104,9 @@ template <typename R> __device__ __forceinline__ void two_sum(R a, R b, R& s, R&
 }
 
 // Warp sum of per-lane compensated values hi + lo in the working precision
-// (pairwise, each addition error-free up to the lo terms), converted to FP64
-// once per warp; the result is valid in lane 0.
-template <typename R> __device__ __forceinline__ double warp_sum_comp(R hi, R lo) {
+// (pairwise, each addition error-free up to the lo terms); lane 0 ends with
+// the warp's (hi, lo), which the caller converts to FP64 there only.
+template <typename R> __device__ __forceinline__ void warp_sum_comp(R& hi, R& lo) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     R h2 = __shfl_down_sync(0xffffffffu, hi, o);
@@ -116,7 +116,6 @@ template <typename R> __device__ __forceinline__ double warp_sum_comp(R hi, R lo
     hi = s;
     lo = lo + l2 + e;
   }
-  return (double)hi + (double)lo;
 }
 
 // ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1 (z = 2 t / W).

@@ -351,13 +351,14 @@ __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __re
   // only exist in the first blocks
   __shared__ double red3[3][kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double w0 = warp_sum_comp<R>(s0, -c0);
-  double w1 = warp_sum_comp<R>(s1, -c1);
+  R lo0 = -c0, lo1 = -c1;
+  warp_sum_comp<R>(s0, lo0);
+  warp_sum_comp<R>(s1, lo1);
   double w2 = 0.0;
   if ((int64_t)blockIdx.x * blockDim.x < n_l1) w2 = warp_sum(l1s);
   if (lane == 0) {
-    red3[0][warp] = w0;
-    red3[1][warp] = w1;
+    red3[0][warp] = (double)s0 + (double)lo0;
+    red3[1][warp] = (double)s1 + (double)lo1;
     red3[2][warp] = w2;
   }
   __syncthreads();

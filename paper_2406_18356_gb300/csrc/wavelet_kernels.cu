@@ -79,11 +79,30 @@ constexpr int kSubSz = 4 * kSIn * kSubS;          // one staged basis (four wind
 
 // Tile sides: large levels use big tiles (less halo), small levels smaller
 // ones so that they still spread over the SMs.
+// Tile sides and resident blocks per SM (compile-time tunables; the defaults
+// are the measured best on GB300).
+#ifndef MS_SYN_T1
+#define MS_SYN_T1 64   // synthesis output tile for n >= 512 (<= kST)
+#endif
+#ifndef MS_ANA_T1
+#define MS_ANA_T1 32   // analysis subband tile for h >= 256 (<= kAT)
+#endif
+#ifndef MS_SYN_MINB
+#define MS_SYN_MINB 2
+#endif
+#ifndef MS_ANA_MINB
+#define MS_ANA_MINB 2
+#endif
+#ifndef MS_ANA_PREFETCH
+#define MS_ANA_PREFETCH 0   // 1: stage the B_k, B_{k-1} detail tiles while filtering
+#endif
+constexpr int kPrefSz = MS_ANA_PREFETCH ? 3 * kAT * kAT : 0;   // one prefetch buffer
+static_assert(MS_SYN_T1 <= kST && MS_ANA_T1 <= kAT, "tile above the staging size");
 __host__ __device__ __forceinline__ int syn_tile(int n) {   // synthesis output side
-  return n >= 512 ? 64 : (n >= 256 ? 32 : (n >= 16 ? 16 : n));
+  return n >= 512 ? MS_SYN_T1 : (n >= 256 ? 32 : (n >= 16 ? 16 : n));
 }
 __host__ __device__ __forceinline__ int ana_tile(int h) {   // analysis subband side
-  return h >= 256 ? 32 : (h >= 16 ? 16 : h);
+  return h >= 256 ? MS_ANA_T1 : (h >= 16 ? 16 : h);
 }
 
 __device__ __forceinline__ int wrap(int i, int n) {
@@ -406,7 +425,7 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
 // one level per launch (dictionary synthesis of the API and the power
 // iteration): blockIdx.x = tile, blockIdx.y = basis
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, MS_SYN_MINB)
     synthesis_kernel(const R* const* __restrict__ coef3, const R* __restrict__ ll_in,
                      R* __restrict__ ll_out, R* __restrict__ x, int N, int j, int J, int M,
                      const FistaCtl* __restrict__ ctl) {
@@ -421,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // buffers come by value and B_k is picked by k % 3, so no pointer table is
 // read before the first load.
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, MS_SYN_MINB)
     synthesis_level_kernel(FistaPass<R> a, int j) {
   pdl_wait();
   pdl_trigger();
@@ -444,7 +463,7 @@ size_t synthesis_smem_bytes(size_t rsz) {
 // B_k and B_{k-1} detail tiles
 size_t analysis_smem_bytes(size_t rsz) {
   // + alignment slack, block-sum scratch, mbarrier and flags
-  return (size_t)(kAnaInSz + 2 * kAnaYSz + 2 * 3 * kAT * kAT) * rsz + 128 +
+  return (size_t)(kAnaInSz + 2 * kAnaYSz + 2 * kPrefSz) * rsz + 128 +
          (kThreads / 32) * sizeof(double) + sizeof(uint64_t) + 2 * sizeof(int);
 }
 }  // namespace
@@ -546,8 +565,8 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   R* ylo = sIn + kAnaInSz;                      // [kAT][kYS]
   R* yhi = ylo + kAnaYSz;
   R* sCur = yhi + kAnaYSz;                     // [3][kAT][kAT] details of B_k (16-B aligned)
-  R* sPrev = sCur + 3 * kAT * kAT;              // [3][kAT][kAT] details of B_{k-1}
-  double* red = reinterpret_cast<double*>(sPrev + 3 * kAT * kAT);   // [8]
+  R* sPrev = sCur + kPrefSz;                    // [3][kAT][kAT] details of B_{k-1}
+  double* red = reinterpret_cast<double*>(sPrev + kPrefSz);   // [8]
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
   int* flags = reinterpret_cast<int*>(bar + 1);                     // [1] TMA issued
   R* gout = sIn;
@@ -567,7 +586,7 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   using V = typename Vec<R>::T;
   const bool vec = (TO % NV) == 0;
   // cp.async prefetch of the FISTA state tiles: 16-byte rows and destination
-  const bool pre = MODE == 1 && vec && (saddr(sCur) & 15u) == 0;
+  const bool pre = MS_ANA_PREFETCH && MODE == 1 && vec && (saddr(sCur) & 15u) == 0;
   const int64_t plane = (int64_t)m * N * N;
   // coefficient-plane offset of (subband s = 1..3, row, col) of this tile
   auto coef_off = [&](int s, int row, int col) -> int64_t {
@@ -741,7 +760,7 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
 // one level per launch (dictionary analysis of the API and the power
 // iteration): blockIdx.x = tile, blockIdx.y = basis
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
     analysis_kernel(const R* __restrict__ x_in, const R* __restrict__ ll_in,
                     R* __restrict__ ll_out, R* __restrict__ out_plain, int N, int j, int J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -766,7 +785,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // leaves its sum of |B_{k+1}| over its tile in l1_parts[part_base + block];
 // the next spectral kernel adds them up (fixed order).
 template <typename R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
     analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a, int j,
                           int use_tma, int part_base) {
   pdl_wait();
@@ -784,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const R* prev = k % 3 == 0 ? a.B2 : (k % 3 == 1 ? a.B0 : a.B1);
   R* next = k % 3 == 0 ? a.B1 : (k % 3 == 1 ? a.B2 : a.B0);
   double* red = reinterpret_cast<double*>(reinterpret_cast<R*>(base) + kAnaInSz +
-                                          2 * kAnaYSz + 6 * kAT * kAT);
+                                          2 * kAnaYSz + 2 * kPrefSz);
   uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
   const bool tma = use_tma != 0 && j == 1;
   if (tma && threadIdx.x == 0) mbar_init(bar, 1);
@@ -805,8 +824,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   // block sum of |B_{k+1}|: error-free working-precision warp sums, FP64
   // once per warp
-  const double ws = warp_sum_comp<R>(l1.s, -l1.c);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ws;
+  R hi = l1.s, lo = -l1.c;
+  warp_sum_comp<R>(hi, lo);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;

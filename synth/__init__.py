@@ -250,6 +250,35 @@ def ska_mid_like(seed: int = 0, device: str = "cpu", max_rows=None) -> Workload:
         480, 8.0, 1024, 200, 20, 0.10, 3.0, 1.28e9, seed, device, max_rows=max_rows)
 
 
+def ska_low_like(seed: int = 0, nchan: int = 4, n_dumps: int = 240, span_h: float = 4.0,
+                 f_lo: float = 50e6, f_hi: float = 350e6) -> Workload:
+    """4096 x 4096, 512 stations log-radial 35 m .. 65 km, 240 dumps over 4 h,
+    4 channels over 50-350 MHz: 125,583,360 rows.  uv scale with frequency,
+    the pixel size is fixed by the top channel.  The visibilities are seeded
+    complex Gaussian values, not a sky: this workload serves operator timing
+    and precision comparisons, where only the geometry matters and every form
+    sees the same values."""
+    rng = np.random.default_rng(seed)
+    enu = layout_log_radial(512, 35.0, 65e3, rng)
+    bl = baselines(enu)
+    ha = (np.arange(n_dumps) + 0.5) / n_dumps * span_h - span_h / 2
+    u0, v0, _ = earth_rotation_uv(bl, ha * (2 * np.pi / 24.0), DEC, LAT, 1.0)
+    freqs = np.linspace(f_lo, f_hi, nchan)
+    uvmax = float(np.max(np.hypot(u0, v0))) * f_hi
+    pixel_size = 1.0 / (3.0 * uvmax)
+    u = np.stack([u0 * f for f in freqs])
+    v = np.stack([v0 * f for f in freqs])
+    buf = np.empty(u.shape + (2,))
+    rng.standard_normal(out=buf)
+    buf *= 1.0 / math.sqrt(2.0)
+    vis = buf.view(np.complex128)[..., 0]
+    npix = 4096
+    return Workload(name=f"ska-low-like-{npix}px-{u.size}vis", npix=npix,
+                    pixel_size=pixel_size, u=u, v=v, vis=vis, flags=None,
+                    truth=np.zeros((1, 1)), ell_px=0.10 * npix / 3.0, delta_px=3.0,
+                    freqs=freqs, noise_sigma=np.ones(nchan))
+
+
 def tiny(npix: int = 32, n_ant: int = 8, n_dumps: int = 6, seed: int = 1,
          device: str = "cpu", split_frac: float = 0.3, delta_px: float = 1.5,
          n_points: int = 4, n_blobs: int = 1) -> Workload:

@@ -98,17 +98,19 @@ def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
-def test_minor_cycle_128px_matches_oracle(ms, precision, tol):
-    """128-pixel image, 4 levels: the analysis input windows that fit inside
-    the image are staged by TMA, the others by wrapped loads."""
+@pytest.mark.parametrize("N", [128, 512])
+def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N):
+    """128 and 512 pixels, 4 levels.  At 512 pixels the level-1 analysis uses
+    32-wide tiles whose interior input windows are staged by TMA (edge
+    windows by wrapped loads), and synthesis uses 32- and 64-wide tiles."""
     J, M, iters = 4, 8, 12
-    w = synth.tiny(npix=128, n_ant=12, n_dumps=10, seed=11)
-    plan = ms.Plan(w.u[0], w.v[0], 128, w.pixel_size, w.ell_px, w.delta_px,
+    w = synth.tiny(npix=N, n_ant=12, n_dumps=10, seed=11)
+    plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px,
                    precision=precision, levels=J, n_bases=M)
-    A = og.GriddedOperator(w.u[0], w.v[0], 128, w.pixel_size)
+    A = og.GriddedOperator(w.u[0], w.v[0], N, w.pixel_size)
     res = A.dirty(w.vis[0])
     lam = 0.05 * np.linalg.norm(res) * 2
-    prob = osv.Problem("low", Dictionary(128, M, J), osv.psf_spectrum(A.psf()), res, lam)
+    prob = osv.Problem("low", Dictionary(N, M, J), osv.psf_spectrum(A.psf()), res, lam)
     ref = osv.fista(prob, iters)
     model, st = plan.minor_cycle("single", cuda(res).to(plan.real_dtype), lam, iters)
     np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
