@@ -59,51 +59,87 @@ template <> __device__ __forceinline__ float fg<float>(int m, int k) { return c_
 template <> __device__ __forceinline__ double fh<double>(int m, int k) { return c_hd[m][k]; }
 template <> __device__ __forceinline__ double fg<double>(int m, int k) { return c_gd[m][k]; }
 
-constexpr int kThreads = 256;
-constexpr int kP = 8;                             // outputs per thread and direction
-// analysis: output tile of 32 x 32 per subband; input tile 2*32 + 16 - 2
-constexpr int kAT = 32;
-constexpr int kAIn = 2 * kAT + kMaxTaps - 2;      // 78
-constexpr int kAInS = kAIn + 2;                   // 80: rows of the TMA box
-constexpr int kYS = kAIn + 1;                     // odd row stride of ylo / yhi
-constexpr int kGS = kAT + 4;                      // 16-byte aligned row stride of the outputs
-// region sizes rounded up to 4 elements so every region starts 16-byte aligned
-constexpr int kAnaInSz = (kAIn * kAInS + 3) / 4 * 4;
-constexpr int kAnaYSz = (kAT * kYS + 3) / 4 * 4;
-// synthesis: output tile 64 x 64; subband positions 64/2 + 16/2 - 1
-constexpr int kST = 64;
-constexpr int kSIn = kST / 2 + kMaxTaps / 2 - 1;  // 39
-constexpr int kSubS = 44;                         // staged row stride: 16-byte rows, >= 40 + 1
-constexpr int kSInS = kSIn + 2;                   // odd row stride of zlo / zhi (41)
-constexpr int kSubSz = 4 * kSIn * kSubS;          // one staged basis (four windows)
+constexpr int kP = 8;   // outputs per thread and direction
 
-// Tile sides: large levels use big tiles (less halo), small levels smaller
-// ones so that they still spread over the SMs.
-// Tile sides and resident blocks per SM (compile-time tunables; the defaults
-// are the measured best on GB300).
+__host__ __device__ constexpr int round4(int x) { return (x + 3) / 4 * 4; }
+
+// Analysis geometry for subband tiles of side AT (per block and basis): the
+// staged input window, the column-filtered rows ylo / yhi and the four output
+// subbands, which alias the window.  Region sizes are multiples of 4 elements
+// so every region starts 16-byte aligned.  Every geometry keeps 256 threads:
+// the small levels run in one wave, and there the per-block critical path
+// (not occupancy) sets the time, so more threads per tile is better.
+template <int AT> struct AG {
+  static constexpr int T = AT;
+  static constexpr int In = 2 * AT + kMaxTaps - 2;   // window side: 78, 46, 30
+  static constexpr int InS = round4(In + 2);         // window row stride: 80, 48, 32
+  static constexpr int YS = In + 1;                  // odd row stride of ylo / yhi
+  static constexpr int GS = AT + 4;                  // 16-byte row stride of the outputs
+  static constexpr int InSz = round4(In * InS);
+  static constexpr int YSz = round4(AT * YS);
+#ifndef MS_ANA_SMALL_THREADS
+  static constexpr int Threads = 256;
+#else
+  static constexpr int Threads = AT >= 32 ? 256 : MS_ANA_SMALL_THREADS;
+#endif
+  static_assert(4 * AT * GS <= InSz, "the outputs alias the input window");
+  static_assert(2 * AT * (AT / kP) <= Threads, "one thread per row unit");
+};
+// Synthesis geometry for output tiles of side ST: four staged subband windows
+// per basis (double-buffered over the bases) and the column-filtered rows.
+template <int ST> struct SG {
+  static constexpr int T = ST;
+  static constexpr int In = ST / 2 + kMaxTaps / 2 - 1;   // window side: 39, 23, 15
+  static constexpr int SubS = round4(In + 1);            // staged row stride: 40, 24, 16
+  static constexpr int ZS = In + 2;                      // odd row stride of zlo / zhi
+  static constexpr int SubSz = 4 * In * SubS;            // one staged basis
+#ifndef MS_SYN_SMALL_THREADS
+  static constexpr int Threads = 256;
+#else
+  static constexpr int Threads = ST >= 64 ? 256 : MS_SYN_SMALL_THREADS;
+#endif
+  static constexpr int Q = (ST * (ST / kP) + Threads - 1) / Threads;   // row units per thread
+};
+// the widest tiles (level 1 at N >= 512); the TMA box of the level-1 window
+constexpr int kAT = 32;
+constexpr int kST = 64;
+
+// Tile sides (compile-time tunables; the defaults are the measured best on
+// GB300): large levels use wide tiles (less halo), small levels narrow ones
+// with small blocks so that they still fill the SMs.
 #ifndef MS_SYN_T1
 #define MS_SYN_T1 64   // synthesis output tile for n >= 512 (<= kST)
+#endif
+#ifndef MS_SYN_T2
+#define MS_SYN_T2 32   // synthesis output tile for 256 <= n < 512
+#endif
+#ifndef MS_SYN_T3
+#define MS_SYN_T3 16   // synthesis output tile for 16 <= n < 256
 #endif
 #ifndef MS_ANA_T1
 #define MS_ANA_T1 32   // analysis subband tile for h >= 256 (<= kAT)
 #endif
-#ifndef MS_SYN_MINB
-#define MS_SYN_MINB 2
+#ifndef MS_ANA_T2
+#define MS_ANA_T2 16   // analysis subband tile for 128 <= h < 256
 #endif
-#ifndef MS_ANA_MINB
-#define MS_ANA_MINB 2
-#endif
-#ifndef MS_ANA_PREFETCH
-#define MS_ANA_PREFETCH 0   // 1: stage the B_k, B_{k-1} detail tiles while filtering
-#endif
-constexpr int kPrefSz = MS_ANA_PREFETCH ? 3 * kAT * kAT : 0;   // one prefetch buffer
-static_assert(MS_SYN_T1 <= kST && MS_ANA_T1 <= kAT, "tile above the staging size");
+static_assert(MS_SYN_T1 <= kST && MS_SYN_T2 <= kST && MS_SYN_T3 <= kST, "synthesis tile");
+static_assert(MS_ANA_T1 <= kAT && MS_ANA_T2 <= kAT, "analysis tile");
+// The largest power of two <= the preferred side that divides the level's
+// side (sides need not be powers of two: N = 48 gives 48, 24, 12, 6).
+__host__ __device__ __forceinline__ int fit_tile(int t, int n) {
+  int p = 1;
+  while (2 * p <= t && n % (2 * p) == 0) p *= 2;
+  return p;
+}
 __host__ __device__ __forceinline__ int syn_tile(int n) {   // synthesis output side
-  return n >= 512 ? MS_SYN_T1 : (n >= 256 ? 32 : (n >= 16 ? 16 : n));
+  return fit_tile(n >= 512 ? MS_SYN_T1 : (n >= 256 ? MS_SYN_T2 : MS_SYN_T3), n);
 }
 __host__ __device__ __forceinline__ int ana_tile(int h) {   // analysis subband side
-  return h >= 256 ? MS_ANA_T1 : (h >= 16 ? 16 : h);
+  return fit_tile(h >= 256 ? MS_ANA_T1 : (h >= 128 ? MS_ANA_T2 : 16), h);
 }
+// geometry (template argument) serving a tile side
+__host__ __device__ __forceinline__ int syn_geom(int TS) { return TS >= 64 ? 64 : (TS >= 32 ? 32 : 16); }
+__host__ __device__ __forceinline__ int ana_geom(int TO) { return TO >= 32 ? 32 : (TO >= 16 ? 16 : 8); }
 
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
@@ -236,14 +272,15 @@ template <> struct Vec<double> { using T = double2; static constexpr int N = 2; 
 // its approximation from the coefficient planes, lower levels from the LL
 // buffer written by the level above.  Level 1 sums the M bases into x, with
 // the next basis's windows prefetched by cp.async while the current one is
-// filtered.
+// filtered.  G = SG<ST> is the geometry serving the level's tile side.
+
 // Stages the four subband windows of one basis: rows from r0/2 - 7, columns
 // from c0/2 - 8 (one column before the filter's first, so that in the image's
 // interior each window row starts on a 16-byte boundary and is copied in
 // whole 16-byte chunks); rows always, columns near the edges, wrap
-// periodically.  Window element (a, b) of subband s is at
-// sub[s][a][b] with b = column - (c0/2 - 8).
-template <typename R>
+// periodically.  Window element (a, b) of subband s is at sub[s][a][b] with
+// b = column - (c0/2 - 8).
+template <typename R, class G>
 __device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N, int h, int r0,
                                             int c0, int cnt, R* sub) {
   const int base_r = r0 / 2 - (kMaxTaps / 2 - 1), base_c = c0 / 2 - kMaxTaps / 2;
@@ -254,7 +291,7 @@ __device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N,
   const bool cheap = h >= kMaxTaps / 2;
   if (base_c >= 0 && base_c + nch * V <= h) {
     const int per_sub = cnt * nch;
-    for (int e = threadIdx.x; e < 4 * per_sub; e += kThreads) {
+    for (int e = threadIdx.x; e < 4 * per_sub; e += G::Threads) {
       const int sb = e / per_sub, rem = e - sb * per_sub;
       const int a = rem / nch, c = rem - a * nch;
       const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
@@ -268,27 +305,28 @@ __device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N,
         src = plane + (int64_t)(h + iy) * N + ix;
       else
         src = plane + (int64_t)(h + iy) * N + h + ix;
-      cp_async<16>(sub + (sb * kSIn + a) * kSubS + c * V, src);
+      cp_async<16>(sub + (sb * G::In + a) * G::SubS + c * V, src);
     }
     return;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int a = warp; a < cnt; a += kThreads / 32) {
+  constexpr int NW = G::Threads / 32;
+  for (int a = warp; a < cnt; a += NW) {
     const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
     for (int b = lane; b < ncol; b += 32) {
       const int ix = cheap ? wrapc(base_c + b, h) : wrap(base_c + b, h);
-      R* d = sub + a * kSubS + b;
+      R* d = sub + a * G::SubS + b;
       cp_async<sizeof(R)>(d, llp ? llp + (int64_t)iy * h + ix : plane + (int64_t)iy * N + ix);
-      cp_async<sizeof(R)>(d + kSIn * kSubS, plane + (int64_t)iy * N + h + ix);
-      cp_async<sizeof(R)>(d + 2 * kSIn * kSubS, plane + (int64_t)(h + iy) * N + ix);
-      cp_async<sizeof(R)>(d + 3 * kSIn * kSubS, plane + (int64_t)(h + iy) * N + h + ix);
+      cp_async<sizeof(R)>(d + G::In * G::SubS, plane + (int64_t)iy * N + h + ix);
+      cp_async<sizeof(R)>(d + 2 * G::In * G::SubS, plane + (int64_t)(h + iy) * N + ix);
+      cp_async<sizeof(R)>(d + 3 * G::In * G::SubS, plane + (int64_t)(h + iy) * N + h + ix);
     }
   }
 }
 
-template <typename R, int MB>
+template <typename R, int MB, class G>
 __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, int c0,
-                                            const R* sub, R* zlo, R* zhi, R (&acc)[2][kP],
+                                            const R* sub, R* zlo, R* zhi, R (&acc)[G::Q][kP],
                                             bool sum_bases, R* ll_out, int n) {
   constexpr int L = 2 * (MB + 1);
   constexpr int NI = L / 2 + 3;
@@ -297,38 +335,39 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
   // high-y/low-x), pair 1 -> zhi from (low-y/high-x, high/high)
   const int nseg = TS / kP > 0 ? TS / kP : 1;
   const int units_a = cnt * 2 * nseg;
-  for (int u = tid; u < units_a; u += kThreads) {
+  for (int u = tid; u < units_a; u += G::Threads) {
     int rest = u / cnt;
     int b = u - rest * cnt;
     int pair = rest & 1, seg = rest >> 1;
     // window column b + 1 is filter column b (the window starts one early)
-    const R* s0 = sub + (pair ? 1 : 0) * kSIn * kSubS + 1;
-    const R* s1 = sub + (pair ? 3 : 2) * kSIn * kSubS + 1;
+    const R* s0 = sub + (pair ? 1 : 0) * G::In * G::SubS + 1;
+    const R* s1 = sub + (pair ? 3 : 2) * G::In * G::SubS + 1;
     const int first = 4 * seg + 8 - L / 2;
     R lo[NI], hi[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-      lo[i] = s0[(first + i) * kSubS + b];
-      hi[i] = s1[(first + i) * kSubS + b];
+      lo[i] = s0[(first + i) * G::SubS + b];
+      hi[i] = s1[(first + i) * G::SubS + b];
     }
     R out[kP];
     fir_up8<R, MB>(lo, hi, out);
     R* z = pair ? zhi : zlo;
 #pragma unroll
-    for (int r = 0; r < kP; ++r) z[(kP * seg + r) * kSInS + b] = out[r];
+    for (int r = 0; r < kP; ++r) z[(kP * seg + r) * G::ZS + b] = out[r];
   }
   __syncthreads();
   // rows (x): units (r, seg), a warp takes consecutive rows of one segment
-  for (int q = 0; q < 2; ++q) {
-    int u = tid + q * kThreads;
+#pragma unroll
+  for (int q = 0; q < G::Q; ++q) {
+    int u = tid + q * G::Threads;
     int r = u & (TS - 1), seg = u >> lts;
     if (seg >= nseg) continue;
     const int first = 4 * seg + 8 - L / 2;
     R lo[NI], hi[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
-      lo[i] = zlo[r * kSInS + first + i];
-      hi[i] = zhi[r * kSInS + first + i];
+      lo[i] = zlo[r * G::ZS + first + i];
+      hi[i] = zhi[r * G::ZS + first + i];
     }
     R out[kP];
     fir_up8<R, MB>(lo, hi, out);
@@ -347,14 +386,14 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
 // One synthesis work item: output tile `tile` of level j for basis mb
 // (level 1: all bases summed into x).  Ends with a block barrier, so the
 // caller may reuse the shared buffers.
-template <typename R>
+template <typename R, class G>
 __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __restrict__ coef,
                                            const R* __restrict__ ll_in, R* __restrict__ ll_out,
                                            R* __restrict__ x, int N, int j, int J, int M,
                                            int tile, int mb) {
-  R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][kSIn][kSubS]
-  R* zlo = subs + 2 * kSubSz;                         // [kST][kSInS]
-  R* zhi = zlo + kST * kSInS;
+  R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][G::In][G::SubS]
+  R* zlo = subs + 2 * G::SubSz;                       // [G::T][G::ZS]
+  R* zhi = zlo + G::T * G::ZS;
   const int h = N >> j, n = 2 * h;
   const int TS = syn_tile(n);
   const int lts = 31 - __clz(TS);
@@ -363,15 +402,15 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
   const int r0 = (tile / tiles_x) * TS, c0 = (tile % tiles_x) * TS;
   const bool sum_bases = (j == 1);
   const int m_lo = sum_bases ? 0 : mb, m_hi = sum_bases ? M : mb + 1;
-  R acc[2][kP];
+  R acc[G::Q][kP];
 #pragma unroll
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < G::Q; ++q)
 #pragma unroll
     for (int cc = 0; cc < kP; ++cc) acc[q][cc] = (R)0;
   auto stage = [&](int m) {
     const R* plane = coef + (int64_t)m * N * N;
     const R* llp = (j == J) ? nullptr : ll_in + (int64_t)m * h * h;
-    synth_stage<R>(plane, llp, N, h, r0, c0, cnt, subs + (m & 1) * kSubSz);
+    synth_stage<R, G>(plane, llp, N, h, r0, c0, cnt, subs + (m & 1) * G::SubSz);
     cp_async_commit();
   };
   stage(m_lo);
@@ -383,12 +422,12 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
       cp_async_wait<0>();
     }
     __syncthreads();
-    const R* sub = subs + (m & 1) * kSubSz;
+    const R* sub = subs + (m & 1) * G::SubSz;
     R* llo = sum_bases ? nullptr : ll_out + (int64_t)m * n * n;
     switch (m) {
-#define MS_SYN(MBV)                                                                    \
-  case MBV:                                                                            \
-    synth_basis<R, MBV>(TS, lts, cnt, r0, c0, sub, zlo, zhi, acc, sum_bases, llo, n);  \
+#define MS_SYN(MBV)                                                                       \
+  case MBV:                                                                               \
+    synth_basis<R, MBV, G>(TS, lts, cnt, r0, c0, sub, zlo, zhi, acc, sum_bases, llo, n);  \
     break;
       MS_SYN(0) MS_SYN(1) MS_SYN(2) MS_SYN(3) MS_SYN(4) MS_SYN(5) MS_SYN(6) MS_SYN(7)
 #undef MS_SYN
@@ -397,8 +436,9 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
   }
   if (sum_bases) {
     const int nseg = TS / kP > 0 ? TS / kP : 1;
-    for (int q = 0; q < 2; ++q) {
-      int u = threadIdx.x + q * kThreads;
+#pragma unroll
+    for (int q = 0; q < G::Q; ++q) {
+      int u = threadIdx.x + q * G::Threads;
       int r = u & (TS - 1), seg = u >> lts;
       if (seg >= nseg) continue;
       R* dst = x + (int64_t)(r0 + r) * N + c0 + kP * seg;
@@ -424,23 +464,23 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
 
 // one level per launch (dictionary synthesis of the API and the power
 // iteration): blockIdx.x = tile, blockIdx.y = basis
-template <typename R>
-__global__ void __launch_bounds__(kThreads, MS_SYN_MINB)
+template <typename R, int ST>
+__global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
     synthesis_kernel(const R* const* __restrict__ coef3, const R* __restrict__ ll_in,
                      R* __restrict__ ll_out, R* __restrict__ x, int N, int j, int J, int M,
                      const FistaCtl* __restrict__ ctl) {
   if (ctl && ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const R* coef = coef3[ctl ? (ctl->k % 3) : 0];
-  synth_item<R>(smem_raw, coef, ll_in, ll_out, x, N, j, J, M, blockIdx.x, blockIdx.y);
+  synth_item<R, SG<ST>>(smem_raw, coef, ll_in, ll_out, x, N, j, J, M, blockIdx.x, blockIdx.y);
 }
 
 // Level j of the minor cycle's synthesis x = W B_k: blockIdx.x = output
 // tile, blockIdx.y = basis (level 1: one block per tile sums all bases).  The
 // buffers come by value and B_k is picked by k % 3, so no pointer table is
 // read before the first load.
-template <typename R>
-__global__ void __launch_bounds__(kThreads, MS_SYN_MINB)
+template <typename R, int ST>
+__global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
     synthesis_level_kernel(FistaPass<R> a, int j) {
   pdl_wait();
   pdl_trigger();
@@ -452,28 +492,25 @@ __global__ void __launch_bounds__(kThreads, MS_SYN_MINB)
   const int64_t half = (int64_t)a.M * (a.N / 2) * (a.N / 2);
   const R* ll_in = (j == a.J) ? nullptr : a.tmp + ((j + 1) & 1) * half;
   R* ll_out = a.tmp + (j & 1) * half;
-  synth_item<R>(smem_raw, coef, ll_in, ll_out, a.x, a.N, j, a.J, a.M, blockIdx.x, blockIdx.y);
+  synth_item<R, SG<ST>>(smem_raw, coef, ll_in, ll_out, a.x, a.N, j, a.J, a.M, blockIdx.x,
+                        blockIdx.y);
 }
 
 namespace {
-size_t synthesis_smem_bytes(size_t rsz) {
-  return (size_t)(2 * kSubSz + 2 * kST * kSInS) * rsz;
+template <int ST> size_t synthesis_smem_bytes(size_t rsz) {
+  return (size_t)(2 * SG<ST>::SubSz + 2 * SG<ST>::T * SG<ST>::ZS) * rsz;
 }
-// input tile (the four output subbands alias it), ylo / yhi, prefetched
-// B_k and B_{k-1} detail tiles
-size_t analysis_smem_bytes(size_t rsz) {
-  // + alignment slack, block-sum scratch, mbarrier and flags
-  return (size_t)(kAnaInSz + 2 * kAnaYSz + 2 * kPrefSz) * rsz + 128 +
-         (kThreads / 32) * sizeof(double) + sizeof(uint64_t) + 2 * sizeof(int);
+// the four output subbands alias the input window; + alignment slack,
+// block-sum scratch, mbarrier and flags
+template <int AT> size_t analysis_smem_bytes(size_t rsz) {
+  return (size_t)(AG<AT>::InSz + 2 * AG<AT>::YSz) * rsz + 128 +
+         (AG<AT>::Threads / 32) * sizeof(double) + sizeof(uint64_t) + 2 * sizeof(int);
 }
 }  // namespace
 
 template <typename R>
 void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
                        const FistaCtl* ctl, cudaStream_t s, int only_level) {
-  const size_t smem = synthesis_smem_bytes(sizeof(R));
-  auto k = synthesis_kernel<R>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
   for (int j = g.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
@@ -483,16 +520,24 @@ void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
     const R* ll_in = (j == g.J) ? nullptr : tmp + ((j + 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
     dim3 grid(tiles, j == 1 ? 1 : g.M);
-    k<<<grid, kThreads, smem, s>>>(coef3_dev, ll_in, ll_out, x, g.N, j, g.J, g.M, ctl);
+    auto go = [&](auto kern, int threads, size_t smem) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<grid, threads, smem, s>>>(coef3_dev, ll_in, ll_out, x, g.N, j, g.J, g.M, ctl);
+    };
+    switch (syn_geom(TS)) {
+      case 64: go(synthesis_kernel<R, 64>, SG<64>::Threads, synthesis_smem_bytes<64>(sizeof(R))); break;
+      case 32: go(synthesis_kernel<R, 32>, SG<32>::Threads, synthesis_smem_bytes<32>(sizeof(R))); break;
+      default: go(synthesis_kernel<R, 16>, SG<16>::Threads, synthesis_smem_bytes<16>(sizeof(R))); break;
+    }
   }
 }
 
 // ------------------------------------------------------------------ analysis
 // Filtering of one basis on the staged input tile: columns (y) into
 // ylo / yhi, then rows (x) into the four subbands gout[0..3] =
-// (approximation, low-y/high-x, high-y/low-x, high/high), 32 x kGS each.
-// TOe (a power of two, 8..32) outputs per subband side, lt = log2(TOe).
-template <typename R, int MB>
+// (approximation, low-y/high-x, high-y/low-x, high/high), G::T x G::GS each.
+// TOe (a power of two, 8..G::T) outputs per subband side, lt = log2(TOe).
+template <typename R, int MB, class G>
 __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R* gout, int TOe,
                                                 int lt) {
   constexpr int L = 2 * (MB + 1);
@@ -500,18 +545,18 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   const int tid = threadIdx.x;
   const int nparts = TOe >> 3;
   const int cols = 2 * TOe + L - 2;
-  for (int u = tid; u < nparts * cols; u += kThreads) {
+  for (int u = tid; u < nparts * cols; u += G::Threads) {
     int part = u / cols;
     int col = u - part * cols;
     R xin[NI];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) xin[i] = sIn[(2 * kP * part + i) * kAInS + col];
+    for (int i = 0; i < NI; ++i) xin[i] = sIn[(2 * kP * part + i) * G::InS + col];
     R lo[kP], hi[kP];
     fir_down8<R, MB>(xin, lo, hi);
 #pragma unroll
     for (int r = 0; r < kP; ++r) {
-      ylo[(kP * part + r) * kYS + col] = lo[r];
-      yhi[(kP * part + r) * kYS + col] = hi[r];
+      ylo[(kP * part + r) * G::YS + col] = lo[r];
+      yhi[(kP * part + r) * G::YS + col] = hi[r];
     }
   }
   __syncthreads();
@@ -522,7 +567,7 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   const bool active = src < 2;
   R xin[NI];
   if (active) {
-    const R* yrow = (src ? yhi : ylo) + r * kYS + 2 * kP * seg;
+    const R* yrow = (src ? yhi : ylo) + r * G::YS + 2 * kP * seg;
 #pragma unroll
     for (int i = 0; i < NI; ++i) xin[i] = yrow[i];
   }
@@ -530,8 +575,8 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   if (!active) return;
   R lo[kP], hi[kP];
   fir_down8<R, MB>(xin, lo, hi);
-  R* o_lo = gout + (src ? 2 : 0) * kAT * kGS + r * kGS + kP * seg;
-  R* o_hi = gout + (src ? 3 : 1) * kAT * kGS + r * kGS + kP * seg;
+  R* o_lo = gout + (src ? 2 : 0) * G::T * G::GS + r * G::GS + kP * seg;
+  R* o_hi = gout + (src ? 3 : 1) * G::T * G::GS + r * G::GS + kP * seg;
   using V = typename Vec<R>::T;
   constexpr int NV = Vec<R>::N;
 #pragma unroll
@@ -541,19 +586,36 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   }
 }
 
-// One analysis work item: subband tile `tile` (of side TO) of level j for
-// basis m.  n = N >> (j-1) is the input side, h = n/2 the subband side.
+// shared-memory layout of an analysis block (after the 128-byte alignment)
+template <typename R, class G> struct AnaSmem {
+  R* sIn;        // [G::In][G::InS]; later the outputs [4][G::T][G::GS]
+  R* ylo;        // [G::T][G::YS]
+  R* yhi;
+  double* red;   // [G::Threads / 32]
+  uint64_t* bar;
+  int* flags;    // [2]
+  __device__ __forceinline__ explicit AnaSmem(unsigned char* base) {
+    sIn = reinterpret_cast<R*>(base);
+    ylo = sIn + G::InSz;
+    yhi = ylo + G::YSz;
+    red = reinterpret_cast<double*>(yhi + G::YSz);
+    bar = reinterpret_cast<uint64_t*>(red + G::Threads / 32);
+    flags = reinterpret_cast<int*>(bar + 1);
+  }
+};
+
+// One analysis work item: subband tile `tile` (of side TO <= G::T) of level
+// j for basis MB.  n = N >> (j-1) is the input side, h = n/2 the subband side.
 // MODE 0: plain analysis (W^H x); input x (level 1) or LL_{j-1}.
 // MODE 1: FISTA step; level 1 input is the gradient image 2 (K W alpha_k - b);
 //         detail (and level-J approximation) outputs go through the prox into
 //         B_{k+1} and |B_{k+1}| accumulates into l1.
-// Level 1 stages its 78 x 78 input window by one TMA tensor copy when the
-// window lies inside the image (the caller has initialized the mbarrier and
-// tracks its phase); other windows are staged by cp.async with periodic wrap.
-// The basis MB is a template parameter, so a block's loop over tiles of one
-// basis keeps the filter taps as compile-time constant-bank operands.
-// Ends with a block barrier, so the caller may reuse the shared buffers.
-template <typename R, int MODE, int MB>
+// With the widest geometry, level 1 stages its 78 x 78 input window by one
+// TMA tensor copy when the window lies inside the image (the caller has
+// initialized the mbarrier and tracks its phase); other windows are staged by
+// cp.async with periodic wrap.  Ends with a block barrier, so the caller may
+// reuse the shared buffers.
+template <typename R, int MODE, int MB, class G>
 __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtensorMap* xmap,
                                               bool use_tma, unsigned& phase, const R* x_in,
                                               const R* ll_in, R* ll_out, R* out_plain,
@@ -561,16 +623,9 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
                                               R thr, int N, int j, int J, int tile,
                                               FistaCtl* ctl, KSum<R>& l1) {
   constexpr int m = MB;
-  R* sIn = reinterpret_cast<R*>(base);         // [kAIn][kAInS]; later gout [4][kAT][kGS]
-  R* ylo = sIn + kAnaInSz;                      // [kAT][kYS]
-  R* yhi = ylo + kAnaYSz;
-  R* sCur = yhi + kAnaYSz;                     // [3][kAT][kAT] details of B_k (16-B aligned)
-  R* sPrev = sCur + kPrefSz;                    // [3][kAT][kAT] details of B_{k-1}
-  double* red = reinterpret_cast<double*>(sPrev + kPrefSz);   // [8]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
-  int* flags = reinterpret_cast<int*>(bar + 1);                     // [1] TMA issued
+  const AnaSmem<R, G> sm(base);
+  R* sIn = sm.sIn;
   R* gout = sIn;
-  (void)red;
 
   const int n = N >> (j - 1), h = n / 2;
   const int TO = ana_tile(h);
@@ -585,8 +640,6 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   constexpr int LNV = NV == 4 ? 2 : 1;
   using V = typename Vec<R>::T;
   const bool vec = (TO % NV) == 0;
-  // cp.async prefetch of the FISTA state tiles: 16-byte rows and destination
-  const bool pre = MS_ANA_PREFETCH && MODE == 1 && vec && (saddr(sCur) & 15u) == 0;
   const int64_t plane = (int64_t)m * N * N;
   // coefficient-plane offset of (subband s = 1..3, row, col) of this tile
   auto coef_off = [&](int s, int row, int col) -> int64_t {
@@ -599,66 +652,53 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   // shared destination, 64-byte descriptor, 16-byte start column); a
   // violation is recorded in ctl->error (MS_ERR_UNSUPPORTED) and the window
   // is staged by cp.async instead.
-  bool tma = use_tma && j == 1 && TO == kAT && p0x + kAInS <= n && p0y + kAIn <= n;
+  bool tma = G::T == kAT && use_tma && j == 1 && TO == kAT && p0x + G::InS <= n &&
+             p0y + G::In <= n;
   if (tma) {
     if (threadIdx.x == 0) {
       const bool aligned = (saddr(sIn) & 127u) == 0 &&
                            (reinterpret_cast<uintptr_t>(xmap) & 63u) == 0 &&
                            ((p0x * (int)sizeof(R)) & 15) == 0;
-      flags[1] = aligned ? 1 : 0;
+      sm.flags[1] = aligned ? 1 : 0;
       if (aligned) {
         // order the block's earlier generic accesses of the window before
         // the asynchronous copy overwrites it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, (unsigned)(kAIn * kAInS * sizeof(R)));
-        tma_load_2d(sIn, xmap, p0x, p0y, bar);
+        mbar_expect_tx(sm.bar, (unsigned)(G::In * G::InS * sizeof(R)));
+        tma_load_2d(sIn, xmap, p0x, p0y, sm.bar);
       } else if (ctl) {
         atomicExch(&ctl->error, 8);
       }
     }
     __syncthreads();
-    tma = flags[1] != 0;
+    tma = sm.flags[1] != 0;
   }
 
   if (!tma) {
-    // stage the input window with periodic wrap (first cp.async group)
+    // stage the input window with periodic wrap
     const R* src = (j == 1) ? x_in : ll_in + (int64_t)m * n * n;
     const bool cheap = n >= ext;   // positions lie in [0, n + ext)
-    constexpr int V = 16 / (int)sizeof(R);
-    const int nch = (ext + V - 1) / V;
-    if (p0x + nch * V <= n && (n % V) == 0) {
+    constexpr int V16 = 16 / (int)sizeof(R);
+    const int nch = (ext + V16 - 1) / V16;
+    if (p0x + nch * V16 <= n && (n % V16) == 0) {
       // the window's columns need no wrap: whole 16-byte chunks per row
       // (p0x = 2 o0x is a multiple of 16), rows wrap
-      for (int e = threadIdx.x; e < ext * nch; e += kThreads) {
+      for (int e = threadIdx.x; e < ext * nch; e += G::Threads) {
         const int a = e / nch, c = e - a * nch;
         const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
-        cp_async<16>(sIn + a * kAInS + c * V, src + (int64_t)py * n + p0x + c * V);
+        cp_async<16>(sIn + a * G::InS + c * V16, src + (int64_t)py * n + p0x + c * V16);
       }
     } else {
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      for (int a = warp; a < ext; a += kThreads / 32) {
+      constexpr int NW = G::Threads / 32;
+      for (int a = warp; a < ext; a += NW) {
         const int py = cheap ? wrapc(p0y + a, n) : wrap(p0y + a, n);
         const R* row = src + (int64_t)py * n;
         for (int b = lane; b < ext; b += 32) {
           const int px = cheap ? wrapc(p0x + b, n) : wrap(p0x + b, n);
-          cp_async<sizeof(R)>(sIn + a * kAInS + b, row + px);
+          cp_async<sizeof(R)>(sIn + a * G::InS + b, row + px);
         }
       }
-    }
-    cp_async_commit();
-  }
-
-  const int lpr = lto - LNV;   // log2(vectors per tile row)
-  if (pre) {   // prefetch the detail tiles of B_k and B_{k-1} (next group)
-    const int per_sub = 1 << (lto + lpr);
-    for (int e = threadIdx.x; e < 3 * per_sub; e += kThreads) {
-      int s = 1 + (e >> (lto + lpr));
-      int rem = e & (per_sub - 1);
-      int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
-      int64_t g = coef_off(s, row, c4);
-      int so = ((s - 1) * kAT + row) * kAT + c4;
-      cp_async<16>(sCur + so, cur + g);
-      cp_async<16>(sPrev + so, prev + g);
     }
     cp_async_commit();
   }
@@ -667,23 +707,20 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   if (tma) {
     // bounded wait for the window; on time-out the tile is skipped (the
     // error is recorded) but every barrier is still passed
-    const bool ok = mbar_wait_bounded(bar, phase);
+    const bool ok = mbar_wait_bounded(sm.bar, phase);
     phase ^= 1u;
     skip = __syncthreads_or(!ok) != 0;
     if (skip && threadIdx.x == 0 && ctl) atomicExch(&ctl->error, 5);
-  } else if (pre) {
-    cp_async_wait<1>();   // the window; the prefetch may still be in flight
   } else {
     cp_async_wait<0>();
   }
   __syncthreads();
   if (!skip) {
-    analysis_filter<R, MB>(sIn, ylo, yhi, gout, TOe, lt);
+    analysis_filter<R, MB, G>(sIn, sm.ylo, sm.yhi, gout, TOe, lt);
   } else {
     __syncthreads();   // the filter's two barriers
     __syncthreads();
   }
-  if (pre) cp_async_wait<0>();
   __syncthreads();
 
   // write / update the tile's coefficients
@@ -698,27 +735,21 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
   if (skip) {
     // nothing is written for a tile whose window never arrived
   } else if (vec) {
+    const int lpr = lto - LNV;    // log2(vectors per tile row)
     const int s_first = (j == J) ? 0 : 1;
     const int lsub = lto + lpr;   // log2(vectors per subband tile)
     const int items = (4 - s_first) << lsub;
-    for (int e = threadIdx.x; e < items; e += kThreads) {
+    for (int e = threadIdx.x; e < items; e += G::Threads) {
       int s = s_first + (e >> lsub);
       int rem = e & ((1 << lsub) - 1);
       int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
-      V gv = *reinterpret_cast<const V*>(gout + (s * kAT + row) * kGS + c4);
+      V gv = *reinterpret_cast<const V*>(gout + (s * G::T + row) * G::GS + c4);
       int64_t off = s ? coef_off(s, row, c4) : plane + (int64_t)(o0y + row) * N + o0x + c4;
       if (MODE == 0) {
         *reinterpret_cast<V*>(out_plain + off) = gv;
       } else {
-        V cv, pv;
-        if (s && pre) {
-          int so = ((s - 1) * kAT + row) * kAT + c4;
-          cv = *reinterpret_cast<const V*>(sCur + so);
-          pv = *reinterpret_cast<const V*>(sPrev + so);
-        } else {
-          cv = *reinterpret_cast<const V*>(cur + off);
-          pv = *reinterpret_cast<const V*>(prev + off);
-        }
+        V cv = *reinterpret_cast<const V*>(cur + off);
+        V pv = *reinterpret_cast<const V*>(prev + off);
         V nv;
         R* np = reinterpret_cast<R*>(&nv);
         const R* gp = reinterpret_cast<const R*>(&gv);
@@ -730,18 +761,18 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
       }
     }
     if (j < J) {   // approximation feeds the next level
-      for (int e = threadIdx.x; e < (1 << lsub); e += kThreads) {
+      for (int e = threadIdx.x; e < (1 << lsub); e += G::Threads) {
         int row = e >> lpr, c4 = (e & ((1 << lpr) - 1)) << LNV;
         *reinterpret_cast<V*>(ll_out + (int64_t)m * h * h + (int64_t)(o0y + row) * h + o0x + c4) =
-            *reinterpret_cast<const V*>(gout + row * kGS + c4);
+            *reinterpret_cast<const V*>(gout + row * G::GS + c4);
       }
     }
   } else {   // tiny levels: scalar path
     const int s_first = (j == J) ? 0 : 1;
-    for (int e = threadIdx.x; e < 4 * TO * TO; e += kThreads) {
+    for (int e = threadIdx.x; e < 4 * TO * TO; e += G::Threads) {
       int s = e / (TO * TO);
       int row = (e / TO) % TO, col = e % TO;
-      R gval = gout[(s * kAT + row) * kGS + col];
+      R gval = gout[(s * G::T + row) * G::GS + col];
       if (s == 0 && j < J) {
         ll_out[(int64_t)m * h * h + (int64_t)(o0y + row) * h + o0x + col] = gval;
         continue;
@@ -759,8 +790,8 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
 
 // one level per launch (dictionary analysis of the API and the power
 // iteration): blockIdx.x = tile, blockIdx.y = basis
-template <typename R>
-__global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
+template <typename R, int AT>
+__global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
     analysis_kernel(const R* __restrict__ x_in, const R* __restrict__ ll_in,
                     R* __restrict__ ll_out, R* __restrict__ out_plain, int N, int j, int J) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -768,11 +799,11 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
   unsigned phase = 0;
   KSum<R> l1;
   switch (blockIdx.y) {
-#define MS_ANA(MBV)                                                                         \
-  case MBV:                                                                                 \
-    analysis_item<R, 0, MBV>(base, nullptr, false, phase, x_in, ll_in, ll_out, out_plain,   \
-                             nullptr, nullptr, nullptr, (R)0, (R)0, (R)0, N, j, J,          \
-                             blockIdx.x, nullptr, l1);                                      \
+#define MS_ANA(MBV)                                                                             \
+  case MBV:                                                                                     \
+    analysis_item<R, 0, MBV, AG<AT>>(base, nullptr, false, phase, x_in, ll_in, ll_out,          \
+                                     out_plain, nullptr, nullptr, nullptr, (R)0, (R)0, (R)0, N, \
+                                     j, J, blockIdx.x, nullptr, l1);                            \
     break;
     MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
 #undef MS_ANA
@@ -784,10 +815,11 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
 // advanced ctl->k, so this builds B_{k+1} with k = ctl->k - 1.  Each block
 // leaves its sum of |B_{k+1}| over its tile in l1_parts[part_base + block];
 // the next spectral kernel adds them up (fixed order).
-template <typename R>
-__global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
+template <typename R, int AT>
+__global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
     analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a, int j,
                           int use_tma, int part_base) {
+  using G = AG<AT>;
   pdl_wait();
   pdl_trigger();
   const int done = a.ctl->done;
@@ -795,6 +827,7 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
   if (done) return;   // uniform: `done` does not change during this kernel
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_align128(smem_raw);
+  const AnaSmem<R, G> sm(base);
   const int k = kc - 1;
   const R t = ctl_t<R>(a.ctl, k & 1);   // momentum t_k
   const R mu = ctl_mu<R>(a.ctl);        // 1 / theta
@@ -802,11 +835,8 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
   const R* cur = k % 3 == 0 ? a.B0 : (k % 3 == 1 ? a.B1 : a.B2);
   const R* prev = k % 3 == 0 ? a.B2 : (k % 3 == 1 ? a.B0 : a.B1);
   R* next = k % 3 == 0 ? a.B1 : (k % 3 == 1 ? a.B2 : a.B0);
-  double* red = reinterpret_cast<double*>(reinterpret_cast<R*>(base) + kAnaInSz +
-                                          2 * kAnaYSz + 2 * kPrefSz);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(red + kThreads / 32);
-  const bool tma = use_tma != 0 && j == 1;
-  if (tma && threadIdx.x == 0) mbar_init(bar, 1);
+  const bool tma = G::T == kAT && use_tma != 0 && j == 1;
+  if (tma && threadIdx.x == 0) mbar_init(sm.bar, 1);
   __syncthreads();
   unsigned phase = 0;
   KSum<R> l1;
@@ -814,10 +844,10 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
   const R* ll_in = (j == 1) ? nullptr : a.tmp + ((j - 1) & 1) * half;
   R* ll_out = a.tmp + (j & 1) * half;
   switch (blockIdx.y) {
-#define MS_ANA(MBV)                                                                             \
-  case MBV:                                                                                     \
-    analysis_item<R, 1, MBV>(base, &xmap, tma, phase, a.grad, ll_in, ll_out, nullptr, cur, prev, \
-                             next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1);             \
+#define MS_ANA(MBV)                                                                          \
+  case MBV:                                                                                  \
+    analysis_item<R, 1, MBV, G>(base, &xmap, tma, phase, a.grad, ll_in, ll_out, nullptr, cur, \
+                                prev, next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1);  \
     break;
     MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
 #undef MS_ANA
@@ -826,11 +856,11 @@ __global__ void __launch_bounds__(kThreads, MS_ANA_MINB)
   // once per warp
   R hi = l1.s, lo = -l1.c;
   warp_sum_comp<R>(hi, lo);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+  if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = (double)hi + (double)lo;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sum = 0.0;
-    for (int q = 0; q < kThreads / 32; ++q) sum += red[q];
+    for (int q = 0; q < G::Threads / 32; ++q) sum += sm.red[q];
     a.l1_parts[part_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x] = sum;
   }
 }
@@ -848,9 +878,6 @@ int analysis_prox_partials(WaveletGeom g) {
 
 template <typename R>
 void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s) {
-  const size_t smem = analysis_smem_bytes(sizeof(R));
-  auto k = analysis_kernel<R>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t half = (int64_t)g.M * (g.N / 2) * (g.N / 2);
   for (int j = 1; j <= g.J; ++j) {
     int h = g.N >> j;
@@ -859,27 +886,41 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
     const R* ll_in = (j == 1) ? nullptr : tmp + ((j - 1) & 1) * half;
     R* ll_out = tmp + (j & 1) * half;
     dim3 grid(tiles, g.M);
-    k<<<grid, kThreads, smem, s>>>(x, ll_in, ll_out, coef, g.N, j, g.J);
+    auto go = [&](auto kern, int threads, size_t smem) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      kern<<<grid, threads, smem, s>>>(x, ll_in, ll_out, coef, g.N, j, g.J);
+    };
+    switch (ana_geom(TO)) {
+      case 32: go(analysis_kernel<R, 32>, AG<32>::Threads, analysis_smem_bytes<32>(sizeof(R))); break;
+      case 16: go(analysis_kernel<R, 16>, AG<16>::Threads, analysis_smem_bytes<16>(sizeof(R))); break;
+      default: go(analysis_kernel<R, 8>, AG<8>::Threads, analysis_smem_bytes<8>(sizeof(R))); break;
+    }
   }
 }
 
 // TMA box of the level-1 input window: {80 columns, 78 rows}
 void analysis_window_box(unsigned* cols, unsigned* rows) {
-  *cols = kAInS;
-  *rows = kAIn;
+  *cols = AG<kAT>::InS;
+  *rows = AG<kAT>::In;
 }
 
 template <typename R>
 cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int only_level) {
-  const size_t smem = synthesis_smem_bytes(sizeof(R));
-  auto k = synthesis_level_kernel<R>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (int j = a.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
     if (only_level < 0 && j == 1) continue;
     int n = 2 * (a.N >> j), TS = syn_tile(n);
     dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M);
-    cudaError_t e = launch_pdl(k, grid, dim3(kThreads), smem, s, a, j);
+    auto go = [&](auto kern, int threads, size_t smem) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      return launch_pdl(kern, grid, dim3(threads), smem, s, a, j);
+    };
+    cudaError_t e;
+    switch (syn_geom(TS)) {
+      case 64: e = go(synthesis_level_kernel<R, 64>, SG<64>::Threads, synthesis_smem_bytes<64>(sizeof(R))); break;
+      case 32: e = go(synthesis_level_kernel<R, 32>, SG<32>::Threads, synthesis_smem_bytes<32>(sizeof(R))); break;
+      default: e = go(synthesis_level_kernel<R, 16>, SG<16>::Threads, synthesis_smem_bytes<16>(sizeof(R))); break;
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -888,9 +929,6 @@ cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int onl
 template <typename R>
 cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_map,
                                  cudaStream_t s, int only_level) {
-  const size_t smem = analysis_smem_bytes(sizeof(R));
-  auto k = analysis_level_kernel<R>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const CUtensorMap m = grad_map ? *grad_map : CUtensorMap{};
   int part_base = 0;
   for (int j = 1; j <= a.J; ++j) {
@@ -899,8 +937,17 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
     const bool run = only_level == 0 || j == only_level || (only_level < 0 && j > 1);
     if (run) {
       dim3 grid(tiles, a.M);
-      cudaError_t e = launch_pdl(k, grid, dim3(kThreads), smem, s, m, a, j, grad_map ? 1 : 0,
-                                 part_base);
+      auto go = [&](auto kern, int threads, size_t smem) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        return launch_pdl(kern, grid, dim3(threads), smem, s, m, a, j, grad_map ? 1 : 0,
+                          part_base);
+      };
+      cudaError_t e;
+      switch (ana_geom(TO)) {
+        case 32: e = go(analysis_level_kernel<R, 32>, AG<32>::Threads, analysis_smem_bytes<32>(sizeof(R))); break;
+        case 16: e = go(analysis_level_kernel<R, 16>, AG<16>::Threads, analysis_smem_bytes<16>(sizeof(R))); break;
+        default: e = go(analysis_level_kernel<R, 8>, AG<8>::Threads, analysis_smem_bytes<8>(sizeof(R))); break;
+      }
       if (e != cudaSuccess) return e;
     }
     part_base += tiles * a.M;

@@ -184,10 +184,11 @@ def test_work_item_split_does_not_change_result(ms, chunk):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("N,J,M", [(32, 4, 8), (64, 3, 8), (128, 4, 8), (16, 4, 3),
-                                   (512, 4, 8), (1024, 4, 8)])
+                                   (48, 4, 8), (80, 4, 5), (512, 4, 8), (1024, 4, 8)])
 def test_dictionary_matches_oracle(ms, precision, N, J, M):
     """Every tile size of the wavelet kernels: 16- to 64-wide synthesis tiles
-    and 8- to 32-wide analysis tiles (the 1024-pixel case has the widest)."""
+    and 8- to 32-wide analysis tiles (the 1024-pixel case has the widest);
+    48 and 80 pixels give level sides that are not powers of two."""
     w = synth.tiny(npix=N)
     plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px, precision=precision,
                    levels=J, n_bases=M)

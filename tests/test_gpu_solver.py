@@ -98,9 +98,10 @@ def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
-@pytest.mark.parametrize("N", [128, 512])
+@pytest.mark.parametrize("N", [48, 128, 512])
 def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N):
-    """128 and 512 pixels, 4 levels.  At 512 pixels the level-1 analysis uses
+    """48 (level sides 48, 24, 12, 6), 128 and 512 pixels, 4 levels.  At 512
+    pixels the level-1 analysis uses
     32-wide tiles whose interior input windows are staged by TMA (edge
     windows by wrapped loads), and synthesis uses 32- and 64-wide tiles."""
     J, M, iters = 4, 8, 12
