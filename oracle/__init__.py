@@ -24,6 +24,9 @@ Modules
                (Sect. 4.3).
 ``imaging``    major cycles, the two-step method (Eqs. LowRes, FullRes) and the
                single-step baseline (Sect. 5).
+``unet``       the learned warm start's network (a small U-Net: convolutions,
+               pooling, upsampling, bfloat16 rounding points), its gradients
+               and the Adam update.
 
 Parity status
 -------------
