@@ -279,6 +279,44 @@ ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vi
                                      const ms_recon_opts* opts, void* img_out,
                                      void* model_out, ms_stats* stats, void* stream);
 
+/* --------------------------------------------------- learned warm start */
+/* A small U-Net maps [step-one image i^_L, long-baseline dirty image i~_H1]
+ * to a starting image x0 for step two (Sect. 3.3); its coefficients
+ * W^H x0 / M are passed to ms_minor_cycle as beta_inout, so FISTA still runs
+ * to its own tolerance and the network only moves the starting point.  The
+ * paper has no network; this is the learned warm-start form.
+ * Architecture (levels L, base width C): per encoder level two 3x3 conv +
+ * ReLU (C 2^l channels) then 2x2 average pooling; bottom level two conv +
+ * ReLU; per decoder level nearest 2x upsampling, concatenation with the
+ * encoder's skip, two conv + ReLU; a 3x3 conv head to one channel plus the
+ * input's first channel.  Weights and activations bfloat16, products on the
+ * tensor cores with FP32 accumulation, FP32 master weights and Adam state.
+ * Images are FP32 device arrays, channels last: in [H][W][2], out / target
+ * [H][W]; H and W must be multiples of 4 * 2^(L-1) and at most max_side.
+ * Parameters (host FP32, conv after conv in execution order): weights
+ * [c_out][3][3][c_in] then biases [c_out]. */
+typedef struct ms_unet ms_unet;
+ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64_t seed,
+                         int32_t device, ms_unet** out);
+ms_status ms_unet_destroy(ms_unet* net);
+const char* ms_unet_last_error(const ms_unet* net);
+ms_status ms_unet_param_count(const ms_unet* net, int64_t* n);
+ms_status ms_unet_get_params(ms_unet* net, float* host, int64_t n);
+/* also clears the Adam state */
+ms_status ms_unet_set_params(ms_unet* net, const float* host, int64_t n);
+/* out = net(in) */
+ms_status ms_unet_forward(ms_unet* net, const float* in, int32_t H, int32_t W, float* out,
+                          void* stream);
+/* out = net(in); loss = mean((out - target)^2) (FP64); grads_host (NULL or
+ * param_count floats) receives d loss / d params (for checking). */
+ms_status ms_unet_gradients(ms_unet* net, const float* in, const float* target, int32_t H,
+                            int32_t W, float* out, float* grads_host, double* loss,
+                            void* stream);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on the
+ * mean squared error; *loss receives the loss before the step. */
+ms_status ms_unet_train_step(ms_unet* net, const float* in, const float* target, int32_t H,
+                             int32_t W, float lr, double* loss, void* stream);
+
 /* ------------------------------------------------------------- profiling */
 
 /* Kernel families timed by the profiler.  SYNTH / ANALYSIS are the wavelet

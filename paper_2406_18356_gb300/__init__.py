@@ -104,6 +104,15 @@ _SIGNATURES = {
                                 ctypes.POINTER(ms_stats), _P],
     "ms_reconstruct_single_step": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P,
                                    ctypes.POINTER(ms_stats), _P],
+    "ms_unet_create": [_I32, _I32, _I32, ctypes.c_uint64, _I32, ctypes.POINTER(_P)],
+    "ms_unet_destroy": [_P],
+    "ms_unet_last_error": [_P],
+    "ms_unet_param_count": [_P, ctypes.POINTER(_I64)],
+    "ms_unet_get_params": [_P, _P, _I64],
+    "ms_unet_set_params": [_P, _P, _I64],
+    "ms_unet_forward": [_P, _P, _I32, _I32, _P, _P],
+    "ms_unet_gradients": [_P, _P, _P, _I32, _I32, _P, _P, ctypes.POINTER(_D), _P],
+    "ms_unet_train_step": [_P, _P, _P, _I32, _I32, ctypes.c_float, ctypes.POINTER(_D), _P],
     "ms_set_profiling": [_P, _I32],
     "ms_get_kernel_profile": [_P, ctypes.POINTER(ms_kernel_profile), _I32],
 }
@@ -123,7 +132,8 @@ def load_library(path: str = LIB_PATH):
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "ms_last_error" else ctypes.c_int
+        fn.restype = (ctypes.c_char_p if name in ("ms_last_error", "ms_unet_last_error")
+                      else ctypes.c_int)
     _lib = lib
     return lib
 
@@ -552,3 +562,122 @@ def ms_set_profiling(plan: Plan, on: bool):
 
 def ms_get_kernel_profile(plan: Plan, reset: bool = False):
     return plan.kernel_profile(reset)
+
+
+class WarmStartNet:
+    """Owns an ``ms_unet`` (the learned warm start; see mstep.h).  Images are
+    FP32 CUDA tensors, channels last: input [H, W, 2], output [H, W]."""
+
+    def __init__(self, levels: int = 3, width: int = 16, max_side: int = 1024,
+                 seed: int = 0, device: int = 0):
+        self._lib = load_library()
+        h = _P()
+        st = self._lib.ms_unet_create(levels, width, max_side, seed, device, ctypes.byref(h))
+        if st != MS_OK:
+            raise MsError(st, "ms_unet_create failed")
+        self._h = h
+        self.levels, self.width, self.max_side, self.device = levels, width, max_side, device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ms_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != MS_OK:
+            msg = self._lib.ms_unet_last_error(self._h)
+            raise MsError(st, msg.decode() if msg else "")
+
+    def _t(self, t, shape, name):
+        torch = _torch()
+        if t is None or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() \
+                or tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {shape}")
+        return t.data_ptr()
+
+    def param_count(self) -> int:
+        n = _I64()
+        self._check(self._lib.ms_unet_param_count(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count(), np.float32)
+        self._check(self._lib.ms_unet_get_params(self._h, out.ctypes.data, out.size))
+        return out
+
+    def set_params(self, params) -> None:
+        p = np.ascontiguousarray(np.asarray(params, np.float32))
+        self._check(self._lib.ms_unet_set_params(self._h, p.ctypes.data, p.size))
+
+    def forward(self, x, out=None, stream=None):
+        torch = _torch()
+        H, W = x.shape[0], x.shape[1]
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=x.device)
+        self._check(self._lib.ms_unet_forward(self._h, self._t(x, (H, W, 2), "in"), H, W,
+                                              self._t(out, (H, W), "out"),
+                                              _stream_handle(stream)))
+        return out
+
+    def gradients(self, x, target, stream=None):
+        """(output, loss, flat gradient array) for checking."""
+        torch = _torch()
+        H, W = x.shape[0], x.shape[1]
+        out = torch.empty((H, W), dtype=torch.float32, device=x.device)
+        g = np.zeros(self.param_count(), np.float32)
+        loss = _D()
+        self._check(self._lib.ms_unet_gradients(
+            self._h, self._t(x, (H, W, 2), "in"), self._t(target, (H, W), "target"), H, W,
+            out.data_ptr(), g.ctypes.data, ctypes.byref(loss), _stream_handle(stream)))
+        return out, float(loss.value), g
+
+    def train_step(self, x, target, lr: float, stream=None) -> float:
+        H, W = x.shape[0], x.shape[1]
+        loss = _D()
+        self._check(self._lib.ms_unet_train_step(
+            self._h, self._t(x, (H, W, 2), "in"), self._t(target, (H, W), "target"), H, W,
+            ctypes.c_float(lr), ctypes.byref(loss), _stream_handle(stream)))
+        return float(loss.value)
+
+
+def ms_unet_create(levels=3, width=16, max_side=1024, seed=0, device=0):
+    return WarmStartNet(levels, width, max_side, seed, device)
+
+
+def ms_unet_destroy(net: WarmStartNet):
+    net.close()
+
+
+def ms_unet_last_error(net: WarmStartNet):
+    msg = net._lib.ms_unet_last_error(net._h)
+    return msg.decode() if msg else ""
+
+
+def ms_unet_param_count(net: WarmStartNet):
+    return net.param_count()
+
+
+def ms_unet_get_params(net: WarmStartNet):
+    return net.get_params()
+
+
+def ms_unet_set_params(net: WarmStartNet, params):
+    net.set_params(params)
+
+
+def ms_unet_forward(net: WarmStartNet, x, out=None, stream=None):
+    return net.forward(x, out, stream)
+
+
+def ms_unet_gradients(net: WarmStartNet, x, target, stream=None):
+    return net.gradients(x, target, stream)
+
+
+def ms_unet_train_step(net: WarmStartNet, x, target, lr, stream=None):
+    return net.train_step(x, target, lr, stream)
