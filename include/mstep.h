@@ -294,7 +294,9 @@ ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vi
  * Images are FP32 device arrays, channels last: in [H][W][2], out / target
  * [H][W]; H and W must be multiples of 4 * 2^(L-1) and at most max_side.
  * Parameters (host FP32, conv after conv in execution order): weights
- * [c_out][3][3][c_in] then biases [c_out]. */
+ * [c_out][3][3][c_in] then biases [c_out].  ms_unet_create draws He-normal
+ * weights from `seed` and zero biases, and starts the head at zero, so an
+ * untrained network returns the step-one image. */
 typedef struct ms_unet ms_unet;
 ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64_t seed,
                          int32_t device, ms_unet** out);

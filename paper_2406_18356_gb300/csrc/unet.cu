@@ -658,6 +658,10 @@ ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64
       return ((st64 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
     };
     for (Layer& l : u->L) {
+      // the head starts at zero: the untrained network returns its first
+      // input channel (the step-one image) unchanged, and training learns a
+      // correction to it
+      if (!l.relu) continue;
       const double sd = std::sqrt(2.0 / (9.0 * l.ci));
       for (size_t i = 0; i < (size_t)l.co * 9 * l.ci; ++i) {
         const double r = std::sqrt(-2.0 * std::log(uni())), t = 6.283185307179586 * uni();

@@ -279,6 +279,18 @@ def ska_low_like(seed: int = 0, nchan: int = 4, n_dumps: int = 240, span_h: floa
                     freqs=freqs, noise_sigma=np.ones(nchan))
 
 
+def c1_style(npix: int, seed: int, device: str = "cpu") -> Workload:
+    """The small workload's recipe at another image size (the learned warm
+    start's training and evaluation skies): 32 antennas in a 2 km disc, 64
+    dumps over 4 h (31,744 rows), split at 25 % of max |uv|, with the point
+    and blob counts scaled with the image area (20 + 3 at 128 pixels)."""
+    area = (npix / 128.0) ** 2
+    return _single_channel(
+        f"c1-style-{npix}px-seed{seed}", 32, lambda r: layout_uniform_disc(32, 1000.0, r),
+        64, 4.0, npix, max(1, int(round(20 * area))), max(1, int(round(3 * area))),
+        0.25, 3.0, 1.28e9, seed, device)
+
+
 def tiny(npix: int = 32, n_ant: int = 8, n_dumps: int = 6, seed: int = 1,
          device: str = "cpu", split_frac: float = 0.3, delta_px: float = 1.5,
          n_points: int = 4, n_blobs: int = 1) -> Workload:
