@@ -293,6 +293,15 @@ template <typename R>
 void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, const R* gl2,
                        const R* gh2, int N, C2<R>* Bs, double* parts, FistaCtl* ctl,
                        int32_t* ticket, cudaStream_t s);
+// the spectral step with the column FFTs fused in (N a power of two); Z holds
+// the row transforms of x_k on entry and the inverse column transforms of the
+// gradient spectrum on exit; tw = exp(-2 pi i m / N), m < N/2
+template <typename R>
+void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
+                     const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
+                     int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s);
+int spec_col_blocks(int N);
+size_t spec_col_smem(int N, size_t complex_bytes);   // dynamic shared memory of a block
 template <typename R>
 void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
                      double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,

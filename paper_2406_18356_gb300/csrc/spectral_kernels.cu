@@ -283,6 +283,77 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // it to the trace, raises `done` on convergence or at the iteration budget,
 // and otherwise advances the iteration index to k + 1 for the analysis pass
 // that builds B_{k+1}.
+// End of a spectral step (blockDim = kThreads): the block sums of the
+// objective's two quadratic terms (working-precision pairs (s, -c), combined
+// error-free within each warp, FP64 once per warp) and of the l1 partials the
+// previous analysis pass left (only the first blocks hold some; has_l1 is
+// uniform over the block); the last block assembles
+// F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it to the trace,
+// raises `done` on convergence or at the iteration budget and otherwise
+// advances the iteration index, the momentum and the step scalars.
+template <typename R>
+__device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, int kit,
+                            double c0v, double lam, double Fprev, double rtol, int max_iters,
+                            double inv_theta, double* parts, FistaCtl* ctl, double* trace,
+                            int32_t* ticket) {
+  __shared__ double red3[3][kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  R lo0 = -c0, lo1 = -c1;
+  warp_sum_comp<R>(s0, lo0);
+  warp_sum_comp<R>(s1, lo1);
+  double w2 = 0.0;
+  if (has_l1) w2 = warp_sum(l1s);
+  if (lane == 0) {
+    red3[0][warp] = (double)s0 + (double)lo0;
+    red3[1][warp] = (double)s1 + (double)lo1;
+    red3[2][warp] = w2;
+  }
+  __syncthreads();
+  double v[3] = {0.0, 0.0, 0.0};
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kThreads / 32; ++q) {
+      v[0] += red3[0][q];
+      v[1] += red3[1][q];
+      v[2] += red3[2][q];
+    }
+  const bool mx[3] = {false, false, false};
+  if (publish_partials<3>(v, parts, ticket)) {
+    double o[3];
+    gather_partials<3>(o, parts, mx, ticket);
+    if (threadIdx.x == 0) {
+      const int k = kit;
+      const double l1 = o[2];
+      double F = o[0] - 2.0 * o[1] + c0v + lam * l1;
+      ctl->l1_cur = l1;
+      ctl->xkx = o[0];
+      ctl->bx = o[1];
+      ctl->F_prev = Fprev;
+      ctl->F_cur = F;
+      trace[k] = F;
+      if (!isfinite(F)) {
+        ctl->error = 4;
+        ctl->done = 1;
+      } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
+        ctl->converged = 1;
+        ctl->done = 1;
+      } else if (k >= max_iters) {
+        ctl->done = 1;
+      } else {
+        ctl->k = k + 1;
+        const double tn = k + 1 >= 2 ? (double)k / (double)(k + 3) : 0.0;   // t_{k+1}
+        ctl->td[(k + 1) & 1] = tn;
+        ctl->tf[(k + 1) & 1] = (float)tn;
+      }
+      ctl->mud = inv_theta;
+      ctl->thrd = lam * inv_theta;
+      ctl->muf = (float)inv_theta;
+      ctl->thrf = (float)(lam * inv_theta);
+      __threadfence();
+    }
+  }
+}
+
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __restrict__ Xk, C2<R>* __restrict__ Xprev,
                                 const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, int N,
@@ -346,64 +417,142 @@ __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __re
       Xprev[k] = S;
     }
   }
-  // block sums: the working-precision pairs (s, -c) are combined error-free
-  // within each warp and reach FP64 once per warp; the l1 partials (FP64)
-  // only exist in the first blocks
-  __shared__ double red3[3][kThreads / 32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  R lo0 = -c0, lo1 = -c1;
-  warp_sum_comp<R>(s0, lo0);
-  warp_sum_comp<R>(s1, lo1);
-  double w2 = 0.0;
-  if ((int64_t)blockIdx.x * blockDim.x < n_l1) w2 = warp_sum(l1s);
-  if (lane == 0) {
-    red3[0][warp] = (double)s0 + (double)lo0;
-    red3[1][warp] = (double)s1 + (double)lo1;
-    red3[2][warp] = w2;
+  spec_finish<R>(s0, c0, s1, c1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, kit, c0v, lam,
+                 Fprev, rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
+}
+
+// In-place radix-2 decimation-in-time FFT of CB columns of length N = 2^logN
+// held in shared memory as a[r][c] (rows bit-reversed on entry, natural on
+// exit); tw[m] = exp(-2 pi i m / N) for m < N/2, conjugated for the inverse.
+template <typename R, int CB>
+__device__ __forceinline__ void col_fft(C2<R>* a, const C2<R>* tw, int N, int logN, bool inverse) {
+  for (int st = 0; st < logN; ++st) {
+    const int h = 1 << st;
+    for (int b = threadIdx.x; b < (N / 2) * CB; b += blockDim.x) {
+      const int c = b % CB, q = b / CB;
+      const int j = q & (h - 1);
+      const int i = ((q >> st) << (st + 1)) + j;
+      C2<R> w = tw[j << (logN - 1 - st)];
+      if (inverse) w.y = -w.y;
+      const C2<R> u = a[i * CB + c], x = a[(i + h) * CB + c];
+      C2<R> v;
+      v.x = x.x * w.x - x.y * w.y;
+      v.y = x.x * w.y + x.y * w.x;
+      C2<R> o0, o1;
+      o0.x = u.x + v.x;
+      o0.y = u.y + v.y;
+      o1.x = u.x - v.x;
+      o1.y = u.y - v.y;
+      a[i * CB + c] = o0;
+      a[(i + h) * CB + c] = o1;
+    }
+    __syncthreads();
+  }
+}
+
+// The spectral step with the column transforms fused in, for N a power of
+// two.  Z holds the row transforms of x_k ([N][N/2+1], cuFFT's half-plane
+// layout); each block takes CB columns: the column FFT gives X^_k (the 2-D
+// transform of x_k, kept in Xk for the next pass's momentum), the step of
+// spec_mul_kernel forms S = 2 (K^((1 + t) X^_k - t X^_{k-1}) - B^) and the
+// objective partials, and the inverse column FFT of S goes back into Z, whose
+// inverse row transforms then give the gradient image.
+template <typename R, int CB>
+__global__ void __launch_bounds__(kThreads) spec_col_kernel(
+    C2<R>* __restrict__ Z, C2<R>* __restrict__ Xk, const C2<R>* __restrict__ Xprev,
+    const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, const C2<R>* __restrict__ tw_g,
+    int N, int logN, double* __restrict__ parts, FistaCtl* __restrict__ ctl,
+    double* __restrict__ trace, int32_t* ticket, const double* __restrict__ l1_parts, int n_l1) {
+  pdl_wait();
+  pdl_trigger();
+  if (ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* A = reinterpret_cast<C2<R>*>(smem_raw);   // [N][CB] forward
+  C2<R>* Bf = A + N * CB;                          // [N][CB] inverse
+  C2<R>* tw = Bf + N * CB;                         // [N/2]
+  const int nc = N / 2 + 1;
+  const int c0 = blockIdx.x * CB;
+  const int kit = ctl->k;
+  const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
+  const double rtol = ctl->rel_tol;
+  const int max_iters = ctl->max_iters;
+  const R t = ctl_t<R>(ctl, kit & 1);
+  const double inv_theta = ctl->inv_theta;
+  const R a = (R)1 + t;
+  const int shift = 32 - logN;
+  for (int m = threadIdx.x; m < N / 2; m += blockDim.x) tw[m] = tw_g[m];
+  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
+    const int r = e / CB, c = e - r * CB;
+    C2<R> z;
+    z.x = (R)0;
+    z.y = (R)0;
+    if (c0 + c < nc) z = Z[(int64_t)r * nc + c0 + c];
+    A[(int)(__brev((unsigned)r) >> shift) * CB + c] = z;
+  }
+  double l1s = 0.0;
+  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = first; i < n_l1; i += (int64_t)gridDim.x * blockDim.x)
+    l1s += __ldcg(l1_parts + i);
+  __syncthreads();
+  col_fft<R, CB>(A, tw, N, logN, false);
+  R s0 = 0, cc0 = 0, s1 = 0, cc1 = 0;
+  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
+    const int r = e / CB, c = e - r * CB;
+    const int col = c0 + c;
+    C2<R> S;
+    S.x = (R)0;
+    S.y = (R)0;
+    if (col < nc) {
+      const int64_t k = (int64_t)r * nc + col;
+      const C2<R> X = A[r * CB + c];
+      const C2<R> P = Xprev[k];
+      const R kk = Ks[k];
+      const C2<R> B = Bs[k];
+      const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
+      R y0 = w * kk * (X.x * X.x + X.y * X.y) - cc0;
+      R t0 = s0 + y0;
+      cc0 = (t0 - s0) - y0;
+      s0 = t0;
+      R y1 = w * (B.x * X.x + B.y * X.y) - cc1;
+      R t1 = s1 + y1;
+      cc1 = (t1 - s1) - y1;
+      s1 = t1;
+      S.x = (R)2 * (kk * (a * X.x - t * P.x) - B.x);
+      S.y = (R)2 * (kk * (a * X.y - t * P.y) - B.y);
+      Xk[k] = X;
+    }
+    Bf[(int)(__brev((unsigned)r) >> shift) * CB + c] = S;
   }
   __syncthreads();
-  double v[3] = {0.0, 0.0, 0.0};
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kThreads / 32; ++q) {
-      v[0] += red3[0][q];
-      v[1] += red3[1][q];
-      v[2] += red3[2][q];
-    }
-  const bool mx[3] = {false, false, false};
-  if (publish_partials<3>(v, parts, ticket)) {
-    double o[3];
-    gather_partials<3>(o, parts, mx, ticket);
-    if (threadIdx.x == 0) {
-      const int k = kit;
-      const double l1 = o[2];
-      double F = o[0] - 2.0 * o[1] + c0v + lam * l1;
-      ctl->l1_cur = l1;
-      ctl->xkx = o[0];
-      ctl->bx = o[1];
-      ctl->F_prev = Fprev;
-      ctl->F_cur = F;
-      trace[k] = F;
-      if (!isfinite(F)) {
-        ctl->error = 4;
-        ctl->done = 1;
-      } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
-        ctl->converged = 1;
-        ctl->done = 1;
-      } else if (k >= max_iters) {
-        ctl->done = 1;
-      } else {
-        ctl->k = k + 1;
-        const double tn = k + 1 >= 2 ? (double)k / (double)(k + 3) : 0.0;   // t_{k+1}
-        ctl->td[(k + 1) & 1] = tn;
-        ctl->tf[(k + 1) & 1] = (float)tn;
-      }
-      ctl->mud = inv_theta;
-      ctl->thrd = lam * inv_theta;
-      ctl->muf = (float)inv_theta;
-      ctl->thrf = (float)(lam * inv_theta);
-      __threadfence();
-    }
+  col_fft<R, CB>(Bf, tw, N, logN, true);
+  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
+    const int r = e / CB, c = e - r * CB;
+    if (c0 + c < nc) Z[(int64_t)r * nc + c0 + c] = Bf[r * CB + c];
   }
+  spec_finish<R>(s0, cc0, s1, cc1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, kit, c0v, lam,
+                 Fprev, rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
+}
+
+#ifndef MS_COL_CB
+#define MS_COL_CB 2   // columns per block of the fused spectral step
+#endif
+constexpr int kColCB = MS_COL_CB;
+int spec_col_blocks(int N) { return (N / 2 + 1 + kColCB - 1) / kColCB; }
+size_t spec_col_smem(int N, size_t complex_bytes) {
+  return (size_t)(2 * N * kColCB + N / 2) * complex_bytes;
+}
+
+template <typename R>
+void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
+                     const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
+                     int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
+  int logN = 0;
+  while ((1 << logN) < N) ++logN;
+  const size_t smem = spec_col_smem(N, sizeof(C2<R>));
+  auto k = spec_col_kernel<R, kColCB>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  launch_pdl(k, dim3(spec_col_blocks(N)), dim3(kThreads), smem, s, Z, Xk, Xprev, Ks, Bs, tw, N,
+             logN, parts, ctl, trace, ticket, l1_parts, n_l1);
 }
 
 template <typename R>
@@ -601,6 +750,9 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                           FistaCtl*, int32_t*, cudaStream_t);                    \
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
+  template void launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*, const C2<R>*,        \
+                                   const C2<R>*, int, double*, FistaCtl*, double*, int32_t*,     \
+                                   const double*, int, cudaStream_t);                            \
   template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
                                    FistaCtl*,                                                    \
                                    double*, int32_t*, const double*, int, cudaStream_t);         \
