@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--fista-iters", type=int, default=FISTA_ITERS)
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--record-traffic", nargs="+", default=None, metavar="NCU_CSV",
+                    help="write the DRAM traffic of one FISTA pass, from ncu --page raw --csv "
+                         "exports, to profiles/")
     ap.add_argument("--batched-channels", type=int, default=64)
     return ap.parse_args()
 
@@ -204,8 +207,56 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def record_traffic(paths, precision):
+    """DRAM bytes per span of the FISTA kernel families from ncu raw-page CSV
+    exports of one FISTA pass captured in launch order (synthesis levels
+    J..1, the spectral step, analysis levels 1..J)."""
+    import csv
+    fams = {}
+    for path in paths:
+        with open(path) as f:
+            rows = [r for r in csv.reader(f)]
+        start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)   # after ncu's log lines
+        rows = rows[start:]
+        h = rows[0]
+        units = rows[1]
+        idx = {n: i for i, n in enumerate(h)}
+        scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+        launches = []
+        for r in rows[2:]:
+            name = r[idx["Kernel Name"]]
+            b = 0.0
+            for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                b += float(r[idx[m]].replace(",", "")) * scale[units[idx[m]]]
+            launches.append((name, b))
+        syn = [b for n, b in launches if "synthesis_level_kernel" in n]
+        ana = [b for n, b in launches if "analysis_level_kernel" in n]
+        if syn:
+            fams["synth"], fams["synth_l1"] = sum(syn[:-1]), syn[-1]
+        if ana:
+            fams["analysis_l1"], fams["analysis"] = ana[0], sum(ana[1:])
+        for n, b in launches:
+            base = n.split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
+            # (the operator kernels' traffic depends on the call's partition, so
+            # only the per-pass families are recorded)
+            for fam, kname in (("spec_mul", "spec_mul_kernel"),):
+                if base == kname and fam not in fams:
+                    fams[fam] = b
+    rec = {"precision": precision, "workload": "ska-mid-like-1024px-9266880vis",
+           "note": "DRAM read + write bytes per span of each kernel family, from ncu; valid "
+                   "while the kernel sources hash to source_sha256",
+           "families": {f: {"dram_bytes_per_span": b, "source_sha256": kernel_source_digest(f)}
+                        for f, b in fams.items()}}
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+
+
 def main():
     args = parse()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.precision)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -518,6 +569,42 @@ def family_bytes(fam, N, M, J, rsz, plan):
     return None
 
 
+FAMILY_SOURCE = {"synth": "wavelet_kernels.cu", "synth_l1": "wavelet_kernels.cu",
+                 "analysis": "wavelet_kernels.cu", "analysis_l1": "wavelet_kernels.cu",
+                 "spec_mul": "spectral_kernels.cu", "degrid": "grid_kernels.cu",
+                 "grid": "grid_kernels.cu", "fold": "grid_kernels.cu"}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_1024px_fp32.json")
+
+
+def kernel_source_digest(fam):
+    """sha256 of the source that defines a family's kernels plus the shared
+    header: a recorded DRAM traffic is valid only for the same kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2406_18356_gb300", "csrc")
+    for f in (FAMILY_SOURCE[fam], "common.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(fam, precision):
+    """DRAM bytes (read + write) of one span of family `fam` from the
+    committed ncu capture, or None when the capture is absent, of another
+    precision, or the kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    fr = rec.get("families", {}).get(fam)
+    if not fr or rec.get("precision") != precision or fam not in FAMILY_SOURCE:
+        return None
+    if fr.get("source_sha256") != kernel_source_digest(fam):
+        return None
+    return fr.get("dram_bytes_per_span")
+
+
 def roofline_of(prof, w, plan, args):
     """Roofline of the dominant kernel family of the library (largest share of
     kernel time, cuFFT excluded): algorithmic bytes of one span (family_bytes)
@@ -540,8 +627,10 @@ def roofline_of(prof, w, plan, args):
         return {"bound": "hbm", "kernel": fam, "achieved": None, "peak": hbm, "unit": "GB/s",
                 "frac": None, "traffic": None, "peak_kind": kind, "frac_by_family": others}
     achieved = bytes_ / avg_s / 1e9
+    traffic = recorded_traffic(fam, args.precision) if w.npix == 1024 else None
     return {"bound": "hbm", "kernel": fam, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+            "frac": achieved / hbm, "traffic": traffic,
+            "traffic_source": os.path.relpath(TRAFFIC_FILE, ROOT) if traffic else None,
             "peak_kind": f"{kind} (hbm_gbs burst copy)",
             "algorithmic_bytes_per_launch": bytes_, "avg_launch_us": avg_s * 1e6,
             "launches": launches, "frac_by_family": others}
