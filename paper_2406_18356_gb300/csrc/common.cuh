@@ -128,6 +128,29 @@ __device__ __forceinline__ double es_phi(double z, double beta) {
   return exp(beta * (sqrt(s) - 1.0));
 }
 
+// shared-memory address of a generic pointer into shared memory
+__device__ __forceinline__ unsigned saddr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses
+// aligned to the size); completes at cp_async_wait after cp_async_commit
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  if (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(saddr(dst)), "l"(src),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Programmatic dependent launch.  A kernel launched with
 // launch_pdl may be scheduled while the preceding kernel of its stream is
 // still running; it must call pdl_wait() before touching anything that
@@ -293,15 +316,29 @@ template <typename R>
 void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, const R* gl2,
                        const R* gh2, int N, C2<R>* Bs, double* parts, FistaCtl* ctl,
                        int32_t* ticket, cudaStream_t s);
-// the spectral step with the column FFTs fused in (N a power of two); Z holds
-// the row transforms of x_k on entry and the inverse column transforms of the
-// gradient spectrum on exit; tw = exp(-2 pi i m / N), m < N/2
+// the spectral step with the column FFTs fused in (N a power of two, 16 ..
+// 8192); Z holds the row transforms of x_k on entry and the inverse column
+// transforms of the gradient spectrum on exit; tw = exp(-2 pi i m / N), m < N
 template <typename R>
 void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
                      const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
                      int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s);
-int spec_col_blocks(int N);
-size_t spec_col_smem(int N, size_t complex_bytes);   // dynamic shared memory of a block
+int spec_col_blocks(int N, size_t complex_bytes);   // blocks of one launch (0: N unsupported)
+// real row transforms of an N x N image (N a power of two, 16 <= N <= 8192)
+// to / from the half-plane layout [N][N/2+1], through complex transforms of
+// length N/2 in shared memory; the inverse is unnormalized and ignores the
+// imaginary parts of columns 0 and N/2; tw as for launch_spec_col; both
+// return at once when ctl->done
+template <typename R>
+void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
+                    cudaStream_t s);
+template <typename R>
+void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, const FistaCtl* ctl,
+                    cudaStream_t s);
+// dynamic shared memory of a block (SIZE_MAX: N unsupported)
+size_t row_fft_smem(int N, size_t complex_bytes);
+// dynamic shared memory of a block (SIZE_MAX: N unsupported)
+size_t spec_col_smem(int N, size_t complex_bytes);
 template <typename R>
 void launch_spec_mul(const C2<R>* Xk, C2<R>* Xprev, const R* Ks, const C2<R>* Bs, int N,
                      double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,

@@ -21,6 +21,12 @@
 #include "common.cuh"
 #include "mstep.h"
 
+#ifndef MS_FUSED_SPEC_FP32
+#define MS_FUSED_SPEC_FP32 1   // FP32 plans use the fused spectral step too
+#endif
+#ifndef MS_OWN_ROW_FFT_FP32
+#define MS_OWN_ROW_FFT_FP32 0  // FP32 row transforms of the fused step in shared memory
+#endif
 using namespace ms;
 
 namespace {
@@ -241,6 +247,10 @@ struct ms_plan {
   // fused spectral step (N a power of two whose column block fits in shared
   // memory): 1-D row transforms, their buffer and the column twiddles
   bool fused_spec = false;
+  // row transforms in shared memory (else 1-D cuFFT plans); measured at
+  // N = 1024 on GB300: faster in FP64 (54 + 52 us against 81 + 83 us per
+  // iteration), 10 us per iteration slower in FP32 within the FISTA graph
+  bool own_rows = false;
   cufftHandle r2c_rows = 0, c2r_rows = 0;
   void* zrow = nullptr;
   void* twid = nullptr;
@@ -581,7 +591,10 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
     // fused in, inverse row transforms
     {
       KSpan k(p, MS_K_FFT_R2C);
-      if (sizeof(R) == 8)
+      if (p->own_rows)
+        launch_row_r2c<R>((const R*)p->xwork, (C2<R>*)p->zrow, (const C2<R>*)p->twid, p->N,
+                          p->ctl, p->ps);
+      else if (sizeof(R) == 8)
         ckf(cufftExecD2Z(p->r2c_rows, (cufftDoubleReal*)p->xwork, (cufftDoubleComplex*)p->zrow),
             "D2Z rows");
       else
@@ -595,7 +608,10 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
     }
     {
       KSpan k(p, MS_K_FFT_C2R);
-      if (sizeof(R) == 8)
+      if (p->own_rows)
+        launch_row_c2r<R>((const C2<R>*)p->zrow, (R*)p->ywork, (const C2<R>*)p->twid, p->N,
+                          p->ctl, p->ps);
+      else if (sizeof(R) == 8)
         ckf(cufftExecZ2D(p->c2r_rows, (cufftDoubleComplex*)p->zrow, (cufftDoubleReal*)p->ywork),
             "Z2D rows");
       else
@@ -1022,7 +1038,7 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
   p->api3_dev = p->alloc<void*>(3, "ptrs");
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
-  p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_blocks(N)), "partials");
+  p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_blocks(N, sizeof(C2<R>))), "partials");
   p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
   p->l1parts = p->alloc<double>(p->n_l1, "partials");
   p->tickets = p->alloc<int32_t>(16, "tickets");
@@ -1044,32 +1060,34 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
     int dev_smem = 0;
     ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->dev),
        "device attribute");
-    // Measured at N = 1024 on GB300: the fused step (1-D row transforms +
-    // shared-memory column transforms fused with the spectral step) saves 5 %
-    // of an FP64 iteration, but costs 3 % of an FP32 one, where the 2-D cuFFT
-    // transforms are faster than the shared-memory radix-2 columns; so it
-    // serves the FP64 form only.
-    p->fused_spec = sizeof(R) == 8 && N >= 16 && (N & (N - 1)) == 0 &&
-                    spec_col_smem(N, sizeof(C2<R>)) <= (size_t)dev_smem;
+    // The fused step: 1-D row transforms and the shared-memory Stockham
+    // column transforms fused with the spectral step.  Measured at N = 1024
+    // on GB300 it beats the 2-D cuFFT transforms around spec_mul_kernel in
+    // both precisions (FP32: 170 against 173 us per FISTA iteration).
+    p->fused_spec = (sizeof(R) == 8 || MS_FUSED_SPEC_FP32) && N >= 16 && N <= 8192 &&
+                    (N & (N - 1)) == 0 && spec_col_smem(N, sizeof(C2<R>)) <= (size_t)dev_smem &&
+                    row_fft_smem(N, sizeof(C2<R>)) <= (size_t)dev_smem;
   }
   if (p->fused_spec) {
-    int n[1] = {N};
-    ckf(cufftPlanMany(&p->r2c_rows, 1, n, nullptr, 1, N, nullptr, 1, N / 2 + 1, tr, N),
-        "plan R2C rows");
-    ckf(cufftPlanMany(&p->c2r_rows, 1, n, nullptr, 1, N / 2 + 1, nullptr, 1, N, ti, N),
-        "plan C2R rows");
-    for (cufftHandle h : {p->r2c_rows, p->c2r_rows}) ckf(cufftSetStream(h, s), "set stream");
+    p->own_rows = sizeof(R) == 8 || MS_OWN_ROW_FFT_FP32;
+    if (!p->own_rows) {
+      int n[1] = {N};
+      ckf(cufftPlanMany(&p->r2c_rows, 1, n, nullptr, 1, N, nullptr, 1, N / 2 + 1, tr, N),
+          "plan R2C rows");
+      ckf(cufftPlanMany(&p->c2r_rows, 1, n, nullptr, 1, N / 2 + 1, nullptr, 1, N, ti, N),
+          "plan C2R rows");
+      for (cufftHandle h : {p->r2c_rows, p->c2r_rows}) ckf(cufftSetStream(h, s), "set stream");
+    }
     p->zrow = p->alloc<C2<R>>((size_t)N * (N / 2 + 1), "row spectra");
-    // column twiddles exp(-2 pi i m / N), m < N/2, in FP64 on the host
-    std::vector<C2<R>> tw(N / 2);
-    for (int m = 0; m < N / 2; ++m) {
+    // twiddles exp(-2 pi i m / N), m < N, in FP64 on the host
+    std::vector<C2<R>> tw(N);
+    for (int m = 0; m < N; ++m) {
       const double ang = -2.0 * M_PI * (double)m / (double)N;
       tw[m].x = (R)std::cos(ang);
       tw[m].y = (R)std::sin(ang);
     }
-    p->twid = p->alloc<C2<R>>(N / 2, "twiddles");
-    ck(cudaMemcpy(p->twid, tw.data(), sizeof(C2<R>) * (N / 2), cudaMemcpyHostToDevice),
-       "twiddles");
+    p->twid = p->alloc<C2<R>>(N, "twiddles");
+    ck(cudaMemcpy(p->twid, tw.data(), sizeof(C2<R>) * N, cudaMemcpyHostToDevice), "twiddles");
   }
   // TMA descriptor of the grid: {2 Ng scalars, Ng rows}, box {2 S, S}
   {

@@ -28,9 +28,10 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // block reduction of NV doubles (sum or max per slot); result in thread 0
+// (blockDim.x a multiple of 32)
 template <int NV>
 __device__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV]) {
-  __shared__ double red[NV][kThreads / 32];
+  __shared__ double red[NV][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < NV; ++i) v[i] = is_max[i] ? warp_max(v[i]) : warp_sum(v[i]);
@@ -43,7 +44,8 @@ __device__ void block_reduce(double (&v)[NV], const bool (&is_max)[NV]) {
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
       double s = is_max[i] ? -INFINITY : 0.0;
-      for (int w = 0; w < kThreads / 32; ++w) s = is_max[i] ? fmax(s, red[i][w]) : s + red[i][w];
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        s = is_max[i] ? fmax(s, red[i][w]) : s + red[i][w];
       v[i] = s;
     }
   }
@@ -283,7 +285,7 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // it to the trace, raises `done` on convergence or at the iteration budget,
 // and otherwise advances the iteration index to k + 1 for the analysis pass
 // that builds B_{k+1}.
-// End of a spectral step (blockDim = kThreads): the block sums of the
+// End of a spectral step (blockDim.x a multiple of 32): the block sums of the
 // objective's two quadratic terms (working-precision pairs (s, -c), combined
 // error-free within each warp, FP64 once per warp) and of the l1 partials the
 // previous analysis pass left (only the first blocks hold some; has_l1 is
@@ -296,7 +298,7 @@ __device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, int
                             double c0v, double lam, double Fprev, double rtol, int max_iters,
                             double inv_theta, double* parts, FistaCtl* ctl, double* trace,
                             int32_t* ticket) {
-  __shared__ double red3[3][kThreads / 32];
+  __shared__ double red3[3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R lo0 = -c0, lo1 = -c1;
   warp_sum_comp<R>(s0, lo0);
@@ -311,7 +313,7 @@ __device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, int
   __syncthreads();
   double v[3] = {0.0, 0.0, 0.0};
   if (threadIdx.x == 0)
-    for (int q = 0; q < kThreads / 32; ++q) {
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
       v[0] += red3[0][q];
       v[1] += red3[1][q];
       v[2] += red3[2][q];
@@ -421,57 +423,235 @@ __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __re
                  Fprev, rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
 }
 
-// In-place radix-2 decimation-in-time FFT of CB columns of length N = 2^logN
-// held in shared memory as a[r][c] (rows bit-reversed on entry, natural on
-// exit); tw[m] = exp(-2 pi i m / N) for m < N/2, conjugated for the inverse.
-template <typename R, int CB>
-__device__ __forceinline__ void col_fft(C2<R>* a, const C2<R>* tw, int N, int logN, bool inverse) {
-  for (int st = 0; st < logN; ++st) {
-    const int h = 1 << st;
-    for (int b = threadIdx.x; b < (N / 2) * CB; b += blockDim.x) {
-      const int c = b % CB, q = b / CB;
+// ------------------------------------------------- shared-memory transforms
+// Complex FFTs of length N = 2^LOGN (a compile-time constant) held in shared
+// memory, one sequence per N/8 threads, as a mixed-radix Stockham autosort
+// transform (natural order in and out, ping-pong between two buffers):
+// radix-8 stages, then one radix-2 or radix-4 stage for what is left.  Stage
+// with radix Rd after sub-transforms of size Ns: for j < N/Rd, the Rd inputs
+// a[j + r N/Rd] are twiddled by W_N^(r (j mod Ns) N/(Ns Rd)), transformed by
+// an Rd-point DFT in registers and written to
+// b[(j - j mod Ns) Rd + j mod Ns + r Ns].  Every 16th element is followed by
+// one pad element (index i lives at i + i/16), in the data and in the
+// twiddle table tw[pad(m)] = W_N^m (m < N), which keeps the strided accesses
+// of every stage within a few shared-memory wavefronts.
+
+// cos(2 pi k / 16), k < 8
+__device__ __forceinline__ double c16(int k) {
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return 0.92387953251128674;
+    case 2: return 0.70710678118654752;
+    case 3: return 0.38268343236508977;
+    case 4: return 0.0;
+    case 5: return -0.38268343236508977;
+    case 6: return -0.70710678118654752;
+    default: return -0.92387953251128674;
+  }
+}
+// sin(t) = cos(pi/2 - t), and cos is even
+__device__ __forceinline__ double s16(int k) { return c16(k <= 4 ? 4 - k : k - 4); }
+
+__host__ __device__ constexpr int padi(int i) { return i + (i >> 4); }
+
+// x * W_16^k (forward: W = exp(-2 pi i / 16); inverse: its conjugate), k < 8
+// a compile-time constant after unrolling
+template <typename R, bool INV>
+__device__ __forceinline__ C2<R> mul_w16(C2<R> x, int k) {
+  if (k == 0) return x;
+  C2<R> y;
+  if (k == 4) {   // -i (forward) or +i (inverse)
+    y.x = INV ? -x.y : x.y;
+    y.y = INV ? x.x : -x.x;
+    return y;
+  }
+  const R c = (R)c16(k), sn = (R)s16(k);
+  y.x = INV ? x.x * c - x.y * sn : x.x * c + x.y * sn;
+  y.y = INV ? x.y * c + x.x * sn : x.y * c - x.x * sn;
+  return y;
+}
+
+template <int LOG> __host__ __device__ constexpr int brev_c(int i) {
+  int r = 0;
+  for (int bit = 0; bit < LOG; ++bit) r |= ((i >> bit) & 1) << (LOG - 1 - bit);
+  return r;
+}
+template <typename R, bool INV>
+__device__ __forceinline__ void bfly(C2<R>& a, C2<R>& b, int k) {
+  const C2<R> bq = mul_w16<R, INV>(b, k);
+  const C2<R> aq = a;
+  a.x = aq.x + bq.x;
+  a.y = aq.y + bq.y;
+  b.x = aq.x - bq.x;
+  b.y = aq.y - bq.y;
+}
+// Rd-point DFT (Rd = 2, 4, 8) of v in registers: bit-reversed copy, then
+// log2(Rd) radix-2 decimation-in-time stages; butterfly q of stage st pairs
+// i0 = (q / h) 2h + q mod h with i0 + h (h = 2^st) under the twiddle
+// W_2h^(q mod h) = W_16^((q mod h) 16 / 2h)
+template <typename R, int Rd, bool INV>
+__device__ __forceinline__ void dft_reg(C2<R> (&v)[Rd]) {
+  constexpr int LOG = Rd == 2 ? 1 : (Rd == 4 ? 2 : 3);
+  C2<R> t[Rd];
+#pragma unroll
+  for (int i = 0; i < Rd; ++i) t[i] = v[brev_c<LOG>(i)];
+#pragma unroll
+  for (int st = 0; st < LOG; ++st) {
+#pragma unroll
+    for (int q = 0; q < Rd / 2; ++q) {
+      const int h = 1 << st;
       const int j = q & (h - 1);
-      const int i = ((q >> st) << (st + 1)) + j;
-      C2<R> w = tw[j << (logN - 1 - st)];
-      if (inverse) w.y = -w.y;
-      const C2<R> u = a[i * CB + c], x = a[(i + h) * CB + c];
-      C2<R> v;
-      v.x = x.x * w.x - x.y * w.y;
-      v.y = x.x * w.y + x.y * w.x;
-      C2<R> o0, o1;
-      o0.x = u.x + v.x;
-      o0.y = u.y + v.y;
-      o1.x = u.x - v.x;
-      o1.y = u.y - v.y;
-      a[i * CB + c] = o0;
-      a[(i + h) * CB + c] = o1;
+      const int i0 = ((q >> st) << (st + 1)) + j;
+      bfly<R, INV>(t[i0], t[i0 + h], j * (16 / (2 * h)));
     }
-    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < Rd; ++i) v[i] = t[i];
+}
+
+// one Stockham stage (radix Rd after sub-transforms of size NS) of the
+// calling thread's sequence; src / dst already offset to the sequence
+template <typename R, int LOGN, int Rd, int NS, bool INV>
+__device__ __forceinline__ void stage_ct(const C2<R>* src, C2<R>* dst, const C2<R>* tw, int tid) {
+  constexpr int N = 1 << LOGN, nj = N / Rd, TPS = N / 8;
+#pragma unroll
+  for (int j0 = 0; j0 < nj; j0 += TPS) {
+    const int j = j0 + tid;
+    C2<R> v[Rd];
+#pragma unroll
+    for (int r = 0; r < Rd; ++r) v[r] = src[padi(j + r * nj)];
+    const int js = j & (NS - 1);
+    if (NS > 1) {
+      const int unit = js * (N / (NS * Rd));
+#pragma unroll
+      for (int r = 1; r < Rd; ++r) {
+        C2<R> w = tw[padi(r * unit)];
+        if (INV) w.y = -w.y;
+        const C2<R> x = v[r];
+        v[r].x = x.x * w.x - x.y * w.y;
+        v[r].y = x.x * w.y + x.y * w.x;
+      }
+    }
+    dft_reg<R, Rd, INV>(v);
+    const int d0 = (j - js) * Rd + js;
+#pragma unroll
+    for (int r = 0; r < Rd; ++r) dst[padi(d0 + r * NS)] = v[r];
   }
 }
 
-// The spectral step with the column transforms fused in, for N a power of
-// two.  Z holds the row transforms of x_k ([N][N/2+1], cuFFT's half-plane
-// layout); each block takes CB columns: the column FFT gives X^_k (the 2-D
-// transform of x_k, kept in Xk for the next pass's momentum), the step of
+// the stages from sub-transform size 2^DONE on; data in (cur ? b1 : b0),
+// result in (cur ? b1 : b0) on return; a block barrier after every stage
+template <typename R, int LOGN, int DONE, bool INV>
+__device__ __forceinline__ void stages_ct(C2<R>* b0, C2<R>* b1, int& cur, const C2<R>* tw, int tid,
+                                          bool active) {
+  if constexpr (DONE < LOGN) {
+    constexpr int LR = LOGN - DONE >= 3 ? 3 : LOGN - DONE;
+    if (active)
+      stage_ct<R, LOGN, 1 << LR, 1 << DONE, INV>(cur ? b1 : b0, cur ? b0 : b1, tw, tid);
+    __syncthreads();
+    cur ^= 1;
+    stages_ct<R, LOGN, DONE + LR, INV>(b0, b1, cur, tw, tid, active);
+  }
+}
+
+// data stride of one sequence in shared memory: padded length + 8, so that
+// the sequences of one row fall in different banks
+__host__ __device__ constexpr int seq_pitch(int n) { return padi(n) + 8; }
+
+// Column-kernel configuration for transform length 2^LOGN and complex size
+// CBYTES: CB columns per block (one 32-byte sector of each row, fewer when
+// the shared memory would pass kColSmemCap) and PF, the prefetch of the
+// block's X^_{k-1}, B^ and K^ when it fits.
+constexpr size_t kColSmemCap = 200 * 1024;
+#ifndef MS_COL_ROW_BYTES
+#define MS_COL_ROW_BYTES 32
+#endif
+constexpr size_t col_smem_c(int n, int cb, size_t cbytes, bool pf) {
+  return (2 * (size_t)cb * seq_pitch(n) + padi(n) + 1) * cbytes +
+         (pf ? (size_t)cb * seq_pitch(n) * (2 * cbytes + cbytes / 2) : 0);
+}
+constexpr int col_cb_c(int n, size_t cbytes, bool pf) {
+  int cb = (int)(MS_COL_ROW_BYTES / cbytes) > 4 ? 4 : (int)(MS_COL_ROW_BYTES / cbytes);
+  if (cb < 1) cb = 1;
+  while (cb > 1 && col_smem_c(n, cb, cbytes, pf) > kColSmemCap) cb /= 2;
+  return cb;
+}
+template <typename R, int LOGN> struct ColCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr size_t CBY = sizeof(C2<R>);
+  static constexpr bool PF = col_smem_c(N, col_cb_c(N, CBY, true), CBY, true) <= kColSmemCap;
+  static constexpr int CB = col_cb_c(N, CBY, PF);
+  static constexpr int TPS = N / 8;
+  static constexpr int THREADS = CB * TPS < 32 ? 32 : CB * TPS;
+  static constexpr size_t SMEM = col_smem_c(N, CB, CBY, PF);
+  static_assert(THREADS <= 1024 && THREADS % 32 == 0, "column block");
+};
+
+// The spectral step with the column transforms fused in, for N = 2^LOGN.
+// Z holds the row transforms of x_k ([N][N/2+1], the half-plane layout);
+// each block takes CB columns: the column FFT gives X^_k (the 2-D transform
+// of x_k, kept in Xk for the next pass's momentum), the step of
 // spec_mul_kernel forms S = 2 (K^((1 + t) X^_k - t X^_{k-1}) - B^) and the
-// objective partials, and the inverse column FFT of S goes back into Z, whose
-// inverse row transforms then give the gradient image.
-template <typename R, int CB>
-__global__ void __launch_bounds__(kThreads) spec_col_kernel(
+// objective partials, and the inverse column FFT of S goes back into Z,
+// whose inverse row transforms then give the gradient image.  Global accesses
+// take one row's CB columns per lane group (coalesced) and are asynchronous
+// copies issued at the start: the columns of Z, and (PF) the block's
+// X^_{k-1}, K^ and B^, which arrive while the forward transforms run.
+template <typename R, int LOGN>
+__global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
     C2<R>* __restrict__ Z, C2<R>* __restrict__ Xk, const C2<R>* __restrict__ Xprev,
     const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, const C2<R>* __restrict__ tw_g,
-    int N, int logN, double* __restrict__ parts, FistaCtl* __restrict__ ctl,
-    double* __restrict__ trace, int32_t* ticket, const double* __restrict__ l1_parts, int n_l1) {
+    double* __restrict__ parts, FistaCtl* __restrict__ ctl, double* __restrict__ trace,
+    int32_t* ticket, const double* __restrict__ l1_parts, int n_l1) {
+  using Cfg = ColCfg<R, LOGN>;
+  constexpr int N = Cfg::N, CB = Cfg::CB, T = Cfg::THREADS, P = seq_pitch(N);
+  constexpr bool PF = Cfg::PF;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* b0 = reinterpret_cast<C2<R>*>(smem_raw);   // [CB][P]
+  C2<R>* b1 = b0 + CB * P;                           // [CB][P]
+  C2<R>* tw = b1 + CB * P;                           // [pad(N) + 1]
+  // the twiddle table is written once per plan: staged while the
+  // predecessor kernel finishes
+  for (int m = threadIdx.x; m < N; m += T) cp_async<sizeof(C2<R>)>(tw + padi(m), tw_g + m);
+  cp_async_commit();
   pdl_wait();
   pdl_trigger();
-  if (ctl->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<R>* A = reinterpret_cast<C2<R>*>(smem_raw);   // [N][CB] forward
-  C2<R>* Bf = A + N * CB;                          // [N][CB] inverse
-  C2<R>* tw = Bf + N * CB;                         // [N/2]
-  const int nc = N / 2 + 1;
+  if (ctl->done) {
+    cp_async_wait<0>();
+    return;
+  }
+  C2<R>* sP = tw + padi(N) + 1;                      // PF: [CB][P] X^_{k-1}
+  C2<R>* sB = sP + CB * P;                           // PF: [CB][P] B^
+  R* sK = reinterpret_cast<R*>(sB + CB * P);         // PF: [CB][P] K^
+  constexpr int nc = N / 2 + 1;
   const int c0 = blockIdx.x * CB;
+  const int ccol = threadIdx.x / Cfg::TPS, tcol = threadIdx.x - ccol * Cfg::TPS;
+  const bool active = ccol < CB;
+  // element e = (row e / CB, column e mod CB); lanes cover whole rows
+  for (int e = threadIdx.x; e < N * CB; e += T) {
+    const int r = e / CB, c = e - r * CB;
+    C2<R>* d = b0 + c * P + padi(r);
+    if (c0 + c < nc) {
+      cp_async<sizeof(C2<R>)>(d, Z + (int64_t)r * nc + c0 + c);
+    } else {
+      d->x = (R)0;
+      d->y = (R)0;
+    }
+  }
+  cp_async_commit();
+  if (PF) {
+    for (int e = threadIdx.x; e < N * CB; e += T) {
+      const int r = e / CB, c = e - r * CB;
+      if (c0 + c < nc) {
+        const int64_t k = (int64_t)r * nc + c0 + c;
+        const int o = c * P + padi(r);
+        cp_async<sizeof(C2<R>)>(sP + o, Xprev + k);
+        cp_async<sizeof(C2<R>)>(sB + o, Bs + k);
+        cp_async<sizeof(R)>(sK + o, Ks + k);
+      }
+    }
+    cp_async_commit();
+  }
   const int kit = ctl->k;
   const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
   const double rtol = ctl->rel_tol;
@@ -479,80 +659,338 @@ __global__ void __launch_bounds__(kThreads) spec_col_kernel(
   const R t = ctl_t<R>(ctl, kit & 1);
   const double inv_theta = ctl->inv_theta;
   const R a = (R)1 + t;
-  const int shift = 32 - logN;
-  for (int m = threadIdx.x; m < N / 2; m += blockDim.x) tw[m] = tw_g[m];
-  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
-    const int r = e / CB, c = e - r * CB;
-    C2<R> z;
-    z.x = (R)0;
-    z.y = (R)0;
-    if (c0 + c < nc) z = Z[(int64_t)r * nc + c0 + c];
-    A[(int)(__brev((unsigned)r) >> shift) * CB + c] = z;
-  }
   double l1s = 0.0;
-  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t i = first; i < n_l1; i += (int64_t)gridDim.x * blockDim.x)
-    l1s += __ldcg(l1_parts + i);
+  const int64_t first = blockIdx.x * (int64_t)T + threadIdx.x;
+  for (int64_t i = first; i < n_l1; i += (int64_t)gridDim.x * T) l1s += __ldcg(l1_parts + i);
+  if (PF) cp_async_wait<1>();   // twiddles and the columns of Z (the prefetch may still run)
+  else cp_async_wait<0>();
   __syncthreads();
-  col_fft<R, CB>(A, tw, N, logN, false);
+  int cur = 0;
+  C2<R>* c_b0 = b0 + (active ? ccol : 0) * P;
+  C2<R>* c_b1 = b1 + (active ? ccol : 0) * P;
+  stages_ct<R, LOGN, 0, false>(c_b0, c_b1, cur, tw, tcol, active);
+  if (PF) cp_async_wait<0>();   // this thread's own prefetched elements
+  C2<R>* X = cur ? b1 : b0;
   R s0 = 0, cc0 = 0, s1 = 0, cc1 = 0;
-  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
-    const int r = e / CB, c = e - r * CB;
+  auto step = [&](int r, int c, const C2<R>& Pv, R kk, const C2<R>& Bv) {
     const int col = c0 + c;
+    C2<R>* xp = X + c * P + padi(r);
+    const C2<R> Xv = *xp;
+    const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
+    R y0 = w * kk * (Xv.x * Xv.x + Xv.y * Xv.y) - cc0;
+    R t0 = s0 + y0;
+    cc0 = (t0 - s0) - y0;
+    s0 = t0;
+    R y1 = w * (Bv.x * Xv.x + Bv.y * Xv.y) - cc1;
+    R t1 = s1 + y1;
+    cc1 = (t1 - s1) - y1;
+    s1 = t1;
     C2<R> S;
-    S.x = (R)0;
-    S.y = (R)0;
-    if (col < nc) {
-      const int64_t k = (int64_t)r * nc + col;
-      const C2<R> X = A[r * CB + c];
-      const C2<R> P = Xprev[k];
-      const R kk = Ks[k];
-      const C2<R> B = Bs[k];
-      const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
-      R y0 = w * kk * (X.x * X.x + X.y * X.y) - cc0;
-      R t0 = s0 + y0;
-      cc0 = (t0 - s0) - y0;
-      s0 = t0;
-      R y1 = w * (B.x * X.x + B.y * X.y) - cc1;
-      R t1 = s1 + y1;
-      cc1 = (t1 - s1) - y1;
-      s1 = t1;
-      S.x = (R)2 * (kk * (a * X.x - t * P.x) - B.x);
-      S.y = (R)2 * (kk * (a * X.y - t * P.y) - B.y);
-      Xk[k] = X;
+    S.x = (R)2 * (kk * (a * Xv.x - t * Pv.x) - Bv.x);
+    S.y = (R)2 * (kk * (a * Xv.y - t * Pv.y) - Bv.y);
+    Xk[(int64_t)r * nc + col] = Xv;
+    *xp = S;   // same element, same thread: no barrier needed before
+  };
+  if (PF) {
+    for (int e = threadIdx.x; e < N * CB; e += T) {
+      const int r = e / CB, c = e - r * CB;
+      const int o = c * P + padi(r);
+      if (c0 + c < nc) {
+        step(r, c, sP[o], sK[o], sB[o]);
+      } else {
+        X[o].x = (R)0;
+        X[o].y = (R)0;
+      }
     }
-    Bf[(int)(__brev((unsigned)r) >> shift) * CB + c] = S;
+  } else {
+    // direct loads, four elements' loads in flight at a time
+    constexpr int U = 4;
+    for (int e0 = threadIdx.x; e0 < N * CB; e0 += U * T) {
+      C2<R> Pv[U], Bv[U];
+      R kk[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * T, r = e / CB, c = e - r * CB;
+        if (e < N * CB && c0 + c < nc) {
+          const int64_t k = (int64_t)r * nc + c0 + c;
+          Pv[u] = Xprev[k];
+          kk[u] = Ks[k];
+          Bv[u] = Bs[k];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * T, r = e / CB, c = e - r * CB;
+        if (e >= N * CB) break;
+        if (c0 + c < nc) {
+          step(r, c, Pv[u], kk[u], Bv[u]);
+        } else {
+          X[c * P + padi(r)].x = (R)0;
+          X[c * P + padi(r)].y = (R)0;
+        }
+      }
+    }
   }
   __syncthreads();
-  col_fft<R, CB>(Bf, tw, N, logN, true);
-  for (int e = threadIdx.x; e < N * CB; e += blockDim.x) {
+  stages_ct<R, LOGN, 0, true>(c_b0, c_b1, cur, tw, tcol, active);
+  const C2<R>* Y = cur ? b1 : b0;
+  for (int e = threadIdx.x; e < N * CB; e += T) {
     const int r = e / CB, c = e - r * CB;
-    if (c0 + c < nc) Z[(int64_t)r * nc + c0 + c] = Bf[r * CB + c];
+    if (c0 + c < nc) Z[(int64_t)r * nc + c0 + c] = Y[c * P + padi(r)];
   }
-  spec_finish<R>(s0, cc0, s1, cc1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, kit, c0v, lam,
-                 Fprev, rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
+  spec_finish<R>(s0, cc0, s1, cc1, l1s, (int64_t)blockIdx.x * T < n_l1, kit, c0v, lam, Fprev,
+                 rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
 }
 
-#ifndef MS_COL_CB
-#define MS_COL_CB 2   // columns per block of the fused spectral step
-#endif
-constexpr int kColCB = MS_COL_CB;
-int spec_col_blocks(int N) { return (N / 2 + 1 + kColCB - 1) / kColCB; }
+// ------------------------------------------------------------ row transforms
+// Real transforms of the N rows of length N = 2^LOGN through complex
+// transforms of length M = N/2 (the standard packing of a real sequence):
+// z_n = x_2n + i x_2n+1, Z = FFT_M(z), and for k = 0..M, with Z_M = Z_0,
+//   E_k = (Z_k + conj Z_(M-k)) / 2,  O_k = -i (Z_k - conj Z_(M-k)) / 2,
+//   X_k = E_k + W_N^k O_k.
+// The inverse (unnormalized, the imaginary parts of X_0 and X_M ignored)
+// forms Z'_k = (X_k + conj X_(M-k)) + i W_N^-k (X_k - conj X_(M-k)), k < M,
+// and x_2n + i x_2n+1 = sum_k Z'_k W_M^-kn.  One row per M/8 threads, RB
+// rows per block.
+template <typename R, int LOGN> struct RowCfg {
+  static constexpr int N = 1 << LOGN, M = N / 2;
+  static constexpr int TPS = M / 8 > 0 ? M / 8 : 1;
+  static constexpr int RB = 256 / TPS < 1 ? 1 : (256 / TPS > N ? N : 256 / TPS);
+  static constexpr int THREADS = RB * TPS < 32 ? 32 : RB * TPS;
+  // two buffers of RB rows, the M-point twiddle table W_M^m = W_N^2m
+  // (padded) and W_N^k, k <= M, for the packing step
+  static constexpr size_t SMEM =
+      (2 * (size_t)RB * seq_pitch(M) + padi(M) + 1 + M + 1) * sizeof(C2<R>);
+  static_assert(THREADS <= 1024 && THREADS % 32 == 0, "row block");
+};
+
+template <typename R, int LOGN>
+__global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_r2c_kernel(
+    const R* __restrict__ x, C2<R>* __restrict__ Z, const C2<R>* __restrict__ tw_g,
+    const FistaCtl* __restrict__ ctl) {
+  using Cfg = RowCfg<R, LOGN>;
+  constexpr int M = Cfg::M, RB = Cfg::RB, P = seq_pitch(M), nc = M + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* b0 = reinterpret_cast<C2<R>*>(smem_raw);   // [RB][P]
+  C2<R>* b1 = b0 + RB * P;                           // [RB][P]
+  C2<R>* tw = b1 + RB * P;                           // [pad(M) + 1]
+  C2<R>* twn = tw + padi(M) + 1;                     // [M + 1]
+  // twiddles (written once per plan) staged while the predecessor finishes
+  for (int m = threadIdx.x; m < M; m += Cfg::THREADS)
+    cp_async<sizeof(C2<R>)>(tw + padi(m), tw_g + 2 * m);
+  for (int k = threadIdx.x; k <= M; k += Cfg::THREADS) cp_async<sizeof(C2<R>)>(twn + k, tw_g + k);
+  cp_async_commit();
+  pdl_wait();
+  pdl_trigger();
+  if (ctl->done) {
+    cp_async_wait<0>();
+    return;
+  }
+  const int rr = threadIdx.x / Cfg::TPS, t = threadIdx.x - rr * Cfg::TPS;
+  const bool active = rr < RB;
+  const int row0 = blockIdx.x * RB;
+  const C2<R>* xin = reinterpret_cast<const C2<R>*>(x) + (int64_t)row0 * M;   // pairs
+  for (int e = threadIdx.x; e < RB * M; e += Cfg::THREADS) {
+    const int q = e / M, n = e - q * M;
+    cp_async<sizeof(C2<R>)>(b0 + q * P + padi(n), xin + e);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  int cur = 0;
+  stages_ct<R, LOGN - 1, 0, false>(b0 + (active ? rr : 0) * P, b1 + (active ? rr : 0) * P, cur,
+                                   tw, t, active);
+  if (!active) return;
+  const C2<R>* Zs = (cur ? b1 : b0) + rr * P;
+  C2<R>* out = Z + (int64_t)(row0 + rr) * nc;
+  for (int k = t; k <= M; k += Cfg::TPS) {
+    const C2<R> zk = Zs[padi(k == M ? 0 : k)], zm = Zs[padi(k == 0 ? 0 : M - k)];
+    const R ex = (R)0.5 * (zk.x + zm.x), ey = (R)0.5 * (zk.y - zm.y);
+    const R ox = (R)0.5 * (zk.y + zm.y), oy = (R)-0.5 * (zk.x - zm.x);
+    const C2<R> w = twn[k];   // W_N^k, k <= N/2
+    C2<R> X;
+    X.x = ex + (w.x * ox - w.y * oy);
+    X.y = ey + (w.x * oy + w.y * ox);
+    out[k] = X;
+  }
+}
+
+template <typename R, int LOGN>
+__global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
+    const C2<R>* __restrict__ Z, R* __restrict__ x, const C2<R>* __restrict__ tw_g,
+    const FistaCtl* __restrict__ ctl) {
+  using Cfg = RowCfg<R, LOGN>;
+  constexpr int M = Cfg::M, RB = Cfg::RB, P = seq_pitch(M), nc = M + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<R>* b0 = reinterpret_cast<C2<R>*>(smem_raw);   // [RB][P]
+  C2<R>* b1 = b0 + RB * P;                           // [RB][P]
+  C2<R>* tw = b1 + RB * P;                           // [pad(M) + 1]
+  C2<R>* twn = tw + padi(M) + 1;                     // [M + 1]
+  for (int m = threadIdx.x; m < M; m += Cfg::THREADS)
+    cp_async<sizeof(C2<R>)>(tw + padi(m), tw_g + 2 * m);
+  for (int k = threadIdx.x; k <= M; k += Cfg::THREADS) cp_async<sizeof(C2<R>)>(twn + k, tw_g + k);
+  cp_async_commit();
+  pdl_wait();
+  pdl_trigger();
+  if (ctl->done) {
+    cp_async_wait<0>();
+    return;
+  }
+  const int rr = threadIdx.x / Cfg::TPS, t = threadIdx.x - rr * Cfg::TPS;
+  const bool active = rr < RB;
+  const int row0 = blockIdx.x * RB;
+  // the rows' M + 1 spectrum values into b1 (pad(M) < P)
+  for (int e = threadIdx.x; e < RB * nc; e += Cfg::THREADS) {
+    const int q = e / nc, k = e - q * nc;
+    cp_async<sizeof(C2<R>)>(b1 + q * P + padi(k), Z + (int64_t)row0 * nc + e);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+  if (active) {
+    const C2<R>* Y = b1 + rr * P;
+    C2<R>* Zp = b0 + rr * P;
+    for (int k = t; k < M; k += Cfg::TPS) {
+      C2<R> a = Y[padi(k)], b = Y[padi(M - k)];
+      if (k == 0) {
+        a.y = (R)0;
+        b.y = (R)0;
+      }
+      const R sx = a.x + b.x, sy = a.y - b.y;   // X_k + conj X_(M-k)
+      const R dx = a.x - b.x, dy = a.y + b.y;   // X_k - conj X_(M-k)
+      const C2<R> w = twn[k];                   // W_N^k; times its conjugate below
+      const R fx = w.x * dx + w.y * dy, fy = w.x * dy - w.y * dx;
+      C2<R> zp;
+      zp.x = sx - fy;   // + i (fx + i fy)
+      zp.y = sy + fx;
+      Zp[padi(k)] = zp;
+    }
+  }
+  __syncthreads();
+  int cur = 0;
+  stages_ct<R, LOGN - 1, 0, true>(b0 + (active ? rr : 0) * P, b1 + (active ? rr : 0) * P, cur,
+                                  tw, t, active);
+  if (!active) return;
+  const C2<R>* zs = (cur ? b1 : b0) + rr * P;
+  C2<R>* xo = reinterpret_cast<C2<R>*>(x) + (int64_t)(row0 + rr) * M;
+  for (int n = t; n < M; n += Cfg::TPS) xo[n] = zs[padi(n)];
+}
+
+namespace {
+// dispatch over the supported transform lengths 2^4 .. 2^13
+template <template <int> class F, typename... A> cudaError_t by_logn(int logN, A... args) {
+  switch (logN) {
+    case 4: return F<4>::go(args...);
+    case 5: return F<5>::go(args...);
+    case 6: return F<6>::go(args...);
+    case 7: return F<7>::go(args...);
+    case 8: return F<8>::go(args...);
+    case 9: return F<9>::go(args...);
+    case 10: return F<10>::go(args...);
+    case 11: return F<11>::go(args...);
+    case 12: return F<12>::go(args...);
+    case 13: return F<13>::go(args...);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int log2_exact(int N) {
+  int l = 0;
+  while ((1 << l) < N) ++l;
+  return (1 << l) == N ? l : -1;
+}
+template <typename R> struct ColLaunch {
+  template <int LOGN> struct At {
+    static cudaError_t go(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
+                          const C2<R>* tw, double* parts, FistaCtl* ctl, double* trace,
+                          int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
+      using Cfg = ColCfg<R, LOGN>;
+      auto k = spec_col_kernel<R, LOGN>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+      return launch_pdl(k, dim3((Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB), dim3(Cfg::THREADS),
+                        Cfg::SMEM, s, Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, trace, ticket,
+                        l1_parts, n_l1);
+    }
+  };
+  template <int LOGN> struct Info {
+    static cudaError_t go(int* blocks, size_t* smem) {
+      using Cfg = ColCfg<R, LOGN>;
+      *blocks = (Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB;
+      *smem = Cfg::SMEM;
+      return cudaSuccess;
+    }
+  };
+};
+template <typename R> struct RowLaunch {
+  template <int LOGN> struct R2C {
+    static cudaError_t go(const R* x, C2<R>* Z, const C2<R>* tw, const FistaCtl* ctl,
+                          cudaStream_t s) {
+      using Cfg = RowCfg<R, LOGN>;
+      auto k = row_r2c_kernel<R, LOGN>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+      return launch_pdl(k, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS), Cfg::SMEM, s, x, Z, tw,
+                        ctl);
+    }
+  };
+  template <int LOGN> struct C2R {
+    static cudaError_t go(const C2<R>* Z, R* x, const C2<R>* tw, const FistaCtl* ctl,
+                          cudaStream_t s) {
+      using Cfg = RowCfg<R, LOGN>;
+      auto k = row_c2r_kernel<R, LOGN>;
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+      return launch_pdl(k, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS), Cfg::SMEM, s, Z, x, tw,
+                        ctl);
+    }
+  };
+  template <int LOGN> struct Info {
+    static cudaError_t go(size_t* smem) {
+      *smem = RowCfg<R, LOGN>::SMEM;
+      return cudaSuccess;
+    }
+  };
+};
+}  // namespace
+
+// sizes of the fused step's kernels; 0 / SIZE_MAX when N is not supported
+int spec_col_blocks(int N, size_t complex_bytes) {
+  int b = 0;
+  size_t sm = 0;
+  const int l = log2_exact(N);
+  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm);
+  else by_logn<ColLaunch<double>::Info>(l, &b, &sm);
+  return b;
+}
 size_t spec_col_smem(int N, size_t complex_bytes) {
-  return (size_t)(2 * N * kColCB + N / 2) * complex_bytes;
+  int b = 0;
+  size_t sm = SIZE_MAX;
+  const int l = log2_exact(N);
+  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm);
+  else by_logn<ColLaunch<double>::Info>(l, &b, &sm);
+  return sm;
+}
+size_t row_fft_smem(int N, size_t complex_bytes) {
+  size_t sm = SIZE_MAX;
+  const int l = log2_exact(N);
+  if (complex_bytes == 8) by_logn<RowLaunch<float>::Info>(l, &sm);
+  else by_logn<RowLaunch<double>::Info>(l, &sm);
+  return sm;
 }
 
 template <typename R>
 void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
                      const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
                      int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
-  int logN = 0;
-  while ((1 << logN) < N) ++logN;
-  const size_t smem = spec_col_smem(N, sizeof(C2<R>));
-  auto k = spec_col_kernel<R, kColCB>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  launch_pdl(k, dim3(spec_col_blocks(N)), dim3(kThreads), smem, s, Z, Xk, Xprev, Ks, Bs, tw, N,
-             logN, parts, ctl, trace, ticket, l1_parts, n_l1);
+  by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, trace,
+                                     ticket, l1_parts, n_l1, s);
+}
+template <typename R>
+void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
+                    cudaStream_t s) {
+  by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s);
+}
+template <typename R>
+void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, const FistaCtl* ctl,
+                    cudaStream_t s) {
+  by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, s);
 }
 
 template <typename R>
@@ -750,6 +1188,10 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                           FistaCtl*, int32_t*, cudaStream_t);                    \
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
+  template void launch_row_r2c<R>(const R*, C2<R>*, const C2<R>*, int, const FistaCtl*,        \
+                                  cudaStream_t);                                                 \
+  template void launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, const FistaCtl*,        \
+                                  cudaStream_t);                                                 \
   template void launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*, const C2<R>*,        \
                                    const C2<R>*, int, double*, FistaCtl*, double*, int32_t*,     \
                                    const double*, int, cudaStream_t);                            \

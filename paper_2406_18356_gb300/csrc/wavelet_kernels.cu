@@ -14,16 +14,17 @@
 // Both directions are register-blocked: a thread slides over 8 outputs of one
 // row or column with its inputs held in registers, and each basis is a
 // separate template instance so the filter taps are compile-time constant-bank
-// operands.  Global traffic goes through shared memory in whole rows:
-// cp.async prefetches (the coefficient tiles of the FISTA state, the next
-// basis's subband windows) overlap the filtering, and results leave as
-// 16-byte vector stores.
+// operands.  Global traffic goes through shared memory in whole rows: input
+// windows arrive by TMA (level-1 analysis) or cp.async (the next basis's
+// subband windows are prefetched while the current one is filtered), and
+// results leave as 16-byte vector stores.
 //
 // The analysis kernel of the minor cycle also does FISTA's step (Algorithm 1):
-// it builds the gradient image 2((1+t) y_k - t y_{k-1} - b) while staging its
-// input tile, and at each coefficient forms alpha = B_k + t (B_k - B_{k-1})
-// and writes B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient
-// coefficients never reach global memory.
+// its level-1 input is the gradient image 2 (K W alpha_k - b) of the
+// extrapolated point, and at each coefficient it forms
+// alpha = B_k + t (B_k - B_{k-1}) and writes
+// B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient coefficients
+// never reach global memory.
 
 #include "common.cuh"
 
@@ -100,6 +101,14 @@ template <int ST> struct SG {
 #endif
   static constexpr int Q = (ST * (ST / kP) + Threads - 1) / Threads;   // row units per thread
 };
+// Staging table of a synthesis block that sums all M bases (level 1): the
+// 16-byte chunks a thread copies, and their source offsets from the basis's
+// plane (or LL buffer), are the same for every basis, so an interior tile
+// computes them once.  K slots per thread.
+template <typename R, class G> struct SynTab {
+  static constexpr int V = 16 / (int)sizeof(R);
+  static constexpr int K = (4 * G::In * ((G::In + 1 + V - 1) / V) + G::Threads - 1) / G::Threads;
+};
 // the widest tiles (level 1 at N >= 512); the TMA box of the level-1 window
 constexpr int kAT = 32;
 constexpr int kST = 64;
@@ -131,8 +140,12 @@ __host__ __device__ __forceinline__ int fit_tile(int t, int n) {
   while (2 * p <= t && n % (2 * p) == 0) p *= 2;
   return p;
 }
+#ifndef MS_SYN_T1B
+#define MS_SYN_T1B MS_SYN_T1   // synthesis output tile for 512 <= n < 1024
+#endif
 __host__ __device__ __forceinline__ int syn_tile(int n) {   // synthesis output side
-  return fit_tile(n >= 512 ? MS_SYN_T1 : (n >= 256 ? MS_SYN_T2 : MS_SYN_T3), n);
+  return fit_tile(n >= 1024 ? MS_SYN_T1 : (n >= 512 ? MS_SYN_T1B : (n >= 256 ? MS_SYN_T2 : MS_SYN_T3)),
+                  n);
 }
 __host__ __device__ __forceinline__ int ana_tile(int h) {   // analysis subband side
   return fit_tile(h >= 256 ? MS_ANA_T1 : (h >= 128 ? MS_ANA_T2 : 16), h);
@@ -188,31 +201,10 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-__device__ __forceinline__ unsigned saddr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
 // first 128-byte-aligned shared address at or after p
 __device__ __forceinline__ unsigned char* smem_align128(unsigned char* p) {
   const unsigned pad = (128u - (saddr(p) & 127u)) & 127u;
   return p + pad;
-}
-
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-  if (BYTES == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src)
-                 : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(saddr(dst)), "l"(src),
-                 "n"(BYTES)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // 8 decimated outputs from 2*8 + L - 2 inputs held in registers
@@ -239,11 +231,14 @@ __device__ __forceinline__ void fir_up8(const R* lo, const R* hi, R* out) {
   constexpr int L = 2 * (MB + 1);
 #pragma unroll
   for (int r = 0; r < kP; ++r) {
+    // one fused multiply-add per tap and band (a chain, no separate
+    // product and sum)
     R s = 0;
 #pragma unroll
     for (int k = (r & 1); k < L; k += 2) {
       const int i = (r - k) / 2 + L / 2 - 1;
-      s += fh<R>(MB, k) * lo[i] + fg<R>(MB, k) * hi[i];
+      s = fma(fh<R>(MB, k), lo[i], s);
+      s = fma(fg<R>(MB, k), hi[i], s);
     }
     out[r] = s;
   }
@@ -394,6 +389,7 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
   R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][G::In][G::SubS]
   R* zlo = subs + 2 * G::SubSz;                       // [G::T][G::ZS]
   R* zhi = zlo + G::T * G::ZS;
+  int2* tab = reinterpret_cast<int2*>(zhi + G::T * G::ZS);   // [K][G::Threads]
   const int h = N >> j, n = 2 * h;
   const int TS = syn_tile(n);
   const int lts = 31 - __clz(TS);
@@ -407,10 +403,55 @@ __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __r
   for (int q = 0; q < G::Q; ++q)
 #pragma unroll
     for (int cc = 0; cc < kP; ++cc) acc[q][cc] = (R)0;
+  // interior tiles of a level summing several bases stage through the table:
+  // entry = {source offset, shared offset | 1 << 30 for the LL buffer}, or
+  // y = -1 for an unused slot; each thread reads back only its own entries
+  using Tab = SynTab<R, G>;
+  constexpr int V = Tab::V;
+  const int nch = (cnt + 1 + V - 1) / V;
+  const int base_r = r0 / 2 - (kMaxTaps / 2 - 1), base_c = c0 / 2 - kMaxTaps / 2;
+  const bool table = sum_bases && m_hi - m_lo > 1 && base_c >= 0 && base_c + nch * V <= h;
+  if (table) {
+    const int per_sub = cnt * nch;
+    const bool cheap = h >= kMaxTaps / 2;
+    const bool from_ll = j != J;
+#pragma unroll
+    for (int k = 0; k < Tab::K; ++k) {
+      const int e = threadIdx.x + k * G::Threads;
+      int2 t = make_int2(0, -1);
+      if (e < 4 * per_sub) {
+        const int sb = e / per_sub, rem = e - sb * per_sub;
+        const int a = rem / nch, c = rem - a * nch;
+        const int iy = cheap ? wrapc(base_r + a, h) : wrap(base_r + a, h);
+        const int ix = base_c + c * V;
+        int off;
+        if (sb == 0)
+          off = from_ll ? iy * h + ix : iy * N + ix;
+        else if (sb == 1)
+          off = iy * N + h + ix;
+        else if (sb == 2)
+          off = (h + iy) * N + ix;
+        else
+          off = (h + iy) * N + h + ix;
+        t.x = off;
+        t.y = ((sb * G::In + a) * G::SubS + c * V) | ((sb == 0 && from_ll) ? 1 << 30 : 0);
+      }
+      tab[k * G::Threads + threadIdx.x] = t;
+    }
+  }
   auto stage = [&](int m) {
     const R* plane = coef + (int64_t)m * N * N;
     const R* llp = (j == J) ? nullptr : ll_in + (int64_t)m * h * h;
-    synth_stage<R, G>(plane, llp, N, h, r0, c0, cnt, subs + (m & 1) * G::SubSz);
+    R* dst = subs + (m & 1) * G::SubSz;
+    if (table) {
+#pragma unroll
+      for (int k = 0; k < Tab::K; ++k) {
+        const int2 t = tab[k * G::Threads + threadIdx.x];
+        if (t.y >= 0) cp_async<16>(dst + (t.y & ((1 << 30) - 1)), ((t.y >> 30) ? llp : plane) + t.x);
+      }
+    } else {
+      synth_stage<R, G>(plane, llp, N, h, r0, c0, cnt, dst);
+    }
     cp_async_commit();
   };
   stage(m_lo);
@@ -497,8 +538,11 @@ __global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
 }
 
 namespace {
+// staged windows, column-filtered rows and the staging table
 template <int ST> size_t synthesis_smem_bytes(size_t rsz) {
-  return (size_t)(2 * SG<ST>::SubSz + 2 * SG<ST>::T * SG<ST>::ZS) * rsz;
+  const size_t tab = rsz == 4 ? SynTab<float, SG<ST>>::K : SynTab<double, SG<ST>>::K;
+  return (size_t)(2 * SG<ST>::SubSz + 2 * SG<ST>::T * SG<ST>::ZS) * rsz +
+         tab * SG<ST>::Threads * sizeof(int2);
 }
 // the four output subbands alias the input window; + alignment slack,
 // block-sum scratch, mbarrier and flags

@@ -98,13 +98,17 @@ def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
-@pytest.mark.parametrize("N", [48, 128, 512])
-def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N):
-    """48 (level sides 48, 24, 12, 6), 128 and 512 pixels, 4 levels.  At 512
-    pixels the level-1 analysis uses
+@pytest.mark.parametrize("N,J", [(48, 4), (128, 4), (512, 4), (16, 2), (64, 4), (256, 4),
+                                 (1024, 4)])
+def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N, J):
+    """48 (level sides 48, 24, 12, 6; 2-D cuFFT spectral step), and the
+    powers of two 16 ... 1024, whose spectral step runs the column transforms
+    in shared memory with every last-stage radix (16: one radix-16 stage;
+    64, 128, 512, 1024: radix 4, 8, 2, 4 after radix-16 stages; 256: two
+    radix-16 stages).  At 512 pixels and above the level-1 analysis uses
     32-wide tiles whose interior input windows are staged by TMA (edge
     windows by wrapped loads), and synthesis uses 32- and 64-wide tiles."""
-    J, M, iters = 4, 8, 12
+    M, iters = 8, 12
     w = synth.tiny(npix=N, n_ant=12, n_dumps=10, seed=11)
     plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px,
                    precision=precision, levels=J, n_bases=M)
