@@ -239,7 +239,8 @@ def record_traffic(paths, precision):
             base = n.split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
             # (the operator kernels' traffic depends on the call's partition, so
             # only the per-pass families are recorded)
-            for fam, kname in (("spec_mul", "spec_mul_kernel"),):
+            for fam, kname in (("spec_mul", "spec_mul_kernel"), ("spec_mul", "spec_col_kernel"),
+                               ("fft_r2c", "row_r2c_kernel"), ("fft_c2r", "row_c2r_kernel")):
                 if base == kname and fam not in fams:
                     fams[fam] = b
     rec = {"precision": precision, "workload": "ska-mid-like-1024px-9266880vis",
@@ -524,6 +525,12 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def fused_spectral_step(N, rsz):
+    """Whether the library runs the spectral step fused with shared-memory
+    column transforms (N a power of two whose blocks fit in shared memory)."""
+    return N & (N - 1) == 0 and 16 <= N <= (8192 if rsz == 4 else 4096)
+
+
 def family_bytes(fam, N, M, J, rsz, plan):
     """Algorithmic HBM bytes of one span of a kernel family (what the
     operation must move at least once; per minor-cycle pass for the FISTA
@@ -540,7 +547,11 @@ def family_bytes(fam, N, M, J, rsz, plan):
       synth        levels J..2: read details + approximation input, write
                    LL_j-1.
       spec_mul     per half-plane element read X_k, X_k-1, B (complex) and
-                   K (real), write S (complex): 9 rsz.
+                   K (real), write S (complex): 9 rsz; fused with the column
+                   transforms (N a power of two): read the row spectra Z,
+                   X_k-1, B and K, write Z and X_k: 11 rsz.
+      fft_r2c /    (our row transforms, N a power of two) read N^2 reals, write
+      fft_c2r      the N (N/2 + 1) half-plane values, or the reverse.
       degrid       per row: packed cell (4 B) + offsets (2 rsz) + observed and
                    residual value (2 x 2 rsz), plus one read of the (2N)^2
                    complex grid.
@@ -561,7 +572,9 @@ def family_bytes(fam, N, M, J, rsz, plan):
             b += 3 * M * q(j) + M * q(j) + M * q(j - 1)
         return b * rsz
     if fam == "spec_mul":
-        return 9 * rsz * N * (N // 2 + 1)
+        return (11 if fused_spectral_step(N, rsz) else 9) * rsz * N * (N // 2 + 1)
+    if fam in ("fft_r2c", "fft_c2r") and fused_spectral_step(N, rsz):
+        return N * N * rsz + N * (N // 2 + 1) * 2 * rsz
     if fam == "degrid":
         counts = plan.partition_counts()
         rows = (counts["L"] + counts["H"]) / 2.0
@@ -571,7 +584,8 @@ def family_bytes(fam, N, M, J, rsz, plan):
 
 FAMILY_SOURCE = {"synth": "wavelet_kernels.cu", "synth_l1": "wavelet_kernels.cu",
                  "analysis": "wavelet_kernels.cu", "analysis_l1": "wavelet_kernels.cu",
-                 "spec_mul": "spectral_kernels.cu", "degrid": "grid_kernels.cu",
+                 "spec_mul": "spectral_kernels.cu", "fft_r2c": "spectral_kernels.cu",
+                 "fft_c2r": "spectral_kernels.cu", "degrid": "grid_kernels.cu",
                  "grid": "grid_kernels.cu", "fold": "grid_kernels.cu"}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_1024px_fp32.json")
 
@@ -607,13 +621,15 @@ def recorded_traffic(fam, precision):
 
 def roofline_of(prof, w, plan, args):
     """Roofline of the dominant kernel family of the library (largest share of
-    kernel time, cuFFT excluded): algorithmic bytes of one span (family_bytes)
+    kernel time, cuFFT's transforms excluded): algorithmic bytes of one span (family_bytes)
     over the span's average CUDA-event duration, against the measured HBM
     copy bandwidth."""
     hbm, kind = _peaks()
     rsz = 4 if args.precision != "fp64" else 8
     N, M, J = w.npix, 8, 4
-    mine = {k: v for k, v in prof.items() if not k.startswith("fft") and v[0] > 0}
+    ours_fft = fused_spectral_step(N, rsz)   # else the FISTA transforms are cuFFT's
+    mine = {k: v for k, v in prof.items()
+            if (ours_fft or not k.startswith("fft")) and k != "fft_grid" and v[0] > 0}
     fam = max(mine, key=lambda k: mine[k][1])
     launches, total_ms = mine[fam]
     avg_s = total_ms / launches / 1000.0

@@ -162,6 +162,9 @@ __device__ __forceinline__ void pdl_trigger() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+#ifndef MS_PDL
+#define MS_PDL 1   // programmatic dependent launch of the FISTA kernels
+#endif
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t s, Args... args) {
@@ -174,7 +177,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = MS_PDL ? 1 : 0;   // without the attribute: an ordinary launch
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
@@ -318,23 +321,28 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
                        int32_t* ticket, cudaStream_t s);
 // the spectral step with the column FFTs fused in (N a power of two, 16 ..
 // 8192); Z holds the row transforms of x_k on entry and the inverse column
-// transforms of the gradient spectrum on exit; tw = exp(-2 pi i m / N), m < N
+// transforms of the gradient spectrum on exit; tw = exp(-2 pi i m / N),
+// m < N; each warp leaves its sums of the objective terms in
+// parts[i W + warp], i = 0..2 (W = spec_col_warps), for launch_row_c2r
 template <typename R>
 void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
-                     const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
-                     int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s);
+                     const C2<R>* tw, int N, double* parts, const FistaCtl* ctl,
+                     const double* l1_parts, int n_l1, cudaStream_t s);
 int spec_col_blocks(int N, size_t complex_bytes);   // blocks of one launch (0: N unsupported)
+int spec_col_warps(int N, size_t complex_bytes);    // warps of one launch (0: N unsupported)
 // real row transforms of an N x N image (N a power of two, 16 <= N <= 8192)
 // to / from the half-plane layout [N][N/2+1], through complex transforms of
 // length N/2 in shared memory; the inverse is unnormalized and ignores the
 // imaginary parts of columns 0 and N/2; tw as for launch_spec_col; both
-// return at once when ctl->done
+// return at once when ctl->done.  With parts non-null, an extra block of the
+// inverse sums the G warp sums launch_spec_col left and runs the iteration
+// control (objective into trace, ctl update).
 template <typename R>
 void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
                     cudaStream_t s);
 template <typename R>
-void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, const FistaCtl* ctl,
-                    cudaStream_t s);
+void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
+                    const double* parts, int G, double* trace, cudaStream_t s);
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)
 size_t row_fft_smem(int N, size_t complex_bytes);
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)

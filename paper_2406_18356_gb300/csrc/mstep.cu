@@ -24,9 +24,6 @@
 #ifndef MS_FUSED_SPEC_FP32
 #define MS_FUSED_SPEC_FP32 1   // FP32 plans use the fused spectral step too
 #endif
-#ifndef MS_OWN_ROW_FFT_FP32
-#define MS_OWN_ROW_FFT_FP32 0  // FP32 row transforms of the fused step in shared memory
-#endif
 using namespace ms;
 
 namespace {
@@ -244,14 +241,9 @@ struct ms_plan {
   int32_t* err = nullptr;
   int trace_cap = 0;
   cufftHandle c2c = 0, r2c = 0, c2r = 0;
-  // fused spectral step (N a power of two whose column block fits in shared
-  // memory): 1-D row transforms, their buffer and the column twiddles
+  // fused spectral step (N a power of two whose blocks fit in shared
+  // memory): the row-transform buffer and the twiddles
   bool fused_spec = false;
-  // row transforms in shared memory (else 1-D cuFFT plans); measured at
-  // N = 1024 on GB300: faster in FP64 (54 + 52 us against 81 + 83 us per
-  // iteration), 10 us per iteration slower in FP32 within the FISTA graph
-  bool own_rows = false;
-  cufftHandle r2c_rows = 0, c2r_rows = 0;
   void* zrow = nullptr;
   void* twid = nullptr;
   CUtensorMap tmap{};
@@ -587,35 +579,23 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
     ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
   }
   if (p->fused_spec) {
-    // row transforms (cuFFT), the spectral step with the column transforms
-    // fused in, inverse row transforms
+    // row transforms, the spectral step with the column transforms fused in,
+    // inverse row transforms (whose block 0 runs the iteration control)
     {
       KSpan k(p, MS_K_FFT_R2C);
-      if (p->own_rows)
-        launch_row_r2c<R>((const R*)p->xwork, (C2<R>*)p->zrow, (const C2<R>*)p->twid, p->N,
-                          p->ctl, p->ps);
-      else if (sizeof(R) == 8)
-        ckf(cufftExecD2Z(p->r2c_rows, (cufftDoubleReal*)p->xwork, (cufftDoubleComplex*)p->zrow),
-            "D2Z rows");
-      else
-        ckf(cufftExecR2C(p->r2c_rows, (cufftReal*)p->xwork, (cufftComplex*)p->zrow), "R2C rows");
+      launch_row_r2c<R>((const R*)p->xwork, (C2<R>*)p->zrow, (const C2<R>*)p->twid, p->N, p->ctl,
+                        p->ps);
     }
     {
       KSpan k(p, MS_K_SPEC_MUL);
       launch_spec_col<R>((C2<R>*)p->zrow, Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs,
-                         (const C2<R>*)p->twid, p->N, p->parts, p->ctl, p->trace,
-                         p->tickets + 0, p->l1parts, p->n_l1, p->ps);
+                         (const C2<R>*)p->twid, p->N, p->parts, p->ctl, p->l1parts, p->n_l1,
+                         p->ps);
     }
     {
       KSpan k(p, MS_K_FFT_C2R);
-      if (p->own_rows)
-        launch_row_c2r<R>((const C2<R>*)p->zrow, (R*)p->ywork, (const C2<R>*)p->twid, p->N,
-                          p->ctl, p->ps);
-      else if (sizeof(R) == 8)
-        ckf(cufftExecZ2D(p->c2r_rows, (cufftDoubleComplex*)p->zrow, (cufftDoubleReal*)p->ywork),
-            "Z2D rows");
-      else
-        ckf(cufftExecC2R(p->c2r_rows, (cufftComplex*)p->zrow, (cufftReal*)p->ywork), "C2R rows");
+      launch_row_c2r<R>((const C2<R>*)p->zrow, (R*)p->ywork, (const C2<R>*)p->twid, p->N, p->ctl,
+                        p->parts, spec_col_warps(p->N, sizeof(C2<R>)), p->trace, p->ps);
     }
   } else {
     {
@@ -1038,7 +1018,7 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
   p->api3_dev = p->alloc<void*>(3, "ptrs");
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
-  p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_blocks(N, sizeof(C2<R>))), "partials");
+  p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_warps(N, sizeof(C2<R>))), "partials");
   p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
   p->l1parts = p->alloc<double>(p->n_l1, "partials");
   p->tickets = p->alloc<int32_t>(16, "tickets");
@@ -1060,24 +1040,15 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
     int dev_smem = 0;
     ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->dev),
        "device attribute");
-    // The fused step: 1-D row transforms and the shared-memory Stockham
-    // column transforms fused with the spectral step.  Measured at N = 1024
-    // on GB300 it beats the 2-D cuFFT transforms around spec_mul_kernel in
-    // both precisions (FP32: 170 against 173 us per FISTA iteration).
+    // The fused step: shared-memory row transforms and Stockham column
+    // transforms fused with the spectral step.  Measured at N = 1024 on
+    // GB300 it beats the 2-D cuFFT transforms around spec_mul_kernel in both
+    // precisions.
     p->fused_spec = (sizeof(R) == 8 || MS_FUSED_SPEC_FP32) && N >= 16 && N <= 8192 &&
                     (N & (N - 1)) == 0 && spec_col_smem(N, sizeof(C2<R>)) <= (size_t)dev_smem &&
                     row_fft_smem(N, sizeof(C2<R>)) <= (size_t)dev_smem;
   }
   if (p->fused_spec) {
-    p->own_rows = sizeof(R) == 8 || MS_OWN_ROW_FFT_FP32;
-    if (!p->own_rows) {
-      int n[1] = {N};
-      ckf(cufftPlanMany(&p->r2c_rows, 1, n, nullptr, 1, N, nullptr, 1, N / 2 + 1, tr, N),
-          "plan R2C rows");
-      ckf(cufftPlanMany(&p->c2r_rows, 1, n, nullptr, 1, N / 2 + 1, nullptr, 1, N, ti, N),
-          "plan C2R rows");
-      for (cufftHandle h : {p->r2c_rows, p->c2r_rows}) ckf(cufftSetStream(h, s), "set stream");
-    }
     p->zrow = p->alloc<C2<R>>((size_t)N * (N / 2 + 1), "row spectra");
     // twiddles exp(-2 pi i m / N), m < N, in FP64 on the host
     std::vector<C2<R>> tw(N);
@@ -1216,7 +1187,7 @@ void destroy(ms_plan* p) {
   if (!p) return;
   cudaSetDevice(p->dev);
   if (p->fista_exec) cudaGraphExecDestroy(p->fista_exec);
-  for (cufftHandle h : {p->c2c, p->r2c, p->c2r, p->r2c_rows, p->c2r_rows})
+  for (cufftHandle h : {p->c2c, p->r2c, p->c2r})
     if (h) cufftDestroy(h);
   for (void* a : p->allocs) cudaFree(a);
   if (p->batch.fft) cufftDestroy(p->batch.fft);

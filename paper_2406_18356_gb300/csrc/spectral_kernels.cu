@@ -285,19 +285,14 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // it to the trace, raises `done` on convergence or at the iteration budget,
 // and otherwise advances the iteration index to k + 1 for the analysis pass
 // that builds B_{k+1}.
-// End of a spectral step (blockDim.x a multiple of 32): the block sums of the
+// Block sums of a spectral step (blockDim.x a multiple of 32): the
 // objective's two quadratic terms (working-precision pairs (s, -c), combined
-// error-free within each warp, FP64 once per warp) and of the l1 partials the
+// error-free within each warp, FP64 once per warp) and the l1 partials the
 // previous analysis pass left (only the first blocks hold some; has_l1 is
-// uniform over the block); the last block assembles
-// F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1, appends it to the trace,
-// raises `done` on convergence or at the iteration budget and otherwise
-// advances the iteration index, the momentum and the step scalars.
+// uniform over the block); the result is valid in thread 0.
 template <typename R>
-__device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, int kit,
-                            double c0v, double lam, double Fprev, double rtol, int max_iters,
-                            double inv_theta, double* parts, FistaCtl* ctl, double* trace,
-                            int32_t* ticket) {
+__device__ void spec_block_sums(R s0, R c0, R s1, R c1, double l1s, bool has_l1,
+                                double (&v)[3]) {
   __shared__ double red3[3][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   R lo0 = -c0, lo1 = -c1;
@@ -311,47 +306,66 @@ __device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, int
     red3[2][warp] = w2;
   }
   __syncthreads();
-  double v[3] = {0.0, 0.0, 0.0};
+  v[0] = v[1] = v[2] = 0.0;
   if (threadIdx.x == 0)
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
       v[0] += red3[0][q];
       v[1] += red3[1][q];
       v[2] += red3[2][q];
     }
+}
+
+// Iteration control from the summed terms o = (<x,Kx>, <b,x>, ||B_k||_1)
+// (one thread): F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1 goes to the
+// trace; `done` rises on a non-finite F, on convergence or at the iteration
+// budget, else the iteration index, the momentum t_(k+1) and the step
+// scalars advance.
+__device__ void spec_control(const double (&o)[3], FistaCtl* ctl, double* trace) {
+  const int k = ctl->k;
+  const double lam = ctl->lam, Fprev = ctl->F_cur, rtol = ctl->rel_tol;
+  const double inv_theta = ctl->inv_theta;
+  const double l1 = o[2];
+  double F = o[0] - 2.0 * o[1] + ctl->c0 + lam * l1;
+  ctl->l1_cur = l1;
+  ctl->xkx = o[0];
+  ctl->bx = o[1];
+  ctl->F_prev = Fprev;
+  ctl->F_cur = F;
+  trace[k] = F;
+  if (!isfinite(F)) {
+    ctl->error = 4;
+    ctl->done = 1;
+  } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
+    ctl->converged = 1;
+    ctl->done = 1;
+  } else if (k >= ctl->max_iters) {
+    ctl->done = 1;
+  } else {
+    ctl->k = k + 1;
+    const double tn = k + 1 >= 2 ? (double)k / (double)(k + 3) : 0.0;   // t_{k+1}
+    ctl->td[(k + 1) & 1] = tn;
+    ctl->tf[(k + 1) & 1] = (float)tn;
+  }
+  ctl->mud = inv_theta;
+  ctl->thrd = lam * inv_theta;
+  ctl->muf = (float)inv_theta;
+  ctl->thrf = (float)(lam * inv_theta);
+  __threadfence();
+}
+
+// End of the unfused spectral step: block sums, then the last block to
+// finish gathers every block's sums (fixed order) and runs the iteration
+// control.
+template <typename R>
+__device__ void spec_finish(R s0, R c0, R s1, R c1, double l1s, bool has_l1, double* parts,
+                            FistaCtl* ctl, double* trace, int32_t* ticket) {
+  double v[3];
+  spec_block_sums<R>(s0, c0, s1, c1, l1s, has_l1, v);
   const bool mx[3] = {false, false, false};
   if (publish_partials<3>(v, parts, ticket)) {
     double o[3];
     gather_partials<3>(o, parts, mx, ticket);
-    if (threadIdx.x == 0) {
-      const int k = kit;
-      const double l1 = o[2];
-      double F = o[0] - 2.0 * o[1] + c0v + lam * l1;
-      ctl->l1_cur = l1;
-      ctl->xkx = o[0];
-      ctl->bx = o[1];
-      ctl->F_prev = Fprev;
-      ctl->F_cur = F;
-      trace[k] = F;
-      if (!isfinite(F)) {
-        ctl->error = 4;
-        ctl->done = 1;
-      } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
-        ctl->converged = 1;
-        ctl->done = 1;
-      } else if (k >= max_iters) {
-        ctl->done = 1;
-      } else {
-        ctl->k = k + 1;
-        const double tn = k + 1 >= 2 ? (double)k / (double)(k + 3) : 0.0;   // t_{k+1}
-        ctl->td[(k + 1) & 1] = tn;
-        ctl->tf[(k + 1) & 1] = (float)tn;
-      }
-      ctl->mud = inv_theta;
-      ctl->thrd = lam * inv_theta;
-      ctl->muf = (float)inv_theta;
-      ctl->thrf = (float)(lam * inv_theta);
-      __threadfence();
-    }
+    if (threadIdx.x == 0) spec_control(o, ctl, trace);
   }
 }
 
@@ -368,12 +382,7 @@ __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __re
   const int nc = N / 2 + 1;
   const int64_t total = (int64_t)N * nc;
   const int kit = ctl->k;
-  // fields the finalizing block needs, read while the loop runs
-  const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
-  const double rtol = ctl->rel_tol;
-  const int max_iters = ctl->max_iters;
   const R t = ctl_t<R>(ctl, kit & 1);
-  const double inv_theta = ctl->inv_theta;
   const R a = (R)1 + t;
   const float inv_nc = 1.0f / (float)nc;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -419,8 +428,8 @@ __global__ void __launch_bounds__(kThreads, 4) spec_mul_kernel(const C2<R>* __re
       Xprev[k] = S;
     }
   }
-  spec_finish<R>(s0, c0, s1, c1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, kit, c0v, lam,
-                 Fprev, rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
+  spec_finish<R>(s0, c0, s1, c1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, parts, ctl, trace,
+                 ticket);
 }
 
 // ------------------------------------------------- shared-memory transforms
@@ -596,13 +605,17 @@ template <typename R, int LOGN> struct ColCfg {
 // whose inverse row transforms then give the gradient image.  Global accesses
 // take one row's CB columns per lane group (coalesced) and are asynchronous
 // copies issued at the start: the columns of Z, and (PF) the block's
-// X^_{k-1}, K^ and B^, which arrive while the forward transforms run.
+// X^_{k-1}, K^ and B^, which arrive while the forward transforms run.  Each
+// warp leaves its sums of the objective terms in parts[i W + warp] (W warps
+// in all; i = <x,Kx>, <b,x>, the l1 partials); the inverse row transform
+// kernel gathers them and runs the iteration control, so this kernel has no
+// grid-wide tail.
 template <typename R, int LOGN>
 __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
     C2<R>* __restrict__ Z, C2<R>* __restrict__ Xk, const C2<R>* __restrict__ Xprev,
     const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, const C2<R>* __restrict__ tw_g,
-    double* __restrict__ parts, FistaCtl* __restrict__ ctl, double* __restrict__ trace,
-    int32_t* ticket, const double* __restrict__ l1_parts, int n_l1) {
+    double* __restrict__ parts, const FistaCtl* __restrict__ ctl,
+    const double* __restrict__ l1_parts, int n_l1) {
   using Cfg = ColCfg<R, LOGN>;
   constexpr int N = Cfg::N, CB = Cfg::CB, T = Cfg::THREADS, P = seq_pitch(N);
   constexpr bool PF = Cfg::PF;
@@ -616,10 +629,6 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
   cp_async_commit();
   pdl_wait();
   pdl_trigger();
-  if (ctl->done) {
-    cp_async_wait<0>();
-    return;
-  }
   C2<R>* sP = tw + padi(N) + 1;                      // PF: [CB][P] X^_{k-1}
   C2<R>* sB = sP + CB * P;                           // PF: [CB][P] B^
   R* sK = reinterpret_cast<R*>(sB + CB * P);         // PF: [CB][P] K^
@@ -652,16 +661,20 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
     }
     cp_async_commit();
   }
+  // the control block and the l1 partials load while the copies run (the
+  // copies were issued before `done` is known: when it is set, they are
+  // waited for and the block returns)
+  const int done = ctl->done;
   const int kit = ctl->k;
-  const double c0v = ctl->c0, lam = ctl->lam, Fprev = ctl->F_cur;
-  const double rtol = ctl->rel_tol;
-  const int max_iters = ctl->max_iters;
   const R t = ctl_t<R>(ctl, kit & 1);
-  const double inv_theta = ctl->inv_theta;
   const R a = (R)1 + t;
   double l1s = 0.0;
   const int64_t first = blockIdx.x * (int64_t)T + threadIdx.x;
   for (int64_t i = first; i < n_l1; i += (int64_t)gridDim.x * T) l1s += __ldcg(l1_parts + i);
+  if (done) {
+    cp_async_wait<0>();
+    return;
+  }
   if (PF) cp_async_wait<1>();   // twiddles and the columns of Z (the prefetch may still run)
   else cp_async_wait<0>();
   __syncthreads();
@@ -738,8 +751,22 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
     const int r = e / CB, c = e - r * CB;
     if (c0 + c < nc) Z[(int64_t)r * nc + c0 + c] = Y[c * P + padi(r)];
   }
-  spec_finish<R>(s0, cc0, s1, cc1, l1s, (int64_t)blockIdx.x * T < n_l1, kit, c0v, lam, Fprev,
-                 rtol, max_iters, inv_theta, parts, ctl, trace, ticket);
+  // this warp's sums (no block barrier at the end): the inverse row
+  // transform kernel that follows gathers them and runs the iteration
+  // control
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (T / 32);
+  const int64_t wi = (int64_t)blockIdx.x * (T / 32) + (threadIdx.x >> 5);
+  R lo0 = -cc0, lo1 = -cc1;
+  warp_sum_comp<R>(s0, lo0);
+  warp_sum_comp<R>(s1, lo1);
+  double w2 = 0.0;
+  if ((int64_t)blockIdx.x * T < n_l1) w2 = warp_sum(l1s);   // uniform over the block
+  if (lane == 0) {
+    parts[wi] = (double)s0 + (double)lo0;
+    parts[nw + wi] = (double)s1 + (double)lo1;
+    parts[2 * nw + wi] = w2;
+  }
 }
 
 // ------------------------------------------------------------ row transforms
@@ -818,7 +845,8 @@ __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_r2c_kernel(
 template <typename R, int LOGN>
 __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
     const C2<R>* __restrict__ Z, R* __restrict__ x, const C2<R>* __restrict__ tw_g,
-    const FistaCtl* __restrict__ ctl) {
+    FistaCtl* __restrict__ ctl, const double* __restrict__ parts, int G,
+    double* __restrict__ trace) {
   using Cfg = RowCfg<R, LOGN>;
   constexpr int M = Cfg::M, RB = Cfg::RB, P = seq_pitch(M), nc = M + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -836,9 +864,35 @@ __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
     cp_async_wait<0>();
     return;
   }
+  if (parts && blockIdx.x == 0) {
+    // the spectral step (the predecessor, complete) left G warp sums of
+    // each objective term: sum them in a fixed order and run the iteration
+    // control, beside the blocks that transform the rows
+    cp_async_wait<0>();
+    double o[3];
+    const bool mx[3] = {false, false, false};
+    o[0] = o[1] = o[2] = 0.0;
+    constexpr int U = 8;   // a thread's loads of U sums per term in flight together
+    for (int b0 = threadIdx.x; b0 < G; b0 += U * blockDim.x) {
+      double x[3][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int b = b0 + u * blockDim.x;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[i][u] = b < G ? __ldcg(parts + (int64_t)i * G + b) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) o[i] += x[i][u];
+    }
+    block_reduce<3>(o, mx);
+    if (threadIdx.x == 0) spec_control(o, ctl, trace);
+    return;
+  }
   const int rr = threadIdx.x / Cfg::TPS, t = threadIdx.x - rr * Cfg::TPS;
   const bool active = rr < RB;
-  const int row0 = blockIdx.x * RB;
+  const int row0 = (blockIdx.x - (parts ? 1 : 0)) * RB;
   // the rows' M + 1 spectrum values into b1 (pad(M) < P)
   for (int e = threadIdx.x; e < RB * nc; e += Cfg::THREADS) {
     const int q = e / nc, k = e - q * nc;
@@ -898,24 +952,37 @@ int log2_exact(int N) {
   while ((1 << l) < N) ++l;
   return (1 << l) == N ? l : -1;
 }
+// The kernels of the fused step run with plain launches: with programmatic
+// dependent launch their early-launched successors measured slower at
+// N = 1024 (10 us per FISTA iteration for the row kernels).
+#ifndef MS_FFT_PDL
+#define MS_FFT_PDL 0
+#endif
+template <typename... KArgs, typename... Args>
+cudaError_t launch_fft(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args... args) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (MS_FFT_PDL) return launch_pdl(kernel, grid, block, smem, s, args...);
+  kernel<<<grid, block, smem, s>>>(args...);
+  return cudaGetLastError();
+}
 template <typename R> struct ColLaunch {
   template <int LOGN> struct At {
     static cudaError_t go(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
-                          const C2<R>* tw, double* parts, FistaCtl* ctl, double* trace,
-                          int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
+                          const C2<R>* tw, double* parts, const FistaCtl* ctl,
+                          const double* l1_parts, int n_l1, cudaStream_t s) {
       using Cfg = ColCfg<R, LOGN>;
-      auto k = spec_col_kernel<R, LOGN>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-      return launch_pdl(k, dim3((Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB), dim3(Cfg::THREADS),
-                        Cfg::SMEM, s, Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, trace, ticket,
-                        l1_parts, n_l1);
+      return launch_fft(spec_col_kernel<R, LOGN>,
+                        dim3((Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB), dim3(Cfg::THREADS),
+                        Cfg::SMEM, s, Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, l1_parts, n_l1);
     }
   };
   template <int LOGN> struct Info {
-    static cudaError_t go(int* blocks, size_t* smem) {
+    static cudaError_t go(int* blocks, size_t* smem, int* warps) {
       using Cfg = ColCfg<R, LOGN>;
       *blocks = (Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB;
       *smem = Cfg::SMEM;
+      *warps = Cfg::THREADS / 32;
       return cudaSuccess;
     }
   };
@@ -925,20 +992,16 @@ template <typename R> struct RowLaunch {
     static cudaError_t go(const R* x, C2<R>* Z, const C2<R>* tw, const FistaCtl* ctl,
                           cudaStream_t s) {
       using Cfg = RowCfg<R, LOGN>;
-      auto k = row_r2c_kernel<R, LOGN>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-      return launch_pdl(k, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS), Cfg::SMEM, s, x, Z, tw,
-                        ctl);
+      return launch_fft(row_r2c_kernel<R, LOGN>, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS),
+                        Cfg::SMEM, s, x, Z, tw, ctl);
     }
   };
   template <int LOGN> struct C2R {
-    static cudaError_t go(const C2<R>* Z, R* x, const C2<R>* tw, const FistaCtl* ctl,
-                          cudaStream_t s) {
+    static cudaError_t go(const C2<R>* Z, R* x, const C2<R>* tw, FistaCtl* ctl,
+                          const double* parts, int G, double* trace, cudaStream_t s) {
       using Cfg = RowCfg<R, LOGN>;
-      auto k = row_c2r_kernel<R, LOGN>;
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
-      return launch_pdl(k, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS), Cfg::SMEM, s, Z, x, tw,
-                        ctl);
+      return launch_fft(row_c2r_kernel<R, LOGN>, dim3(Cfg::N / Cfg::RB + (parts ? 1 : 0)),
+                        dim3(Cfg::THREADS), Cfg::SMEM, s, Z, x, tw, ctl, parts, G, trace);
     }
   };
   template <int LOGN> struct Info {
@@ -951,20 +1014,28 @@ template <typename R> struct RowLaunch {
 }  // namespace
 
 // sizes of the fused step's kernels; 0 / SIZE_MAX when N is not supported
-int spec_col_blocks(int N, size_t complex_bytes) {
-  int b = 0;
+int spec_col_warps(int N, size_t complex_bytes) {
+  int b = 0, w = 0;
   size_t sm = 0;
   const int l = log2_exact(N);
-  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm);
-  else by_logn<ColLaunch<double>::Info>(l, &b, &sm);
+  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm, &w);
+  else by_logn<ColLaunch<double>::Info>(l, &b, &sm, &w);
+  return b * w;
+}
+int spec_col_blocks(int N, size_t complex_bytes) {
+  int b = 0, w = 0;
+  size_t sm = 0;
+  const int l = log2_exact(N);
+  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm, &w);
+  else by_logn<ColLaunch<double>::Info>(l, &b, &sm, &w);
   return b;
 }
 size_t spec_col_smem(int N, size_t complex_bytes) {
-  int b = 0;
+  int b = 0, w = 0;
   size_t sm = SIZE_MAX;
   const int l = log2_exact(N);
-  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm);
-  else by_logn<ColLaunch<double>::Info>(l, &b, &sm);
+  if (complex_bytes == 8) by_logn<ColLaunch<float>::Info>(l, &b, &sm, &w);
+  else by_logn<ColLaunch<double>::Info>(l, &b, &sm, &w);
   return sm;
 }
 size_t row_fft_smem(int N, size_t complex_bytes) {
@@ -977,10 +1048,10 @@ size_t row_fft_smem(int N, size_t complex_bytes) {
 
 template <typename R>
 void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
-                     const C2<R>* tw, int N, double* parts, FistaCtl* ctl, double* trace,
-                     int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
-  by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, trace,
-                                     ticket, l1_parts, n_l1, s);
+                     const C2<R>* tw, int N, double* parts, const FistaCtl* ctl,
+                     const double* l1_parts, int n_l1, cudaStream_t s) {
+  by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts, ctl,
+                                     l1_parts, n_l1, s);
 }
 template <typename R>
 void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
@@ -988,9 +1059,9 @@ void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl
   by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s);
 }
 template <typename R>
-void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, const FistaCtl* ctl,
-                    cudaStream_t s) {
-  by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, s);
+void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
+                    const double* parts, int G, double* trace, cudaStream_t s) {
+  by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, parts, G, trace, s);
 }
 
 template <typename R>
@@ -1190,11 +1261,11 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
   template void launch_row_r2c<R>(const R*, C2<R>*, const C2<R>*, int, const FistaCtl*,        \
                                   cudaStream_t);                                                 \
-  template void launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, const FistaCtl*,        \
-                                  cudaStream_t);                                                 \
+  template void launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, FistaCtl*,              \
+                                  const double*, int, double*, cudaStream_t);                    \
   template void launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*, const C2<R>*,        \
-                                   const C2<R>*, int, double*, FistaCtl*, double*, int32_t*,     \
-                                   const double*, int, cudaStream_t);                            \
+                                   const C2<R>*, int, double*, const FistaCtl*, const double*,   \
+                                   int, cudaStream_t);                                           \
   template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
                                    FistaCtl*,                                                    \
                                    double*, int32_t*, const double*, int, cudaStream_t);         \
