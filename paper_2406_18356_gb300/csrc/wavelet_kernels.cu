@@ -26,6 +26,8 @@
 // B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient coefficients
 // never reach global memory.
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace ms {
@@ -124,6 +126,9 @@ constexpr int kST = 64;
 #endif
 #ifndef MS_SYN_T3
 #define MS_SYN_T3 16   // synthesis output tile for 16 <= n < 256
+#endif
+#ifndef MS_ANA_L1_TILE
+#define MS_ANA_L1_TILE 1   // level-1 analysis: one block per tile over all bases
 #endif
 #ifndef MS_ANA_T1
 #define MS_ANA_T1 32   // analysis subband tile for h >= 256 (<= kAT)
@@ -909,6 +914,207 @@ __global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
   }
 }
 
+// Level 1 of the minor cycle's analysis + FISTA step with one block per
+// subband tile looping over the M bases (for the widest geometry, 1 < J):
+// the gradient window is staged once (TMA, or cp.async with wrap at the
+// image edge) and serves every basis, and the tiles of B_k and B_{k-1} of the
+// next basis arrive by cp.async (double-buffered) while the current basis is
+// filtered.  The filter's outputs alias its column-filtered rows (both are
+// dead / rewritten only after the block barriers that separate them), so
+// the window survives.  The block's sum of |B_{k+1}| over all bases goes to
+// l1_parts[part_base + tile]; it zeroes the other M - 1 slots of its tile.
+template <typename R> struct AnaTile {
+  using G = AG<kAT>;
+  static constexpr int T = G::T;
+  static constexpr int PF = 2 * 2 * 3 * T * T;   // [buffer][B_k, B_k-1][subband 1..3][T][T]
+  static constexpr size_t bytes() {
+    return (size_t)(G::InSz + 2 * G::YSz + PF) * sizeof(R) + 128 +
+           (G::Threads / 32) * sizeof(double) + sizeof(uint64_t) + 2 * sizeof(int);
+  }
+  static_assert(4 * T * G::GS <= 2 * G::YSz, "the outputs alias the filtered rows");
+};
+
+template <typename R>
+__global__ void __launch_bounds__(AG<kAT>::Threads, 2)
+    analysis_l1_tile_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a,
+                            int use_tma, int part_base) {
+  using A = AnaTile<R>;
+  using G = typename A::G;
+  constexpr int T = A::T;
+  pdl_wait();
+  pdl_trigger();
+  const int done = a.ctl->done;
+  const int kc = a.ctl->k;
+  if (done) return;   // uniform: `done` does not change during this kernel
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* base = smem_align128(smem_raw);
+  R* sIn = reinterpret_cast<R*>(base);   // [G::In][G::InS]
+  R* ylo = sIn + G::InSz;                // [T][G::YS]; also the outputs [4][T][G::GS]
+  R* yhi = ylo + G::YSz;
+  R* gout = ylo;
+  R* pf = yhi + G::YSz;                  // [2][2][3][T][T]
+  double* red = reinterpret_cast<double*>(pf + A::PF);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(red + G::Threads / 32);
+  int* flags = reinterpret_cast<int*>(bar + 1);
+
+  const int k = kc - 1;
+  const R t = ctl_t<R>(a.ctl, k & 1);   // momentum t_k
+  const R mu = ctl_mu<R>(a.ctl);        // 1 / theta
+  const R thr = ctl_thr<R>(a.ctl);      // lambda / theta
+  const R* cur = k % 3 == 0 ? a.B0 : (k % 3 == 1 ? a.B1 : a.B2);
+  const R* prev = k % 3 == 0 ? a.B2 : (k % 3 == 1 ? a.B0 : a.B1);
+  R* next = k % 3 == 0 ? a.B1 : (k % 3 == 1 ? a.B2 : a.B0);
+  const int N = a.N, n = N, h = N / 2;
+  const int tile = blockIdx.x;
+  const int tiles_x = h / T;
+  const int o0y = (tile / tiles_x) * T, o0x = (tile % tiles_x) * T;
+  const int p0y = 2 * o0y, p0x = 2 * o0x;
+  constexpr int ext = G::In;   // 2 T + 14
+  constexpr int NV = Vec<R>::N;
+  constexpr int LNV = NV == 4 ? 2 : 1;
+  using V = typename Vec<R>::T;
+  const int64_t half = (int64_t)a.M * (N / 2) * (N / 2);
+  R* ll_out = a.tmp + half;   // level 1 writes LL buffer (1 & 1)
+
+  // coefficient offset of (subband s = 1..3, row, col) of this tile in basis m
+  auto coef_off = [&](int m, int s, int row, int col) -> int64_t {
+    return (int64_t)m * N * N + (int64_t)((s >= 2 ? h : 0) + o0y + row) * N + (s & 1 ? h : 0) +
+           o0x + col;
+  };
+  // prefetch of basis m's B_k and B_k-1 tiles into buffer m & 1
+  auto prefetch = [&](int m) {
+    constexpr int V16 = 16 / (int)sizeof(R);
+    constexpr int CPR = T / V16;   // 16-byte chunks per tile row
+    R* dst = pf + (m & 1) * (2 * 3 * T * T);
+    for (int e = threadIdx.x; e < 2 * 3 * T * CPR; e += G::Threads) {
+      const int arr = e / (3 * T * CPR), r = e - arr * (3 * T * CPR);
+      const int sb = r / (T * CPR), r2 = r - sb * (T * CPR);
+      const int row = r2 / CPR, ch = r2 - row * CPR;
+      cp_async<16>(dst + ((arr * 3 + sb) * T + row) * T + ch * V16,
+                   (arr ? prev : cur) + coef_off(m, sb + 1, row, ch * V16));
+    }
+    cp_async_commit();
+  };
+
+  // the window: TMA when interior and aligned, else cp.async with wrap
+  if (threadIdx.x == 0) mbar_init(bar, 1);
+  __syncthreads();
+  bool tma = use_tma != 0 && p0x + G::InS <= n && p0y + G::In <= n;
+  if (tma) {
+    if (threadIdx.x == 0) {
+      const bool aligned = (saddr(sIn) & 127u) == 0 &&
+                           (reinterpret_cast<uintptr_t>(&xmap) & 63u) == 0 &&
+                           ((p0x * (int)sizeof(R)) & 15) == 0;
+      flags[1] = aligned ? 1 : 0;
+      if (aligned) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (unsigned)(G::In * G::InS * sizeof(R)));
+        tma_load_2d(sIn, &xmap, p0x, p0y, bar);
+      } else {
+        atomicExch(&a.ctl->error, 8);
+      }
+    }
+    __syncthreads();
+    tma = flags[1] != 0;
+  }
+  if (!tma) {
+    const R* src = a.grad;
+    const bool cheap = n >= ext;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = G::Threads / 32;
+    for (int r = warp; r < ext; r += NW) {
+      const int py = cheap ? wrapc(p0y + r, n) : wrap(p0y + r, n);
+      const R* row = src + (int64_t)py * n;
+      for (int b = lane; b < ext; b += 32) {
+        const int px = cheap ? wrapc(p0x + b, n) : wrap(p0x + b, n);
+        cp_async<sizeof(R)>(sIn + r * G::InS + b, row + px);
+      }
+    }
+  }
+  cp_async_commit();   // (empty on the TMA path)
+  prefetch(0);
+  bool skip = false;
+  if (tma) {
+    unsigned phase = 0;
+    const bool ok = mbar_wait_bounded(bar, phase);
+    skip = __syncthreads_or(!ok) != 0;
+    if (skip && threadIdx.x == 0) atomicExch(&a.ctl->error, 5);
+  }
+  cp_async_wait<1>();   // the window's copies (the first prefetch may still run)
+  __syncthreads();
+  if (skip) {
+    cp_async_wait<0>();
+    return;   // uniform: nothing is written for a tile whose window never arrived
+  }
+
+  KSum<R> l1;
+  constexpr int lto = 5, lpr = lto - LNV, lsub = lto + lpr;   // T = 32
+  static_assert(T == 32, "level-1 tile side");
+  constexpr int items = 3 << lsub;
+  // the bases in sequence, each a straight-line step (a loop around a
+  // switch over the bases raised register pressure into spills)
+  auto step = [&](auto mb) {
+    constexpr int m = decltype(mb)::value;
+    if (m >= a.M) return;
+    if (m + 1 < a.M) prefetch(m + 1);
+    analysis_filter<R, m, G>(sIn, ylo, yhi, gout, T, lto);
+    if (m + 1 < a.M) cp_async_wait<1>();
+    else cp_async_wait<0>();
+    __syncthreads();   // the filter's outputs and basis m's prefetch are visible
+    const R* pc = pf + (m & 1) * (2 * 3 * T * T);
+    const R* pp = pc + 3 * T * T;
+    for (int e = threadIdx.x; e < items; e += G::Threads) {
+      const int sb = e >> lsub;   // subband 1..3 is sb + 1
+      const int rem = e & ((1 << lsub) - 1);
+      const int row = rem >> lpr, c4 = (rem & ((1 << lpr) - 1)) << LNV;
+      const V gv = *reinterpret_cast<const V*>(gout + ((sb + 1) * T + row) * G::GS + c4);
+      const V cv = *reinterpret_cast<const V*>(pc + (sb * T + row) * T + c4);
+      const V qv = *reinterpret_cast<const V*>(pp + (sb * T + row) * T + c4);
+      V nv;
+      R* np = reinterpret_cast<R*>(&nv);
+      const R* gp = reinterpret_cast<const R*>(&gv);
+      const R* cp = reinterpret_cast<const R*>(&cv);
+      const R* qp = reinterpret_cast<const R*>(&qv);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const R alpha = cp[q] + t * (cp[q] - qp[q]);
+        const R z = alpha - mu * gp[q];
+        const R az = fabs(z) - thr;
+        const R nb = az > (R)0 ? copysign(az, z) : (R)0;
+        l1.add(fabs(nb));
+        np[q] = nb;
+      }
+      *reinterpret_cast<V*>(next + coef_off(m, sb + 1, row, c4)) = nv;
+    }
+    // the approximation feeds level 2
+    for (int e = threadIdx.x; e < (1 << lsub); e += G::Threads) {
+      const int row = e >> lpr, c4 = (e & ((1 << lpr) - 1)) << LNV;
+      *reinterpret_cast<V*>(ll_out + (int64_t)m * h * h + (int64_t)(o0y + row) * h + o0x + c4) =
+          *reinterpret_cast<const V*>(gout + row * G::GS + c4);
+    }
+    __syncthreads();   // gout and prefetch buffer m & 1 are reused
+  };
+  step(std::integral_constant<int, 0>{});
+  step(std::integral_constant<int, 1>{});
+  step(std::integral_constant<int, 2>{});
+  step(std::integral_constant<int, 3>{});
+  step(std::integral_constant<int, 4>{});
+  step(std::integral_constant<int, 5>{});
+  step(std::integral_constant<int, 6>{});
+  step(std::integral_constant<int, 7>{});
+  static_assert(kMaxBases == 8, "one step per basis");
+  R hi = l1.s, lo = -l1.c;
+  warp_sum_comp<R>(hi, lo);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)hi + (double)lo;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int q = 0; q < G::Threads / 32; ++q) sum += red[q];
+    a.l1_parts[part_base + tile] = sum;
+    for (int m = 1; m < a.M; ++m) a.l1_parts[part_base + (int64_t)m * gridDim.x + tile] = 0.0;
+  }
+}
+
 int analysis_prox_partials(WaveletGeom g) {
   int total = 0;
   for (int j = 1; j <= g.J; ++j) {
@@ -979,7 +1185,19 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
     const int h = a.N >> j, TO = ana_tile(h);
     const int tiles = (h / TO) * (h / TO);
     const bool run = only_level == 0 || j == only_level || (only_level < 0 && j > 1);
-    if (run) {
+    bool done_here = false;
+    if constexpr (sizeof(R) == 4) {
+      if (run && MS_ANA_L1_TILE && j == 1 && a.J > 1 && TO == kAT && grad_map) {
+        const size_t smem = AnaTile<R>::bytes();
+        auto kern = analysis_l1_tile_kernel<R>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = launch_pdl(kern, dim3(tiles), dim3(AG<kAT>::Threads), smem, s, m,
+                                         a, 1, part_base);
+        if (e != cudaSuccess) return e;
+        done_here = true;
+      }
+    }
+    if (run && !done_here) {
       dim3 grid(tiles, a.M);
       auto go = [&](auto kern, int threads, size_t smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
