@@ -210,7 +210,7 @@ class ClockSampler:
 def record_traffic(paths, precision):
     """DRAM bytes per span of the FISTA kernel families from ncu raw-page CSV
     exports of one FISTA pass captured in launch order (synthesis levels
-    J..1, the spectral step, analysis levels 1..J)."""
+    J..1, the spectral step's kernels, analysis levels 1..J)."""
     import csv
     fams = {}
     for path in paths:
@@ -230,7 +230,8 @@ def record_traffic(paths, precision):
                 b += float(r[idx[m]].replace(",", "")) * scale[units[idx[m]]]
             launches.append((name, b))
         syn = [b for n, b in launches if "synthesis_level_kernel" in n]
-        ana = [b for n, b in launches if "analysis_level_kernel" in n]
+        ana = [b for n, b in launches
+               if "analysis_level_kernel" in n or "analysis_l1_tile_kernel" in n]
         if syn:
             fams["synth"], fams["synth_l1"] = sum(syn[:-1]), syn[-1]
         if ana:

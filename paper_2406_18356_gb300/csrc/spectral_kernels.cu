@@ -596,6 +596,20 @@ template <typename R, int LOGN> struct ColCfg {
   static_assert(THREADS <= 1024 && THREADS % 32 == 0, "column block");
 };
 
+// A compensated sum hi + lo as an FP32 pair (hi, lo) (exact for FP32 input;
+// about 48 significant bits for FP64).
+template <typename R> __device__ __forceinline__ float2 fp32_pair(R hi, R lo) {
+  if constexpr (sizeof(R) == 4) {
+    float s, e;
+    two_sum<float>(hi, lo, s, e);
+    return make_float2(s, e);
+  } else {
+    const double v = hi + lo;
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
 // The spectral step with the column transforms fused in, for N = 2^LOGN.
 // Z holds the row transforms of x_k ([N][N/2+1], the half-plane layout);
 // each block takes CB columns: the column FFT gives X^_k (the 2-D transform
@@ -763,9 +777,11 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
   double w2 = 0.0;
   if ((int64_t)blockIdx.x * T < n_l1) w2 = warp_sum(l1s);   // uniform over the block
   if (lane == 0) {
-    parts[wi] = (double)s0 + (double)lo0;
-    parts[nw + wi] = (double)s1 + (double)lo1;
-    parts[2 * nw + wi] = w2;
+    // as FP32 (hi, lo) pairs, which the control block adds in FP32
+    float2* pp = reinterpret_cast<float2*>(parts);
+    pp[wi] = fp32_pair<R>(s0, lo0);
+    pp[nw + wi] = fp32_pair<R>(s1, lo1);
+    pp[2 * nw + wi] = fp32_pair<double>(w2, 0.0);
   }
 }
 
@@ -854,9 +870,12 @@ __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
   C2<R>* b1 = b0 + RB * P;                           // [RB][P]
   C2<R>* tw = b1 + RB * P;                           // [pad(M) + 1]
   C2<R>* twn = tw + padi(M) + 1;                     // [M + 1]
-  for (int m = threadIdx.x; m < M; m += Cfg::THREADS)
-    cp_async<sizeof(C2<R>)>(tw + padi(m), tw_g + 2 * m);
-  for (int k = threadIdx.x; k <= M; k += Cfg::THREADS) cp_async<sizeof(C2<R>)>(twn + k, tw_g + k);
+  if (!(parts && blockIdx.x == 0)) {   // (the control block needs no twiddles)
+    for (int m = threadIdx.x; m < M; m += Cfg::THREADS)
+      cp_async<sizeof(C2<R>)>(tw + padi(m), tw_g + 2 * m);
+    for (int k = threadIdx.x; k <= M; k += Cfg::THREADS)
+      cp_async<sizeof(C2<R>)>(twn + k, tw_g + k);
+  }
   cp_async_commit();
   pdl_wait();
   pdl_trigger();
@@ -866,28 +885,53 @@ __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
   }
   if (parts && blockIdx.x == 0) {
     // the spectral step (the predecessor, complete) left G warp sums of
-    // each objective term: sum them in a fixed order and run the iteration
-    // control, beside the blocks that transform the rows
-    cp_async_wait<0>();
-    double o[3];
-    const bool mx[3] = {false, false, false};
-    o[0] = o[1] = o[2] = 0.0;
-    constexpr int U = 8;   // a thread's loads of U sums per term in flight together
+    // each objective term as FP32 (hi, lo) pairs: add them in a fixed order
+    // with error-free FP32 additions (the FP64 pipe is slow) and run the
+    // iteration control, beside the blocks that transform the rows
+    __shared__ float2 wred[3][32];
+    const float2* pp = reinterpret_cast<const float2*>(parts);
+    float hi[3] = {0.f, 0.f, 0.f}, lo[3] = {0.f, 0.f, 0.f};
+    constexpr int U = 8;   // a thread's loads of U pairs per term in flight together
     for (int b0 = threadIdx.x; b0 < G; b0 += U * blockDim.x) {
-      double x[3][U];
+      float2 x[3][U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int b = b0 + u * blockDim.x;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) x[i][u] = b < G ? __ldcg(parts + (int64_t)i * G + b) : 0.0;
+        for (int i = 0; i < 3; ++i)
+          x[i][u] = b < G ? __ldcg(pp + (int64_t)i * G + b) : make_float2(0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) o[i] += x[i][u];
+        for (int i = 0; i < 3; ++i) {
+          float sm, e;
+          two_sum<float>(hi[i], x[i][u].x, sm, e);
+          hi[i] = sm;
+          lo[i] += x[i][u].y + e;
+        }
     }
-    block_reduce<3>(o, mx);
-    if (threadIdx.x == 0) spec_control(o, ctl, trace);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      warp_sum_comp<float>(hi[i], lo[i]);
+      if (lane == 0) wred[i][warp] = make_float2(hi[i], lo[i]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double o[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        float h = 0.f, l = 0.f;
+        if (lane < nw) {
+          h = wred[i][lane].x;
+          l = wred[i][lane].y;
+        }
+        warp_sum_comp<float>(h, l);
+        o[i] = (double)h + (double)l;
+      }
+      if (lane == 0) spec_control(o, ctl, trace);
+    }
     return;
   }
   const int rr = threadIdx.x / Cfg::TPS, t = threadIdx.x - rr * Cfg::TPS;
