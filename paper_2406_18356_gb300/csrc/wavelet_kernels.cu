@@ -212,6 +212,12 @@ __device__ __forceinline__ unsigned char* smem_align128(unsigned char* p) {
   return p + pad;
 }
 
+// Tile sides up to MS_COMPACT_T use the compact filters (below).
+#ifndef MS_COMPACT_T
+#define MS_COMPACT_T 16   // tile sides up to this use the compact filters
+#endif
+template <int T> constexpr bool kCompact = T <= MS_COMPACT_T;
+
 // 8 decimated outputs from 2*8 + L - 2 inputs held in registers
 template <typename R, int MB>
 __device__ __forceinline__ void fir_down8(const R* x, R* lo, R* hi) {
@@ -324,6 +330,68 @@ __device__ __forceinline__ void synth_stage(const R* plane, const R* llp, int N,
   }
 }
 
+// The compact synthesis filter (see analysis_filter_compact): output pairs
+// (2 rr, 2 rr + 1) of a unit both read inputs rr - kk + L/2 - 1, kk < L/2,
+// with the even and the odd taps; same summation order as fir_up8.  Used
+// for the levels that write an LL buffer (not the basis sum of level 1).
+template <typename R, int MB, class G>
+__device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, int r0, int c0,
+                                                    const R* sub, R* zlo, R* zhi, R* ll_out,
+                                                    int n) {
+  constexpr int L = 2 * (MB + 1);
+  const int tid = threadIdx.x;
+  const int nseg = TS / kP > 0 ? TS / kP : 1;
+  const int units_a = cnt * 2 * nseg;
+  for (int u = tid; u < units_a; u += G::Threads) {
+    int rest = u / cnt;
+    int b = u - rest * cnt;
+    int pair = rest & 1, seg = rest >> 1;
+    const R* s0 = sub + (pair ? 1 : 0) * G::In * G::SubS + 1 + b;
+    const R* s1 = sub + (pair ? 3 : 2) * G::In * G::SubS + 1 + b;
+    const int first = 4 * seg + 8 - L / 2;
+    R* z = (pair ? zhi : zlo) + (kP * seg) * G::ZS + b;
+#pragma unroll 1
+    for (int rr = 0; rr < kP / 2; ++rr) {
+      R e = 0, o = 0;
+#pragma unroll
+      for (int kk = 0; kk < L / 2; ++kk) {
+        const int i = first + rr - kk + L / 2 - 1;
+        const R x = s0[i * G::SubS], y = s1[i * G::SubS];
+        e = fma(fh<R>(MB, 2 * kk), x, e);
+        e = fma(fg<R>(MB, 2 * kk), y, e);
+        o = fma(fh<R>(MB, 2 * kk + 1), x, o);
+        o = fma(fg<R>(MB, 2 * kk + 1), y, o);
+      }
+      z[(2 * rr) * G::ZS] = e;
+      z[(2 * rr + 1) * G::ZS] = o;
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < G::Q; ++q) {
+    int u = tid + q * G::Threads;
+    int r = u & (TS - 1), seg = u >> lts;
+    if (seg >= nseg) continue;
+    const int first = 4 * seg + 8 - L / 2;
+    const R* lr = zlo + r * G::ZS + first;
+    const R* hr = zhi + r * G::ZS + first;
+    R* dst = ll_out + (int64_t)(r0 + r) * n + c0 + kP * seg;
+#pragma unroll 1
+    for (int rr = 0; rr < kP / 2; ++rr) {
+      R e = 0, o = 0;
+#pragma unroll
+      for (int kk = 0; kk < L / 2; ++kk) {
+        const int i = rr - kk + L / 2 - 1;
+        e = fma(fh<R>(MB, 2 * kk), lr[i], e);
+        e = fma(fg<R>(MB, 2 * kk), hr[i], e);
+        o = fma(fh<R>(MB, 2 * kk + 1), lr[i], o);
+        o = fma(fg<R>(MB, 2 * kk + 1), hr[i], o);
+      }
+      if (kP * seg + 2 * rr < TS) dst[2 * rr] = e;
+      if (kP * seg + 2 * rr + 1 < TS) dst[2 * rr + 1] = o;
+    }
+  }
+}
+
 template <typename R, int MB, class G>
 __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, int c0,
                                             const R* sub, R* zlo, R* zhi, R (&acc)[G::Q][kP],
@@ -331,6 +399,12 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
   constexpr int L = 2 * (MB + 1);
   constexpr int NI = L / 2 + 3;
   const int tid = threadIdx.x;
+  if constexpr (kCompact<G::T>) {
+    if (!sum_bases) {
+      synth_basis_compact<R, MB, G>(TS, lts, cnt, r0, c0, sub, zlo, zhi, ll_out, n);
+      return;
+    }
+  }
   // columns (y): units (b, pair, seg); pair 0 -> zlo from (approximation,
   // high-y/low-x), pair 1 -> zhi from (low-y/high-x, high/high)
   const int nseg = TS / kP > 0 ? TS / kP : 1;
@@ -582,11 +656,66 @@ void launch_synthesis3(const R* const* coef3_dev, R* x, R* tmp, WaveletGeom g,
 }
 
 // ------------------------------------------------------------------ analysis
+// Small tiles (the coarse levels) run the same filters with the output loop
+// rolled and the inputs read from shared memory per tap: a few times more
+// shared-memory loads, a fraction of the code.  A coarse level's blocks each
+// execute one basis's filter once, so its time is set by the instruction
+// fetch of that code, not by the loads.  The sums are formed in the same
+// order as the register-blocked versions, so results are identical.
+
+template <typename R, int MB, class G>
+__device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R* yhi, R* gout,
+                                                        int TOe, int lt) {
+  constexpr int L = 2 * (MB + 1);
+  const int tid = threadIdx.x;
+  const int nparts = TOe >> 3;
+  const int cols = 2 * TOe + L - 2;
+  for (int u = tid; u < nparts * cols; u += G::Threads) {
+    const int part = u / cols;
+    const int col = u - part * cols;
+    const R* xc = sIn + (2 * kP * part) * G::InS + col;
+#pragma unroll 1
+    for (int r = 0; r < kP; ++r) {
+      R a = 0, d = 0;
+#pragma unroll
+      for (int k = 0; k < L; ++k) {
+        const R x = xc[(2 * r + k) * G::InS];
+        a += fh<R>(MB, k) * x;
+        d += fg<R>(MB, k) * x;
+      }
+      ylo[(kP * part + r) * G::YS + col] = a;
+      yhi[(kP * part + r) * G::YS + col] = d;
+    }
+  }
+  __syncthreads();
+  const int lp = lt - 3;
+  const int r = tid & (TOe - 1), seg = (tid >> lt) & (nparts - 1), src = tid >> (lt + lp);
+  __syncthreads();   // (the barrier pair of the register-blocked version)
+  if (src >= 2) return;
+  const R* yrow = (src ? yhi : ylo) + r * G::YS + 2 * kP * seg;
+  R* o_lo = gout + (src ? 2 : 0) * G::T * G::GS + r * G::GS + kP * seg;
+  R* o_hi = gout + (src ? 3 : 1) * G::T * G::GS + r * G::GS + kP * seg;
+#pragma unroll 1
+  for (int q = 0; q < kP; ++q) {
+    R a = 0, d = 0;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+      const R x = yrow[2 * q + k];
+      a += fh<R>(MB, k) * x;
+      d += fg<R>(MB, k) * x;
+    }
+    o_lo[q] = a;
+    o_hi[q] = d;
+  }
+}
+
 // Filtering of one basis on the staged input tile: columns (y) into
 // ylo / yhi, then rows (x) into the four subbands gout[0..3] =
 // (approximation, low-y/high-x, high-y/low-x, high/high), G::T x G::GS each.
 // TOe (a power of two, 8..G::T) outputs per subband side, lt = log2(TOe).
-template <typename R, int MB, class G>
+// (ROWS_IN_REGS: the register-blocked version whatever the tile side, for
+// callers whose outputs alias the column-filtered rows)
+template <typename R, int MB, class G, bool ROWS_IN_REGS = false>
 __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R* gout, int TOe,
                                                 int lt) {
   constexpr int L = 2 * (MB + 1);
@@ -594,44 +723,48 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   const int tid = threadIdx.x;
   const int nparts = TOe >> 3;
   const int cols = 2 * TOe + L - 2;
-  for (int u = tid; u < nparts * cols; u += G::Threads) {
-    int part = u / cols;
-    int col = u - part * cols;
-    R xin[NI];
+  if constexpr (kCompact<G::T> && !ROWS_IN_REGS) {
+    analysis_filter_compact<R, MB, G>(sIn, ylo, yhi, gout, TOe, lt);
+  } else {
+    for (int u = tid; u < nparts * cols; u += G::Threads) {
+      int part = u / cols;
+      int col = u - part * cols;
+      R xin[NI];
 #pragma unroll
-    for (int i = 0; i < NI; ++i) xin[i] = sIn[(2 * kP * part + i) * G::InS + col];
+      for (int i = 0; i < NI; ++i) xin[i] = sIn[(2 * kP * part + i) * G::InS + col];
+      R lo[kP], hi[kP];
+      fir_down8<R, MB>(xin, lo, hi);
+#pragma unroll
+      for (int r = 0; r < kP; ++r) {
+        ylo[(kP * part + r) * G::YS + col] = lo[r];
+        yhi[(kP * part + r) * G::YS + col] = hi[r];
+      }
+    }
+    __syncthreads();
+    // rows: unit = (row r, segment, source); a warp takes consecutive rows of
+    // one segment
+    const int lp = lt - 3;   // log2(nparts)
+    const int r = tid & (TOe - 1), seg = (tid >> lt) & (nparts - 1), src = tid >> (lt + lp);
+    const bool active = src < 2;
+    R xin[NI];
+    if (active) {
+      const R* yrow = (src ? yhi : ylo) + r * G::YS + 2 * kP * seg;
+#pragma unroll
+      for (int i = 0; i < NI; ++i) xin[i] = yrow[i];
+    }
+    __syncthreads();   // the outputs overwrite the input tile
+    if (!active) return;
     R lo[kP], hi[kP];
     fir_down8<R, MB>(xin, lo, hi);
+    R* o_lo = gout + (src ? 2 : 0) * G::T * G::GS + r * G::GS + kP * seg;
+    R* o_hi = gout + (src ? 3 : 1) * G::T * G::GS + r * G::GS + kP * seg;
+    using V = typename Vec<R>::T;
+    constexpr int NV = Vec<R>::N;
 #pragma unroll
-    for (int r = 0; r < kP; ++r) {
-      ylo[(kP * part + r) * G::YS + col] = lo[r];
-      yhi[(kP * part + r) * G::YS + col] = hi[r];
+    for (int q = 0; q < kP; q += NV) {
+      *reinterpret_cast<V*>(o_lo + q) = *reinterpret_cast<const V*>(lo + q);
+      *reinterpret_cast<V*>(o_hi + q) = *reinterpret_cast<const V*>(hi + q);
     }
-  }
-  __syncthreads();
-  // rows: unit = (row r, segment, source); a warp takes consecutive rows of
-  // one segment
-  const int lp = lt - 3;   // log2(nparts)
-  const int r = tid & (TOe - 1), seg = (tid >> lt) & (nparts - 1), src = tid >> (lt + lp);
-  const bool active = src < 2;
-  R xin[NI];
-  if (active) {
-    const R* yrow = (src ? yhi : ylo) + r * G::YS + 2 * kP * seg;
-#pragma unroll
-    for (int i = 0; i < NI; ++i) xin[i] = yrow[i];
-  }
-  __syncthreads();   // the outputs overwrite the input tile
-  if (!active) return;
-  R lo[kP], hi[kP];
-  fir_down8<R, MB>(xin, lo, hi);
-  R* o_lo = gout + (src ? 2 : 0) * G::T * G::GS + r * G::GS + kP * seg;
-  R* o_hi = gout + (src ? 3 : 1) * G::T * G::GS + r * G::GS + kP * seg;
-  using V = typename Vec<R>::T;
-  constexpr int NV = Vec<R>::N;
-#pragma unroll
-  for (int q = 0; q < kP; q += NV) {
-    *reinterpret_cast<V*>(o_lo + q) = *reinterpret_cast<const V*>(lo + q);
-    *reinterpret_cast<V*>(o_hi + q) = *reinterpret_cast<const V*>(hi + q);
   }
 }
 
@@ -1057,7 +1190,7 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
     constexpr int m = decltype(mb)::value;
     if (m >= a.M) return;
     if (m + 1 < a.M) prefetch(m + 1);
-    analysis_filter<R, m, G>(sIn, ylo, yhi, gout, T, lto);
+    analysis_filter<R, m, G, true>(sIn, ylo, yhi, gout, T, lto);
     if (m + 1 < a.M) cp_async_wait<1>();
     else cp_async_wait<0>();
     __syncthreads();   // the filter's outputs and basis m's prefetch are visible
