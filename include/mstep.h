@@ -324,7 +324,10 @@ ms_status ms_unet_train_step(ms_unet* net, const float* in, const float* target,
 /* Kernel families timed by the profiler.  SYNTH / ANALYSIS are the wavelet
  * levels 2..J, *_L1 the first level (the largest); ANALYSIS includes the
  * fused prox of the minor cycle; FFT_GRID is the Ng x Ng transform of the
- * major cycle, FFT_R2C / FFT_C2R the N x N transforms of the minor cycle. */
+ * major cycle, FFT_R2C / FFT_C2R the N x N transforms of the minor cycle
+ * (for N a power of two: the row transforms, the inverse one with the
+ * iteration control) and SPEC_MUL its spectral step (for N a power of two:
+ * fused with the column transforms). */
 typedef enum {
   MS_K_DEGRID = 0, MS_K_GRID = 1, MS_K_FOLD = 2, MS_K_FFT_GRID = 3, MS_K_PAD_CROP = 4,
   MS_K_SYNTH = 5, MS_K_SYNTH_L1 = 6, MS_K_FFT_R2C = 7, MS_K_SPEC_MUL = 8,

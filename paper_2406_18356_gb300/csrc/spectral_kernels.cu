@@ -9,8 +9,16 @@
 // with H^ the (real) PSF spectrum and I^, L^ the spectra of i~ and l_L, so the
 // gradient of Eqs. GradL / GradH is 2 W^H (K x - b) and the Lipschitz constant
 // of Sect. 3.4 is 2 M max K^.  Inner products use Parseval on the rfft
-// half-plane (columns 0 and N/2 once, the others twice).  All reductions are
-// FP64, per-block partials summed by the last block in a fixed order.
+// half-plane (columns 0 and N/2 once, the others twice).  Reductions sum
+// compensated working-precision pairs within warps; across warps and blocks
+// they sum FP64 partials (or, in the fused spectral step, FP32 (hi, lo)
+// pairs, since the FP64 pipe is slow) in a fixed order.
+//
+// For N a power of two the FISTA pass's spectral step is three kernels of
+// this file: real row transforms, the column transforms fused with the
+// spectral multiply and the objective terms, and the inverse row transforms
+// (whose extra block runs the iteration control); other N use 2-D cuFFT
+// transforms around spec_mul_kernel.
 #include "common.cuh"
 
 namespace ms {
