@@ -803,10 +803,15 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
 // forms Z'_k = (X_k + conj X_(M-k)) + i W_N^-k (X_k - conj X_(M-k)), k < M,
 // and x_2n + i x_2n+1 = sum_k Z'_k W_M^-kn.  One row per M/8 threads, RB
 // rows per block.
+#ifndef MS_ROW_THREADS
+#define MS_ROW_THREADS 512   // threads per block of the row transforms (rows x N/16)
+#endif
 template <typename R, int LOGN> struct RowCfg {
   static constexpr int N = 1 << LOGN, M = N / 2;
   static constexpr int TPS = M / 8 > 0 ? M / 8 : 1;
-  static constexpr int RB = 256 / TPS < 1 ? 1 : (256 / TPS > N ? N : 256 / TPS);
+  static constexpr int RB = MS_ROW_THREADS / TPS < 1
+                                ? 1
+                                : (MS_ROW_THREADS / TPS > N ? N : MS_ROW_THREADS / TPS);
   static constexpr int THREADS = RB * TPS < 32 ? 32 : RB * TPS;
   // two buffers of RB rows, the M-point twiddle table W_M^m = W_N^2m
   // (padded) and W_N^k, k <= M, for the packing step
