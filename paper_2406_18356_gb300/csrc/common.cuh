@@ -325,9 +325,10 @@ void launch_b_spectrum(const C2<R>* Ihat, const C2<R>* Lhat, const R* Hhat, cons
 // m < N; each warp leaves its sums of the objective terms in
 // parts[i W + warp], i = 0..2 (W = spec_col_warps), for launch_row_c2r
 template <typename R>
-void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
-                     const C2<R>* tw, int N, double* parts, const FistaCtl* ctl,
-                     const double* l1_parts, int n_l1, cudaStream_t s);
+cudaError_t launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks,
+                            const C2<R>* Bs, const C2<R>* tw, int N, double* parts,
+                            const FistaCtl* ctl, const double* l1_parts, int n_l1,
+                            cudaStream_t s);
 int spec_col_blocks(int N, size_t complex_bytes);   // blocks of one launch (0: N unsupported)
 int spec_col_warps(int N, size_t complex_bytes);    // warps of one launch (0: N unsupported)
 // real row transforms of an N x N image (N a power of two, 16 <= N <= 8192)
@@ -338,11 +339,11 @@ int spec_col_warps(int N, size_t complex_bytes);    // warps of one launch (0: N
 // inverse sums the G warp sums launch_spec_col left and runs the iteration
 // control (objective into trace, ctl update).
 template <typename R>
-void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
-                    cudaStream_t s);
+cudaError_t launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
+                           cudaStream_t s);
 template <typename R>
-void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
-                    const double* parts, int G, double* trace, cudaStream_t s);
+cudaError_t launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
+                           const double* parts, int G, double* trace, cudaStream_t s);
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)
 size_t row_fft_smem(int N, size_t complex_bytes);
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)

@@ -580,22 +580,24 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
   }
   if (p->fused_spec) {
     // row transforms, the spectral step with the column transforms fused in,
-    // inverse row transforms (whose block 0 runs the iteration control)
+    // inverse row transforms (whose extra block runs the iteration control)
+    const C2<R>* tw = (const C2<R>*)p->twid;
+    C2<R>* Z = (C2<R>*)p->zrow;
     {
       KSpan k(p, MS_K_FFT_R2C);
-      launch_row_r2c<R>((const R*)p->xwork, (C2<R>*)p->zrow, (const C2<R>*)p->twid, p->N, p->ctl,
-                        p->ps);
+      ck(launch_row_r2c<R>((const R*)p->xwork, Z, tw, p->N, p->ctl, p->ps), "row transforms");
     }
     {
       KSpan k(p, MS_K_SPEC_MUL);
-      launch_spec_col<R>((C2<R>*)p->zrow, Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs,
-                         (const C2<R>*)p->twid, p->N, p->parts, p->ctl, p->l1parts, p->n_l1,
-                         p->ps);
+      ck(launch_spec_col<R>(Z, Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs, tw, p->N, p->parts,
+                            p->ctl, p->l1parts, p->n_l1, p->ps),
+         "spectral step");
     }
     {
       KSpan k(p, MS_K_FFT_C2R);
-      launch_row_c2r<R>((const C2<R>*)p->zrow, (R*)p->ywork, (const C2<R>*)p->twid, p->N, p->ctl,
-                        p->parts, spec_col_warps(p->N, sizeof(C2<R>)), p->trace, p->ps);
+      ck(launch_row_c2r<R>(Z, (R*)p->ywork, tw, p->N, p->ctl, p->parts,
+                           spec_col_warps(p->N, sizeof(C2<R>)), p->trace, p->ps),
+         "inverse row transforms");
     }
   } else {
     {

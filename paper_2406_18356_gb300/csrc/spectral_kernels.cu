@@ -1104,21 +1104,22 @@ size_t row_fft_smem(int N, size_t complex_bytes) {
 }
 
 template <typename R>
-void launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
-                     const C2<R>* tw, int N, double* parts, const FistaCtl* ctl,
-                     const double* l1_parts, int n_l1, cudaStream_t s) {
-  by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts, ctl,
-                                     l1_parts, n_l1, s);
+cudaError_t launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks,
+                            const C2<R>* Bs, const C2<R>* tw, int N, double* parts,
+                            const FistaCtl* ctl, const double* l1_parts, int n_l1,
+                            cudaStream_t s) {
+  return by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts,
+                                            ctl, l1_parts, n_l1, s);
 }
 template <typename R>
-void launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
-                    cudaStream_t s) {
-  by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s);
+cudaError_t launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
+                           cudaStream_t s) {
+  return by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s);
 }
 template <typename R>
-void launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
-                    const double* parts, int G, double* trace, cudaStream_t s) {
-  by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, parts, G, trace, s);
+cudaError_t launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
+                           const double* parts, int G, double* trace, cudaStream_t s) {
+  return by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, parts, G, trace, s);
 }
 
 template <typename R>
@@ -1316,13 +1317,13 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
                                           FistaCtl*, int32_t*, cudaStream_t);                    \
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
-  template void launch_row_r2c<R>(const R*, C2<R>*, const C2<R>*, int, const FistaCtl*,        \
-                                  cudaStream_t);                                                 \
-  template void launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, FistaCtl*,              \
-                                  const double*, int, double*, cudaStream_t);                    \
-  template void launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*, const C2<R>*,        \
-                                   const C2<R>*, int, double*, const FistaCtl*, const double*,   \
-                                   int, cudaStream_t);                                           \
+  template cudaError_t launch_row_r2c<R>(const R*, C2<R>*, const C2<R>*, int,                \
+                                         const FistaCtl*, cudaStream_t);                         \
+  template cudaError_t launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, FistaCtl*,      \
+                                         const double*, int, double*, cudaStream_t);             \
+  template cudaError_t launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*,             \
+                                          const C2<R>*, const C2<R>*, int, double*,              \
+                                          const FistaCtl*, const double*, int, cudaStream_t);    \
   template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
                                    FistaCtl*,                                                    \
                                    double*, int32_t*, const double*, int, cudaStream_t);         \
