@@ -168,6 +168,15 @@ __device__ __forceinline__ int wrapc(int i, int n) {
   return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// u / d (integer quotient) for 0 <= u < 2^22, d >= 1, through the FP32
+// reciprocal inv = 1 / d: (u + 0.5) / d lies at least 0.5 / d from an
+// integer, and the two roundings move it by at most (u / d) 2^-23 < 0.5 / d,
+// so truncation gives the quotient (a few instructions instead of an integer
+// division)
+__device__ __forceinline__ int div_small(int u, float inv) {
+  return (int)(((float)u + 0.5f) * inv);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
                    (unsigned)__cvta_generic_to_shared(bar)),
@@ -342,8 +351,9 @@ __device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, in
   const int tid = threadIdx.x;
   const int nseg = TS / kP > 0 ? TS / kP : 1;
   const int units_a = cnt * 2 * nseg;
+  const float inv_cnt = 1.0f / (float)cnt;
   for (int u = tid; u < units_a; u += G::Threads) {
-    int rest = u / cnt;
+    int rest = div_small(u, inv_cnt);
     int b = u - rest * cnt;
     int pair = rest & 1, seg = rest >> 1;
     const R* s0 = sub + (pair ? 1 : 0) * G::In * G::SubS + 1 + b;
@@ -409,8 +419,9 @@ __device__ __forceinline__ void synth_basis(int TS, int lts, int cnt, int r0, in
   // high-y/low-x), pair 1 -> zhi from (low-y/high-x, high/high)
   const int nseg = TS / kP > 0 ? TS / kP : 1;
   const int units_a = cnt * 2 * nseg;
+  const float inv_cnt = 1.0f / (float)cnt;
   for (int u = tid; u < units_a; u += G::Threads) {
-    int rest = u / cnt;
+    int rest = div_small(u, inv_cnt);
     int b = u - rest * cnt;
     int pair = rest & 1, seg = rest >> 1;
     // window column b + 1 is filter column b (the window starts one early)
@@ -670,8 +681,9 @@ __device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R*
   const int tid = threadIdx.x;
   const int nparts = TOe >> 3;
   const int cols = 2 * TOe + L - 2;
+  const float inv_cols = 1.0f / (float)cols;
   for (int u = tid; u < nparts * cols; u += G::Threads) {
-    const int part = u / cols;
+    const int part = div_small(u, inv_cols);
     const int col = u - part * cols;
     const R* xc = sIn + (2 * kP * part) * G::InS + col;
 #pragma unroll 1
@@ -726,8 +738,9 @@ __device__ __forceinline__ void analysis_filter(const R* sIn, R* ylo, R* yhi, R*
   if constexpr (kCompact<G::T> && !ROWS_IN_REGS) {
     analysis_filter_compact<R, MB, G>(sIn, ylo, yhi, gout, TOe, lt);
   } else {
+    const float inv_cols = 1.0f / (float)cols;
     for (int u = tid; u < nparts * cols; u += G::Threads) {
-      int part = u / cols;
+      int part = div_small(u, inv_cols);
       int col = u - part * cols;
       R xin[NI];
 #pragma unroll
