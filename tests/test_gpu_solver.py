@@ -123,6 +123,38 @@ def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N, J):
     plan.close()
 
 
+_WIDE = {}
+
+
+def _wide_reference(N):
+    """Oracle FISTA at N = 2048 / 4096 (2 bases, 2 levels, 3 iterations),
+    computed once per size."""
+    if N not in _WIDE:
+        w = synth.tiny(npix=N, n_ant=12, n_dumps=10, seed=11)
+        A = og.GriddedOperator(w.u[0], w.v[0], N, w.pixel_size)
+        res = A.dirty(w.vis[0])
+        lam = 0.05 * np.linalg.norm(res) * 2
+        prob = osv.Problem("low", Dictionary(N, 2, 2), osv.psf_spectrum(A.psf()), res, lam)
+        _WIDE[N] = (w, res, lam, prob, osv.fista(prob, 3))
+    return _WIDE[N]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
+@pytest.mark.parametrize("N", [2048, 4096])
+def test_minor_cycle_wide_images_match_oracle(ms, precision, tol, N):
+    """The spectral step's transforms at 2048 and 4096 pixels: last radix 4
+    and 8, one column per block, and (FP64 at 4096) the column kernel
+    without the shared-memory prefetch of X^_{k-1}, K^ and B^."""
+    w, res, lam, prob, ref = _wide_reference(N)
+    plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px,
+                   precision=precision, levels=2, n_bases=2)
+    model, st = plan.minor_cycle("single", cuda(res).to(plan.real_dtype), lam, 3)
+    np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
+    assert rel(model.cpu().numpy(), prob.W.synth(ref.beta)) <= 10 * tol
+    plan.close()
+
+
 def test_minor_cycle_relative_tolerance_stop_and_warm_start(ms):
     J, M = 3, 8
     w, plan = _setup(ms, J=J, M=M)
