@@ -31,8 +31,9 @@ Modules
 Parity status
 -------------
 Every function is pinned by a ``-m "not gpu"`` test against something other
-than itself (closed forms, brute force, invariants, special cases), except the
-end-to-end reconstructions of ``imaging``: their final images have no printed
-worked example in the paper, so beyond the pins of their parts they are
-**parity unpinned**.
+than itself (closed forms, brute force, invariants, special cases).  The
+end-to-end reconstructions of ``imaging`` have no printed worked example in
+the paper; they are pinned by exact recovery: with one noise-free visibility
+at every image frequency and lambda = 0, the single-step image is the sky and
+the two-step image converges to it.
 """

@@ -65,3 +65,54 @@ def test_minor_cycles_lower_their_objective():
             assert trace[-1] <= trace[0]
     dirty = GriddedOperator(u, v, 32, w.pixel_size).dirty(vis)
     assert oi.psnr(single.image, w.truth) > oi.psnr(dirty, w.truth)
+
+
+def _complete_coverage(npix, dl, rng):
+    """One visibility at every frequency of the npix x npix image DFT (on the
+    oversampled grid's cells) for a random real sky, exact under the gridded
+    model (no noise)."""
+    k = np.arange(-npix // 2, npix // 2)
+    kx, ky = np.meshgrid(k, k)
+    u = kx.ravel() / (npix * dl)
+    v = ky.ravel() / (npix * dl)
+    sky = rng.standard_normal((npix, npix))
+    return u, v, sky, GriddedOperator(u, v, npix, dl).forward(sky)
+
+
+def test_single_step_recovers_the_sky_with_complete_coverage():
+    # With every image frequency sampled on the grid, A^H A is exactly the
+    # PSF's circular convolution, so with lambda = 0 the minor cycle's model
+    # is exact and the major cycles reach the sky itself (the fixed point
+    # A^H (v - A x) = 0 of a full-rank A): a check of the residual and PSF
+    # normalization, the model update and image = residual + model.
+    rng = np.random.default_rng(3)
+    u, v, sky, vis = _complete_coverage(16, 1e-4, rng)
+    opts = oi.ReconOptions(n_major=3, fista_iters=100, lambda_single=0.0, levels=2, n_bases=2)
+    out = oi.reconstruct_single_step(vis, u, v, 16, 1e-4, opts)
+    assert np.linalg.norm(out.image - sky) <= 1e-12 * np.linalg.norm(sky)
+    assert np.linalg.norm(out.residuals[-1]) <= 1e-12 * np.linalg.norm(out.residuals[0])
+
+
+def test_two_step_recovers_the_sky_with_complete_coverage():
+    # Step one (V_L) fixes the frequencies inside its disk, step two (V_H and
+    # the low-passed step-one image) the rest; with lambda = 0 the final
+    # image converges to the sky as the major cycles proceed.
+    rng = np.random.default_rng(4)
+    u, v, sky, vis = _complete_coverage(16, 1e-4, rng)
+    errs = []
+    for n_major in (1, 3, 6):
+        opts = oi.ReconOptions(n_major=n_major, fista_iters=300, lambda_low=0.0, lambda_full=0.0,
+                               levels=2, n_bases=2, sigma2=1.0, eta2=1e-3)
+        low, full = oi.reconstruct_two_step(vis, u, v, 16, 1e-4, 4.0, 1.5, opts)
+        errs.append(np.linalg.norm(full.image - sky) / np.linalg.norm(sky))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] <= 1e-5
+    # step one alone only knows the frequencies its baselines sample
+    assert np.linalg.norm(low.image - sky) > 0.1 * np.linalg.norm(sky)
+
+
+def test_psnr_closed_form():
+    truth = np.zeros((8, 8))
+    truth[2, 3] = -4.0                    # peak magnitude 4
+    image = truth + 0.5                   # mse 0.25
+    assert abs(oi.psnr(image, truth) - 10.0 * np.log10(16.0 / 0.25)) < 1e-12
