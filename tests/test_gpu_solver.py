@@ -229,3 +229,30 @@ def test_two_step_needs_both_partitions(ms):
         plan.reconstruct_two_step(cuda(w.vis[0]))
     assert e.value.status == ms.MS_ERR_ARG
     plan.close()
+
+
+def test_complete_coverage_recovers_the_sky(ms):
+    """One noise-free visibility at every image frequency and lambda = 0: the
+    library's single-step image equals the sky and its two-step image
+    converges to it, as the oracle's do (the exact-recovery pins of the
+    oracle); FP64."""
+    N, dl = 16, 1e-4
+    k = np.arange(-N // 2, N // 2)
+    kx, ky = np.meshgrid(k, k)
+    u, v = kx.ravel() / (N * dl), ky.ravel() / (N * dl)
+    sky = np.random.default_rng(4).standard_normal((N, N))
+    vis = og.GriddedOperator(u, v, N, dl).forward(sky)
+    plan = ms.Plan(u, v, N, dl, 4.0, 1.5, precision="fp64", levels=2, n_bases=2)
+    tv = cuda(vis)
+    single, _ = plan.reconstruct_single_step(
+        tv, ms.ReconOptions(n_major=3, fista_iters=100, lambda_single=0.0))
+    assert rel(single.cpu().numpy(), sky) <= 1e-10
+    opts = ms.ReconOptions(n_major=6, fista_iters=300, lambda_low=0.0, lambda_full=0.0,
+                           sigma2=1.0, eta2=1e-3)
+    low, img, st = plan.reconstruct_two_step(tv, opts)
+    ro = oi.ReconOptions(n_major=6, fista_iters=300, lambda_low=0.0, lambda_full=0.0, levels=2,
+                         n_bases=2, sigma2=1.0, eta2=1e-3)
+    o_low, o_full = oi.reconstruct_two_step(vis, u, v, N, dl, 4.0, 1.5, ro)
+    assert rel(img.cpu().numpy(), o_full.image) <= 1e-8
+    assert rel(img.cpu().numpy(), sky) <= 1e-5
+    plan.close()
