@@ -1,8 +1,8 @@
 // libmstep: plan object, C ABI and the orchestration of the method.
 //
 // Host code only sequences kernels: every step of the path (partitioning,
-// sorting, gridding, FFT stages through cuFFT, wavelets, FISTA, reductions)
-// runs on the device.  All work of a call is issued on a plan-owned stream
+// sorting, gridding, the operator's FFTs through cuFFT, wavelets, FISTA with
+// its own spectral-step transforms, reductions) runs on the device.  All work of a call is issued on a plan-owned stream
 // that is ordered after the caller's stream at entry, and the caller's stream
 // is ordered after it at exit.
 #include <cuda.h>
