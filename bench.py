@@ -60,6 +60,9 @@ def parse():
                     help="write the DRAM traffic of one FISTA pass, from ncu --page raw --csv "
                          "exports, to profiles/")
     ap.add_argument("--batched-channels", type=int, default=64)
+    ap.add_argument("--no-c1", action="store_true",
+                    help="skip the 128-pixel oracle reconstruction of the CPU baseline")
+    ap.add_argument("--oracle-phases", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -107,14 +110,157 @@ def oracle_vis_rate(w, rows: int):
     return rows / t, t, rows
 
 
-def cpu_cores_used():
-    return 1
+def _oracle_rows_worker(path, lo, hi, npix, pixel_size):
+    """(pool worker, one BLAS thread) oracle degrid + grid of rows [lo, hi) of
+    the sample file; returns the seconds spent."""
+    import numpy as np
+    from oracle.gridding import GriddedOperator
+    d = np.load(path)
+    A = GriddedOperator(d["u"][lo:hi], d["v"][lo:hi], npix, pixel_size)
+    x = np.zeros((npix, npix))
+    x[npix // 2, npix // 2] = 1.0
+    t0 = time.perf_counter()
+    A.forward(x)
+    A.adjoint(d["vis"][lo:hi])
+    return time.perf_counter() - t0
+
+
+def oracle_phases(spec):
+    """Time the oracle's phases on this process's BLAS threads (the parent
+    sets them): degrid + grid of `rows` sample rows (FFT time removed), one
+    forward + inverse Ng^2 FFT, one FISTA iteration of the 1024-pixel
+    problem (M = 8, J = 4), and, if asked, the full 128-pixel two-step and
+    single-step reconstruction.  With spec["pool"] > 1 the degrid + grid
+    rows are split over that many single-thread worker processes (spawned).
+    Prints one JSON object."""
+    import numpy as np
+    out = {"threads": spec["threads"]}
+    d = np.load(spec["data"])
+    npix, ps, rows = int(d["npix"]), float(d["pixel_size"]), int(spec["rows"])
+    rows = min(rows, d["u"].size)
+    if spec.get("pool", 1) > 1:
+        import multiprocessing as mp
+        k = spec["pool"]
+        os.environ["OPENBLAS_NUM_THREADS"] = os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["MKL_NUM_THREADS"] = "1"
+        ctx = mp.get_context("spawn")
+        bounds = [(rows * i // k, rows * (i + 1) // k) for i in range(k)]
+        with ctx.Pool(k) as pool:
+            pool.starmap(_oracle_rows_worker, [(spec["data"], 0, 64, npix, ps)] * k)   # warm
+            t0 = time.perf_counter()
+            pool.starmap(_oracle_rows_worker, [(spec["data"], a, b, npix, ps) for a, b in bounds])
+            wall = time.perf_counter() - t0
+        out["grid_degrid"] = {"rows": rows, "s": wall, "vis_per_s": rows / wall,
+                              "processes": k}
+    else:
+        t = _oracle_rows_worker(spec["data"], 0, rows, npix, ps)
+        out["grid_degrid"] = {"rows": rows, "s": t, "vis_per_s": rows / t, "processes": 1}
+    ng = 2 * npix
+    g = np.zeros((ng, ng), complex)
+    t0 = time.perf_counter()
+    np.fft.fft2(g)
+    np.fft.ifft2(g)
+    out["fft_ng2_pair_ms"] = 1000 * (time.perf_counter() - t0)
+    if spec.get("fista"):
+        from oracle import solver as osv
+        from oracle.wavelets import Dictionary
+        rng = np.random.default_rng(0)
+        hh = np.exp(-0.5 * (osv.radial_frequency(npix) / (0.1 * npix)) ** 2)
+        prob = osv.Problem("low", Dictionary(npix, 8, 4), hh, rng.standard_normal((npix, npix)),
+                           0.1)
+        t0 = time.perf_counter()
+        osv.fista(prob, 1)
+        t1 = time.perf_counter()
+        osv.fista(prob, 2)
+        t2 = time.perf_counter()
+        out["fista_iteration_1024px_s"] = (t2 - t1) - (t1 - t0)
+    if spec.get("c1"):
+        import synth
+        from oracle import imaging as oi
+        w = synth.small_fp64()
+        ro = oi.ReconOptions(n_major=5, fista_iters=200, lambda_rule="max_fixed",
+                             lambda_low=1e-3, lambda_full=1e-3, lambda_single=1e-3)
+        t0 = time.perf_counter()
+        low, full = oi.reconstruct_two_step(w.vis[0], w.u[0], w.v[0], 128, w.pixel_size,
+                                            w.ell_px, w.delta_px, ro)
+        t1 = time.perf_counter()
+        single = oi.reconstruct_single_step(w.vis[0], w.u[0], w.v[0], 128, w.pixel_size, ro)
+        t2 = time.perf_counter()
+        out["c1_two_step_s"] = t1 - t0
+        out["c1_single_step_s"] = t2 - t1
+        if spec.get("c1_images"):
+            np.savez(spec["c1_images"], low=low.image, full=full.image, single=single.image)
+    print(json.dumps(out), flush=True)
+
+
+def host_cores():
+    """(nproc, cores this process may run on)"""
+    n = os.cpu_count() or 1
+    try:
+        aff = len(os.sched_getaffinity(0))
+    except Exception:
+        aff = n
+    return n, aff
+
+
+def run_oracle_phases(spec, threads):
+    """oracle_phases in a fresh interpreter whose BLAS / OpenMP pools have
+    `threads` threads (set before numpy loads)."""
+    env = dict(os.environ)
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    spec = dict(spec, threads=threads)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-phases",
+                        json.dumps(spec)], env=env, capture_output=True, text=True, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle timing failed: {r.stderr[-2000:]}")
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_leg(w, rows, tmpdir, c1=True):
+    """The oracle timed on this host: single-threaded and on all cores."""
+    import numpy as np
+    nproc, cores = host_cores()
+    path = os.path.join(tmpdir, "oracle_sample.npz")
+    n = min(max(rows, 1), w.nvis)
+    n_all = min(w.nvis, max(n, 250_000 * cores))
+    np.savez(path, u=np.asarray(w.u[0][:n_all]), v=np.asarray(w.v[0][:n_all]),
+             vis=np.asarray(w.vis[0][:n_all]), npix=w.npix, pixel_size=w.pixel_size)
+    c1_path = os.path.join(tmpdir, "c1_oracle_images.npz")
+    one = run_oracle_phases({"data": path, "rows": n, "fista": True, "c1": c1,
+                             "c1_images": c1_path if c1 else ""}, 1)
+    allc = run_oracle_phases({"data": path, "rows": n_all, "fista": True, "pool": cores},
+                             cores)
+    value = one["grid_degrid"]["vis_per_s"]
+    out = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"oracle degrid+grid of the first {n} rows of this workload (FFT time "
+                      f"removed), one thread, {one['grid_degrid']['s']:.1f} s"),
+           "nproc": nproc, "cores_available": cores,
+           "single_thread": {"grid_degrid_vis_per_s": value,
+                             "fft_2048sq_pair_ms": one["fft_ng2_pair_ms"],
+                             "fista_iteration_1024px_s": one.get("fista_iteration_1024px_s"),
+                             "c1_two_step_s": one.get("c1_two_step_s"),
+                             "c1_single_step_s": one.get("c1_single_step_s")},
+           "all_cores": {"cores": cores,
+                         "grid_degrid_vis_per_s": allc["grid_degrid"]["vis_per_s"],
+                         "grid_degrid_rows": allc["grid_degrid"]["rows"],
+                         "grid_degrid_processes": allc["grid_degrid"]["processes"],
+                         "fista_iteration_1024px_s": allc.get("fista_iteration_1024px_s"),
+                         "fista_threads": cores,
+                         "fft_2048sq_pair_ms": allc["fft_ng2_pair_ms"],
+                         "note": "degrid+grid split over single-thread processes; the FISTA "
+                                 "iteration on the BLAS thread pool; numpy's FFT is "
+                                 "single-threaded"}}
+    return out, (c1_path if c1 and os.path.exists(c1_path) else None)
 
 
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
+    # one BLAS / OpenMP thread: the oracle as a single-threaded program
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     import synth
     w = synth.ska_mid_like(device="cpu" if not _cuda_ok() else "cuda")
     for _ in range(max(args.warmup, 0)):
@@ -132,8 +278,9 @@ def run_reference(args):
             "ms_per_step": 1000 * statistics.mean(secs), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, "fp64"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores_used(),
-                             "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": sample,
+                             "nproc": host_cores()[0]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -256,6 +403,9 @@ def record_traffic(paths, precision):
 
 def main():
     args = parse()
+    if args.oracle_phases:
+        oracle_phases(json.loads(args.oracle_phases))
+        return
     if args.record_traffic:
         record_traffic(args.record_traffic, args.precision)
         return
@@ -378,8 +528,15 @@ def main():
                "ms_per_step": 1000 * e2e_s / args.steps}
 
     tte = None
+    errors = {}
     if rank == 0 and not args.no_time_to_eps:
-        tte = time_to_eps(ms, w, dev, args.eps)
+        tte, low64, img64 = time_to_eps(ms, w, dev, args.eps)
+        if args.precision != "fp64":
+            # the timed run's images against the plain FP64 form of the same schedule
+            rel = lambda a, b: float((a.double().cpu() - b).norm() / b.norm())
+            errors["vs_fp64_gpu"] = {"two_step_low": rel(low, low64),
+                                     "two_step_full": rel(img, img64),
+                                     "workload": w.name}
     plan.close()
 
     batched = None
@@ -388,10 +545,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs, rows = oracle_vis_rate(w, args.cpu_sample_rows)
-        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores_used(), "kind": "oracle",
-               "sample": f"oracle degrid+grid of the first {rows} rows of this workload "
-                         f"(FFT time removed), {secs:.1f} s"}
+        import tempfile
+        with tempfile.TemporaryDirectory() as tmp:
+            cpu, c1_path = cpu_baseline_leg(w, args.cpu_sample_rows, tmp, c1=not args.no_c1)
+            if c1_path:
+                errors["c1_vs_oracle"] = c1_error_vs_oracle(ms, dev, c1_path, args.precision)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -406,6 +564,7 @@ def main():
                 "gpu_launches": gpu_launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "time_to_eps": tte, "batched": batched,
+                "image_rel_l2_errors": errors or None,
                 "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}
                 if prof else None}
         print(json.dumps(line), flush=True)
@@ -414,42 +573,89 @@ def main():
         pg.destroy_process_group()
 
 
-def time_to_eps(ms, w, dev, eps, max_iters=1000):
-    """Wall time of the two-step reconstruction of the same workload (one
-    major cycle per step) with every minor cycle run until
-    |F_k - F_k-1| <= eps |F_k| (at most max_iters iterations): the chosen
-    form (FP32 data, Kahan-compensated gridding, FP64 reductions) against the
-    plain FP64 form, both on this GPU, plus the relative L2 difference of
-    their final images."""
+def time_to_eps(ms, w, dev, eps, ref_iters=3000, max_iters=4000):
+    """Time to the same objective tolerance, chosen form against plain form,
+    on this GPU.  Problems: the first minor cycle of each step of the
+    two-step method on this workload: step one's (Eq. LowRes) on i~_L1, and
+    step two's (Eq. FullRes) on i~_H1 with i^_L from a plain FP64 step one
+    of the benchmark schedule (5 x 100).  Both forms get the same input
+    images (computed in FP64).  F* is the lowest objective of a ref_iters
+    iteration plain FP64 run of each problem; each form then runs FISTA from
+    zero until F(beta_k) <= F* (1 + eps) (the library's objective target;
+    the device flag is read every 32 iterations), timed with CUDA events.
+    Chosen form: FP32 data with FP64 reductions (the FP32 + Kahan plan).
+    Also returns the FP64 two-step images (the plain form of the benchmark
+    schedule) for the error of the FP32 images."""
+    import numpy as np
     import torch
-    out, imgs = {}, {}
-    for form in ("fp32_kahan", "fp64"):
-        plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
-                       precision=form, device=dev.index or 0)
-        vis = torch.from_numpy(w.vis[0]).to(dev).to(plan.complex_dtype)
-        low = torch.empty((w.npix, w.npix), dtype=plan.real_dtype, device=dev)
-        img = torch.empty_like(low)
-        plan.reconstruct_two_step(vis, ms.ReconOptions(n_major=1, fista_iters=16),
-                                  low_out=low, out=img)   # warm: plans, graph
-        opts = ms.ReconOptions(n_major=1, fista_iters=max_iters, rel_tol=eps)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, _, st = plan.reconstruct_two_step(vis, opts, low_out=low, out=img)
-        e1.record()
-        torch.cuda.synchronize()
-        out[form] = {"ms": e0.elapsed_time(e1), "fista_iterations": st.total_iterations,
-                     "last_cycle_converged": bool(st.converged),
-                     "objective": st.objective}
-        imgs[form] = img.double().cpu()
-        plan.close()
-        del vis
-    diff = float((imgs["fp32_kahan"] - imgs["fp64"]).norm() / imgs["fp64"].norm())
-    return {"eps": eps, "max_iters": max_iters,
-            "workload": f"{w.name}, two-step, 1 major cycle per step",
-            "chosen": out["fp32_kahan"], "plain": out["fp64"],
-            "speedup": out["fp64"]["ms"] / out["fp32_kahan"]["ms"],
-            "image_rel_l2_chosen_vs_plain": diff}
+    plan64 = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
+                     precision="fp64", device=dev.index or 0)
+    vis64 = torch.from_numpy(w.vis[0]).to(dev).to(plan64.complex_dtype)
+    low64, img64, _ = plan64.reconstruct_two_step(vis64, ms.ReconOptions(n_major=N_MAJOR,
+                                                                         fista_iters=FISTA_ITERS))
+    res = {"low": plan64.grid("L", vis64), "full": plan64.grid("H", vis64)}
+    lam = {k: plan64.lam(r, 0.05, 1) for k, r in res.items()}
+    s2 = plan64.sigma2_hat(res["full"])
+    kw = {"low": {}, "full": {"l_low": low64, "sigma2": s2, "eta2": 1e-3 * s2}}
+    fstar = {}
+    for k in ("low", "full"):
+        _, st = plan64.minor_cycle(k, res[k], lam[k], ref_iters, **kw[k])
+        fstar[k] = float(np.min(st.trace))
+    out = {"eps": eps, "reference_iterations": ref_iters, "max_iters": max_iters,
+           "workload": f"{w.name}: first minor cycle of step one and of step two",
+           "target": "F(beta_k) <= F* (1 + eps), F* from the long plain FP64 run",
+           "f_star": fstar,
+           "chosen_parts": "FP32 data, Kahan-compensated gridding, FP64 reductions; the "
+                           "batched form is measured in the batched leg; the learned warm "
+                           "start needs a trained network and is not part of this leg"}
+    for form, plan in (("plain", plan64), ("chosen", None)):
+        if plan is None:
+            plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px,
+                           precision="fp32_kahan", device=dev.index or 0)
+        cast = lambda t: t.to(plan.real_dtype).contiguous()
+        rec = {}
+        for k in ("low", "full"):
+            kk = {a: (cast(b) if torch.is_tensor(b) else b) for a, b in kw[k].items()}
+            plan.set_objective_target(float("-inf"))
+            plan.minor_cycle(k, cast(res[k]), lam[k], 16, **kk)   # warm: K^, graph
+            plan.set_objective_target(fstar[k] * (1 + eps))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = plan.minor_cycle(k, cast(res[k]), lam[k], max_iters, **kk)
+            e1.record()
+            torch.cuda.synchronize()
+            plan.set_objective_target(float("-inf"))
+            rec[k] = {"ms": e0.elapsed_time(e1), "iterations": st.iterations,
+                      "reached": bool(st.converged), "objective": st.objective}
+        rec["ms"] = rec["low"]["ms"] + rec["full"]["ms"]
+        out[form] = rec
+        if form == "chosen":
+            plan.close()
+    out["speedup"] = out["plain"]["ms"] / out["chosen"]["ms"]
+    plan64.close()
+    return out, low64.double().cpu(), img64.double().cpu()
+
+
+def c1_error_vs_oracle(ms, dev, c1_path, precision):
+    """Relative L2 error of this form's 128-pixel two-step and single-step
+    images (5 x 200, lambda = 1e-3 max|i~_1|) against the FP64 oracle's."""
+    import numpy as np
+    import torch
+    import synth
+    ref = np.load(c1_path)
+    w = synth.small_fp64()
+    plan = ms.Plan(w.u[0], w.v[0], 128, w.pixel_size, w.ell_px, w.delta_px,
+                   precision=precision, device=dev.index or 0)
+    opts = ms.ReconOptions(n_major=5, fista_iters=200, lambda_rule="max_fixed",
+                           lambda_low=1e-3, lambda_full=1e-3, lambda_single=1e-3)
+    tv = torch.from_numpy(w.vis[0]).to(dev).to(plan.complex_dtype)
+    low, img, _ = plan.reconstruct_two_step(tv, opts)
+    single, _ = plan.reconstruct_single_step(tv, opts)
+    plan.close()
+    rel = lambda a, b: float(np.linalg.norm(a.double().cpu().numpy() - b) / np.linalg.norm(b))
+    return {"workload": w.name, "precision": precision, "two_step_low": rel(low, ref["low"]),
+            "two_step_full": rel(img, ref["full"]), "single_step": rel(single, ref["single"])}
 
 
 def batched_leg(ms, dev, nchan, precision, steps=3):
@@ -556,6 +762,10 @@ def family_bytes(fam, N, M, J, rsz, plan):
       degrid       per row: packed cell (4 B) + offsets (2 rsz) + observed and
                    residual value (2 x 2 rsz), plus one read of the (2N)^2
                    complex grid.
+      grid         per row: packed cell + offsets + value (4 + 4 rsz), plus one
+                   write of the (2N)^2 complex grid.
+      fold         (the design's reduction of the gridding tiles) every work
+                   item's scratch tile read once, the grid written once.
     """
     q = lambda j: (N >> j) ** 2   # subband side^2 at level j
     if fam == "analysis_l1":
@@ -580,6 +790,20 @@ def family_bytes(fam, N, M, J, rsz, plan):
         counts = plan.partition_counts()
         rows = (counts["L"] + counts["H"]) / 2.0
         return rows * (4 + 2 * rsz + 4 * rsz) + 4 * N * N * 2 * rsz
+    if fam == "grid":
+        # per row: packed cell (4 B) + offsets (2 rsz) + value (2 rsz); one
+        # write of the (2N)^2 complex grid
+        counts = plan.partition_counts()
+        rows = (counts["L"] + counts["H"]) / 2.0
+        return rows * (4 + 4 * rsz) + 4 * N * N * 2 * rsz
+    if fam == "fold":
+        # the design's reduction: read every work item's scratch tile, write
+        # the grid once (mean of the two partitions' calls)
+        b = 0.0
+        for part in ("L", "H"):
+            items, cells, cell_bytes = plan.partition_layout(part)
+            b += items * cells * cell_bytes + 4 * N * N * 2 * rsz
+        return b / 2.0
     return None
 
 

@@ -62,6 +62,7 @@ typedef enum { MS_STEP_LOW = 0, MS_STEP_FULL = 1, MS_STEP_SINGLE = 2 } ms_step;
 typedef enum { MS_LAMBDA_NORM2_2N = 0, MS_LAMBDA_MAX_FIXED = 1 } ms_lambda_rule;
 
 typedef struct ms_plan ms_plan;
+typedef struct ms_unet ms_unet;   /* the learned warm start's network (below) */
 
 typedef struct {
   const double* u;        /* host [nchan * nvis] baseline u, wavelengths        */
@@ -115,6 +116,10 @@ typedef struct {
   double lambda_single;   /* c for the single-step method (paper: 0.01)       */
   double sigma2;          /* <= 0: estimate on i~_H1 (Sect. 4.3)              */
   double eta2;            /* <= 0: 1e-3 sigma^2 (Sect. 4.3)                   */
+  ms_unet* warm_start;    /* NULL, or a network on the plan's device: step
+                             two's first minor cycle then starts from
+                             ms_warm_start_coefficients(net, i^_L, i~_H1)
+                             instead of zero (ms_reconstruct_two_step only)   */
 } ms_recon_opts;
 
 /* ------------------------------------------------------------------ plan */
@@ -136,6 +141,11 @@ const char* ms_last_error(const ms_plan* plan);
 /* Row counts of a partition (Sect. 3.1): out[0] = |V_L|, out[1] = |V_H|,
  * out[2] = |V_L n V_H|, out[3] = unflagged rows, for channel chan. */
 ms_status ms_partition_counts(ms_plan* plan, int32_t chan, int64_t out[4]);
+
+/* Gridding layout of a partition: out[0] = its work items, out[1] = cells
+ * of one work item's scratch tile ((tile + 6)^2), out[2] = bytes per
+ * scratch cell (8 for FP32, 16 for FP64 and the compensated FP32 form). */
+ms_status ms_partition_layout(ms_plan* plan, int32_t part, int32_t chan, int64_t out[3]);
 
 /* The rows of partition `part` in the plan's sorted (tile) order, copied to
  * host `rows` [count]; count = ms_partition_counts of that partition. */
@@ -262,6 +272,14 @@ ms_status ms_minor_cycle(ms_plan* plan, int32_t step, int32_t chan,
                          double rel_tol, void* beta_inout, void* model_out,
                          ms_stats* stats, void* stream);
 
+/* Objective target of the plan's later minor cycles (ms_minor_cycle and
+ * the reconstruct calls), for time-to-tolerance comparisons of the forms:
+ * with a finite target, a minor cycle also stops (stats->converged = 1) at
+ * the first k with F(beta_k) <= target (Algorithm 1's objective, evaluated
+ * in FP64 as for the relative-change test).  target = -inf turns it off
+ * (the default); NaN is MS_ERR_ARG. */
+ms_status ms_set_objective_target(ms_plan* plan, double target);
+
 /* ----------------------------------------------------------- reconstruct */
 
 /* The two-step method: step one (Eq. LowRes) on V_L for n_major cycles, final
@@ -297,7 +315,6 @@ ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vi
  * [c_out][3][3][c_in] then biases [c_out].  ms_unet_create draws He-normal
  * weights from `seed` and zero biases, and starts the head at zero, so an
  * untrained network returns the step-one image. */
-typedef struct ms_unet ms_unet;
 ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64_t seed,
                          int32_t device, ms_unet** out);
 ms_status ms_unet_destroy(ms_unet* net);
@@ -314,10 +331,43 @@ ms_status ms_unet_forward(ms_unet* net, const float* in, int32_t H, int32_t W, f
 ms_status ms_unet_gradients(ms_unet* net, const float* in, const float* target, int32_t H,
                             int32_t W, float* out, float* grads_host, double* loss,
                             void* stream);
+/* Checking aids (no part of the method): keep = 1 makes later
+ * ms_unet_gradients calls keep every layer's bfloat16 pre-activation
+ * gradient (memory for max_side is allocated on the first enable).
+ * ms_unet_layer_tensor copies to host FP32 `host` [H_l][W_l][c] (n floats,
+ * H_l = H >> level of the layer, H x W of the last forward pass) layer
+ * `layer`'s (execution order) stored bfloat16 input activation (which = 0,
+ * c = c_in), its stored output after the ReLU (1, c = c_out; not the head)
+ * or its kept pre-activation gradient (2, c = c_out), so that each layer's
+ * products can be checked on exactly the values the device used.
+ * Errors: MS_ERR_ARG (range, size, nothing kept). */
+ms_status ms_unet_keep_intermediates(ms_unet* net, int32_t keep);
+ms_status ms_unet_layer_tensor(ms_unet* net, int32_t layer, int32_t which, float* host,
+                               int64_t n);
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on the
  * mean squared error; *loss receives the loss before the step. */
 ms_status ms_unet_train_step(ms_unet* net, const float* in, const float* target, int32_t H,
                              int32_t W, float lr, double* loss, void* stream);
+
+/* lambda of major cycle n (>= 1) of a step from its residual image i~_n
+ * (dev N*N), as the reconstruct calls set it: rule NORM2_2N gives
+ * coef ||i~_n||_2 2^n (Sect. 5, App. A.2), MAX_FIXED gives coef max|i~_n|
+ * (the residual taken as the step's first).  Reductions in FP64; result to
+ * host *lambda.  Errors: MS_ERR_ARG (rule, n < 1, NULL pointers). */
+ms_status ms_lambda(ms_plan* plan, int32_t rule, double coef, int32_t n,
+                    const void* residual, double* lambda, void* stream);
+
+/* The learned warm start of step two (Sect. 3.3's full-resolution problem):
+ * s = max|i~_H1|, x0 = s net([i^_L, i~_H1] / s) (the network sees images
+ * scaled to unit peak), beta = W^H x0 / M (dev [M][N][N]), so that
+ * W beta = x0 (W W^H = M I).  low_image (i^_L) and residual_h1 (i~_H1) are
+ * dev N*N; x0_out (dev N*N) may be NULL.  N must be a valid network size
+ * (a multiple of 4 * 2^(levels-1), at most the network's max_side) and the
+ * network must live on the plan's device.  The network runs on `stream`
+ * (the plan's ordering rules apply). */
+ms_status ms_warm_start_coefficients(ms_plan* plan, ms_unet* net, const void* low_image,
+                                     const void* residual_h1, void* beta_out, void* x0_out,
+                                     void* stream);
 
 /* ------------------------------------------------------------- profiling */
 

@@ -100,8 +100,10 @@ def run_low_step(vis, u, v, npix, pixel_size, opts: ReconOptions, coef: float) -
 
 
 def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
-                  opts: ReconOptions) -> StepResult:
-    """Step two (Sect. 3.3, Eq. FullRes) with l_{L_n} = i^_L - sum_{j<n} i_j."""
+                  opts: ReconOptions, beta0_first: Optional[np.ndarray] = None) -> StepResult:
+    """Step two (Sect. 3.3, Eq. FullRes) with l_{L_n} = i^_L - sum_{j<n} i_j.
+    beta0_first: start of the first minor cycle (a warm start) instead of
+    zero; the later cycles start from zero."""
     A = _operator(u, v, npix, pixel_size, opts)
     W = Dictionary(npix, opts.n_bases, opts.levels)
     Hhat = psf_spectrum(A.psf())
@@ -121,7 +123,8 @@ def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
         l_low = low_image - model
         prob = Problem("full", W, Hhat, res, lam, gl=gl, gh=gh, l_low=l_low)
         theta = prob.lipschitz_closed_form()
-        fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol)
+        fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol,
+                   beta0=beta0_first if n == 1 else None)
         model = model + W.synth(fr.beta)
         out.residuals.append(res)
         out.lambdas.append(lam)
@@ -135,13 +138,15 @@ def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
 
 
 def reconstruct_two_step(vis, u, v, npix, pixel_size, ell, delta,
-                         opts: Optional[ReconOptions] = None):
-    """Partition (Sect. 3.1), step one on V_L, step two on V_H and i^_L."""
+                         opts: Optional[ReconOptions] = None,
+                         beta0_full: Optional[np.ndarray] = None):
+    """Partition (Sect. 3.1), step one on V_L, step two on V_H and i^_L;
+    beta0_full optionally starts step two's first minor cycle."""
     opts = opts or ReconOptions()
     in_l, in_h = partition(u, v, npix, pixel_size, ell, delta)
     low = run_low_step(vis[in_l], u[in_l], v[in_l], npix, pixel_size, opts, opts.lambda_low)
     full = run_full_step(vis[in_h], u[in_h], v[in_h], npix, pixel_size, low.image,
-                         ell, delta, opts)
+                         ell, delta, opts, beta0_first=beta0_full)
     return low, full
 
 

@@ -72,7 +72,7 @@ class ms_recon_opts(ctypes.Structure):
                 ("rel_tol", ctypes.c_double), ("lambda_rule", ctypes.c_int32),
                 ("lambda_low", ctypes.c_double), ("lambda_full", ctypes.c_double),
                 ("lambda_single", ctypes.c_double), ("sigma2", ctypes.c_double),
-                ("eta2", ctypes.c_double)]
+                ("eta2", ctypes.c_double), ("warm_start", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -83,6 +83,7 @@ _SIGNATURES = {
     "ms_last_error": [_P],
     "ms_partition_counts": [_P, _I32, ctypes.POINTER(_I64)],
     "ms_partition_rows": [_P, _I32, _I32, _P],
+    "ms_partition_layout": [_P, _I32, _I32, ctypes.POINTER(_I64)],
     "ms_degrid": [_P, _I32, _I32, _P, _P, _P, _P],
     "ms_grid": [_P, _I32, _I32, _P, _P, _P],
     "ms_grid_static_scratch": [_P, _I32, _I32, _P, _P, _P],
@@ -113,7 +114,12 @@ _SIGNATURES = {
     "ms_unet_forward": [_P, _P, _I32, _I32, _P, _P],
     "ms_unet_gradients": [_P, _P, _P, _I32, _I32, _P, _P, ctypes.POINTER(_D), _P],
     "ms_unet_train_step": [_P, _P, _P, _I32, _I32, ctypes.c_float, ctypes.POINTER(_D), _P],
+    "ms_unet_keep_intermediates": [_P, _I32],
+    "ms_unet_layer_tensor": [_P, _I32, _I32, _P, _I64],
     "ms_set_profiling": [_P, _I32],
+    "ms_set_objective_target": [_P, _D],
+    "ms_lambda": [_P, _I32, _D, _I32, _P, ctypes.POINTER(_D), _P],
+    "ms_warm_start_coefficients": [_P, _P, _P, _P, _P, _P, _P],
     "ms_get_kernel_profile": [_P, ctypes.POINTER(ms_kernel_profile), _I32],
 }
 
@@ -193,11 +199,13 @@ class ReconOptions:
     lambda_single: float = 0.01
     sigma2: float = 0.0                # <= 0: estimate (Sect. 4.3)
     eta2: float = 0.0                  # <= 0: 1e-3 sigma^2
+    warm_start: Optional["WarmStartNet"] = None   # network for step two's first start
 
     def to_c(self) -> ms_recon_opts:
         rule = {"norm2_2n": MS_LAMBDA_NORM2_2N, "max_fixed": MS_LAMBDA_MAX_FIXED}[self.lambda_rule]
+        net = self.warm_start._h if self.warm_start is not None else None
         return ms_recon_opts(self.n_major, self.fista_iters, self.rel_tol, rule, self.lambda_low,
-                             self.lambda_full, self.lambda_single, self.sigma2, self.eta2)
+                             self.lambda_full, self.lambda_single, self.sigma2, self.eta2, net)
 
 
 class Plan:
@@ -286,6 +294,12 @@ class Plan:
         out = (_I64 * 4)()
         self._check(self._lib.ms_partition_counts(self._h, chan, out))
         return {"L": out[0], "H": out[1], "LH": out[2], "ALL": out[3]}
+
+    def partition_layout(self, part: str, chan: int = 0):
+        """(work items, cells per work-item tile, bytes per scratch cell)"""
+        out = (_I64 * 3)()
+        self._check(self._lib.ms_partition_layout(self._h, PARTS[part], chan, out))
+        return int(out[0]), int(out[1]), int(out[2])
 
     def partition_rows(self, part: str, chan: int = 0) -> np.ndarray:
         n = self.partition_counts(chan)[part]
@@ -454,6 +468,38 @@ class Plan:
     def set_profiling(self, on: bool):
         self._check(self._lib.ms_set_profiling(self._h, 1 if on else 0))
 
+    def lam(self, residual, coef: float = 0.05, n: int = 1, rule: str = "norm2_2n",
+            stream=None) -> float:
+        """lambda of major cycle n from its residual image (ms_lambda)."""
+        r = {"norm2_2n": MS_LAMBDA_NORM2_2N, "max_fixed": MS_LAMBDA_MAX_FIXED}[rule]
+        out = _D()
+        self._check(self._lib.ms_lambda(
+            self._h, r, float(coef), int(n),
+            self._need(residual, self.real_dtype, self.npix ** 2, "residual"),
+            ctypes.byref(out), _stream_handle(stream)))
+        return float(out.value)
+
+    def warm_start_coefficients(self, net: "WarmStartNet", low_image, residual_h1,
+                                beta_out=None, x0_out=None, stream=None):
+        """(beta, x0): W^H x0 / M with x0 the network's start of step two."""
+        torch = _torch()
+        n2 = self.npix ** 2
+        if beta_out is None:
+            beta_out = torch.empty((self.n_bases, self.npix, self.npix), dtype=self.real_dtype,
+                                   device=low_image.device)
+        if x0_out is None:
+            x0_out = self._image(None)
+        self._check(self._lib.ms_warm_start_coefficients(
+            self._h, net._h, self._need(low_image, self.real_dtype, n2, "low_image"),
+            self._need(residual_h1, self.real_dtype, n2, "residual_h1"),
+            self._need(beta_out, self.real_dtype, self.n_bases * n2, "beta_out"),
+            self._need(x0_out, self.real_dtype, n2, "x0_out"), _stream_handle(stream)))
+        return beta_out, x0_out
+
+    def set_objective_target(self, target: float = float("-inf")):
+        """Later minor cycles also stop once F(beta_k) <= target (-inf: off)."""
+        self._check(self._lib.ms_set_objective_target(self._h, float(target)))
+
     def kernel_profile(self, reset: bool = False) -> dict:
         """{family: (timed launch groups, total ms)} from CUDA events."""
         out = ms_kernel_profile()
@@ -472,6 +518,10 @@ def ms_plan_destroy(plan: Plan):
 
 def ms_partition_counts(plan: Plan, chan: int = 0):
     return plan.partition_counts(chan)
+
+
+def ms_partition_layout(plan: Plan, part: str, chan: int = 0):
+    return plan.partition_layout(part, chan)
 
 
 def ms_partition_rows(plan: Plan, part: str, chan: int = 0):
@@ -560,6 +610,19 @@ def ms_set_profiling(plan: Plan, on: bool):
     plan.set_profiling(on)
 
 
+def ms_lambda(plan: Plan, residual, coef=0.05, n=1, rule="norm2_2n", stream=None):
+    return plan.lam(residual, coef, n, rule, stream)
+
+
+def ms_warm_start_coefficients(plan: Plan, net, low_image, residual_h1, beta_out=None,
+                               x0_out=None, stream=None):
+    return plan.warm_start_coefficients(net, low_image, residual_h1, beta_out, x0_out, stream)
+
+
+def ms_set_objective_target(plan: Plan, target: float):
+    plan.set_objective_target(target)
+
+
 def ms_get_kernel_profile(plan: Plan, reset: bool = False):
     return plan.kernel_profile(reset)
 
@@ -637,6 +700,20 @@ class WarmStartNet:
             out.data_ptr(), g.ctypes.data, ctypes.byref(loss), _stream_handle(stream)))
         return out, float(loss.value), g
 
+    def keep_intermediates(self, keep: bool = True) -> None:
+        """Keep every layer's pre-activation gradient in later gradients()
+        calls (a checking aid)."""
+        self._check(self._lib.ms_unet_keep_intermediates(self._h, 1 if keep else 0))
+
+    def layer_tensor(self, layer: int, which: str, shape) -> np.ndarray:
+        """A layer's stored bfloat16 input ('in'), output ('out') or kept
+        pre-activation gradient ('grad') of the last pass, as FP32 [H_l, W_l, c]."""
+        code = {"in": 0, "out": 1, "grad": 2}[which]
+        out = np.zeros(shape, np.float32)
+        self._check(self._lib.ms_unet_layer_tensor(self._h, layer, code, out.ctypes.data,
+                                                   out.size))
+        return out
+
     def train_step(self, x, target, lr: float, stream=None) -> float:
         H, W = x.shape[0], x.shape[1]
         loss = _D()
@@ -681,3 +758,11 @@ def ms_unet_gradients(net: WarmStartNet, x, target, stream=None):
 
 def ms_unet_train_step(net: WarmStartNet, x, target, lr, stream=None):
     return net.train_step(x, target, lr, stream)
+
+
+def ms_unet_keep_intermediates(net: WarmStartNet, keep=True):
+    net.keep_intermediates(keep)
+
+
+def ms_unet_layer_tensor(net: WarmStartNet, layer, which, shape):
+    return net.layer_tensor(layer, which, shape)

@@ -80,6 +80,7 @@ struct FistaCtl {
   float muf, thrf;
   double td[2];
   double mud, thrd;
+  double F_target;    // stop once F <= F_target (-inf: no target)
 };
 
 template <typename R> __device__ __forceinline__ R ctl_t(const FistaCtl* c, int slot);
@@ -180,6 +181,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cfg.numAttrs = MS_PDL ? 1 : 0;   // without the attribute: an ordinary launch
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
+
+// Streaming multiprocessors of the current device (queried once per device
+// and cached): grid caps of the grid-stride kernels are multiples of it.
+int sm_count();
 
 // -------------------------------------------------------------------------
 // launch wrappers (defined in the .cu files); all take the launch stream

@@ -119,7 +119,7 @@ template <typename R>
 void launch_pad(const R* image, const R* psi, int npix, int Ng, C2<R>* grid, cudaStream_t s) {
   int64_t total = (int64_t)Ng * Ng;
   int blocks = (int)((total + kThreads - 1) / kThreads);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   pad_kernel<R><<<blocks, kThreads, 0, s>>>(image, psi, npix, Ng, grid);
 }
 
@@ -128,7 +128,7 @@ void launch_crop(const C2<R>* grid, const R* psi, int npix, int Ng, double scale
                  cudaStream_t s) {
   int64_t total = (int64_t)npix * npix;
   int blocks = (int)((total + kThreads - 1) / kThreads);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   crop_kernel<R><<<blocks, kThreads, 0, s>>>(grid, psi, npix, Ng, (R)scale, image);
 }
 
@@ -530,7 +530,7 @@ void launch_fold(const void* scratch, const int32_t* tile_items, int Ng, int til
                  C2<R>* grid, cudaStream_t s) {
   int64_t total = (int64_t)Ng * Ng;
   int blocks = (int)((total + kThreads - 1) / kThreads);
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   fold_kernel<R, KAHAN><<<blocks, kThreads, 0, s>>>(
       reinterpret_cast<const typename ScratchOf<R, KAHAN>::T*>(scratch), tile_items, Ng, tile,
       ntx, grid);
@@ -614,17 +614,17 @@ int blocks_for(int64_t n, int cap) {
 template <typename R>
 void launch_job_of(const BatchJob<R>* jobs, int njobs, int max_items, int32_t* job_of,
                    cudaStream_t s) {
-  job_of_kernel<R><<<dim3(blocks_for(max_items, 152), njobs), kThreads, 0, s>>>(jobs, job_of);
+  job_of_kernel<R><<<dim3(blocks_for(max_items, sm_count()), njobs), kThreads, 0, s>>>(jobs, job_of);
 }
 
 template <typename R>
 void launch_batch_gather(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s) {
-  batch_gather_kernel<R><<<dim3(blocks_for(max_n, 152 * 4), njobs), kThreads, 0, s>>>(jobs);
+  batch_gather_kernel<R><<<dim3(blocks_for(max_n, sm_count() * 4), njobs), kThreads, 0, s>>>(jobs);
 }
 
 template <typename R>
 void launch_batch_scatter(const BatchJob<R>* jobs, int njobs, int64_t max_n, cudaStream_t s) {
-  batch_scatter_kernel<R><<<dim3(blocks_for(max_n, 152 * 4), njobs), kThreads, 0, s>>>(jobs);
+  batch_scatter_kernel<R><<<dim3(blocks_for(max_n, sm_count() * 4), njobs), kThreads, 0, s>>>(jobs);
 }
 
 template <typename R, bool KAHAN>
@@ -645,7 +645,7 @@ void launch_grid_batch(const BatchJob<R>* jobs, const int32_t* job_of, int total
 template <typename R, bool KAHAN>
 void launch_fold_batch(const BatchJob<R>* jobs, int njobs, const void* scratch, int Ng,
                        int tile, int ntx, cudaStream_t s) {
-  fold_batch_kernel<R, KAHAN><<<dim3(blocks_for((int64_t)Ng * Ng, 152 * 8), njobs), kThreads, 0,
+  fold_batch_kernel<R, KAHAN><<<dim3(blocks_for((int64_t)Ng * Ng, sm_count() * 8), njobs), kThreads, 0,
                                 s>>>(
       jobs, reinterpret_cast<const typename ScratchOf<R, KAHAN>::T*>(scratch), Ng, tile, ntx);
 }
@@ -671,14 +671,14 @@ void launch_degrid_batch(const CUtensorMap* tmap, const BatchJob<R>* jobs,
 template <typename R>
 void launch_pad_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
                       cudaStream_t s) {
-  pad_batch_kernel<R><<<dim3(blocks_for((int64_t)Ng * Ng, 152 * 8), njobs), kThreads, 0, s>>>(
+  pad_batch_kernel<R><<<dim3(blocks_for((int64_t)Ng * Ng, sm_count() * 8), njobs), kThreads, 0, s>>>(
       jobs, psi, npix, Ng);
 }
 
 template <typename R>
 void launch_crop_batch(const BatchJob<R>* jobs, int njobs, const R* psi, int npix, int Ng,
                        cudaStream_t s) {
-  crop_batch_kernel<R><<<dim3(blocks_for((int64_t)npix * npix, 152 * 8), njobs), kThreads, 0,
+  crop_batch_kernel<R><<<dim3(blocks_for((int64_t)npix * npix, sm_count() * 8), njobs), kThreads, 0,
                          s>>>(jobs, psi, npix, Ng);
 }
 

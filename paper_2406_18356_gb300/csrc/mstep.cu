@@ -26,6 +26,9 @@
 #endif
 using namespace ms;
 
+// the device a network was created on (defined with the network)
+int ms_unet_device_of(const ms_unet* net);
+
 namespace {
 
 // ---------------------------------------------------------------- helpers
@@ -179,6 +182,33 @@ __global__ void init_ctl_kernel(FistaCtl* ctl, int max_iters, double rel_tol, do
 
 __global__ void set_eta_kernel(FistaCtl* ctl, double eta2) { ctl->eta2 = eta2; }
 
+__global__ void set_target_kernel(FistaCtl* ctl, double target) { ctl->F_target = target; }
+
+// Network input of the learned warm start: [i^_L, i~_H1] / max|i~_H1|,
+// channels last (FP32 [n][2]); the peak comes from launch_image_norms.
+template <typename R>
+__global__ void ws_input_kernel(const R* __restrict__ low, const R* __restrict__ res,
+                                const FistaCtl* __restrict__ ctl, int64_t n,
+                                float* __restrict__ in) {
+  const double a = ctl->absmax;
+  const float sc = a > 0.0 ? (float)(1.0 / a) : 0.0f;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    in[2 * k] = (float)low[k] * sc;
+    in[2 * k + 1] = (float)res[k] * sc;
+  }
+}
+
+// x0 = max|i~_H1| times the network's output
+template <typename R>
+__global__ void ws_output_kernel(const float* __restrict__ out, const FistaCtl* __restrict__ ctl,
+                                 int64_t n, R* __restrict__ x0) {
+  const R a = (R)ctl->absmax;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    x0[k] = (R)out[k] * a;
+}
+
 __global__ void check_noise_kernel(FistaCtl* ctl) {
   if (!(ctl->sigma2 > 0.0) || !(ctl->eta2 > 0.0) || !isfinite(ctl->sigma2) ||
       !isfinite(ctl->eta2))
@@ -249,6 +279,12 @@ struct ms_plan {
   CUtensorMap tmap{};
   std::string msg;
   std::vector<double> htrace;
+  double obj_target = -INFINITY;   // objective target of the minor cycles (-inf: none)
+  // learned warm start: network input / output (FP32), x0 and beta_0
+  float* ws_in = nullptr;
+  float* ws_out = nullptr;
+  void* ws_x0 = nullptr;
+  void* ws_beta = nullptr;
   // profiling: CUDA-event spans per kernel family
   bool prof = false;
   bool capturing = false;
@@ -361,6 +397,13 @@ struct Timer {
   }
 };
 
+// Restores the calling thread's current device when it goes out of scope.
+struct DeviceGuard {
+  int prev = 0;
+  DeviceGuard() { cudaGetDevice(&prev); }
+  ~DeviceGuard() { cudaSetDevice(prev); }
+};
+
 struct Scope {
   ms_plan* p;
   cudaStream_t user;
@@ -464,29 +507,32 @@ void degrid_sorted(ms_plan* p, PartDev& pd, const void* obs_sorted, void* out_so
   if (tm) tm->spans[0].push_back({a, tm->mark()});
 }
 
-// sorted visibilities -> image = Re(D Z^H F^H G^H y) / sum(w)
+// sorted visibilities -> image = Re(D Z^H F^H G^H y) / sum(w); the gridding
+// kernel's per-work-item tiles go to `scratch` (NULL: the plan's buffer)
 template <typename R>
-void grid_sorted(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image, Timer* tm) {
+void grid_sorted(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image, Timer* tm,
+                 void* scratch = nullptr) {
+  if (!scratch) scratch = p->scratch;
   int a = tm ? tm->mark() : 0;
   if (p->prec == MS_FP32_KAHAN) {
     {
       KSpan k(p, MS_K_GRID);
       launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
-                               (const float2*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx,
+                               (const float2*)vis_sorted, scratch, p->Ng, p->T, p->ntx,
                                p->beta, p->ps);
     }
     KSpan k(p, MS_K_FOLD);
-    launch_fold<float, true>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
+    launch_fold<float, true>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
                              p->ps);
   } else {
     {
       KSpan k(p, MS_K_GRID);
       launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
-                            (const C2<R>*)vis_sorted, p->scratch, p->Ng, p->T, p->ntx, p->beta,
+                            (const C2<R>*)vis_sorted, scratch, p->Ng, p->T, p->ntx, p->beta,
                             p->ps);
     }
     KSpan k(p, MS_K_FOLD);
-    launch_fold<R, false>(p->scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid,
+    launch_fold<R, false>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid,
                           p->ps);
   }
   int b = tm ? tm->mark() : 0;
@@ -688,6 +734,8 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     ck(cudaMemsetAsync(p->B[0], 0, sizeof(R) * ncoef, p->ps), "memset");
   ck(cudaMemcpyAsync(p->B[2], p->B[0], sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
      "copy");
+  set_target_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->obj_target);
+  const bool poll = rel_tol > 0 || std::isfinite(p->obj_target);
   // ||B_0||_1 enters the first objective through the analysis partials
   ck(cudaMemsetAsync(p->l1parts, 0, sizeof(double) * p->n_l1, p->ps), "memset");
   launch_l1<R>((const R*)p->B[0], ncoef, p->parts, p->l1parts, p->tickets + 4, p->ps);
@@ -697,7 +745,7 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     for (int i = 0; i < passes; ++i) {
       record_fista_pass<R>(p, i & 1);
       if ((i + 1) % kPasses == 0 && p->pending.size() > 4096) harvest(p);
-      if (rel_tol > 0 && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes) {
+      if (poll && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes) {
         int32_t done = 0;
         ck(cudaMemcpyAsync(&done, &p->ctl->done, sizeof(done), cudaMemcpyDeviceToHost, p->ps),
            "read done");
@@ -712,7 +760,7 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
   while (launched < passes) {
     ck(cudaGraphLaunch(p->fista_exec, p->ps), "graph launch");
     launched += kPasses;
-    if (rel_tol > 0 && launched < passes && (launched / kPasses) % 4 == 0) {
+    if (poll && launched < passes && (launched / kPasses) % 4 == 0) {
       int32_t done = 0;
       ck(cudaMemcpyAsync(&done, &p->ctl->done, sizeof(done), cudaMemcpyDeviceToHost, p->ps),
          "read done");
@@ -747,6 +795,39 @@ template <typename R> void fill_stats(ms_plan* p, ms_stats* st, bool copy_trace)
 
 int step_part(int step) {
   return step == MS_STEP_LOW ? MS_PART_L : (step == MS_STEP_FULL ? MS_PART_H : MS_PART_ALL);
+}
+
+// ------------------------------------------------------- learned warm start
+// beta = W^H x0 / M with x0 = s net([i^_L, i~_H1] / s), s = max|i~_H1|
+// (Sect. 3.3's problem, started from the network's image)
+template <typename R>
+void warm_start_beta(ms_plan* p, ms_unet* net, const void* low, const void* res, void* beta,
+                     void* x0_out) {
+  arg(net != nullptr, "warm start network is NULL");
+  arg(ms_unet_device_of(net) == p->dev, "the warm start network lives on another device");
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N;
+  if (!p->ws_in) {
+    p->ws_in = p->alloc<float>(2 * n2, "warm start input");
+    p->ws_out = p->alloc<float>(n2, "warm start output");
+  }
+  R* x0 = (R*)x0_out;
+  if (!x0) {
+    if (!p->ws_x0) p->ws_x0 = p->alloc<R>(n2, "warm start image");
+    x0 = (R*)p->ws_x0;
+  }
+  launch_image_norms<R>((const R*)res, n2, p->parts, p->ctl, p->tickets + 5, p->ps);
+  const int nb = (int)std::min<int64_t>((n2 + 255) / 256, (int64_t)sm_count() * 8);
+  ws_input_kernel<R><<<nb, 256, 0, p->ps>>>((const R*)low, (const R*)res, p->ctl, n2, p->ws_in);
+  const ms_status st = ms_unet_forward(net, p->ws_in, N, N, p->ws_out, p->ps);
+  if (st != MS_OK)
+    throw Fail{st, std::string("warm start network: ") + ms_unet_last_error(net)};
+  ws_output_kernel<R><<<nb, 256, 0, p->ps>>>(p->ws_out, p->ctl, n2, x0);
+  WaveletGeom g{p->N, p->J, p->M};
+  launch_analysis<R>(x0, (R*)beta, (R*)p->wtmp, g, p->ps);
+  launch_axpby<R>((const R*)beta, nullptr, (R*)beta, 1.0 / p->M, 0.0, (int64_t)p->M * n2,
+                  p->ps);
+  ck(cudaGetLastError(), "warm start kernels");
 }
 
 // ------------------------------------------------------------- reconstruct
@@ -784,8 +865,17 @@ void run_step(ms_plan* p, int step, int chan, const ms_recon_opts& o, const void
     launch_set_lambda(p->ctl, o.lambda_rule, coef, n, n == 1 ? 1 : 0, p->ps);
     if (step == MS_STEP_FULL)
       launch_axpby<R>((const R*)low_image, model, l, 1.0, -1.0, n2, p->ps);   // l = i^_L - sum i_j
+    const void* beta0 = nullptr;
+    if (step == MS_STEP_FULL && n == 1 && o.warm_start) {
+      // the learned warm start: step two's first minor cycle starts from the
+      // network's image of [i^_L, i~_H1]
+      if (!p->ws_beta) p->ws_beta = p->alloc<R>((size_t)p->M * n2, "warm start coefficients");
+      // (its norms of i~_H1 leave lambda, already set from them, unchanged)
+      warm_start_beta<R>(p, o.warm_start, low_image, res, p->ws_beta, nullptr);
+      beta0 = p->ws_beta;
+    }
     int a = tm.mark();
-    run_fista<R>(p, step, pd, res, step == MS_STEP_FULL ? l : nullptr, nullptr, o.fista_iters,
+    run_fista<R>(p, step, pd, res, step == MS_STEP_FULL ? l : nullptr, beta0, o.fista_iters,
                  o.rel_tol);
     tm.spans[2].push_back({a, tm.mark()});
     launch_axpby<R>(model, (const R*)p->xwork, model, 1.0, 1.0, n2, p->ps);   // i^ += W beta
@@ -1187,6 +1277,7 @@ void minor_cycle(ms_plan* p, int step, int chan, const void* residual, const voi
 
 void destroy(ms_plan* p) {
   if (!p) return;
+  DeviceGuard guard;
   cudaSetDevice(p->dev);
   if (p->fista_exec) cudaGraphExecDestroy(p->fista_exec);
   for (cufftHandle h : {p->c2c, p->r2c, p->c2r})
@@ -1458,26 +1549,6 @@ void* static_grid_scratch(int dev) {
   return g_scratch_addr[dev];
 }
 
-// the gridding half of grid_sorted with a caller-given scratch base
-template <typename R>
-void grid_sorted_with(ms_plan* p, PartDev& pd, const void* vis_sorted, void* image,
-                      void* scratch) {
-  if (p->prec == MS_FP32_KAHAN) {
-    launch_grid<float, true>(pd.items, pd.nitems, pd.cell, (const float2*)pd.frac,
-                             (const float2*)vis_sorted, scratch, p->Ng, p->T, p->ntx, p->beta,
-                             p->ps);
-    launch_fold<float, true>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (float2*)p->grid,
-                             p->ps);
-  } else {
-    launch_grid<R, false>(pd.items, pd.nitems, pd.cell, (const C2<R>*)pd.frac,
-                          (const C2<R>*)vis_sorted, scratch, p->Ng, p->T, p->ntx, p->beta,
-                          p->ps);
-    launch_fold<R, false>(scratch, pd.tile_items, p->Ng, p->T, p->ntx, (C2<R>*)p->grid, p->ps);
-  }
-  fft_c2c<R>(p, CUFFT_INVERSE);
-  const double sc = pd.n > 0 ? 1.0 / (double)pd.n : 0.0;
-  launch_crop<R>((const C2<R>*)p->grid, (const R*)p->psi, p->N, p->Ng, sc, (R*)image, p->ps);
-}
 }  // namespace
 
 extern "C" {
@@ -1506,8 +1577,7 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     p->d.u = p->d.v = nullptr;
     p->d.flags = nullptr;
     p->dev = d->device;
-    int prev = 0;
-    cudaGetDevice(&prev);
+    DeviceGuard guard;   // the caller's device is current again on every exit
     ck(cudaSetDevice(p->dev), "set device");
     p->N = d->npix;
     p->Ng = 2 * d->npix;
@@ -1525,14 +1595,14 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     if (d->chunk > 0) {
       p->chunk = d->chunk;
     } else {
-      int64_t c = (d->nvis + 152 * 8 - 1) / (152 * 8);
+      const int64_t per = (int64_t)sm_count() * 8;   // about 8 work items per SM
+      int64_t c = (d->nvis + per - 1) / per;
       p->chunk = (int)std::min<int64_t>(std::max<int64_t>(c, 512), 8192);
     }
     ck(cudaStreamCreateWithFlags(&p->ps, cudaStreamNonBlocking), "stream");
     ck(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming), "event");
     ck(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming), "event");
     DISPATCH(p, build_plan<R>(p, d));
-    cudaSetDevice(prev);
   });
   if (st != MS_OK) {
     fprintf(stderr, "ms_plan_create: %s\n", p->msg.c_str());
@@ -1559,10 +1629,21 @@ ms_status ms_partition_counts(ms_plan* p, int32_t chan, int64_t out[4]) {
   });
 }
 
+ms_status ms_partition_layout(ms_plan* p, int32_t part, int32_t chan, int64_t out[3]) {
+  return guarded(p, [&] {
+    arg(out != nullptr, "out is NULL");
+    PartDev& pd = part_of(p, part, chan);
+    out[0] = pd.nitems;
+    out[1] = (int64_t)p->S * p->S;
+    out[2] = (int64_t)grid_scratch_cell_bytes(p->prec);
+  });
+}
+
 ms_status ms_partition_rows(ms_plan* p, int32_t part, int32_t chan, int32_t* rows) {
   return guarded(p, [&] {
     PartDev& pd = part_of(p, part, chan);
     arg(rows != nullptr || pd.n == 0, "rows is NULL");
+    DeviceGuard guard;
     ck(cudaSetDevice(p->dev), "set device");
     if (pd.n) ck(cudaMemcpy(rows, pd.idx, sizeof(int32_t) * pd.n, cudaMemcpyDeviceToHost), "copy");
   });
@@ -1717,8 +1798,46 @@ ms_status ms_reconstruct_single_step(ms_plan* p, int32_t chan, const void* vis,
   });
 }
 
+ms_status ms_lambda(ms_plan* p, int32_t rule, double coef, int32_t n, const void* residual,
+                    double* lambda, void* stream) {
+  return guarded(p, [&] {
+    arg(residual && lambda, "residual and lambda are required");
+    arg(rule == MS_LAMBDA_NORM2_2N || rule == MS_LAMBDA_MAX_FIXED, "unknown lambda rule");
+    arg(n >= 1 && n <= 1000, "n must be 1..1000");
+    arg(std::isfinite(coef), "coef must be finite");
+    Scope sc(p, stream);
+    const int64_t n2 = (int64_t)p->N * p->N;
+    DISPATCH(p, launch_image_norms<R>((const R*)residual, n2, p->parts, p->ctl, p->tickets + 5,
+                                      p->ps));
+    launch_set_lambda(p->ctl, rule, coef, n, 1, p->ps);
+    ck(cudaMemcpyAsync(lambda, &p->ctl->lam, sizeof(double), cudaMemcpyDeviceToHost, p->ps),
+       "read lambda");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    sc.finish();
+  });
+}
+
+ms_status ms_warm_start_coefficients(ms_plan* p, ms_unet* net, const void* low_image,
+                                     const void* residual_h1, void* beta_out, void* x0_out,
+                                     void* stream) {
+  return guarded(p, [&] {
+    arg(low_image && residual_h1 && beta_out, "low_image, residual_h1 and beta_out are required");
+    Scope sc(p, stream);
+    DISPATCH(p, warm_start_beta<R>(p, net, low_image, residual_h1, beta_out, x0_out));
+    sc.finish();
+  });
+}
+
+ms_status ms_set_objective_target(ms_plan* p, double target) {
+  return guarded(p, [&] {
+    arg(!std::isnan(target), "target must not be NaN (use -inf to turn it off)");
+    p->obj_target = std::isfinite(target) ? target : -INFINITY;
+  });
+}
+
 ms_status ms_set_profiling(ms_plan* p, int32_t on) {
   return guarded(p, [&] {
+    DeviceGuard guard;
     ck(cudaSetDevice(p->dev), "set device");
     harvest(p);
     p->prof = on != 0;
@@ -1728,6 +1847,7 @@ ms_status ms_set_profiling(ms_plan* p, int32_t on) {
 ms_status ms_get_kernel_profile(ms_plan* p, ms_kernel_profile* out, int32_t reset) {
   return guarded(p, [&] {
     arg(out != nullptr, "out is NULL");
+    DeviceGuard guard;
     ck(cudaSetDevice(p->dev), "set device");
     ck(cudaStreamSynchronize(p->ps), "synchronize");
     harvest(p);
@@ -1763,7 +1883,7 @@ ms_status ms_grid_static_scratch(ms_plan* p, int32_t part, int32_t chan, const v
     void* scratch = static_grid_scratch(p->dev);
     DISPATCH(p, {
       launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
-      grid_sorted_with<R>(p, pd, p->vis_a, dirty, scratch);
+      grid_sorted<R>(p, pd, p->vis_a, dirty, nullptr, scratch);
     });
     sc.finish();
   });

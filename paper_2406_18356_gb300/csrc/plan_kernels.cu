@@ -13,11 +13,26 @@ constexpr int kRadixChunk = kRadixBlock * kRadixRounds;   // rows per sort block
 
 int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
-  if (g > 152 * 64) g = 152 * 64;
+  const int64_t cap = (int64_t)sm_count() * 64;
+  if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;
 }
 }  // namespace
+
+int sm_count() {
+  constexpr int kDevices = 64;
+  static int cache[kDevices] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return 152;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 152;   // the attribute query cannot fail on a live device; GB300's count
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
 
 // Row k: grid coordinate g = u Ng dl (uv origin at 0), first footprint cell
 // c0 = floor(g - W/2) + 1, centre offset f = (g - c0) - (W-1)/2 in (-0.5, 0.5].

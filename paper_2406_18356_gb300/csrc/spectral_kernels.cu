@@ -112,7 +112,7 @@ __device__ __forceinline__ double half_plane_weight(int col, int N) {
 
 int nparts_for(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
-  if (b > 152 * 4) b = 152 * 4;
+  if (b > sm_count() * 4) b = sm_count() * 4;
   if (b < 1) b = 1;
   return (int)b;
 }
@@ -325,9 +325,9 @@ __device__ void spec_block_sums(R s0, R c0, R s1, R c1, double l1s, bool has_l1,
 
 // Iteration control from the summed terms o = (<x,Kx>, <b,x>, ||B_k||_1)
 // (one thread): F(B_k) = <x,Kx> - 2<b,x> + c0 + lambda ||B_k||_1 goes to the
-// trace; `done` rises on a non-finite F, on convergence or at the iteration
-// budget, else the iteration index, the momentum t_(k+1) and the step
-// scalars advance.
+// trace; `done` rises on a non-finite F, on convergence (relative change, or
+// F at or below the objective target), or at the iteration budget, else the
+// iteration index, the momentum t_(k+1) and the step scalars advance.
 __device__ void spec_control(const double (&o)[3], FistaCtl* ctl, double* trace) {
   const int k = ctl->k;
   const double lam = ctl->lam, Fprev = ctl->F_cur, rtol = ctl->rel_tol;
@@ -344,6 +344,9 @@ __device__ void spec_control(const double (&o)[3], FistaCtl* ctl, double* trace)
     ctl->error = 4;
     ctl->done = 1;
   } else if (k >= 1 && rtol > 0.0 && fabs(F - Fprev) <= rtol * fabs(F)) {
+    ctl->converged = 1;
+    ctl->done = 1;
+  } else if (F <= ctl->F_target) {
     ctl->converged = 1;
     ctl->done = 1;
   } else if (k >= ctl->max_iters) {

@@ -28,7 +28,8 @@ namespace {
 using bf16 = __nv_bfloat16;
 constexpr int kT = 256;
 
-int blocks(int64_t n, int cap = 152 * 16) {
+int blocks(int64_t n, int cap = 0) {
+  if (cap <= 0) cap = sm_count() * 16;
   int64_t b = (n + kT - 1) / kT;
   if (b > cap) b = cap;
   return b < 1 ? 1 : (int)b;
@@ -419,6 +420,7 @@ struct Layer {
   bf16 *Wb = nullptr, *Wt = nullptr;         // packed bf16 weights
   const bf16* in = nullptr;                  // forward input (bf16 [P][ci])
   bf16* out = nullptr;                       // forward output (bf16 [P][co]) (not the head)
+  bf16* dz_keep = nullptr;                   // kept pre-activation gradient [P][cop]
 };
 
 struct Fail {
@@ -448,6 +450,8 @@ struct ms_unet {
   std::vector<float*> dskip;
   double* parts = nullptr;
   int adam_t = 0;
+  bool keep = false;         // keep every layer's pre-activation gradient
+  int last_h = 0, last_w = 0;   // image size of the last forward pass
   std::string msg;
   template <typename T> T* alloc(size_t n) {
     void* p = nullptr;
@@ -459,6 +463,8 @@ struct ms_unet {
     for (void* p : allocs) cudaFree(p);
   }
 };
+
+int ms_unet_device_of(const ms_unet* net) { return net ? net->dev : -1; }
 
 namespace {
 template <typename F> ms_status guard(ms_unet* u, F&& f) {
@@ -496,6 +502,9 @@ void conv_backward(ms_unet* u, Layer& l, const float* g, int ldg, int H, int W, 
   const int64_t P = (int64_t)H * W;
   relu_grad_kernel<<<blocks(P * l.cop), kT, 0, s>>>(g, ldg, l.relu ? l.out : nullptr, P, l.co,
                                                     l.cop, u->dz);
+  if (u->keep)
+    ck(cudaMemcpyAsync(l.dz_keep, u->dz, sizeof(bf16) * P * l.cop, cudaMemcpyDeviceToDevice, s),
+       "keep gradient");
   colsum_kernel<<<l.co, kT, 0, s>>>(u->dz, P, l.cop, l.gb);
   transpose_kernel<<<blocks(P * l.cop), kT, 0, s>>>(u->dz, P, l.cop, u->dzT);
   im2col_t_kernel<<<blocks(P * l.kp), kT, 0, s>>>(l.in, H, W, l.ci, l.kp, u->colsT);
@@ -519,6 +528,8 @@ void forward(ms_unet* u, const float* in, int H, int W, cudaStream_t s) {
   arg(H % (4 << (u->levels - 1)) == 0 && W % (4 << (u->levels - 1)) == 0,
       "image sides must be divisible by 4 * 2^(levels-1)");
   pack(u, s);
+  u->last_h = H;
+  u->last_w = W;
   const int Lv = u->levels;
   to_bf16_kernel<<<blocks((int64_t)H * W * 2), kT, 0, s>>>(in, (int64_t)H * W * 2, u->xin);
   size_t li = 0;
@@ -798,6 +809,40 @@ ms_status ms_unet_gradients(ms_unet* u, const float* in, const float* target, in
       ck(e, "copy gradients");
     }
     ck(cudaGetLastError(), "kernel launch");
+  });
+}
+
+ms_status ms_unet_keep_intermediates(ms_unet* u, int32_t keep) {
+  return guard(u, [&] {
+    ck(cudaSetDevice(u->dev), "set device");
+    if (keep && !u->keep) {
+      const int64_t P0 = (int64_t)u->max_side * u->max_side;
+      for (Layer& l : u->L)
+        if (!l.dz_keep) l.dz_keep = u->alloc<bf16>((size_t)(P0 >> (2 * l.level)) * l.cop);
+    }
+    u->keep = keep != 0;
+  });
+}
+
+ms_status ms_unet_layer_tensor(ms_unet* u, int32_t layer, int32_t which, float* host, int64_t n) {
+  return guard(u, [&] {
+    arg(layer >= 0 && layer < (int)u->L.size(), "layer out of range");
+    arg(which >= 0 && which <= 2, "which must be 0 (input), 1 (output) or 2 (gradient)");
+    arg(u->last_h > 0, "no forward pass yet");
+    const Layer& l = u->L[layer];
+    const int64_t P = (int64_t)(u->last_h >> l.level) * (u->last_w >> l.level);
+    const int c = which == 0 ? l.ci : l.co;
+    arg(host && n == P * c, "host buffer of H_l W_l channels floats required");
+    const bf16* src = which == 0 ? l.in : (which == 1 ? l.out : l.dz_keep);
+    arg(src != nullptr, which == 1 ? "the head keeps no bfloat16 output"
+                                   : "no kept gradient: enable ms_unet_keep_intermediates "
+                                     "before ms_unet_gradients");
+    const int ld = which == 2 ? l.cop : c;   // row length of the stored array
+    ck(cudaSetDevice(u->dev), "set device");
+    std::vector<bf16> h((size_t)P * ld);
+    ck(cudaMemcpy(h.data(), src, sizeof(bf16) * h.size(), cudaMemcpyDeviceToHost), "copy");
+    for (int64_t p = 0; p < P; ++p)
+      for (int k = 0; k < c; ++k) host[p * c + k] = __bfloat162float(h[(size_t)p * ld + k]);
   });
 }
 

@@ -41,22 +41,24 @@ def make_problem(ms, seed: int, npix: int, n_major: int = 5, fista_iters: int = 
                                                                fista_iters=fista_iters))
     res = plan.grid("H", vis)
     s2 = plan.sigma2_hat(res)
+    # training pairs use the scaling ms_warm_start_coefficients applies to the
+    # network's input at inference: images divided by max|i~_H1|
     scale = 1.0 / float(res.abs().max())
     x = torch.stack([low.float(), res.float()], dim=2).mul(scale).contiguous()
     return {"plan": plan, "x": x, "scale": scale, "low": low, "res": res,
-            "lam": 0.05 * float(res.double().norm()) * 2, "sigma2": s2, "eta2": 1e-3 * s2}
+            "lam": plan.lam(res, 0.05, 1), "sigma2": s2, "eta2": 1e-3 * s2}
 
 
-def solve(ms, prob, max_iters: int, rel_tol: float, x0=None):
-    """Step two's first minor cycle, from zero or from the image x0, with the
-    relative-change stop rel_tol (0: exactly max_iters iterations); returns
-    (model image, stats, wall ms)."""
+def solve(ms, prob, max_iters: int, rel_tol: float, net=None):
+    """Step two's first minor cycle, from zero or from the network's start
+    (the library's ms_warm_start_coefficients), with the relative-change stop
+    rel_tol (0: exactly max_iters iterations); returns (model image, stats,
+    wall ms)."""
     import torch
     plan = prob["plan"]
     beta = None
-    if x0 is not None:
-        beta = plan.dictionary_analysis(x0.to(plan.real_dtype).contiguous()) / plan.n_bases
-        beta = beta.contiguous()
+    if net is not None:
+        beta, _ = plan.warm_start_coefficients(net, prob["low"], prob["res"])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     model, st = plan.minor_cycle("full", prob["res"], prob["lam"], max_iters,
@@ -107,18 +109,23 @@ def evaluate(ms, net, seeds, npix: int, rel_tol: float = 1e-6, max_iters: int = 
     first iteration within e of the best objective any start reached (and the
     time to it from the run's per-iteration time)."""
     out = []
+    # an untrained network returns its first input channel: the step-one
+    # image as the start, through the same library call
+    identity = ms.WarmStartNet(levels=net.levels, width=8, max_side=net.max_side, seed=0)
     for seed in seeds:
         prob = make_problem(ms, seed, npix)
-        x_net = net.forward(prob["x"]).div(prob["scale"])
-        starts = {"zero": None, "low": prob["low"], "net": x_net}
+        starts = {"zero": None, "low": identity, "net": net}
         rec = {"seed": int(seed)}
         runs = {}
-        for name, x0 in starts.items():
-            _, st, ms_ = solve(ms, prob, max_iters, rel_tol, x0=x0)
+        x0s = {}
+        for name, nt in starts.items():
+            if nt is not None:
+                x0s[name] = prob["plan"].warm_start_coefficients(nt, prob["low"], prob["res"])[1]
+            _, st, ms_ = solve(ms, prob, max_iters, rel_tol, net=nt)
             rec[f"stop_iters_{name}"] = st.iterations
             rec[f"stop_ms_{name}"] = ms_
             rec[f"stop_objective_{name}"] = st.objective
-            model, lt, lms = solve(ms, prob, max_iters, 0.0, x0=x0)
+            model, lt, lms = solve(ms, prob, max_iters, 0.0, net=nt)
             runs[name] = (model, lt.trace, lms / max(lt.iterations, 1))
         f_best = min(float(np.min(r[1])) for r in runs.values())
         for name, (_, trace, ms_per_iter) in runs.items():
@@ -130,10 +137,11 @@ def evaluate(ms, net, seeds, npix: int, rel_tol: float = 1e-6, max_iters: int = 
         for name in ("low", "net"):
             rec[f"solution_rel_diff_{name}"] = float((runs[name][0].double() - ref).norm()
                                                      / ref.norm())
-            x0 = starts[name].double()
+            x0 = x0s[name].double()
             rec[f"start_rel_err_{name}"] = float((x0 - ref).norm() / ref.norm())
         out.append(rec)
         prob["plan"].close()
+    identity.close()
     return out
 
 

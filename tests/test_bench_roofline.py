@@ -70,3 +70,46 @@ def test_dominant_family_and_fraction():
 def test_recorded_traffic_needs_matching_precision():
     assert bench.recorded_traffic("synth", "fp64") is None
     assert bench.recorded_traffic("grid", "fp32") is None   # not a per-pass family
+
+
+class _FakePlan:
+    """partition counts and gridding layout of a plan, without a GPU"""
+
+    def partition_counts(self, chan=0):
+        return {"L": 3000, "H": 5000, "LH": 100, "ALL": 7900}
+
+    def partition_layout(self, part, chan=0):
+        return {"L": 7, "H": 11}[part], 38 * 38, 8
+
+
+def test_gridding_and_fold_bytes():
+    plan = _FakePlan()
+    rows = (3000 + 5000) / 2
+    grid = 4 * N * N * 2 * 4
+    # per row: packed cell (4 B) + two offsets + one complex value (FP32)
+    assert bench.family_bytes("grid", N, M, J, 4, plan) == rows * (4 + 4 * 4) + grid
+    # degridding also reads the observed value and writes the residual
+    assert bench.family_bytes("degrid", N, M, J, 4, plan) == rows * (4 + 2 * 4 + 4 * 4) + grid
+    # the fold reads every work item's (T + 6)^2 tile once and writes the grid
+    fold = ((7 + 11) / 2) * 38 * 38 * 8 + grid
+    assert bench.family_bytes("fold", N, M, J, 4, plan) == fold
+
+
+def test_host_cores_reports_the_machine():
+    nproc, cores = bench.host_cores()
+    assert nproc == os.cpu_count() and 1 <= cores <= nproc
+
+
+def test_oracle_phases_run_in_a_pinned_child(tmp_path):
+    """The oracle timing child sees one BLAS thread and reports its phases
+    (a tiny sample, no FISTA or 128-pixel run)."""
+    import numpy as np
+    import synth
+    w = synth.tiny(npix=32, n_ant=8, n_dumps=6, seed=1)
+    path = str(tmp_path / "s.npz")
+    np.savez(path, u=w.u[0], v=w.v[0], vis=w.vis[0], npix=32, pixel_size=w.pixel_size)
+    one = bench.run_oracle_phases({"data": path, "rows": 100}, 1)
+    assert one["threads"] == 1 and one["grid_degrid"]["rows"] == 100
+    assert one["grid_degrid"]["vis_per_s"] > 0 and one["fft_ng2_pair_ms"] > 0
+    two = bench.run_oracle_phases({"data": path, "rows": 100, "pool": 2}, 2)
+    assert two["grid_degrid"]["processes"] == 2 and two["grid_degrid"]["rows"] == 100

@@ -23,6 +23,11 @@ def ms():
     return pkg
 
 
+# Model images W beta_K after a minor cycle: the final-image bar of the
+# benchmark definition (1e-4 relative L2) for the FP32 form, 1e-8 for FP64.
+IMAGE_TOL = {"fp64": 1e-8, "fp32": 1e-4}
+
+
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
 
@@ -67,6 +72,45 @@ def test_lipschitz_closed_form_matches_oracle(ms, step, part):
     plan.close()
 
 
+def _separated_case(N=32, dl=1e-4, n_dc=10, n_rand=300, seed=7):
+    """Rows at the uv origin plus uniformly random rows: the DC term of every
+    partition's PSF spectrum stands well above the rest, so the largest
+    eigenvalue of the normal operator is separated from the next one."""
+    rng = np.random.default_rng(seed)
+    u1, v1 = synth.random_uv(n_rand, N, dl, rng, frac_of_grid=0.2)
+    return (np.concatenate([np.zeros(n_dc), u1]), np.concatenate([np.zeros(n_dc), v1]))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-5)])
+@pytest.mark.parametrize("step,part", [("low", "L"), ("single", "ALL"), ("full", "H")])
+def test_power_iteration_reaches_the_closed_form(ms, precision, tol, step, part):
+    """Sect. 3.4: with orthogonal bases and circulant operators the Lipschitz
+    constant is 2 M max K^; the library's power iteration through W (FP64
+    reductions) must reach it on a spectrum whose top eigenvalue is separated
+    (ratio of the next one checked on the oracle's K^; 300 iterations shrink
+    the Rayleigh-quotient error by that ratio to the power 600)."""
+    N, dl, ell, delta, s2, e2 = 32, 1e-4, 1.0, 0.5, 1.0, 1.2
+    u, v = _separated_case(N, dl)
+    in_l, in_h = og.partition(u, v, N, dl, ell, delta)
+    mask = {"L": in_l, "H": in_h, "ALL": np.ones_like(in_l)}[part]
+    A = og.GriddedOperator(u[mask], v[mask], N, dl)
+    Hhat = osv.psf_spectrum(A.psf())
+    if step == "full":
+        gl, gh = osv.filter_responses(N, ell, delta, s2, e2)
+        K = (gh * Hhat) ** 2 + gl ** 2
+    else:
+        K = Hhat ** 2
+    top = np.sort(np.unique(np.round(K.ravel() / K.max(), 12)))[::-1]
+    assert top[1] <= 0.9, top[:3]
+    plan = ms.Plan(u, v, N, dl, ell, delta, precision=precision, levels=3, n_bases=8)
+    closed, power = plan.lipschitz(step, sigma2=s2, eta2=e2, power_iters=300)
+    err = abs(power - closed) / closed
+    print(f"power iteration {step} {precision}: {err:.2e} (next/top {top[1]:.3f})")
+    assert abs(closed - 2 * 8 * K.max()) <= (1e-10 if precision == "fp64" else 1e-5) * closed
+    assert err <= tol
+    plan.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 2e-4)])
 @pytest.mark.parametrize("step,part", [("low", "L"), ("single", "ALL"), ("full", "H")])
 def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
@@ -92,7 +136,9 @@ def test_minor_cycle_matches_oracle(ms, precision, tol, step, part):
                                  sigma2=s2, eta2=e2)
     assert st.iterations == iters
     np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
-    assert rel(model.cpu().numpy(), prob.W.synth(ref.beta)) <= 10 * tol
+    e_model = rel(model.cpu().numpy(), prob.W.synth(ref.beta))
+    print(f"minor cycle {step} {precision}: model image {e_model:.2e}")
+    assert e_model <= IMAGE_TOL[precision]
     assert abs(st.theta - prob.lipschitz_closed_form()) <= 1e-6 * st.theta
     plan.close()
 
@@ -119,7 +165,9 @@ def test_minor_cycle_larger_images_match_oracle(ms, precision, tol, N, J):
     ref = osv.fista(prob, iters)
     model, st = plan.minor_cycle("single", cuda(res).to(plan.real_dtype), lam, iters)
     np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
-    assert rel(model.cpu().numpy(), prob.W.synth(ref.beta)) <= 10 * tol
+    e_model = rel(model.cpu().numpy(), prob.W.synth(ref.beta))
+    print(f"minor cycle {N} px {precision}: model image {e_model:.2e}")
+    assert e_model <= IMAGE_TOL[precision]
     plan.close()
 
 
@@ -151,7 +199,9 @@ def test_minor_cycle_wide_images_match_oracle(ms, precision, tol, N):
                    precision=precision, levels=2, n_bases=2)
     model, st = plan.minor_cycle("single", cuda(res).to(plan.real_dtype), lam, 3)
     np.testing.assert_allclose(st.trace, ref.objective, rtol=tol)
-    assert rel(model.cpu().numpy(), prob.W.synth(ref.beta)) <= 10 * tol
+    e_model = rel(model.cpu().numpy(), prob.W.synth(ref.beta))
+    print(f"minor cycle {N} px {precision}: model image {e_model:.2e}")
+    assert e_model <= IMAGE_TOL[precision]
     plan.close()
 
 
@@ -255,4 +305,85 @@ def test_complete_coverage_recovers_the_sky(ms):
     o_low, o_full = oi.reconstruct_two_step(vis, u, v, N, dl, 4.0, 1.5, ro)
     assert rel(img.cpu().numpy(), o_full.image) <= 1e-8
     assert rel(img.cpu().numpy(), sky) <= 1e-5
+    plan.close()
+
+
+def _warm_net(ms, side, seed=3):
+    """A network whose head is not zero (so its start differs from the
+    step-one image)."""
+    net = ms.WarmStartNet(levels=2, width=8, max_side=side, seed=seed)
+    p = net.get_params()
+    n_head = 8 * 9 + 1   # the head's weights [1][3][3][8] and bias, stored last
+    p[-n_head:-1] = np.random.default_rng(seed).standard_normal(n_head - 1) * 0.05
+    net.set_params(p)
+    return net
+
+
+def test_warm_start_coefficients_follow_the_network(ms):
+    """ms_warm_start_coefficients: x0 = s net([i^_L, i~_H1] / s) with s =
+    max|i~_H1| (the network against the oracle's network), and beta = W^H x0 / M
+    (the oracle's dictionary on the library's x0), FP64 plan."""
+    import torch
+    from oracle import unet as ou
+    w, plan = _setup(ms, "fp64", N=32, J=3, M=8, seed=9)
+    tv = cuda(w.vis[0])
+    low, _, _ = plan.reconstruct_two_step(tv, ms.ReconOptions(n_major=2, fista_iters=20))
+    res = plan.grid("H", tv)
+    net = _warm_net(ms, 32)
+    beta, x0 = plan.warm_start_coefficients(net, low, res)
+    lo, r = low.cpu().numpy(), res.cpu().numpy()
+    s = np.max(np.abs(r))
+    xin = np.stack([lo, r], axis=2).astype(np.float32).astype(np.float64) / s
+    params = []
+    flat, off = net.get_params().astype(np.float64), 0
+    spec = ou.UNetSpec(levels=2, width=8)
+    for co, ci in spec.conv_shapes():
+        nw = co * 9 * ci
+        params.append({"w": flat[off:off + nw].reshape(co, 3, 3, ci), "b": flat[off + nw:off + nw + co]})
+        off += nw + co
+    y, _ = ou.forward(spec, params, np.stack([lo, r], axis=2).astype(np.float32).astype(np.float64)
+                      * np.float32(1.0 / s), quantize=True)
+    x0_ref = y * s
+    e_x0 = rel(x0.cpu().numpy(), x0_ref)
+    assert e_x0 <= 2e-3, e_x0
+    Wd = Dictionary(32, 8, 3)
+    b_ref = Wd.analysis(x0.cpu().numpy()) / 8
+    assert rel(beta.cpu().numpy(), b_ref) <= 1e-12
+    assert rel(Wd.synth(beta.cpu().numpy()), x0.cpu().numpy()) <= 1e-12   # W beta = x0
+    net.close()
+    plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-4)])
+def test_two_step_with_warm_start_handle_matches_oracle(ms, precision, tol):
+    """ms_reconstruct_two_step with a network in the options: step two's first
+    minor cycle starts from the network's coefficients; the oracle's two-step
+    method started from the same beta_0 gives the same images."""
+    w, plan = _setup(ms, precision, seed=9)
+    u, v, vis = w.u[0], w.v[0], w.vis[0]
+    tv = cuda(vis).to(plan.complex_dtype)
+    net = _warm_net(ms, 32)
+    opts = ms.ReconOptions(n_major=3, fista_iters=25, warm_start=net)
+    low, img, st = plan.reconstruct_two_step(tv, opts)
+    # the start the library used: the network on its own i^_L and i~_H1
+    beta0, _ = plan.warm_start_coefficients(net, low, plan.grid("H", tv))
+    ro = oi.ReconOptions(n_major=3, fista_iters=25, levels=3)
+    o_low, o_full = oi.reconstruct_two_step(vis, u, v, 32, w.pixel_size, w.ell_px, w.delta_px, ro,
+                                            beta0_full=beta0.double().cpu().numpy())
+    e_low, e_img = rel(low.cpu().numpy(), o_low.image), rel(img.cpu().numpy(), o_full.image)
+    print(f"two-step with warm start {precision}: low {e_low:.2e} full {e_img:.2e}")
+    assert e_low <= tol and e_img <= tol
+    # the start changed the answer's path: without it the image differs
+    _, img0, _ = plan.reconstruct_two_step(tv, ms.ReconOptions(n_major=3, fista_iters=25))
+    assert rel(img0.cpu().numpy(), img.cpu().numpy()) > 10 * tol
+    net.close()
+    plan.close()
+
+
+def test_lambda_entry_point_matches_the_rule(ms):
+    w, plan = _setup(ms, "fp64", seed=9)
+    res = plan.grid("L", cuda(w.vis[0]))
+    r = res.cpu().numpy()
+    assert abs(plan.lam(res, 0.05, 3) - 0.05 * np.linalg.norm(r) * 8) <= 1e-12 * np.linalg.norm(r)
+    assert abs(plan.lam(res, 1e-3, 2, rule="max_fixed") - 1e-3 * np.abs(r).max()) <= 1e-15
     plan.close()

@@ -1,6 +1,7 @@
 """ms_grid_static_scratch: the gridding entry point whose per-work-item tiles
-live in the library's fixed static scratch array.  Two calls in a row through
-the C ABI must each reproduce ms_grid's dirty image, and a partition whose
+live in the library's fixed static scratch array.  Calls in a row through
+the C ABI must each reproduce ms_grid's dirty image and leave the device's
+free memory unchanged after the first, and a partition whose
 scratch need exceeds the array is refused with MS_ERR_ARG.  This file is
 named to be collected last, so it also runs after every other GPU test has
 used the library."""
@@ -35,12 +36,18 @@ def test_static_scratch_grid_matches_ms_grid_twice(ms, precision, part):
     vis = torch.from_numpy(w.vis[0]).cuda().to(plan.complex_dtype)
     ref = plan.grid(part, vis)
     torch.cuda.synchronize()
-    outs = []
-    for _ in range(2):
-        out = torch.full((64, 64), float("nan"), dtype=plan.real_dtype, device="cuda")
+    outs = [torch.full((64, 64), float("nan"), dtype=plan.real_dtype, device="cuda")
+            for _ in range(3)]
+    torch.cuda.synchronize()
+    free = []
+    for out in outs:
         plan.grid_static_scratch(part, vis, out)
         torch.cuda.synchronize()
-        outs.append(out.cpu().numpy())
+        free.append(torch.cuda.mem_get_info()[0])
+    # the first call may load the module's static array; no later call takes
+    # device memory
+    assert free[1] == free[0] and free[2] == free[0], free
+    outs = [o.cpu().numpy() for o in outs]
     r = ref.cpu().numpy()
     assert np.isfinite(r).all() and np.abs(r).max() > 0
     # same kernels, same summation order as ms_grid: identical results
