@@ -195,15 +195,16 @@ void launch_classify(const double* u, const double* v, const uint8_t* flags, int
                      int Ng, int npix, double dl, double ell, double delta, int tile,
                      int ntx, uint32_t* cell, double2* frac, uint32_t* tile_id,
                      uint8_t* member, cudaStream_t s);
-void launch_make_keys(const uint32_t* tile_id, const uint8_t* member, int64_t n,
-                      uint8_t mask, uint32_t sentinel, uint32_t* keys, int32_t* vals,
-                      cudaStream_t s);
+void launch_make_keys(const uint32_t* tile_id, const uint32_t* cell, const uint8_t* member,
+                      int64_t n, uint8_t mask, int log2_tile, uint32_t sentinel, uint32_t* keys,
+                      int32_t* vals, cudaStream_t s);
 // stable LSD radix sort of (keys, vals) on the low `bits` bits of keys;
 // tmp buffers of n elements; returns the pointers holding the result
 void radix_sort(uint32_t** keys, int32_t** vals, uint32_t* ktmp, int32_t* vtmp, int64_t n,
                 int bits, int32_t* hist, int64_t hist_cap, cudaStream_t s);
 int64_t radix_hist_size(int64_t n);
-void launch_count_tiles(const uint32_t* keys, int64_t n, int32_t* counts, cudaStream_t s);
+void launch_count_tiles(const uint32_t* keys, int64_t n, int shift, int32_t* counts,
+                        cudaStream_t s);
 void launch_exclusive_scan(const int32_t* in, int32_t* out, int n, cudaStream_t s);
 void launch_chunks_per_tile(const int32_t* counts, int ntiles, int chunk, int32_t* nchunks,
                             cudaStream_t s);
@@ -284,6 +285,11 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
 // image 2 (K W alpha_k - b) written by the inverse FFT, the synthesized image
 // x = W B_k, the approximation ping-pong, the control block and the per-block
 // partial sums of ||B_{k+1}||_1.
+// CTAs of each basis's group in the one-launch coarse levels: basis m owns
+// CTAs [first[m], first[m + 1]).
+struct CoarseGroups {
+  int first[kMaxBases + 1];
+};
 template <typename R> struct FistaPass {
   R* B0;
   R* B1;
@@ -294,6 +300,10 @@ template <typename R> struct FistaPass {
   FistaCtl* ctl;
   double* l1_parts;
   int N, J, M;
+  int coarse_ctas;     // CTAs of the one-launch coarse levels (0: one launch per level)
+  int coarse_budget;   // their shared-memory budget per CTA (bytes)
+  CoarseGroups coarse_groups;
+  int* coarse_bar;     // group barrier state, two ints per basis, zero at rest
 };
 // The minor cycle's synthesis levels (J..1) and analysis + FISTA-update
 // levels (1..J), one launch per level.  only_level: 0 = all levels, j > 0 =
@@ -307,6 +317,13 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
                                  cudaStream_t s, int only_level = 0);
 int analysis_prox_partials(WaveletGeom g);
 void analysis_window_box(unsigned* cols, unsigned* rows);
+// The one-launch coarse levels (2..J of both transforms, one cooperative
+// launch per transform) on the current device: the CTAs of each basis's
+// group (in proportion to its filter length) and the shared-memory budget
+// per CTA with which all of them are resident at once.  Returns the number
+// of CTAs, or 0 when the geometry needs the per-level kernels (N not a power
+// of two, N < 256, N >> J < 8, J < 2) or no such launch fits.
+int coarse_groups(WaveletGeom g, size_t rsz, CoarseGroups* groups, int* budget);
 
 // spectral_kernels.cu
 int spectral_partials(int N);

@@ -62,6 +62,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned phase)
 // footprint: tap i is at distance t = f + (W-1)/2 - i cells from the sample.
 // phi = exp(beta (sqrt(1 - z^2) - 1)) is evaluated as
 // exp(-beta z^2 / (1 + sqrt(1 - z^2))) so the centre taps keep full precision.
+// FP64: correctly rounded library sqrt / exp and an IEEE division.  FP32:
+// the SFU's approximate square root, reciprocal and base-2 exponential
+// (relative errors near 2^-22 each, far inside the FP32 form's 1e-5 bar),
+// with exp(x) = 2^(x log2 e).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float exp2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 template <typename R>
 __device__ __forceinline__ void es_weights(R f, R beta, R* w) {
   const R c = (R)(4.0 / (kW * kW));
@@ -72,6 +91,18 @@ __device__ __forceinline__ void es_weights(R f, R beta, R* w) {
     R s = (R)1 - z2;
     s = s > (R)0 ? s : (R)0;
     w[i] = exp(-beta * z2 / ((R)1 + sqrt(s)));
+  }
+}
+template <>
+__device__ __forceinline__ void es_weights<float>(float f, float beta, float* w) {
+  const float c = 4.0f / (kW * kW);
+  const float nb = -beta * 1.4426950408889634f;   // -beta log2(e)
+#pragma unroll
+  for (int i = 0; i < kW; ++i) {
+    const float t = f + (float)(kHalfW - i);
+    const float z2 = t * t * c;
+    const float s = fmaxf(1.0f - z2, 0.0f);
+    w[i] = exp2_approx(nb * z2 * rcp_approx(1.0f + sqrt_approx(s)));
   }
 }
 }  // namespace
@@ -293,13 +324,63 @@ template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_warps()
   return (KAHAN || sizeof(R) == 8) ? 4 : 8;
 }
 
-// A warp grids one visibility at a time: lane t < 32 takes tap t, lanes
-// 0..16 then take taps 32..48 (tap t = (i, j) = (t mod 7, t div 7)).  The 49
-// cells of one visibility are distinct, so a read-modify-write per lane needs
-// no atomics; __syncwarp orders successive visibilities.  Each warp owns its
-// sub-tile, so no two warps ever touch the same word; the compensated form
-// keeps a Kahan correction word per cell component.  At the end the warps'
-// tiles are summed in a fixed order into the item's scratch tile.
+// Adds v (and, compensated, its correction) to a tile cell.
+template <typename R, bool KAHAN>
+__device__ __forceinline__ void cell_add(C2<R>* my, C2<R>* myc, int c, C2<R> v) {
+  C2<R> a = my[c];
+  if (KAHAN) {
+    C2<R> cp = myc[c];
+    const R yr = v.x - cp.x, yi = v.y - cp.y;
+    const R tr = a.x + yr, ti = a.y + yi;
+    cp.x = (tr - a.x) - yr;
+    cp.y = (ti - a.y) - yi;
+    a.x = tr;
+    a.y = ti;
+    myc[c] = cp;
+  } else {
+    a.x += v.x;
+    a.y += v.y;
+  }
+  my[c] = a;
+}
+
+// Register sum of one tap over a run of visibilities (compensated for the
+// Kahan form).
+template <typename R, bool KAHAN> struct TapSum {
+  R sr = 0, si = 0, cr = 0, ci = 0;
+  __device__ __forceinline__ void add(R w, C2<R> v) {
+    if (KAHAN) {
+      const R yr = w * v.x - cr, yi = w * v.y - ci;
+      const R tr = sr + yr, ti = si + yi;
+      cr = (tr - sr) - yr;
+      ci = (ti - si) - yi;
+      sr = tr;
+      si = ti;
+    } else {
+      sr = fma(w, v.x, sr);
+      si = fma(w, v.y, si);
+    }
+  }
+  __device__ __forceinline__ C2<R> value() const {
+    C2<R> o;
+    o.x = sr - cr;
+    o.y = si - ci;
+    return o;
+  }
+  __device__ __forceinline__ void clear() { sr = si = cr = ci = (R)0; }
+};
+
+// A warp grids its share of the work item's rows, which the plan sorts by
+// anchor cell inside the tile: lane t takes tap t (t < 32) and lanes 0..16
+// also tap t + 32 (tap (i, j) = (t mod 7, t div 7)).  While consecutive rows
+// share an anchor cell, every lane sums its taps' contributions in registers;
+// when the anchor changes, the lanes add their sums to the 49 distinct cells
+// of the footprint in the warp's own sub-tile (no atomics) and __syncwarp
+// orders that update before the next.  The rows' ES weights, values and
+// anchors are staged 32 at a time in shared memory.  The compensated form
+// sums each run with Kahan compensation and adds it into compensated cells.
+// At the end the warps' sub-tiles are summed in a fixed order into the
+// item's scratch tile.
 // One gridding work item `it`; its tile goes to scratch tile `scratch_tile`.
 template <typename R, bool KAHAN>
 __device__ __forceinline__ void grid_item(const WorkItem it, const uint32_t* __restrict__ cell,
@@ -338,11 +419,14 @@ __device__ __forceinline__ void grid_item(const WorkItem it, const uint32_t* __r
   const int i1 = lane % kW, j1 = lane / kW;
   const int i2 = (lane + 32) % kW, j2 = (lane + 32) / kW;
   const bool two = lane + 32 < kW * kW;
+  const int off1 = j1 * S + i1, off2 = j2 * S + i2;
 
   const int per = (it.count + NW - 1) / NW;
   const int ws = it.start + warp * per;
   int we = ws + per;
   if (we > it.start + it.count) we = it.start + it.count;
+  TapSum<R, KAHAN> t1, t2;
+  int run = -1;   // anchor (tile-local cell index) of the current run
   for (int base = ws; base < we; base += 32) {
     int k = base + lane;
     if (k < we) {
@@ -358,49 +442,27 @@ __device__ __forceinline__ void grid_item(const WorkItem it, const uint32_t* __r
     __syncwarp();
     int nb = we - base < 32 ? we - base : 32;
     for (int sidx = 0; sidx < nb; ++sidx) {
+      const int c0 = sc[sidx];   // uniform over the warp
+      if (c0 != run) {
+        if (run >= 0) {
+          cell_add<R, KAHAN>(my, myc, run + off1, t1.value());
+          if (two) cell_add<R, KAHAN>(my, myc, run + off2, t2.value());
+          __syncwarp();   // this run's cells before the next run's
+        }
+        run = c0;
+        t1.clear();
+        t2.clear();
+      }
       const R* w = sw + sidx * 2 * kW;
       const C2<R> val = sv[sidx];
-      const int c0 = sc[sidx];
-      {
-        R wt = w[i1] * w[kW + j1];
-        int c = c0 + j1 * S + i1;
-        C2<R> a = my[c];
-        if (KAHAN) {
-          C2<R> cp = myc[c];
-          R yr = wt * val.x - cp.x, yi = wt * val.y - cp.y;
-          R tr = a.x + yr, ti = a.y + yi;
-          cp.x = (tr - a.x) - yr;
-          cp.y = (ti - a.y) - yi;
-          a.x = tr;
-          a.y = ti;
-          myc[c] = cp;
-        } else {
-          a.x += wt * val.x;
-          a.y += wt * val.y;
-        }
-        my[c] = a;
-      }
-      if (two) {
-        R wt = w[i2] * w[kW + j2];
-        int c = c0 + j2 * S + i2;
-        C2<R> a = my[c];
-        if (KAHAN) {
-          C2<R> cp = myc[c];
-          R yr = wt * val.x - cp.x, yi = wt * val.y - cp.y;
-          R tr = a.x + yr, ti = a.y + yi;
-          cp.x = (tr - a.x) - yr;
-          cp.y = (ti - a.y) - yi;
-          a.x = tr;
-          a.y = ti;
-          myc[c] = cp;
-        } else {
-          a.x += wt * val.x;
-          a.y += wt * val.y;
-        }
-        my[c] = a;
-      }
-      __syncwarp();
+      t1.add(w[i1] * w[kW + j1], val);
+      if (two) t2.add(w[i2] * w[kW + j2], val);
     }
+    __syncwarp();   // the staging buffers are rewritten
+  }
+  if (run >= 0) {
+    cell_add<R, KAHAN>(my, myc, run + off1, t1.value());
+    if (two) cell_add<R, KAHAN>(my, myc, run + off2, t2.value());
   }
   __syncthreads();
   Acc* dst = scratch + scratch_tile * cells;

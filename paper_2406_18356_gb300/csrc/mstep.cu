@@ -266,6 +266,10 @@ struct ms_plan {
   double* parts = nullptr;     // reduction partials (one reduction at a time)
   double* l1parts = nullptr;   // per-block |B_k+1| partials of the analysis levels
   int n_l1 = 0;                // their number
+  int coarse_ctas = 0;         // CTAs of the one-launch coarse levels (0: one launch per level)
+  int coarse_budget = 0;       // their shared-memory budget per CTA
+  CoarseGroups coarse_gr{};    // their split over the bases
+  int* coarse_bar = nullptr;   // their group barrier state
   int32_t* tickets = nullptr;
   double* scal = nullptr;
   int32_t* err = nullptr;
@@ -605,6 +609,10 @@ template <typename R> FistaPass<R> fista_pass_args(ms_plan* p) {
   a.N = p->N;
   a.J = p->J;
   a.M = p->M;
+  a.coarse_ctas = p->coarse_ctas;
+  a.coarse_budget = p->coarse_budget;
+  a.coarse_groups = p->coarse_gr;
+  a.coarse_bar = p->coarse_bar;
   return a;
 }
 
@@ -735,6 +743,9 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
   ck(cudaMemcpyAsync(p->B[2], p->B[0], sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps),
      "copy");
   set_target_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->obj_target);
+  // the coarse levels' group barriers start at rest (a wait that ran out
+  // may have left a count behind)
+  ck(cudaMemsetAsync(p->coarse_bar, 0, sizeof(int) * 2 * kMaxBases, p->ps), "memset");
   const bool poll = rel_tol > 0 || std::isfinite(p->obj_target);
   // ||B_0||_1 enters the first objective through the analysis partials
   ck(cudaMemsetAsync(p->l1parts, 0, sizeof(double) * p->n_l1, p->ps), "memset");
@@ -1027,9 +1038,13 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   int32_t* counts = dalloc<int32_t>(p->ntiles + 1, "counts");
   int32_t* tstart = dalloc<int32_t>(p->ntiles + 2, "tstart");
   int32_t* nch = dalloc<int32_t>(p->ntiles + 1, "nchunks");
+  // sort key: tile, then the anchor cell inside the tile (2 log2 T bits)
+  int lg_t = 0;
+  while ((1 << lg_t) < p->T) ++lg_t;
   int bits = 0;
   while ((1u << bits) <= (unsigned)p->ntiles) ++bits;
-  bits = ((bits + 7) / 8) * 8;
+  bits = ((bits + 2 * lg_t + 7) / 8) * 8;
+  const uint32_t sentinel = (uint32_t)p->ntiles << (2 * lg_t);
   const uint8_t masks[3] = {4 | 1, 4 | 2, 4};
   p->ch.resize(d->nchan);
   for (int c = 0; c < d->nchan; ++c) {
@@ -1044,12 +1059,12 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
                     p->ntx, cell_all, frac_all, tile_id, member, s);
     for (int pt = 0; pt < 3; ++pt) {
       PartDev& pd = p->ch[c].part[pt];
-      launch_make_keys(tile_id, member, nvis, masks[pt], (uint32_t)p->ntiles, keys, vals, s);
+      launch_make_keys(tile_id, cell_all, member, nvis, masks[pt], lg_t, sentinel, keys, vals, s);
       uint32_t* k = keys;
       int32_t* v = vals;
       radix_sort(&k, &v, ktmp, vtmp, nvis, bits, hist, hcap, s);
       ck(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (p->ntiles + 1), s), "memset");
-      launch_count_tiles(k, nvis, counts, s);
+      launch_count_tiles(k, nvis, 2 * lg_t, counts, s);
       int32_t excluded = 0;
       ck(cudaMemcpyAsync(&excluded, counts + p->ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost,
                          s),
@@ -1112,6 +1127,10 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
   p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_warps(N, sizeof(C2<R>))), "partials");
   p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
+  p->coarse_ctas =
+      coarse_groups(WaveletGeom{N, p->J, p->M}, sizeof(R), &p->coarse_gr, &p->coarse_budget);
+  p->coarse_bar = p->alloc<int>(2 * kMaxBases, "coarse barrier");
+  ck(cudaMemset(p->coarse_bar, 0, sizeof(int) * 2 * kMaxBases), "memset");
   p->l1parts = p->alloc<double>(p->n_l1, "partials");
   p->tickets = p->alloc<int32_t>(16, "tickets");
   p->scal = p->alloc<double>(16, "scalars");

@@ -78,21 +78,31 @@ void launch_classify(const double* u, const double* v, const uint8_t* flags, int
                                                     tile, ntx, cell, frac, tile_id, member);
 }
 
+// Sort key of a row: its tile, then its anchor cell inside the tile (row v,
+// then column u), so that rows sharing an anchor are adjacent in plan order;
+// rows outside the partition get the sentinel (after every tile).
 __global__ void make_keys_kernel(const uint32_t* __restrict__ tile_id,
+                                 const uint32_t* __restrict__ cell,
                                  const uint8_t* __restrict__ member, int64_t n, uint8_t mask,
-                                 uint32_t sentinel, uint32_t* __restrict__ keys,
+                                 int log2_tile, uint32_t sentinel, uint32_t* __restrict__ keys,
                                  int32_t* __restrict__ vals) {
+  const uint32_t tmask = (1u << log2_tile) - 1u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    keys[i] = (member[i] & mask) == mask ? tile_id[i] : sentinel;
+    const uint32_t c = cell[i];
+    const uint32_t lu = (c & 0xffffu) & tmask, lv = (c >> 16) & tmask;
+    keys[i] = (member[i] & mask) == mask
+                  ? (tile_id[i] << (2 * log2_tile)) | (lv << log2_tile) | lu
+                  : sentinel;
     vals[i] = (int32_t)i;
   }
 }
 
-void launch_make_keys(const uint32_t* tile_id, const uint8_t* member, int64_t n, uint8_t mask,
-                      uint32_t sentinel, uint32_t* keys, int32_t* vals, cudaStream_t s) {
-  make_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(tile_id, member, n, mask, sentinel, keys,
-                                                     vals);
+void launch_make_keys(const uint32_t* tile_id, const uint32_t* cell, const uint8_t* member,
+                      int64_t n, uint8_t mask, int log2_tile, uint32_t sentinel, uint32_t* keys,
+                      int32_t* vals, cudaStream_t s) {
+  make_keys_kernel<<<grid_for(n, 256), 256, 0, s>>>(tile_id, cell, member, n, mask, log2_tile,
+                                                     sentinel, keys, vals);
 }
 
 // ---------------------------------------------------------------- radix sort
@@ -210,15 +220,16 @@ void radix_sort(uint32_t** keys, int32_t** vals, uint32_t* ktmp, int32_t* vtmp, 
   *vals = va;
 }
 
-__global__ void count_tiles_kernel(const uint32_t* __restrict__ keys, int64_t n,
+__global__ void count_tiles_kernel(const uint32_t* __restrict__ keys, int64_t n, int shift,
                                    int32_t* __restrict__ counts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&counts[keys[i]], 1);
+    atomicAdd(&counts[keys[i] >> shift], 1);
 }
 
-void launch_count_tiles(const uint32_t* keys, int64_t n, int32_t* counts, cudaStream_t s) {
-  if (n > 0) count_tiles_kernel<<<grid_for(n, 256), 256, 0, s>>>(keys, n, counts);
+void launch_count_tiles(const uint32_t* keys, int64_t n, int shift, int32_t* counts,
+                        cudaStream_t s) {
+  if (n > 0) count_tiles_kernel<<<grid_for(n, 256), 256, 0, s>>>(keys, n, shift, counts);
 }
 
 __global__ void chunks_kernel(const int32_t* __restrict__ counts, int ntiles, int chunk,

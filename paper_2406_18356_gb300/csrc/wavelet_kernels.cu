@@ -26,6 +26,7 @@
 // B_{k+1} = soft(alpha - g/theta, lambda/theta), so gradient coefficients
 // never reach global memory.
 
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1261,6 +1262,115 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
   }
 }
 
+#include "coarse_levels.cuh"
+
+namespace {
+template <typename R>
+size_t coarse_smem(bool analysis, WaveletGeom g, const CoarseGroups& gr, int budget) {
+  int cs_min = 1 << 30;
+  for (int m = 0; m < g.M; ++m) cs_min = std::min(cs_min, gr.first[m + 1] - gr.first[m]);
+  return strip_smem_bytes(analysis, g.N, g.J, cs_min, sizeof(R), (size_t)budget);
+}
+
+// l1 partial slots of level 1 (the per-tile kernel's share) and in all
+int level1_partials(WaveletGeom g) {
+  const int h = g.N >> 1, TO = ana_tile(h);
+  return (h / TO) * (h / TO) * g.M;
+}
+
+template <typename R>
+cudaError_t launch_coarse(const FistaPass<R>& a, bool analysis, int part_base, int part_end,
+                          cudaStream_t s) {
+  const WaveletGeom g{a.N, a.J, a.M};
+  const size_t smem = coarse_smem<R>(analysis, g, a.coarse_groups, a.coarse_budget);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.coarse_ctas);
+  cfg.blockDim = dim3(kStripThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every group resident at once
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (analysis) {
+    auto kern = coarse_analysis_kernel<R>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaLaunchKernelEx(&cfg, kern, a, a.coarse_groups, a.coarse_bar, part_base, part_end,
+                              a.coarse_budget);
+  }
+  auto kern = coarse_synthesis_kernel<R>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaLaunchKernelEx(&cfg, kern, a, a.coarse_groups, a.coarse_bar, a.coarse_budget);
+}
+
+// CTAs of both strip kernels resident per SM with `budget` bytes of shared
+// memory per CTA
+template <typename R> int coarse_per_sm(WaveletGeom g, const CoarseGroups& gr, int budget) {
+  int per = 1 << 30;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  for (int an = 0; an < 2; ++an) {
+    const size_t smem = coarse_smem<R>(an != 0, g, gr, budget);
+    if (smem == 0 || smem > (size_t)optin) return 0;   // strips too wide for shared memory
+    int blocks = 0;
+    cudaError_t e;
+    if (an) {
+      auto kern = coarse_analysis_kernel<R>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripThreads, smem);
+    } else {
+      auto kern = coarse_synthesis_kernel<R>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, kStripThreads, smem);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();   // clear: "does not fit" is an answer here, not an error
+      return 0;
+    }
+    per = std::min(per, blocks);
+  }
+  return per;
+}
+}  // namespace
+
+int coarse_groups(WaveletGeom g, size_t rsz, CoarseGroups* gr, int* budget) {
+#ifdef MS_NO_COARSE_GROUPS
+  return 0;
+#endif
+  const bool pow2 = g.N > 0 && (g.N & (g.N - 1)) == 0;
+  if (!pow2 || g.N < 256 || g.J < 2 || (g.N >> g.J) < 8 || g.M < 1) return 0;
+  int dev = 0, coop = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+    return 0;
+  const int span = analysis_prox_partials(g) - level1_partials(g);
+  // one CTA per SM; group m gets CTAs in proportion to its work per row:
+  // the filters' 2 (m + 1) taps plus a share that does not grow with them
+  // (staging, stores, the prox), measured at about 4 taps' worth
+  auto weight = [](int m) { return m + 1 + 2; };
+  int total_w = 0;
+  for (int m = 0; m < g.M; ++m) total_w += weight(m);
+  const int ctas = std::min(sm_count(), span);   // one l1 partial per CTA in the coarse share
+  if (ctas < g.M) return 0;
+  gr->first[0] = 0;
+  for (int m = 0; m < g.M; ++m)
+    gr->first[m + 1] = gr->first[m] + std::max(1, ctas * weight(m) / total_w);
+  for (int m = g.M + 1; m <= kMaxBases; ++m) gr->first[m] = gr->first[g.M];
+  const int used = gr->first[g.M];
+  if (used > ctas) return 0;
+  for (int b : {200 * 1024, 160 * 1024}) {
+    const int per = rsz == 4 ? coarse_per_sm<float>(g, *gr, b) : coarse_per_sm<double>(g, *gr, b);
+    if (per >= 1 && per * sm_count() >= used) {
+      *budget = b;
+      return used;
+    }
+  }
+  return 0;
+}
+
 int analysis_prox_partials(WaveletGeom g) {
   int total = 0;
   for (int j = 1; j <= g.J; ++j) {
@@ -1302,6 +1412,8 @@ void analysis_window_box(unsigned* cols, unsigned* rows) {
 
 template <typename R>
 cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int only_level) {
+  if (only_level < 0 && a.coarse_ctas > 0)   // levels J..2 as one cooperative launch
+    return launch_coarse<R>(a, false, 0, 0, s);
   for (int j = a.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
     if (only_level < 0 && j == 1) continue;
@@ -1326,6 +1438,10 @@ template <typename R>
 cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_map,
                                  cudaStream_t s, int only_level) {
   const CUtensorMap m = grad_map ? *grad_map : CUtensorMap{};
+  if (only_level < 0 && a.coarse_ctas > 0) {   // levels 2..J as one cooperative launch
+    const WaveletGeom g{a.N, a.J, a.M};
+    return launch_coarse<R>(a, true, level1_partials(g), analysis_prox_partials(g), s);
+  }
   int part_base = 0;
   for (int j = 1; j <= a.J; ++j) {
     const int h = a.N >> j, TO = ana_tile(h);

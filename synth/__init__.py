@@ -291,6 +291,22 @@ def c1_style(npix: int, seed: int, device: str = "cpu") -> Workload:
         0.25, 3.0, 1.28e9, seed, device)
 
 
+def paper_like(npix: int, seed: int = 0, split_frac: float = 0.205, delta_px: float = 3.0,
+               device: str = "cpu") -> Workload:
+    """The paper's simulation setting in kind (Sect. 4.1: 64 dishes, 4 h at
+    120 s, one channel; 2016 baselines x 120 dumps = 241,920 rows), with a
+    MeerKAT-like log-radial layout (29 m .. 8 km) in place of the array file
+    the paper uses, and a random sky of points and blobs scaled with the
+    image area (50 + 6 at 512 pixels).  The paper's partition centres 20, 35,
+    55 px of its 512-pixel images are 0.117, 0.205, 0.322 of the longest
+    baseline's radius (N/3 pixels here)."""
+    area = (npix / 512.0) ** 2
+    return _single_channel(
+        f"paper-like-{npix}px-seed{seed}", 64, lambda r: layout_log_radial(64, 29.0, 8000.0, r),
+        120, 4.0, npix, max(1, int(round(50 * area))), max(1, int(round(6 * area))),
+        split_frac, delta_px, 1.28e9, seed, device)
+
+
 def tiny(npix: int = 32, n_ant: int = 8, n_dumps: int = 6, seed: int = 1,
          device: str = "cpu", split_frac: float = 0.3, delta_px: float = 1.5,
          n_points: int = 4, n_blobs: int = 1) -> Workload:

@@ -64,7 +64,8 @@ CASES = {
 @pytest.mark.parametrize("case", list(CASES))
 def test_partition_rows_match_oracle(ms, case):
     """Bit-exact: every partition holds exactly the oracle's rows; the plan
-    order is by tile, rows in original order inside a tile."""
+    order is by tile, then by anchor cell inside the tile (row, column), rows
+    sharing an anchor in original order."""
     w = CASES[case]()
     plan = _plan(ms, w)
     in_l, in_h = og.partition(w.u[0], w.v[0], w.npix, w.pixel_size, w.ell_px, w.delta_px)
@@ -74,13 +75,14 @@ def test_partition_rows_match_oracle(ms, case):
     Ng = 2 * w.npix
     T = 32 if Ng % 32 == 0 else 16
     A = og.GriddedOperator(w.u[0], w.v[0], w.npix, w.pixel_size)
-    tu = ((A.c0u + Ng // 2) % Ng) // T
-    tv = ((A.c0v + Ng // 2) % Ng) // T
-    tile = tv * (Ng // T) + tu
+    cu = (A.c0u + Ng // 2) % Ng
+    cv = (A.c0v + Ng // 2) % Ng
+    tile = (cv // T) * (Ng // T) + cu // T
+    anchor = (tile.astype(np.int64) * T + cv % T) * T + cu % T
     for part, mask in (("L", in_l), ("H", in_h), ("ALL", np.ones_like(in_l))):
         rows = plan.partition_rows(part)
         np.testing.assert_array_equal(np.sort(rows), np.flatnonzero(mask))
-        key = tile[rows].astype(np.int64) * (1 << 32) + rows
+        key = anchor[rows] * (1 << 32) + rows
         assert np.all(np.diff(key) > 0)
     plan.close()
 
