@@ -165,55 +165,63 @@ __device__ __forceinline__ void strip_analysis_level(
       const int r = u % rc, rest = u / rc;
       const int seg = rest % segs, src = rest / segs;
       const R* yrow = (src ? yhi : ylo) + r * YS + 2 * kP * seg;
+      const int gi = c0 + r, u0 = kP * seg;
+      // src 0: approximation (a) and low-y/high-x (d); src 1: high-y/low-x
+      // (a) and high/high (d).  The prox operands B_k, B_k-1 of d are
+      // loaded before the filter runs, so their latency hides behind it.
+      const bool a_prox = src == 1 || last;
+      const int64_t off_a = src ? plane + (int64_t)(h + gi) * N + u0 : plane + (int64_t)gi * N + u0;
+      const int64_t off_d = off_a + h;
+      using Vt = typename Vec<R>::T;
+      constexpr int NV = Vec<R>::N;
+      Vt ca[kP / NV], pa[kP / NV], cd[kP / NV], pd[kP / NV];
+#pragma unroll
+      for (int q = 0; q < kP / NV; ++q) {
+        cd[q] = *reinterpret_cast<const Vt*>(cur + off_d + q * NV);
+        pd[q] = *reinterpret_cast<const Vt*>(prev + off_d + q * NV);
+      }
       R xin[NI];
 #pragma unroll
       for (int i = 0; i < NI; ++i) xin[i] = yrow[i];
       R a[kP], d[kP];
       fir_down8<R, MB>(xin, a, d);
-      const int gi = c0 + r, u0 = kP * seg;
-      // src 0: approximation (a) and low-y/high-x (d); src 1: high-y/low-x
-      // (a) and high/high (d)
-      using Vt = typename Vec<R>::T;
-      constexpr int NV = Vec<R>::N;
-      auto prox8 = [&](const R* g8, int64_t off) {
+      auto prox8 = [&](const R* g8, const Vt* cv, const Vt* pv, int64_t off) {
 #pragma unroll
-        for (int q0 = 0; q0 < kP; q0 += NV) {
-          const Vt cv = *reinterpret_cast<const Vt*>(cur + off + q0);
-          const Vt pv = *reinterpret_cast<const Vt*>(prev + off + q0);
-          const R* cp = reinterpret_cast<const R*>(&cv);
-          const R* pp = reinterpret_cast<const R*>(&pv);
+        for (int q = 0; q < kP / NV; ++q) {
+          const R* cp = reinterpret_cast<const R*>(&cv[q]);
+          const R* pp = reinterpret_cast<const R*>(&pv[q]);
           Vt nv;
           R* np = reinterpret_cast<R*>(&nv);
 #pragma unroll
           for (int e = 0; e < NV; ++e) {
             const R alpha = cp[e] + t * (cp[e] - pp[e]);
-            const R z = alpha - mu * g8[q0 + e];
+            const R z = alpha - mu * g8[q * NV + e];
             const R az = fabs(z) - thr;
             const R nb = az > (R)0 ? copysign(az, z) : (R)0;
             l1.add(fabs(nb));
             np[e] = nb;
           }
-          *reinterpret_cast<Vt*>(next + off + q0) = nv;
+          *reinterpret_cast<Vt*>(next + off + q * NV) = nv;
         }
       };
-      if (src == 0) {
-        if (last) {
-          prox8(a, plane + (int64_t)gi * N + u0);
-        } else {
+      if (a_prox) {
 #pragma unroll
-          for (int q0 = 0; q0 < kP; q0 += NV) {
-            Vt v;
-            R* vp = reinterpret_cast<R*>(&v);
-#pragma unroll
-            for (int e = 0; e < NV; ++e) vp[e] = a[q0 + e];
-            *reinterpret_cast<Vt*>(ll_out + (size_t)gi * h + u0 + q0) = v;
-          }
+        for (int q = 0; q < kP / NV; ++q) {
+          ca[q] = *reinterpret_cast<const Vt*>(cur + off_a + q * NV);
+          pa[q] = *reinterpret_cast<const Vt*>(prev + off_a + q * NV);
         }
-        prox8(d, plane + (int64_t)gi * N + h + u0);
+        prox8(a, ca, pa, off_a);
       } else {
-        prox8(a, plane + (int64_t)(h + gi) * N + u0);
-        prox8(d, plane + (int64_t)(h + gi) * N + h + u0);
+#pragma unroll
+        for (int q0 = 0; q0 < kP; q0 += NV) {
+          Vt v;
+          R* vp = reinterpret_cast<R*>(&v);
+#pragma unroll
+          for (int e = 0; e < NV; ++e) vp[e] = a[q0 + e];
+          *reinterpret_cast<Vt*>(ll_out + (size_t)gi * h + u0 + q0) = v;
+        }
       }
+      prox8(d, cd, pd, off_d);
     }
     __syncthreads();   // the chunk's buffers are reused
   }
@@ -316,6 +324,20 @@ __device__ __forceinline__ void strip_synthesis_level(const R* __restrict__ ap, 
   }
 }
 
+#ifdef MS_COARSE_PROBE
+// per-CTA timestamps of the coarse kernels (timing experiments only)
+__device__ unsigned long long g_coarse_probe[2][512][8];
+__device__ __forceinline__ void probe(int kind, int slot) {
+  if (threadIdx.x == 0 && blockIdx.x < 512) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    g_coarse_probe[kind][blockIdx.x][slot] = t;
+  }
+}
+#else
+__device__ __forceinline__ void probe(int, int) {}
+#endif
+
 // the CTA's basis and its rank in the basis's group
 __device__ __forceinline__ void group_of(const CoarseGroups& gr, int M, int& m, int& rank,
                                          int& cs) {
@@ -353,6 +375,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
   const int64_t half = (int64_t)a.M * (N / 2) * (N / 2);
   const int64_t region = (int64_t)m * (N / 2) * (N / 2);
   const R* plane = coef + (int64_t)m * N * N;
+  probe(0, 0);
   for (int j = J; j >= 2; --j) {
     const int h = N >> j, n = 2 * h;
     const R* ap = (j == J) ? plane : a.tmp + ((j + 1) & 1) * half + region;
@@ -367,7 +390,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
       MS_SS(0) MS_SS(1) MS_SS(2) MS_SS(3) MS_SS(4) MS_SS(5) MS_SS(6) MS_SS(7)
 #undef MS_SS
     }
+    probe(0, 1 + 2 * (J - j));
     if (j > 2) group_barrier(bar + 2 * m, cs, a.ctl);   // LL_{j-1} complete for level j - 1
+    probe(0, 2 + 2 * (J - j));
   }
 }
 
@@ -398,6 +423,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
   const int64_t region = (int64_t)m * (N / 2) * (N / 2);
   const int64_t plane = (int64_t)m * N * N;
   KSum<R> l1;
+  probe(1, 0);
   for (int j = 2; j <= J; ++j) {
     const int n = N >> (j - 1), h = n / 2;
     const R* in = a.tmp + ((j - 1) & 1) * half + region;
@@ -414,7 +440,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
       MS_SA(0) MS_SA(1) MS_SA(2) MS_SA(3) MS_SA(4) MS_SA(5) MS_SA(6) MS_SA(7)
 #undef MS_SA
     }
+    probe(1, 1 + 2 * (j - 2));
     if (j < J) group_barrier(bar + 2 * m, cs, a.ctl);   // LL_j complete for level j + 1
+    probe(1, 2 + 2 * (j - 2));
   }
   // block sum of |B_{k+1}| (working-precision pairs within a warp, FP64 once
   // per warp), in a fixed order

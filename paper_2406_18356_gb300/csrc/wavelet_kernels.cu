@@ -1264,6 +1264,18 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
 
 #include "coarse_levels.cuh"
 
+// CTAs per SM of the one-launch coarse levels and their shared-memory
+// budget per CTA (compile-time tunables; the defaults are the measured best)
+#ifndef MS_COARSE_CTAS_PER_SM
+#define MS_COARSE_CTAS_PER_SM 1
+#endif
+#ifndef MS_COARSE_BUDGET_KB
+#define MS_COARSE_BUDGET_KB 200
+#endif
+#ifndef MS_COARSE_WOFF
+#define MS_COARSE_WOFF 24   // fixed share of a basis's work per row, in taps / 2 (measured best)
+#endif
+
 namespace {
 template <typename R>
 size_t coarse_smem(bool analysis, WaveletGeom g, const CoarseGroups& gr, int budget) {
@@ -1350,10 +1362,11 @@ int coarse_groups(WaveletGeom g, size_t rsz, CoarseGroups* gr, int* budget) {
   // one CTA per SM; group m gets CTAs in proportion to its work per row:
   // the filters' 2 (m + 1) taps plus a share that does not grow with them
   // (staging, stores, the prox), measured at about 4 taps' worth
-  auto weight = [](int m) { return m + 1 + 2; };
+  auto weight = [](int m) { return m + 1 + MS_COARSE_WOFF; };
   int total_w = 0;
   for (int m = 0; m < g.M; ++m) total_w += weight(m);
-  const int ctas = std::min(sm_count(), span);   // one l1 partial per CTA in the coarse share
+  // one l1 partial per CTA in the coarse share
+  const int ctas = std::min(MS_COARSE_CTAS_PER_SM * sm_count(), span);
   if (ctas < g.M) return 0;
   gr->first[0] = 0;
   for (int m = 0; m < g.M; ++m)
@@ -1361,7 +1374,7 @@ int coarse_groups(WaveletGeom g, size_t rsz, CoarseGroups* gr, int* budget) {
   for (int m = g.M + 1; m <= kMaxBases; ++m) gr->first[m] = gr->first[g.M];
   const int used = gr->first[g.M];
   if (used > ctas) return 0;
-  for (int b : {200 * 1024, 160 * 1024}) {
+  for (int b : {MS_COARSE_BUDGET_KB * 1024, MS_COARSE_BUDGET_KB * 1024 * 4 / 5}) {
     const int per = rsz == 4 ? coarse_per_sm<float>(g, *gr, b) : coarse_per_sm<double>(g, *gr, b);
     if (per >= 1 && per * sm_count() >= used) {
       *budget = b;
@@ -1370,6 +1383,14 @@ int coarse_groups(WaveletGeom g, size_t rsz, CoarseGroups* gr, int* budget) {
   }
   return 0;
 }
+
+#ifdef MS_COARSE_PROBE
+}  // namespace ms
+extern "C" int ms_coarse_probe_read(unsigned long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, ms::g_coarse_probe, sizeof(ms::g_coarse_probe));
+}
+namespace ms {
+#endif
 
 int analysis_prox_partials(WaveletGeom g) {
   int total = 0;
