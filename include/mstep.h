@@ -49,6 +49,15 @@ typedef enum {
 
 typedef enum { MS_FP64 = 0, MS_FP32 = 1, MS_FP32_KAHAN = 2 } ms_precision;
 
+/* Minor-cycle dictionaries (App. A.1).  DAUBECHIES: W = [Psi_1 .. Psi_M],
+ * the periodized orthonormal 2-D db1..dbM transforms (W W^H = M I, step size
+ * 2 M max K^ in closed form, Sect. 3.4).  IUWT: W = T^H, T the isotropic
+ * undecimated "a trous" B3-spline transform with J levels (J + 1 planes
+ * [w_1 .. w_J, c_J], T^H T not a multiple of I), step size by power
+ * iteration (Sect. 3.4): 100 iterations in FP64 reductions from a fixed
+ * pseudo-random start, once per minor-cycle problem. */
+typedef enum { MS_DICT_DAUBECHIES = 0, MS_DICT_IUWT = 1 } ms_dictionary;
+
 /* Baseline partitions of Sect. 3.1: L = {r <= ell + delta} (short baselines),
  * H = {r >= ell - delta} (long baselines), ALL = every unflagged row. */
 typedef enum { MS_PART_L = 0, MS_PART_H = 1, MS_PART_ALL = 2 } ms_part;
@@ -83,6 +92,7 @@ typedef struct {
   int32_t tile;           /* gridding tile side: 0 = default, or 16 / 32      */
   int32_t chunk;          /* visibilities per work item: 0 = automatic          */
   int32_t device;         /* CUDA device ordinal                                */
+  int32_t dictionary;     /* ms_dictionary; MS_DICT_IUWT ignores n_bases        */
 } ms_plan_desc;
 
 typedef struct {

@@ -27,6 +27,8 @@ MS_STEP_LOW, MS_STEP_FULL, MS_STEP_SINGLE = 0, 1, 2
 MS_LAMBDA_NORM2_2N, MS_LAMBDA_MAX_FIXED = 0, 1
 
 PRECISIONS = {"fp64": MS_FP64, "fp32": MS_FP32, "fp32_kahan": MS_FP32_KAHAN}
+MS_DICT_DAUBECHIES, MS_DICT_IUWT = 0, 1
+DICTIONARIES = {"daubechies": MS_DICT_DAUBECHIES, "iuwt": MS_DICT_IUWT}
 PARTS = {"L": MS_PART_L, "H": MS_PART_H, "ALL": MS_PART_ALL}
 STEPS = {"low": MS_STEP_LOW, "full": MS_STEP_FULL, "single": MS_STEP_SINGLE}
 
@@ -45,7 +47,8 @@ class ms_plan_desc(ctypes.Structure):
                 ("oversample", ctypes.c_int32), ("es_beta", ctypes.c_double),
                 ("levels", ctypes.c_int32), ("n_bases", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("chunk", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("dictionary", ctypes.c_int32)]
 
 
 class ms_stats(ctypes.Structure):
@@ -214,7 +217,8 @@ class Plan:
     def __init__(self, u, v, npix: int, pixel_size: float, ell_px: float, delta_px: float,
                  flags=None, precision: str = "fp64", levels: int = 4, n_bases: int = 8,
                  kernel_width: int = 7, oversample: int = 2, es_beta: float = 0.0,
-                 tile: int = 0, chunk: int = 0, device: int = 0):
+                 tile: int = 0, chunk: int = 0, device: int = 0,
+                 dictionary: str = "daubechies"):
         lib = load_library()
         u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)))
         v = np.ascontiguousarray(np.atleast_2d(np.asarray(v, dtype=np.float64)))
@@ -229,12 +233,15 @@ class Plan:
         self.npix = int(npix)
         self.precision = precision
         self.prec = PRECISIONS[precision]
-        self.levels, self.n_bases = levels, n_bases
+        self.dictionary = dictionary
+        # coefficient planes: M Daubechies bases, or J + 1 IUWT planes
+        self.levels = levels
+        self.n_bases = levels + 1 if dictionary == "iuwt" else n_bases
         self.device = device
         d = ms_plan_desc(u.ctypes.data, v.ctypes.data, fl.ctypes.data if fl is not None else None,
                          self.nvis, self.nchan, self.npix, pixel_size, ell_px, delta_px,
                          kernel_width, oversample, es_beta, levels, n_bases, self.prec, tile,
-                         chunk, device)
+                         chunk, device, DICTIONARIES[dictionary])
         h = _P()
         st = lib.ms_plan_create(ctypes.byref(d), ctypes.byref(h))
         if st != MS_OK:

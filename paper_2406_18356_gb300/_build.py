@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmstep.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["plan_kernels.cu", "grid_kernels.cu", "wavelet_kernels.cu",
-           "spectral_kernels.cu", "mstep.cu", "unet.cu"]
+           "spectral_kernels.cu", "iuwt_kernels.cu", "mstep.cu", "unet.cu"]
 
 
 def _nvcc() -> str:

@@ -317,6 +317,18 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
                                  cudaStream_t s, int only_level = 0);
 int analysis_prox_partials(WaveletGeom g);
 void analysis_window_box(unsigned* cols, unsigned* rows);
+
+// iuwt_kernels.cu: the IUWT dictionary W = T^H (J levels, J + 1 planes).
+// fp = NULL: plain transforms of alpha / img; fp = the minor cycle's pass:
+// synthesis of B_k into x, analysis of the gradient image into FISTA's step
+// on B_k+1 (iuwt_prox_partials(J) l1 partials).  work: 3 N x N images.
+template <typename R>
+cudaError_t launch_iuwt_synthesis(const FistaPass<R>* fp, const R* alpha, R* x, R* work, int N,
+                                  int J, cudaStream_t s);
+template <typename R>
+cudaError_t launch_iuwt_analysis(const FistaPass<R>* fp, const R* img, R* alpha, R* work, int N,
+                                 int J, cudaStream_t s);
+int iuwt_prox_partials(int J);
 // The one-launch coarse levels (2..J of both transforms, one cooperative
 // launch per transform) on the current device: the CTAs of each basis's
 // group (in proportion to its filter length) and the shared-memory budget

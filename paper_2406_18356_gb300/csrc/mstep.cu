@@ -184,6 +184,19 @@ __global__ void set_eta_kernel(FistaCtl* ctl, double eta2) { ctl->eta2 = eta2; }
 
 __global__ void set_target_kernel(FistaCtl* ctl, double target) { ctl->F_target = target; }
 
+__global__ void scale_scalar_kernel(const double* in, double a, double* out) { *out = a * *in; }
+
+// step size from a device value (the IUWT's power iteration)
+__global__ void set_theta_kernel(FistaCtl* ctl, const double* theta) {
+  const double th = *theta;
+  if (!(th > 0.0) || !isfinite(th)) {
+    ctl->error = 4;
+    return;
+  }
+  ctl->theta = th;
+  ctl->inv_theta = 1.0 / th;
+}
+
 // Network input of the learned warm start: [i^_L, i~_H1] / max|i~_H1|,
 // channels last (FP32 [n][2]); the peak comes from launch_image_norms.
 template <typename R>
@@ -266,6 +279,7 @@ struct ms_plan {
   double* parts = nullptr;     // reduction partials (one reduction at a time)
   double* l1parts = nullptr;   // per-block |B_k+1| partials of the analysis levels
   int n_l1 = 0;                // their number
+  int dict = MS_DICT_DAUBECHIES;   // minor-cycle dictionary
   int coarse_ctas = 0;         // CTAs of the one-launch coarse levels (0: one launch per level)
   int coarse_budget = 0;       // their shared-memory budget per CTA
   CoarseGroups coarse_gr{};    // their split over the bases
@@ -624,11 +638,15 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
   C2<R>* Fk = (C2<R>*)p->F[parity];
   C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
   const FistaPass<R> a = fista_pass_args<R>(p);
-  if (p->J > 1) {
-    KSpan k(p, MS_K_SYNTH);
-    ck(launch_synthesis_pass<R>(a, p->ps, -1), "synthesis");
-  }
-  {
+  if (p->dict == MS_DICT_IUWT) {
+    KSpan k(p, MS_K_SYNTH_L1);
+    ck(launch_iuwt_synthesis<R>(&a, nullptr, a.x, (R*)p->wtmp, p->N, p->J, p->ps),
+       "IUWT synthesis");
+  } else {
+    if (p->J > 1) {
+      KSpan k(p, MS_K_SYNTH);
+      ck(launch_synthesis_pass<R>(a, p->ps, -1), "synthesis");
+    }
     KSpan k(p, MS_K_SYNTH_L1);
     ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
   }
@@ -668,6 +686,13 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
       fft_c2r<R>(p, Fo, p->ywork);   // gradient image 2 (K W alpha_k - b)
     }
   }
+  if (p->dict == MS_DICT_IUWT) {
+    KSpan k(p, MS_K_ANALYSIS_L1);
+    ck(launch_iuwt_analysis<R>(&a, (const R*)p->ywork, nullptr, (R*)p->wtmp, p->N, p->J,
+                               p->ps),
+       "IUWT analysis");
+    return;
+  }
   const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
   {
     KSpan k(p, MS_K_ANALYSIS_L1);
@@ -697,6 +722,52 @@ template <typename R> void ensure_fista_graph(ms_plan* p) {
   cudaGraphDestroy(graph);
 }
 
+// ------------------------------------------------------------- dictionary
+constexpr int kIuwtPowerIterations = 100;   // power iterations of the IUWT step size
+
+// x = W alpha and alpha = W^H x with the plan's dictionary (plain calls)
+template <typename R> void dict_synthesis(ms_plan* p, const R* alpha, R* x) {
+  if (p->dict == MS_DICT_IUWT) {
+    ck(launch_iuwt_synthesis<R>(nullptr, alpha, x, (R*)p->wtmp, p->N, p->J, p->ps),
+       "IUWT synthesis");
+    return;
+  }
+  set_ptrs_kernel<<<1, 1, 0, p->ps>>>(p->api3_dev, (void*)alpha, (void*)alpha, (void*)alpha);
+  launch_synthesis3<R>((const R* const*)p->api3_dev, x, (R*)p->wtmp,
+                       WaveletGeom{p->N, p->J, p->M}, nullptr, p->ps);
+}
+template <typename R> void dict_analysis(ms_plan* p, const R* x, R* alpha) {
+  if (p->dict == MS_DICT_IUWT) {
+    ck(launch_iuwt_analysis<R>(nullptr, x, alpha, (R*)p->wtmp, p->N, p->J, p->ps),
+       "IUWT analysis");
+    return;
+  }
+  launch_analysis<R>(x, alpha, (R*)p->wtmp, WaveletGeom{p->N, p->J, p->M}, p->ps);
+}
+
+// 2 lambda_max(W^H K W) by power iteration (Sect. 3.4) into p->scal[2]
+// (device), from the plan's K^: Rayleigh quotient of the normalized
+// iterate, reductions in FP64.  Uses B[0], B[1] and the work images.
+template <typename R> void power_theta(ms_plan* p, int iters) {
+  const int64_t ncoef = (int64_t)p->M * p->N * p->N;
+  R* v = (R*)p->B[0];
+  R* w = (R*)p->B[1];
+  double* sc = p->scal;
+  launch_hash_fill<R>(v, ncoef, 12345, p->ps);
+  for (int it = 0; it < iters; ++it) {
+    launch_dot<R>(v, v, ncoef, p->parts, sc + 0, p->tickets + 7, p->ps);
+    launch_normalize<R>(v, ncoef, sc + 0, p->ps);
+    dict_synthesis<R>(p, v, (R*)p->xwork);
+    fft_r2c<R>(p, p->xwork, p->spec);
+    launch_spec_apply<R>((C2<R>*)p->spec, (const R*)p->Ks, p->N, p->ps);
+    fft_c2r<R>(p, p->spec, p->ywork);
+    dict_analysis<R>(p, (const R*)p->ywork, w);
+    launch_dot<R>(v, w, ncoef, p->parts, sc + 1, p->tickets + 8, p->ps);
+    ck(cudaMemcpyAsync(v, w, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps), "copy");
+  }
+  scale_scalar_kernel<<<1, 1, 0, p->ps>>>(sc + 1, 2.0, sc + 2);
+}
+
 // Prepare K^, theta (once per step and channel) into the plan buffers.
 // step: LOW/SINGLE use the partition PSF only; FULL adds the filters built
 // from ctl->sigma2, ctl->eta2.
@@ -711,6 +782,11 @@ template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, doubl
   } else {
     launch_normal_spectrum<R>((const R*)pd.Hhat, nullptr, nullptr, p->N, p->M, (R*)p->Ks,
                               p->parts, p->ctl, p->tickets + 2, p->ps);
+  }
+  if (p->dict == MS_DICT_IUWT) {
+    // no closed form (T^H T is not a multiple of I): power iteration
+    power_theta<R>(p, kIuwtPowerIterations);
+    set_theta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->scal + 2);
   }
 }
 
@@ -815,6 +891,8 @@ template <typename R>
 void warm_start_beta(ms_plan* p, ms_unet* net, const void* low, const void* res, void* beta,
                      void* x0_out) {
   arg(net != nullptr, "warm start network is NULL");
+  arg(p->dict == MS_DICT_DAUBECHIES,
+      "the warm start's coefficients W^H x0 / M need the Daubechies dictionary (W W^H = M I)");
   arg(ms_unet_device_of(net) == p->dev, "the warm start network lives on another device");
   const int N = p->N;
   const int64_t n2 = (int64_t)N * N;
@@ -990,7 +1068,7 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   const int64_t nvis = d->nvis;
   cudaStream_t s = p->ps;
   // Daubechies filters
-  {
+  if (p->dict == MS_DICT_DAUBECHIES) {
     std::vector<double> h(kMaxBases * kMaxTaps, 0.0);
     std::vector<int> len(kMaxBases, 0);
     for (int m = 0; m < p->M; ++m) {
@@ -1122,13 +1200,18 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   p->Ks = p->alloc<R>(nspec, "spectrum");
   p->gl2 = p->alloc<R>(nspec, "filter");
   p->gh2 = p->alloc<R>(nspec, "filter");
-  p->wtmp = p->alloc<R>(ncoef, "wavelet tmp");   // two LL buffers of M (N/2)^2
+  // two LL buffers of M (N/2)^2 (Daubechies), or three work images (IUWT)
+  p->wtmp = p->alloc<R>(std::max<int64_t>(ncoef, 3 * n2), "wavelet tmp");
   p->api3_dev = p->alloc<void*>(3, "ptrs");
   p->ctl = p->alloc<FistaCtl>(1, "ctl");
   p->parts = p->alloc<double>(std::max(4096, 3 * spec_col_warps(N, sizeof(C2<R>))), "partials");
-  p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
-  p->coarse_ctas =
-      coarse_groups(WaveletGeom{N, p->J, p->M}, sizeof(R), &p->coarse_gr, &p->coarse_budget);
+  if (p->dict == MS_DICT_IUWT) {
+    p->n_l1 = iuwt_prox_partials(p->J);
+  } else {
+    p->n_l1 = analysis_prox_partials(WaveletGeom{N, p->J, p->M});
+    p->coarse_ctas =
+        coarse_groups(WaveletGeom{N, p->J, p->M}, sizeof(R), &p->coarse_gr, &p->coarse_budget);
+  }
   p->coarse_bar = p->alloc<int>(2 * kMaxBases, "coarse barrier");
   ck(cudaMemset(p->coarse_bar, 0, sizeof(int) * 2 * kMaxBases), "memset");
   p->l1parts = p->alloc<double>(p->n_l1, "partials");
@@ -1223,25 +1306,8 @@ void lipschitz(ms_plan* p, int step, int chan, double sigma2, double eta2, int p
   if (closed) *closed = h.theta;
   if (power) *power = 0.0;
   if (power_iters <= 0) return;
-  const int64_t ncoef = (int64_t)p->M * p->N * p->N;
-  WaveletGeom g{p->N, p->J, p->M};
-  R* v = (R*)p->B[0];
-  R* w = (R*)p->B[1];
-  launch_hash_fill<R>(v, ncoef, 12345, p->ps);
-  set_ptrs_kernel<<<1, 1, 0, p->ps>>>(p->api3_dev, v, v, v);
+  power_theta<R>(p, power_iters);
   double* sc = p->scal;
-  for (int it = 0; it < power_iters; ++it) {
-    launch_dot<R>(v, v, ncoef, p->parts, sc + 0, p->tickets + 7, p->ps);
-    launch_normalize<R>(v, ncoef, sc + 0, p->ps);
-    launch_synthesis3<R>((const R* const*)p->api3_dev, (R*)p->xwork, (R*)p->wtmp, g, nullptr,
-                         p->ps);
-    fft_r2c<R>(p, p->xwork, p->spec);
-    launch_spec_apply<R>((C2<R>*)p->spec, (const R*)p->Ks, p->N, p->ps);
-    fft_c2r<R>(p, p->spec, p->ywork);
-    launch_analysis<R>((const R*)p->ywork, w, (R*)p->wtmp, g, p->ps);
-    launch_dot<R>(v, w, ncoef, p->parts, sc + 1, p->tickets + 8, p->ps);
-    ck(cudaMemcpyAsync(v, w, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps), "copy");
-  }
   double rho = 0;
   ck(cudaMemcpyAsync(&rho, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, p->ps), "copy");
   ck(cudaStreamSynchronize(p->ps), "synchronize");
@@ -1584,7 +1650,10 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     arg(d->nchan >= 1, "nchan must be >= 1");
     arg(d->kernel_width == 7, "only kernel_width = 7 is supported");
     arg(d->oversample == 2, "only oversample = 2 is supported");
-    arg(d->n_bases >= 1 && d->n_bases <= kMaxBases, "n_bases must be 1..8");
+    arg(d->dictionary == MS_DICT_DAUBECHIES || d->dictionary == MS_DICT_IUWT,
+        "unknown dictionary");
+    arg(d->dictionary == MS_DICT_IUWT || (d->n_bases >= 1 && d->n_bases <= kMaxBases),
+        "n_bases must be 1..8");
     arg(d->levels >= 1 && d->levels <= kMaxLevels, "levels must be 1..8");
     arg(d->npix >= 16 && d->npix % 16 == 0 && d->npix <= 16384, "npix must be a multiple of 16");
     arg(d->npix % (1 << d->levels) == 0 && (d->npix >> d->levels) >= 1,
@@ -1607,7 +1676,8 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     p->ntx = p->Ng / p->T;
     p->ntiles = p->ntx * p->ntx;
     p->J = d->levels;
-    p->M = d->n_bases;
+    p->dict = d->dictionary;
+    p->M = p->dict == MS_DICT_IUWT ? d->levels + 1 : d->n_bases;   // coefficient planes
     p->prec = d->precision;
     p->rsz = p->prec == MS_FP64 ? 8 : 4;
     p->beta = d->es_beta > 0 ? d->es_beta : 2.30 * kW;
@@ -1730,11 +1800,7 @@ ms_status ms_dictionary_synthesis(ms_plan* p, const void* alpha, void* x, void* 
   return guarded(p, [&] {
     arg(alpha && x, "alpha and x are required");
     Scope sc(p, stream);
-    WaveletGeom g{p->N, p->J, p->M};
-    DISPATCH(p, {
-      set_ptrs_kernel<<<1, 1, 0, p->ps>>>(p->api3_dev, (void*)alpha, (void*)alpha, (void*)alpha);
-      launch_synthesis3<R>((const R* const*)p->api3_dev, (R*)x, (R*)p->wtmp, g, nullptr, p->ps);
-    });
+    DISPATCH(p, dict_synthesis<R>(p, (const R*)alpha, (R*)x));
     sc.finish();
   });
 }
@@ -1743,8 +1809,7 @@ ms_status ms_dictionary_analysis(ms_plan* p, const void* x, void* alpha, void* s
   return guarded(p, [&] {
     arg(alpha && x, "alpha and x are required");
     Scope sc(p, stream);
-    WaveletGeom g{p->N, p->J, p->M};
-    DISPATCH(p, launch_analysis<R>((const R*)x, (R*)alpha, (R*)p->wtmp, g, p->ps));
+    DISPATCH(p, dict_analysis<R>(p, (const R*)x, (R*)alpha));
     sc.finish();
   });
 }
