@@ -14,6 +14,11 @@ Readings of the paper taken here (each also listed in the design notes):
 * sigma^2 is estimated on i~_{H_1} by the 5 x 5 window rule and eta^2 =
   1e-3 sigma^2 (Sect. 4.3) unless given.
 * FISTA starts from zero each major cycle and returns its last prox output.
+* The PSF operator of the minor cycle is a circular N x N convolution
+  (Sect. 3.4 allows circulant operators) or, with convolution="linear",
+  the linear convolution by the 2N x 2N PSF that A^H A / sum(w) is on the
+  N x N field (the circular one makes the major cycle diverge when the PSF
+  is wide; see the pins).
 """
 from __future__ import annotations
 
@@ -44,6 +49,7 @@ class ReconOptions:
     beta: Optional[float] = None
     levels: int = 4
     n_bases: int = 8
+    convolution: str = "circular"        # or "linear": the PSF operator on the N x N field
 
 
 @dataclass
@@ -71,12 +77,21 @@ def _operator(u, v, npix, pixel_size, opts: ReconOptions) -> GriddedOperator:
                            oversample=opts.oversample, beta=opts.beta)
 
 
+def _psf2_spectrum(u, v, npix, pixel_size, opts: ReconOptions):
+    """Spectrum of the PSF on a 2N x 2N field (offsets up to +-N), for the
+    linear reading of the PSF operator; None for the circular one."""
+    if opts.convolution != "linear":
+        return None
+    return psf_spectrum(_operator(u, v, 2 * npix, pixel_size, opts).psf())
+
+
 def run_low_step(vis, u, v, npix, pixel_size, opts: ReconOptions, coef: float) -> StepResult:
     """Step one (Sect. 3.2, Eq. LowRes); also the single-step method on all
     visibilities (Sect. 5)."""
     A = _operator(u, v, npix, pixel_size, opts)
     W = Dictionary(npix, opts.n_bases, opts.levels)
     Hhat = psf_spectrum(A.psf())
+    Hhat2 = _psf2_spectrum(u, v, npix, pixel_size, opts)
     model = np.zeros((npix, npix))
     out = StepResult(image=model, model=model)
     first = None
@@ -84,7 +99,7 @@ def run_low_step(vis, u, v, npix, pixel_size, opts: ReconOptions, coef: float) -
         res = A.residual_image(vis, model)
         first = res if first is None else first
         lam = _lambda(opts.lambda_rule, coef, res, first, n)
-        prob = Problem("low", W, Hhat, res, lam)
+        prob = Problem("low", W, Hhat, res, lam, Hhat2=Hhat2)
         theta = prob.lipschitz_closed_form()
         fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol)
         model = model + W.synth(fr.beta)
@@ -107,6 +122,7 @@ def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
     A = _operator(u, v, npix, pixel_size, opts)
     W = Dictionary(npix, opts.n_bases, opts.levels)
     Hhat = psf_spectrum(A.psf())
+    Hhat2 = _psf2_spectrum(u, v, npix, pixel_size, opts)
     model = np.zeros((npix, npix))
     out = StepResult(image=model, model=model)
     first = None
@@ -121,7 +137,7 @@ def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
             gl, gh = filter_responses(npix, ell, delta, s2, e2)
         lam = _lambda(opts.lambda_rule, opts.lambda_full, res, first, n)
         l_low = low_image - model
-        prob = Problem("full", W, Hhat, res, lam, gl=gl, gh=gh, l_low=l_low)
+        prob = Problem("full", W, Hhat, res, lam, gl=gl, gh=gh, l_low=l_low, Hhat2=Hhat2)
         theta = prob.lipschitz_closed_form()
         fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol,
                    beta0=beta0_first if n == 1 else None)

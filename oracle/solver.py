@@ -46,6 +46,17 @@ def apply_spectral(x: np.ndarray, response: np.ndarray) -> np.ndarray:
     return np.fft.irfft2(response * np.fft.rfft2(x), s=x.shape)
 
 
+def apply_linear(x: np.ndarray, response2: np.ndarray) -> np.ndarray:
+    """Linear convolution of an N x N image with the PSF whose 2N x 2N
+    half-plane spectrum is response2, restricted to the image: zero-pad x to
+    2N x 2N, filter circularly there (offsets within +-N never wrap), keep
+    the first N x N."""
+    n = x.shape[0]
+    xp = np.zeros((2 * n, 2 * n))
+    xp[:n, :n] = x
+    return np.fft.irfft2(response2 * np.fft.rfft2(xp), s=xp.shape)[:n, :n]
+
+
 def psf_spectrum(psf: np.ndarray) -> np.ndarray:
     """H^ = DFT of the PSF centred at pixel (N/2, N/2); real by symmetry, so
     the (rounding-level) imaginary part is dropped."""
@@ -96,8 +107,14 @@ class Problem:
     gl: Optional[np.ndarray] = None      # full step only
     gh: Optional[np.ndarray] = None
     l_low: Optional[np.ndarray] = None   # l_{L_n}, full step only
+    Hhat2: Optional[np.ndarray] = None   # 2N PSF spectrum: H is a linear convolution
 
     def H(self, x):
+        """The PSF operator: circular convolution on N x N (Sect. 3.4's
+        reading), or, given the 2N x 2N PSF's spectrum, the linear
+        convolution that A^H A / sum(w) is on images of the N x N field."""
+        if self.Hhat2 is not None:
+            return apply_linear(x, self.Hhat2)
         return apply_spectral(x, self.Hhat)
 
     def GL(self, x):
@@ -134,6 +151,14 @@ class Problem:
         return (self.gh * self.Hhat) ** 2 + self.gl ** 2
 
     def lipschitz_closed_form(self) -> float:
+        """2 M max K^ (exact for circulant operators); with the linear
+        convolution an upper bound: ||P H P^T|| <= max|H2^|, so
+        2 M (max g_H^2 max H2^2 + max g_L^2) (full) or 2 M max H2^2."""
+        if self.Hhat2 is not None:
+            h2 = float(np.max(self.Hhat2 ** 2))
+            if self.kind == "low":
+                return 2.0 * self.W.M * h2
+            return 2.0 * self.W.M * (float(np.max(self.gh ** 2)) * h2 + float(np.max(self.gl ** 2)))
         return 2.0 * self.W.M * float(np.max(self.normal_spectrum()))
 
     def normal_op(self, alpha) -> np.ndarray:
