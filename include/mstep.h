@@ -58,6 +58,21 @@ typedef enum { MS_FP64 = 0, MS_FP32 = 1, MS_FP32_KAHAN = 2 } ms_precision;
  * pseudo-random start, once per minor-cycle problem. */
 typedef enum { MS_DICT_DAUBECHIES = 0, MS_DICT_IUWT = 1 } ms_dictionary;
 
+/* The PSF operator H of the minor cycle (Sects. 3.2-3.4).  CIRCULAR: the
+ * N x N circular convolution by the PSF, diagonal in the N x N DFT (K^ =
+ * |H^|^2 ..., step size 2 M max K^, the closed form of Sect. 3.4).  LINEAR:
+ * the linear convolution that A^H A / sum(w) is on images of the N x N
+ * field, H x = P F2^-1(H2^ . F2(P^T x)) with P^T the zero padding to
+ * 2N x 2N and H2^ the spectrum of the PSF of the same partition on a
+ * 2N x 2N field with the same pixel size (computed once at plan creation,
+ * from a temporary 2N plan).  H is then not circulant and 2 M max K^ holds
+ * only as a bound (2 M max H2^2, or 2 M (max g_H^2 max H2^2 + max g_L^2),
+ * since ||P H P^T|| <= max |H2^|, 2-5x above the constant on small
+ * cases), so the step size is a power iteration as for the IUWT (100
+ * iterations from the same fixed start, once per minor-cycle problem).  LINEAR
+ * needs the Daubechies dictionary and N <= 8192 (MS_ERR_ARG otherwise). */
+typedef enum { MS_CONV_CIRCULAR = 0, MS_CONV_LINEAR = 1 } ms_convolution;
+
 /* Baseline partitions of Sect. 3.1: L = {r <= ell + delta} (short baselines),
  * H = {r >= ell - delta} (long baselines), ALL = every unflagged row. */
 typedef enum { MS_PART_L = 0, MS_PART_H = 1, MS_PART_ALL = 2 } ms_part;
@@ -93,6 +108,7 @@ typedef struct {
   int32_t chunk;          /* visibilities per work item: 0 = automatic          */
   int32_t device;         /* CUDA device ordinal                                */
   int32_t dictionary;     /* ms_dictionary; MS_DICT_IUWT ignores n_bases        */
+  int32_t convolution;    /* ms_convolution of the minor cycle's PSF operator    */
 } ms_plan_desc;
 
 typedef struct {
@@ -261,9 +277,12 @@ ms_status ms_dictionary_analysis(ms_plan* plan, const void* x, void* alpha, void
 ms_status ms_sigma2_hat(ms_plan* plan, const void* image, double* sigma2, void* stream);
 
 /* Lipschitz constant of the gradient (Sect. 3.4) for a step of a partition:
- * closed form 2 M max K^ (K^ = |H^|^2, or |g_H H^|^2 + |g_L|^2 for FULL with
- * the given sigma2, eta2), and, if power_iters > 0, 2 lambda_max by power
- * iteration through W in FP64 reductions.  Results to host. */
+ * *closed = the step size the minor cycle uses: the closed form 2 M max K^
+ * (K^ = |H^|^2, or |g_H H^|^2 + |g_L|^2 for FULL with the given sigma2,
+ * eta2), or, for the IUWT dictionary or the linear PSF operator, the
+ * 100-iteration power estimate; and, if power_iters > 0, *power = 2 lambda_max
+ * by a power iteration of that many steps through W (FP64 reductions, on the
+ * plan's PSF operator).  Results to host. */
 ms_status ms_lipschitz(ms_plan* plan, int32_t step, int32_t chan, double sigma2,
                        double eta2, int32_t power_iters, double* theta_closed,
                        double* theta_power, void* stream);
@@ -387,11 +406,15 @@ ms_status ms_warm_start_coefficients(ms_plan* plan, ms_unet* net, const void* lo
  * major cycle, FFT_R2C / FFT_C2R the N x N transforms of the minor cycle
  * (for N a power of two: the row transforms, the inverse one with the
  * iteration control) and SPEC_MUL its spectral step (for N a power of two:
- * fused with the column transforms). */
+ * fused with the column transforms).  LINEAR_PSF is the 2N x 2N linear
+ * PSF operator of the minor cycle (padding, transforms, multiply, crop) when
+ * the plan uses MS_CONV_LINEAR; its objective and control kernels count as
+ * SPEC_MUL. */
 typedef enum {
   MS_K_DEGRID = 0, MS_K_GRID = 1, MS_K_FOLD = 2, MS_K_FFT_GRID = 3, MS_K_PAD_CROP = 4,
   MS_K_SYNTH = 5, MS_K_SYNTH_L1 = 6, MS_K_FFT_R2C = 7, MS_K_SPEC_MUL = 8,
-  MS_K_FFT_C2R = 9, MS_K_ANALYSIS = 10, MS_K_ANALYSIS_L1 = 11, MS_K_COUNT = 12
+  MS_K_FFT_C2R = 9, MS_K_ANALYSIS = 10, MS_K_ANALYSIS_L1 = 11, MS_K_LINEAR_PSF = 12,
+  MS_K_COUNT = 13
 } ms_kernel_family;
 
 typedef struct {

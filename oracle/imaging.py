@@ -18,7 +18,8 @@ Readings of the paper taken here (each also listed in the design notes):
   (Sect. 3.4 allows circulant operators) or, with convolution="linear",
   the linear convolution by the 2N x 2N PSF that A^H A / sum(w) is on the
   N x N field (the circular one makes the major cycle diverge when the PSF
-  is wide; see the pins).
+  is wide; see the pins).  Its step size is a power iteration from a fixed
+  counter-based start (the closed form is then only a bound).
 """
 from __future__ import annotations
 
@@ -28,8 +29,8 @@ from typing import List, Optional
 import numpy as np
 
 from .gridding import GriddedOperator, partition
-from .solver import (Problem, eta2_hat, filter_responses, fista, psf_spectrum,
-                     sigma2_hat)
+from .solver import (POWER_ITERS, Problem, eta2_hat, filter_responses, fista, power_start,
+                     psf_spectrum, sigma2_hat)
 from .wavelets import Dictionary
 
 
@@ -85,6 +86,19 @@ def _psf2_spectrum(u, v, npix, pixel_size, opts: ReconOptions):
     return psf_spectrum(_operator(u, v, 2 * npix, pixel_size, opts).psf())
 
 
+def _step_size(prob: Problem, previous: Optional[float]) -> float:
+    """theta of Sect. 3.4: the closed form 2 M max K^ for the circular
+    operator; for the linear one (not circulant, where the closed form is only
+    a bound, 2-5x above the constant on small cases) a power iteration from the
+    fixed start, once per step (the operator is the same in every cycle)."""
+    if prob.Hhat2 is None:
+        return prob.lipschitz_closed_form()
+    if previous is not None:
+        return previous
+    return prob.lipschitz_power_iteration(
+        iters=POWER_ITERS, start=power_start((prob.W.M, prob.W.npix, prob.W.npix)))
+
+
 def run_low_step(vis, u, v, npix, pixel_size, opts: ReconOptions, coef: float) -> StepResult:
     """Step one (Sect. 3.2, Eq. LowRes); also the single-step method on all
     visibilities (Sect. 5)."""
@@ -100,7 +114,7 @@ def run_low_step(vis, u, v, npix, pixel_size, opts: ReconOptions, coef: float) -
         first = res if first is None else first
         lam = _lambda(opts.lambda_rule, coef, res, first, n)
         prob = Problem("low", W, Hhat, res, lam, Hhat2=Hhat2)
-        theta = prob.lipschitz_closed_form()
+        theta = _step_size(prob, theta if n > 1 else None)
         fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol)
         model = model + W.synth(fr.beta)
         out.residuals.append(res)
@@ -138,7 +152,7 @@ def run_full_step(vis, u, v, npix, pixel_size, low_image, ell, delta,
         lam = _lambda(opts.lambda_rule, opts.lambda_full, res, first, n)
         l_low = low_image - model
         prob = Problem("full", W, Hhat, res, lam, gl=gl, gh=gh, l_low=l_low, Hhat2=Hhat2)
-        theta = prob.lipschitz_closed_form()
+        theta = _step_size(prob, theta if n > 1 else None)
         fr = fista(prob, opts.fista_iters, theta=theta, rel_tol=opts.rel_tol,
                    beta0=beta0_first if n == 1 else None)
         model = model + W.synth(fr.beta)

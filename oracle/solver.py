@@ -169,11 +169,16 @@ class Problem:
         return self.W.analysis(self.H(self.GH(self.GH(self.H(x)))) + self.GL(self.GL(x)))
 
     def lipschitz_power_iteration(self, iters: int = 200, seed: int = 0,
-                                  tol: float = 0.0) -> float:
+                                  tol: float = 0.0,
+                                  start: Optional[np.ndarray] = None) -> float:
         """theta = 2 lambda_max by power iteration (Sect. 3.4, the method the
-        paper names for dictionaries without the closed form)."""
-        rng = np.random.default_rng(seed)
-        v = rng.standard_normal((self.W.M, self.W.npix, self.W.npix))
+        paper names for dictionaries without the closed form), from `start`
+        (else a normal random vector drawn with `seed`)."""
+        shape = (self.W.M, self.W.npix, self.W.npix)
+        if start is None:
+            v = np.random.default_rng(seed).standard_normal(shape)
+        else:
+            v = np.array(start, dtype=np.float64).reshape(shape)
         v /= np.linalg.norm(v)
         lam = 0.0
         for _ in range(iters):
@@ -185,6 +190,35 @@ class Problem:
                 break
             lam = new
         return 2.0 * lam
+
+
+def splitmix64(n: int, seed: int) -> np.ndarray:
+    """Outputs 1..n of the SplitMix64 generator (Steele, Lea and Flood, 2014)
+    from state `seed`: the state advances by the odd constant 0x9E3779B97F4A7C15
+    and each output is the state through the two xor-shift-multiply rounds
+    (30, 0xBF58476D1CE4E5B9; 27, 0x94D049BB133111EB) and a final xor-shift by
+    31, all modulo 2^64."""
+    k = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + np.uint64(0x9E3779B97F4A7C15) * k
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+# The start vector of the power iterations that set the step size where the
+# closed form does not hold: SplitMix64 outputs from this seed, their top 53
+# bits as a fraction of 2^53 mapped to [-1, 1), in the coefficients' flat
+# order; 100 iterations (the counter-based start lets the CUDA path, which
+# implements the same generator, reach the same estimate).
+POWER_SEED = 12345
+POWER_ITERS = 100
+
+
+def power_start(shape) -> np.ndarray:
+    n = int(np.prod(shape))
+    z = splitmix64(n, POWER_SEED)
+    return ((z >> np.uint64(11)).astype(np.float64) * (2.0 / 2.0 ** 53) - 1.0).reshape(shape)
 
 
 def soft_threshold(x: np.ndarray, t: float) -> np.ndarray:

@@ -29,6 +29,8 @@ MS_LAMBDA_NORM2_2N, MS_LAMBDA_MAX_FIXED = 0, 1
 PRECISIONS = {"fp64": MS_FP64, "fp32": MS_FP32, "fp32_kahan": MS_FP32_KAHAN}
 MS_DICT_DAUBECHIES, MS_DICT_IUWT = 0, 1
 DICTIONARIES = {"daubechies": MS_DICT_DAUBECHIES, "iuwt": MS_DICT_IUWT}
+MS_CONV_CIRCULAR, MS_CONV_LINEAR = 0, 1
+CONVOLUTIONS = {"circular": MS_CONV_CIRCULAR, "linear": MS_CONV_LINEAR}
 PARTS = {"L": MS_PART_L, "H": MS_PART_H, "ALL": MS_PART_ALL}
 STEPS = {"low": MS_STEP_LOW, "full": MS_STEP_FULL, "single": MS_STEP_SINGLE}
 
@@ -48,7 +50,7 @@ class ms_plan_desc(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("n_bases", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("chunk", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("dictionary", ctypes.c_int32)]
+                ("dictionary", ctypes.c_int32), ("convolution", ctypes.c_int32)]
 
 
 class ms_stats(ctypes.Structure):
@@ -67,7 +69,7 @@ class ms_kernel_profile(ctypes.Structure):
 
 
 KERNEL_FAMILIES = ["degrid", "grid", "fold", "fft_grid", "pad_crop", "synth", "synth_l1",
-                   "fft_r2c", "spec_mul", "fft_c2r", "analysis", "analysis_l1"]
+                   "fft_r2c", "spec_mul", "fft_c2r", "analysis", "analysis_l1", "linear_psf"]
 
 
 class ms_recon_opts(ctypes.Structure):
@@ -218,7 +220,7 @@ class Plan:
                  flags=None, precision: str = "fp64", levels: int = 4, n_bases: int = 8,
                  kernel_width: int = 7, oversample: int = 2, es_beta: float = 0.0,
                  tile: int = 0, chunk: int = 0, device: int = 0,
-                 dictionary: str = "daubechies"):
+                 dictionary: str = "daubechies", convolution: str = "circular"):
         lib = load_library()
         u = np.ascontiguousarray(np.atleast_2d(np.asarray(u, dtype=np.float64)))
         v = np.ascontiguousarray(np.atleast_2d(np.asarray(v, dtype=np.float64)))
@@ -238,10 +240,11 @@ class Plan:
         self.levels = levels
         self.n_bases = levels + 1 if dictionary == "iuwt" else n_bases
         self.device = device
+        self.convolution = convolution
         d = ms_plan_desc(u.ctypes.data, v.ctypes.data, fl.ctypes.data if fl is not None else None,
                          self.nvis, self.nchan, self.npix, pixel_size, ell_px, delta_px,
                          kernel_width, oversample, es_beta, levels, n_bases, self.prec, tile,
-                         chunk, device, DICTIONARIES[dictionary])
+                         chunk, device, DICTIONARIES[dictionary], CONVOLUTIONS[convolution])
         h = _P()
         st = lib.ms_plan_create(ctypes.byref(d), ctypes.byref(h))
         if st != MS_OK:

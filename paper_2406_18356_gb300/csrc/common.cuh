@@ -407,5 +407,27 @@ template <typename R>
 void launch_normalize(R* x, int64_t n, const double* den, cudaStream_t s);
 template <typename R>
 void launch_hash_fill(R* x, int64_t n, uint64_t seed, cudaStream_t s);
+// the linear PSF operator of the minor cycle (2N x 2N zero padding)
+template <typename R>
+void launch_lin_pad(const R* x, R* xp, int N, const FistaCtl* ctl, cudaStream_t s);
+template <typename R>
+void launch_lin_mul(C2<R>* S, const R* H2, int N, const FistaCtl* ctl, cudaStream_t s);
+template <typename R>
+void launch_lin_crop(const R* q, const R* add, R* out, int N, double scale, const FistaCtl* ctl,
+                     cudaStream_t s);
+template <typename R>
+void launch_lin_low_step(const R* q, const R* res, R* ycur, const R* yprev, R* rp, int N,
+                         double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
+                         const double* l1_parts, int n_l1, cudaStream_t s);
+template <typename R>
+void launch_lin_full_diff(const R* q, const R* res, const R* x, const R* l, R* de, int N,
+                          const FistaCtl* ctl, cudaStream_t s);
+template <typename R>
+void launch_lin_full_spec(const C2<R>* dek, const C2<R>* dep, const R* gl2, const R* gh2,
+                          C2<R>* uv, int N, double* parts, FistaCtl* ctl, double* trace,
+                          int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s);
+template <typename R>
+void launch_lin_theta(const R* H2, int N, const R* gl2, const R* gh2, int M, double* parts,
+                      FistaCtl* ctl, int32_t* ticket, cudaStream_t s);
 
 }  // namespace ms

@@ -241,6 +241,7 @@ struct PartDev {
   int32_t* tile_items = nullptr;
   void* Hhat = nullptr;
   bool have_psf = false;
+  void* Hhat2 = nullptr;   // real spectrum of the PSF on the 2N x 2N field (linear operator)
 };
 
 struct ChanDev {
@@ -314,6 +315,16 @@ struct ms_plan {
   std::vector<Span> pending;
   int64_t k_launch[16] = {};
   double k_ms[16] = {};
+  // linear PSF operator of the minor cycle (MS_CONV_LINEAR): the 2N x 2N pad
+  // and product images and their spectrum, the current problem's H2^, i~ and
+  // l, the ring of H x_k (LOW / SINGLE), the stacked [D; E] images, their
+  // spectra by pass parity, the filtered spectra [U^; V^] and their images
+  int conv = MS_CONV_CIRCULAR;
+  void *lp = nullptr, *lq = nullptr, *ls = nullptr, *lh2 = nullptr;
+  void *lres = nullptr, *ll = nullptr, *ly[2] = {};
+  void *lde = nullptr, *ldes[2] = {}, *luvs = nullptr, *luv = nullptr;
+  cufftHandle r2c2 = 0, c2r2 = 0, r2cb = 0, c2rb = 0;
+  cudaGraphExec_t lin_exec[2] = {};   // captured linear passes: LOW / SINGLE, FULL
   // captured FISTA passes
   cudaGraphExec_t fista_exec = nullptr;
   int fista_graph_step = -1;
@@ -498,6 +509,20 @@ template <typename R> void fft_c2r(ms_plan* p, void* in, void* out) {
     ckf(cufftExecC2R(p->c2r, (cufftComplex*)in, (cufftReal*)out), "C2R");
 }
 
+// real <-> half-plane transforms with a given cuFFT plan
+template <typename R> void exec_r2c(cufftHandle h, const void* in, void* out) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecD2Z(h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out), "D2Z");
+  else
+    ckf(cufftExecR2C(h, (cufftReal*)in, (cufftComplex*)out), "R2C");
+}
+template <typename R> void exec_c2r(cufftHandle h, void* in, void* out) {
+  if (sizeof(R) == 8)
+    ckf(cufftExecZ2D(h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out), "Z2D");
+  else
+    ckf(cufftExecC2R(h, (cufftComplex*)in, (cufftReal*)out), "C2R");
+}
+
 // model grid = F Z D image (centred)
 template <typename R> void image_to_grid(ms_plan* p, const void* image, Timer* tm) {
   {
@@ -634,22 +659,47 @@ template <typename R> FistaPass<R> fista_pass_args(ms_plan* p) {
 // X^_k = F x, the spectral step (objective, iteration control, gradient
 // spectrum with the momentum folded in), the inverse FFT to the gradient
 // image, and analysis + prox into B_{k+1} (levels 1..J).
-template <typename R> void record_fista_pass(ms_plan* p, int parity) {
-  C2<R>* Fk = (C2<R>*)p->F[parity];
-  C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
-  const FistaPass<R> a = fista_pass_args<R>(p);
+// x_k = W B_k into xwork (levels J..1)
+template <typename R> void record_synthesis(ms_plan* p, const FistaPass<R>& a) {
   if (p->dict == MS_DICT_IUWT) {
     KSpan k(p, MS_K_SYNTH_L1);
     ck(launch_iuwt_synthesis<R>(&a, nullptr, a.x, (R*)p->wtmp, p->N, p->J, p->ps),
        "IUWT synthesis");
-  } else {
-    if (p->J > 1) {
-      KSpan k(p, MS_K_SYNTH);
-      ck(launch_synthesis_pass<R>(a, p->ps, -1), "synthesis");
-    }
-    KSpan k(p, MS_K_SYNTH_L1);
-    ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
+    return;
   }
+  if (p->J > 1) {
+    KSpan k(p, MS_K_SYNTH);
+    ck(launch_synthesis_pass<R>(a, p->ps, -1), "synthesis");
+  }
+  KSpan k(p, MS_K_SYNTH_L1);
+  ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
+}
+
+// B_k+1 = prox(z_k - mu W^H g) from the gradient image g in ywork (levels 1..J)
+template <typename R> void record_analysis(ms_plan* p, const FistaPass<R>& a) {
+  if (p->dict == MS_DICT_IUWT) {
+    KSpan k(p, MS_K_ANALYSIS_L1);
+    ck(launch_iuwt_analysis<R>(&a, (const R*)p->ywork, nullptr, (R*)p->wtmp, p->N, p->J,
+                               p->ps),
+       "IUWT analysis");
+    return;
+  }
+  const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
+  {
+    KSpan k(p, MS_K_ANALYSIS_L1);
+    ck(launch_analysis_pass<R>(a, gmap, p->ps, 1), "analysis");
+  }
+  if (p->J > 1) {
+    KSpan k(p, MS_K_ANALYSIS);
+    ck(launch_analysis_pass<R>(a, gmap, p->ps, -1), "analysis");
+  }
+}
+
+template <typename R> void record_fista_pass(ms_plan* p, int parity) {
+  C2<R>* Fk = (C2<R>*)p->F[parity];
+  C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
+  const FistaPass<R> a = fista_pass_args<R>(p);
+  record_synthesis<R>(p, a);
   if (p->fused_spec) {
     // row transforms, the spectral step with the column transforms fused in,
     // inverse row transforms (whose extra block runs the iteration control)
@@ -686,31 +736,78 @@ template <typename R> void record_fista_pass(ms_plan* p, int parity) {
       fft_c2r<R>(p, Fo, p->ywork);   // gradient image 2 (K W alpha_k - b)
     }
   }
-  if (p->dict == MS_DICT_IUWT) {
-    KSpan k(p, MS_K_ANALYSIS_L1);
-    ck(launch_iuwt_analysis<R>(&a, (const R*)p->ywork, nullptr, (R*)p->wtmp, p->N, p->J,
-                               p->ps),
-       "IUWT analysis");
-    return;
-  }
-  const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
-  {
-    KSpan k(p, MS_K_ANALYSIS_L1);
-    ck(launch_analysis_pass<R>(a, gmap, p->ps, 1), "analysis");
-  }
-  if (p->J > 1) {
-    KSpan k(p, MS_K_ANALYSIS);
-    ck(launch_analysis_pass<R>(a, gmap, p->ps, -1), "analysis");
-  }
+  record_analysis<R>(p, a);
 }
 
-template <typename R> void ensure_fista_graph(ms_plan* p) {
-  if (p->fista_exec) return;
+// q = P^T-padded x through the 2N x 2N product with H2^ (lq holds the 2N x 2N
+// result; P q = H x)
+template <typename R> void linear_psf(ms_plan* p, const R* x, const FistaCtl* ctl) {
+  KSpan k(p, MS_K_LINEAR_PSF);
+  launch_lin_pad<R>(x, (R*)p->lp, p->N, ctl, p->ps);
+  exec_r2c<R>(p->r2c2, p->lp, p->ls);
+  launch_lin_mul<R>((C2<R>*)p->ls, (const R*)p->lh2, p->N, ctl, p->ps);
+  exec_c2r<R>(p->c2r2, p->ls, p->lq);
+}
+
+// One FISTA iteration with the linear PSF operator (the pass of
+// record_fista_pass with the smooth part evaluated in the image domain; the
+// pass parity selects the ring slots of y_k / [D^_k; E^_k] as there).
+template <typename R> void record_linear_pass(ms_plan* p, int parity, bool full) {
+  const FistaPass<R> a = fista_pass_args<R>(p);
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N;
+  record_synthesis<R>(p, a);
+  linear_psf<R>(p, (const R*)p->xwork, p->ctl);   // y_k = H x_k
+  if (!full) {
+    {
+      KSpan k(p, MS_K_SPEC_MUL);
+      launch_lin_low_step<R>((const R*)p->lq, (const R*)p->lres, (R*)p->ly[parity],
+                             (const R*)p->ly[parity ^ 1], (R*)p->lp, N, p->parts, p->ctl,
+                             p->trace, p->tickets + 0, p->l1parts, p->n_l1, p->ps);
+    }
+    KSpan k(p, MS_K_LINEAR_PSF);   // gradient image 2 H r
+    exec_r2c<R>(p->r2c2, p->lp, p->ls);
+    launch_lin_mul<R>((C2<R>*)p->ls, (const R*)p->lh2, N, p->ctl, p->ps);
+    exec_c2r<R>(p->c2r2, p->ls, p->lq);
+    launch_lin_crop<R>((const R*)p->lq, nullptr, (R*)p->ywork, N, 2.0, p->ctl, p->ps);
+  } else {
+    {
+      KSpan k(p, MS_K_SPEC_MUL);
+      launch_lin_full_diff<R>((const R*)p->lq, (const R*)p->lres, (const R*)p->xwork,
+                              (const R*)p->ll, (R*)p->lde, N, p->ctl, p->ps);
+      exec_r2c<R>(p->r2cb, p->lde, p->ldes[parity]);
+      launch_lin_full_spec<R>((const C2<R>*)p->ldes[parity], (const C2<R>*)p->ldes[parity ^ 1],
+                              (const R*)p->gl2, (const R*)p->gh2, (C2<R>*)p->luvs, N, p->parts,
+                              p->ctl, p->trace, p->tickets + 0, p->l1parts, p->n_l1, p->ps);
+      exec_c2r<R>(p->c2rb, p->luvs, p->luv);   // [u; v] = [G_H^2 D_z; G_L^2 E_z]
+    }
+    linear_psf<R>(p, (const R*)p->luv, p->ctl);
+    KSpan k(p, MS_K_LINEAR_PSF);   // gradient image 2 (H u + v)
+    launch_lin_crop<R>((const R*)p->lq, (const R*)p->luv + n2, (R*)p->ywork, N, 2.0, p->ctl,
+                       p->ps);
+  }
+  record_analysis<R>(p, a);
+}
+
+template <typename R> void record_pass(ms_plan* p, int parity, int step) {
+  if (p->conv == MS_CONV_LINEAR)
+    record_linear_pass<R>(p, parity, step == MS_STEP_FULL);
+  else
+    record_fista_pass<R>(p, parity);
+}
+
+// the graph of kPasses passes of `step` (one for the circular operator;
+// for the linear one, one per problem kind)
+template <typename R> cudaGraphExec_t ensure_fista_graph(ms_plan* p, int step) {
+  cudaGraphExec_t* exec = p->conv == MS_CONV_LINEAR
+                              ? &p->lin_exec[step == MS_STEP_FULL ? 1 : 0]
+                              : &p->fista_exec;
+  if (*exec) return *exec;
   cudaGraph_t graph;
   ck(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal), "begin capture");
   p->capturing = true;
   try {
-    for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p, i & 1);
+    for (int i = 0; i < kPasses; ++i) record_pass<R>(p, i & 1, step);
   } catch (...) {
     p->capturing = false;
     cudaStreamEndCapture(p->ps, &graph);
@@ -718,12 +815,23 @@ template <typename R> void ensure_fista_graph(ms_plan* p) {
   }
   p->capturing = false;
   ck(cudaStreamEndCapture(p->ps, &graph), "end capture");
-  ck(cudaGraphInstantiate(&p->fista_exec, graph, 0), "graph instantiate");
+  ck(cudaGraphInstantiate(exec, graph, 0), "graph instantiate");
   cudaGraphDestroy(graph);
+  return *exec;
+}
+
+void drop_graphs(ms_plan* p) {
+  for (cudaGraphExec_t* e : {&p->fista_exec, &p->lin_exec[0], &p->lin_exec[1]})
+    if (*e) {
+      cudaGraphExecDestroy(*e);
+      *e = nullptr;
+    }
 }
 
 // ------------------------------------------------------------- dictionary
-constexpr int kIuwtPowerIterations = 100;   // power iterations of the IUWT step size
+// power iterations of the step size where the closed form does not hold
+// (the IUWT dictionary, the linear PSF operator)
+constexpr int kPowerIterations = 100;
 
 // x = W alpha and alpha = W^H x with the plan's dictionary (plain calls)
 template <typename R> void dict_synthesis(ms_plan* p, const R* alpha, R* x) {
@@ -745,10 +853,37 @@ template <typename R> void dict_analysis(ms_plan* p, const R* x, R* alpha) {
   launch_analysis<R>(x, alpha, (R*)p->wtmp, WaveletGeom{p->N, p->J, p->M}, p->ps);
 }
 
+// The normal operator of the current problem with the linear PSF operator,
+// out = H H x (LOW / SINGLE) or H G_H^2 H x + G_L^2 x (FULL), plain launches.
+template <typename R> void linear_normal(ms_plan* p, bool full, const R* x, R* out) {
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N;
+  linear_psf<R>(p, x, nullptr);
+  if (!full) {
+    launch_lin_crop<R>((const R*)p->lq, nullptr, (R*)p->luv, N, 1.0, nullptr, p->ps);
+    linear_psf<R>(p, (const R*)p->luv, nullptr);
+    launch_lin_crop<R>((const R*)p->lq, nullptr, out, N, 1.0, nullptr, p->ps);
+    return;
+  }
+  // [H x; x] -> spectra -> [G_H^2 H x; G_L^2 x] -> images
+  launch_lin_crop<R>((const R*)p->lq, nullptr, (R*)p->lde, N, 1.0, nullptr, p->ps);
+  ck(cudaMemcpyAsync((R*)p->lde + n2, x, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps),
+     "copy");
+  exec_r2c<R>(p->r2cb, p->lde, p->ldes[0]);
+  launch_lin_full_spec<R>((const C2<R>*)p->ldes[0], nullptr, (const R*)p->gl2, (const R*)p->gh2,
+                          (C2<R>*)p->luvs, N, nullptr, nullptr, nullptr, nullptr, nullptr, 0,
+                          p->ps);
+  exec_c2r<R>(p->c2rb, p->luvs, p->luv);
+  linear_psf<R>(p, (const R*)p->luv, nullptr);
+  launch_lin_crop<R>((const R*)p->lq, (const R*)p->luv + n2, out, N, 1.0, nullptr, p->ps);
+}
+
 // 2 lambda_max(W^H K W) by power iteration (Sect. 3.4) into p->scal[2]
-// (device), from the plan's K^: Rayleigh quotient of the normalized
-// iterate, reductions in FP64.  Uses B[0], B[1] and the work images.
-template <typename R> void power_theta(ms_plan* p, int iters) {
+// (device), from the plan's K^ (or, with the linear PSF operator, the
+// operator itself for the problem kind `full`): Rayleigh quotient of the
+// normalized iterate, reductions in FP64.  Uses B[0], B[1] and the work
+// images.
+template <typename R> void power_theta(ms_plan* p, int iters, bool full) {
   const int64_t ncoef = (int64_t)p->M * p->N * p->N;
   R* v = (R*)p->B[0];
   R* w = (R*)p->B[1];
@@ -758,9 +893,13 @@ template <typename R> void power_theta(ms_plan* p, int iters) {
     launch_dot<R>(v, v, ncoef, p->parts, sc + 0, p->tickets + 7, p->ps);
     launch_normalize<R>(v, ncoef, sc + 0, p->ps);
     dict_synthesis<R>(p, v, (R*)p->xwork);
-    fft_r2c<R>(p, p->xwork, p->spec);
-    launch_spec_apply<R>((C2<R>*)p->spec, (const R*)p->Ks, p->N, p->ps);
-    fft_c2r<R>(p, p->spec, p->ywork);
+    if (p->conv == MS_CONV_LINEAR) {
+      linear_normal<R>(p, full, (const R*)p->xwork, (R*)p->ywork);
+    } else {
+      fft_r2c<R>(p, p->xwork, p->spec);
+      launch_spec_apply<R>((C2<R>*)p->spec, (const R*)p->Ks, p->N, p->ps);
+      fft_c2r<R>(p, p->spec, p->ywork);
+    }
     dict_analysis<R>(p, (const R*)p->ywork, w);
     launch_dot<R>(v, w, ncoef, p->parts, sc + 1, p->tickets + 8, p->ps);
     ck(cudaMemcpyAsync(v, w, sizeof(R) * ncoef, cudaMemcpyDeviceToDevice, p->ps), "copy");
@@ -774,6 +913,26 @@ template <typename R> void power_theta(ms_plan* p, int iters) {
 template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, double ell,
                                         double delta) {
   ensure_psf<R>(p, pd);
+  if (p->conv == MS_CONV_LINEAR) {
+    // the problem's H2^ into the buffer the captured passes read
+    ck(cudaMemcpyAsync(p->lh2, pd.Hhat2, sizeof(R) * 2 * p->N * (p->N + 1),
+                       cudaMemcpyDeviceToDevice, p->ps),
+       "copy");
+    const bool full = step == MS_STEP_FULL;
+    if (full) {
+      check_noise_kernel<<<1, 1, 0, p->ps>>>(p->ctl);
+      launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
+    }
+    // the bound (and c0 = 0), then the step size itself: the operator is not
+    // circulant, so the closed form is only a bound; power iteration from
+    // the fixed start as for the IUWT
+    launch_lin_theta<R>((const R*)p->lh2, p->N, full ? (const R*)p->gl2 : nullptr,
+                        full ? (const R*)p->gh2 : nullptr, p->M, p->parts, p->ctl,
+                        p->tickets + 2, p->ps);
+    power_theta<R>(p, kPowerIterations, full);
+    set_theta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->scal + 2);
+    return;
+  }
   if (step == MS_STEP_FULL) {
     check_noise_kernel<<<1, 1, 0, p->ps>>>(p->ctl);
     launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
@@ -785,7 +944,7 @@ template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, doubl
   }
   if (p->dict == MS_DICT_IUWT) {
     // no closed form (T^H T is not a multiple of I): power iteration
-    power_theta<R>(p, kIuwtPowerIterations);
+    power_theta<R>(p, kPowerIterations, false);
     set_theta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->scal + 2);
   }
 }
@@ -799,13 +958,26 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
   const int64_t npix2 = (int64_t)N * N;
   const int64_t ncoef = (int64_t)p->M * npix2;
   const int64_t nspec = (int64_t)N * (N / 2 + 1);
-  fft_r2c<R>(p, residual, p->spec);
-  if (step == MS_STEP_FULL) {
+  if (p->conv == MS_CONV_LINEAR) {
+    // i~ (and l) into the buffers the captured passes read; y_-1 and the
+    // spectra of pass -1 zero (their weight t_0 is zero, but must be finite)
+    ck(cudaMemcpyAsync(p->lres, residual, sizeof(R) * npix2, cudaMemcpyDeviceToDevice, p->ps),
+       "copy");
+    if (step == MS_STEP_FULL) {
+      ck(cudaMemcpyAsync(p->ll, l_low, sizeof(R) * npix2, cudaMemcpyDeviceToDevice, p->ps),
+         "copy");
+      ck(cudaMemsetAsync(p->ldes[1], 0, sizeof(C2<R>) * 2 * nspec, p->ps), "memset");
+    } else {
+      ck(cudaMemsetAsync(p->ly[1], 0, sizeof(R) * npix2, p->ps), "memset");
+    }
+  } else if (step == MS_STEP_FULL) {
+    fft_r2c<R>(p, residual, p->spec);
     fft_r2c<R>(p, l_low, p->spec2);
     launch_b_spectrum<R>((const C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)pd.Hhat,
                          (const R*)p->gl2, (const R*)p->gh2, N, (C2<R>*)p->Bs, p->parts, p->ctl,
                          p->tickets + 3, p->ps);
   } else {
+    fft_r2c<R>(p, residual, p->spec);
     launch_b_spectrum<R>((const C2<R>*)p->spec, nullptr, (const R*)pd.Hhat, nullptr, nullptr, N,
                          (C2<R>*)p->Bs, p->parts, p->ctl, p->tickets + 3, p->ps);
   }
@@ -830,7 +1002,7 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
   const int passes = max_iters + 1;
   if (p->prof) {   // direct launches, each kernel family bracketed by events
     for (int i = 0; i < passes; ++i) {
-      record_fista_pass<R>(p, i & 1);
+      record_pass<R>(p, i & 1, step);
       if ((i + 1) % kPasses == 0 && p->pending.size() > 4096) harvest(p);
       if (poll && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes) {
         int32_t done = 0;
@@ -842,10 +1014,10 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     }
     return;
   }
-  ensure_fista_graph<R>(p);
+  cudaGraphExec_t exec = ensure_fista_graph<R>(p, step);
   int launched = 0;
   while (launched < passes) {
-    ck(cudaGraphLaunch(p->fista_exec, p->ps), "graph launch");
+    ck(cudaGraphLaunch(exec, p->ps), "graph launch");
     launched += kPasses;
     if (poll && launched < passes && (launched / kPasses) % 4 == 0) {
       int32_t done = 0;
@@ -1002,10 +1174,7 @@ void ensure_trace(ms_plan* p, int iters) {
   }
   p->trace_cap = std::max(iters + 2, 1024);
   p->trace = p->alloc<double>(p->trace_cap, "trace");
-  if (p->fista_exec) {   // the captured passes point at the old trace
-    cudaGraphExecDestroy(p->fista_exec);
-    p->fista_exec = nullptr;
-  }
+  drop_graphs(p);   // the captured passes point at the old trace
 }
 
 template <typename R>
@@ -1067,16 +1236,18 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   const int N = p->N, Ng = p->Ng;
   const int64_t nvis = d->nvis;
   cudaStream_t s = p->ps;
-  // Daubechies filters
-  if (p->dict == MS_DICT_DAUBECHIES) {
+  // Daubechies filters: the device's table holds db1..db8 whatever this
+  // plan's M, so that plans of different M (and the temporary plans of the
+  // linear PSF operator) leave it the same for each other
+  {
     std::vector<double> h(kMaxBases * kMaxTaps, 0.0);
     std::vector<int> len(kMaxBases, 0);
-    for (int m = 0; m < p->M; ++m) {
+    for (int m = 0; m < kMaxBases; ++m) {
       std::vector<double> f = daubechies(m + 1);
       len[m] = (int)f.size();
       for (size_t k = 0; k < f.size(); ++k) h[m * kMaxTaps + k] = f[k];
     }
-    set_wavelet_filters(h.data(), len.data(), p->M);
+    set_wavelet_filters(h.data(), len.data(), kMaxBases);
     ck(cudaGetLastError(), "wavelet filters");
   }
   // deapodization table
@@ -1230,6 +1401,27 @@ template <typename R> void build_plan(ms_plan* p, const ms_plan_desc* d) {
   ckf(cufftPlan2d(&p->r2c, N, N, tr), "plan R2C");
   ckf(cufftPlan2d(&p->c2r, N, N, ti), "plan C2R");
   for (cufftHandle h : {p->c2c, p->r2c, p->c2r}) ckf(cufftSetStream(h, s), "set stream");
+  if (p->conv == MS_CONV_LINEAR) {
+    const int64_t n4 = 4 * n2, s2 = (int64_t)2 * N * (N + 1);
+    p->lp = p->alloc<R>(n4, "linear pad");
+    p->lq = p->alloc<R>(n4, "linear product");
+    p->ls = p->alloc<C2<R>>(s2, "linear spectrum");
+    p->lh2 = p->alloc<R>(s2, "linear PSF spectrum");
+    p->lres = p->alloc<R>(n2, "image");
+    p->ll = p->alloc<R>(n2, "image");
+    for (auto& y : p->ly) y = p->alloc<R>(n2, "image");
+    p->lde = p->alloc<R>(2 * n2, "image");
+    for (auto& q : p->ldes) q = p->alloc<C2<R>>(2 * nspec, "spectrum");
+    p->luvs = p->alloc<C2<R>>(2 * nspec, "spectrum");
+    p->luv = p->alloc<R>(2 * n2, "image");
+    ckf(cufftPlan2d(&p->r2c2, 2 * N, 2 * N, tr), "plan R2C 2N");
+    ckf(cufftPlan2d(&p->c2r2, 2 * N, 2 * N, ti), "plan C2R 2N");
+    int nn[2] = {N, N};   // two stacked N x N transforms, contiguous
+    ckf(cufftPlanMany(&p->r2cb, 2, nn, nullptr, 1, 0, nullptr, 1, 0, tr, 2), "plan R2C x2");
+    ckf(cufftPlanMany(&p->c2rb, 2, nn, nullptr, 1, 0, nullptr, 1, 0, ti, 2), "plan C2R x2");
+    for (cufftHandle h : {p->r2c2, p->c2r2, p->r2cb, p->c2rb})
+      ckf(cufftSetStream(h, s), "set stream");
+  }
   {
     int dev_smem = 0;
     ck(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->dev),
@@ -1306,7 +1498,7 @@ void lipschitz(ms_plan* p, int step, int chan, double sigma2, double eta2, int p
   if (closed) *closed = h.theta;
   if (power) *power = 0.0;
   if (power_iters <= 0) return;
-  power_theta<R>(p, power_iters);
+  power_theta<R>(p, power_iters, step == MS_STEP_FULL);
   double* sc = p->scal;
   double rho = 0;
   ck(cudaMemcpyAsync(&rho, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, p->ps), "copy");
@@ -1364,8 +1556,8 @@ void destroy(ms_plan* p) {
   if (!p) return;
   DeviceGuard guard;
   cudaSetDevice(p->dev);
-  if (p->fista_exec) cudaGraphExecDestroy(p->fista_exec);
-  for (cufftHandle h : {p->c2c, p->r2c, p->c2r})
+  drop_graphs(p);
+  for (cufftHandle h : {p->c2c, p->r2c, p->c2r, p->r2c2, p->c2r2, p->r2cb, p->c2rb})
     if (h) cufftDestroy(h);
   for (void* a : p->allocs) cudaFree(a);
   if (p->batch.fft) cufftDestroy(p->batch.fft);
@@ -1636,6 +1828,44 @@ void* static_grid_scratch(int dev) {
 
 }  // namespace
 
+// H2^ of every channel and partition for the linear PSF operator: the real
+// spectrum of the PSF on a 2N x 2N field with the same pixel size, from a
+// temporary plan of side 2N whose partition bounds are 2 ell, 2 delta (the
+// radius r = |uv| N dl doubles with N, exactly, so each row falls in the same
+// partitions).  d still carries the caller's u, v and flags.
+template <typename R> void build_linear_psf(ms_plan* p, const ms_plan_desc* d) {
+  ms_plan_desc d2 = *d;
+  d2.npix = 2 * d->npix;
+  d2.ell_px = 2.0 * d->ell_px;
+  d2.delta_px = 2.0 * d->delta_px;
+  d2.levels = 1;
+  d2.n_bases = 1;
+  d2.dictionary = MS_DICT_DAUBECHIES;
+  d2.convolution = MS_CONV_CIRCULAR;
+  d2.tile = 0;
+  d2.chunk = 0;
+  ms_plan* q = nullptr;
+  const ms_status st = ms_plan_create(&d2, &q);
+  if (st != MS_OK) throw Fail{st, "linear PSF operator: the 2N x 2N plan could not be built"};
+  const size_t bytes = sizeof(R) * 2 * p->N * (p->N + 1);
+  try {
+    ck(cudaSetDevice(q->dev), "set device");
+    for (size_t c = 0; c < p->ch.size(); ++c)
+      for (int pt = 0; pt < 3; ++pt) {
+        PartDev& qd = q->ch[c].part[pt];
+        ensure_psf<R>(q, qd);
+        PartDev& pd = p->ch[c].part[pt];
+        pd.Hhat2 = p->alloc<R>(bytes / sizeof(R), "linear PSF spectrum");
+        ck(cudaMemcpyAsync(pd.Hhat2, qd.Hhat, bytes, cudaMemcpyDeviceToDevice, q->ps), "copy");
+        ck(cudaStreamSynchronize(q->ps), "synchronize");
+      }
+  } catch (...) {
+    destroy(q);
+    throw;
+  }
+  destroy(q);
+}
+
 extern "C" {
 
 ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
@@ -1661,6 +1891,11 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     arg(d->pixel_size > 0 && std::isfinite(d->pixel_size), "pixel_size must be > 0");
     arg(d->delta_px > 0 && std::isfinite(d->ell_px), "delta must be > 0 and ell finite");
     arg(d->precision >= MS_FP64 && d->precision <= MS_FP32_KAHAN, "unknown precision");
+    arg(d->convolution == MS_CONV_CIRCULAR || d->convolution == MS_CONV_LINEAR,
+        "unknown convolution");
+    arg(d->convolution == MS_CONV_CIRCULAR ||
+            (d->dictionary == MS_DICT_DAUBECHIES && d->npix <= 8192),
+        "the linear PSF operator needs the Daubechies dictionary and npix <= 8192");
     p->d = *d;
     p->d.u = p->d.v = nullptr;
     p->d.flags = nullptr;
@@ -1679,6 +1914,7 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     p->dict = d->dictionary;
     p->M = p->dict == MS_DICT_IUWT ? d->levels + 1 : d->n_bases;   // coefficient planes
     p->prec = d->precision;
+    p->conv = d->convolution;
     p->rsz = p->prec == MS_FP64 ? 8 : 4;
     p->beta = d->es_beta > 0 ? d->es_beta : 2.30 * kW;
     if (d->chunk > 0) {
@@ -1692,6 +1928,7 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     ck(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming), "event");
     ck(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming), "event");
     DISPATCH(p, build_plan<R>(p, d));
+    if (p->conv == MS_CONV_LINEAR) DISPATCH(p, build_linear_psf<R>(p, d));
   });
   if (st != MS_OK) {
     fprintf(stderr, "ms_plan_create: %s\n", p->msg.c_str());
@@ -2011,6 +2248,7 @@ ms_status ms_plan_autotune(const ms_plan_desc* desc, int32_t chan, int32_t reps,
       ms_plan_desc d = *desc;
       d.tile = tiles[ti];
       d.chunk = chunks[ci];
+      d.convolution = MS_CONV_CIRCULAR;   // the gridding layout only
       ms_plan* q = nullptr;
       st = ms_plan_create(&d, &q);
       if (st != MS_OK) break;

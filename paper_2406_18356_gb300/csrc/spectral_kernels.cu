@@ -1312,6 +1312,296 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
   set_lambda_kernel<<<1, 1, 0, s>>>(ctl, rule, coef, n, first);
 }
 
+// ------------------------------------------------- linear PSF operator
+// The minor cycle's PSF operator read as the linear convolution that
+// A^H A / sum(w) is on images of the N x N field:
+//   H x = P F2^-1( H2^ . F2( P^T x ) ),
+// P^T the zero padding to 2N x 2N, P the restriction to the first N x N,
+// F2 the 2N x 2N DFT and H2^ the real spectrum of the PSF on the 2N x 2N
+// field (offsets up to +-N, so no product wraps).  The transforms are
+// cuFFT's; these kernels pad, multiply, restrict and run the iteration
+// control.  With it the smooth parts are no longer diagonal in the N x N
+// Fourier basis, so a FISTA pass evaluates them in the image domain:
+//   LOW:  y_k = H x_k, f = ||y_k - i~||^2, gradient image 2 H r,
+//         r = (1 + t_k) y_k - t_k y_k-1 - i~ (= H z - i~ at the extrapolated
+//         point z, H being linear);
+//   FULL: D_k = y_k - i~, E_k = x_k - l, f = ||G_H D_k||^2 + ||G_L E_k||^2
+//         (Parseval on the N x N half-plane), gradient image
+//         2 (H G_H^2 D_z + G_L^2 E_z) with D_z, E_z the momentum combinations
+//         of the last two spectra.
+// Kernels given a control block return once `done` is set (uniform early
+// exit); with ctl == nullptr they always run (plain operator calls).
+// Row loops: one block per row (grid-stride), threads across the row.
+
+template <typename R>
+__global__ void lin_pad_kernel(const R* __restrict__ x, R* __restrict__ xp, int N,
+                               const FistaCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  const int N2 = 2 * N;
+  for (int row = blockIdx.x; row < N2; row += gridDim.x) {
+    R* out = xp + (int64_t)row * N2;
+    const R* in = x + (int64_t)row * N;
+    for (int c = threadIdx.x; c < N2; c += blockDim.x)
+      out[c] = (row < N && c < N) ? in[c] : (R)0;
+  }
+}
+
+// S *= H2^ / (2N)^2 (the inverse transform is unnormalized)
+template <typename R>
+__global__ void lin_mul_kernel(C2<R>* __restrict__ S, const R* __restrict__ H2, int64_t n, R inv,
+                               const FistaCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const R h = H2[k] * inv;
+    C2<R> v = S[k];
+    v.x *= h;
+    v.y *= h;
+    S[k] = v;
+  }
+}
+
+// out = scale (P q + add), q a 2N x 2N image, add an N x N image or null
+template <typename R>
+__global__ void lin_crop_kernel(const R* __restrict__ q, const R* __restrict__ add,
+                                R* __restrict__ out, int N, R scale,
+                                const FistaCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  const int N2 = 2 * N;
+  for (int row = blockIdx.x; row < N; row += gridDim.x) {
+    const R* qr = q + (int64_t)row * N2;
+    const int64_t o = (int64_t)row * N;
+    for (int c = threadIdx.x; c < N; c += blockDim.x)
+      out[o + c] = scale * (qr[c] + (add ? add[o + c] : (R)0));
+  }
+}
+
+// this thread's share of the |B_k| partials left by the previous analysis
+__device__ __forceinline__ double lin_l1_share(const double* __restrict__ l1_parts, int n_l1) {
+  double l1s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_l1;
+       i += (int64_t)gridDim.x * blockDim.x)
+    l1s += __ldcg(l1_parts + i);
+  return l1s;
+}
+
+template <typename R> __device__ __forceinline__ void kahan_add(R& s, R& c, R y) {
+  y -= c;
+  const R t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// LOW / SINGLE: y_k = P q into ycur, f = ||y_k - i~||^2 (with ||B_k||_1 the
+// iteration control, in the last block), and r = (1 + t_k) y_k - t_k y_k-1 - i~
+// zero-padded into rp
+template <typename R>
+__global__ void lin_low_step_kernel(const R* __restrict__ q, const R* __restrict__ res,
+                                    R* __restrict__ ycur, const R* __restrict__ yprev,
+                                    R* __restrict__ rp, int N, double* __restrict__ parts,
+                                    FistaCtl* __restrict__ ctl, double* __restrict__ trace,
+                                    int32_t* ticket, const double* __restrict__ l1_parts,
+                                    int n_l1) {
+  if (ctl->done) return;   // uniform: `done` changes only in this kernel's last block
+  const int kit = ctl->k;
+  const R t = ctl_t<R>(ctl, kit & 1);
+  const R a = (R)1 + t;
+  const int N2 = 2 * N;
+  const double l1s = lin_l1_share(l1_parts, n_l1);
+  R s0 = 0, c0 = 0;
+  for (int row = blockIdx.x; row < N2; row += gridDim.x) {
+    R* out = rp + (int64_t)row * N2;
+    if (row >= N) {
+      for (int c = threadIdx.x; c < N2; c += blockDim.x) out[c] = (R)0;
+      continue;
+    }
+    const R* qr = q + (int64_t)row * N2;
+    const int64_t o = (int64_t)row * N;
+    for (int c = threadIdx.x; c < N2; c += blockDim.x) {
+      if (c >= N) {
+        out[c] = (R)0;
+        continue;
+      }
+      const R y = qr[c];
+      const R b = res[o + c];
+      const R d = y - b;
+      kahan_add<R>(s0, c0, d * d);
+      out[c] = a * y - t * yprev[o + c] - b;
+      ycur[o + c] = y;
+    }
+  }
+  double v[3];
+  spec_block_sums<R>(s0, c0, (R)0, (R)0, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, v);
+  const bool mx[3] = {false, false, false};
+  if (publish_partials<3>(v, parts, ticket)) {
+    double o[3];
+    gather_partials<3>(o, parts, mx, ticket);
+    if (threadIdx.x == 0) {
+      const double oo[3] = {o[0], 0.0, o[2]};
+      spec_control(oo, ctl, trace);
+    }
+  }
+}
+
+// FULL: D_k = P q - i~ and E_k = x_k - l, stacked [D; E] (N x N each)
+template <typename R>
+__global__ void lin_full_diff_kernel(const R* __restrict__ q, const R* __restrict__ res,
+                                     const R* __restrict__ x, const R* __restrict__ l,
+                                     R* __restrict__ de, int N, const FistaCtl* __restrict__ ctl) {
+  if (ctl && ctl->done) return;
+  const int N2 = 2 * N;
+  const int64_t n2 = (int64_t)N * N;
+  for (int row = blockIdx.x; row < N; row += gridDim.x) {
+    const R* qr = q + (int64_t)row * N2;
+    const int64_t o = (int64_t)row * N;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+      de[o + c] = qr[c] - res[o + c];
+      de[n2 + o + c] = x[o + c] - l[o + c];
+    }
+  }
+}
+
+// FULL, on the N x N half-plane: f = (sum w g_H^2 |D^_k|^2 + w g_L^2 |E^_k|^2) / N^2
+// (w = 1 on columns 0 and N/2, else 2) with the control, and the filtered
+// momentum spectra U^ = g_H^2 ((1 + t) D^_k - t D^_k-1) / N^2,
+// V^ = g_L^2 ((1 + t) E^_k - t E^_k-1) / N^2, stacked [U^; V^].  With ctl ==
+// nullptr (the plain normal operator) t = 0 and no objective.
+template <typename R>
+__global__ void lin_full_spec_kernel(const C2<R>* __restrict__ dek, const C2<R>* __restrict__ dep,
+                                     const R* __restrict__ gl2, const R* __restrict__ gh2,
+                                     C2<R>* __restrict__ uv, int N, double* __restrict__ parts,
+                                     FistaCtl* __restrict__ ctl, double* __restrict__ trace,
+                                     int32_t* ticket, const double* __restrict__ l1_parts,
+                                     int n_l1) {
+  if (ctl && ctl->done) return;
+  const R t = ctl ? ctl_t<R>(ctl, ctl->k & 1) : (R)0;
+  const R a = (R)1 + t;
+  const int nc = N / 2 + 1;
+  const int64_t total = (int64_t)N * nc;
+  const R inv = (R)(1.0 / ((double)N * N));
+  const double l1s = ctl ? lin_l1_share(l1_parts, n_l1) : 0.0;
+  R s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+  for (int row = blockIdx.x; row < N; row += gridDim.x) {
+    for (int col = threadIdx.x; col < nc; col += blockDim.x) {
+      const int64_t k = (int64_t)row * nc + col;
+      const C2<R> D = dek[k], E = dek[total + k];
+      const R gh = gh2[k], gl = gl2[k];
+      C2<R> U, V;
+      if (ctl) {
+        const R w = (col == 0 || col == N / 2) ? (R)1 : (R)2;
+        kahan_add<R>(s0, c0, w * gh * (D.x * D.x + D.y * D.y));
+        kahan_add<R>(s1, c1, w * gl * (E.x * E.x + E.y * E.y));
+        const C2<R> Dp = dep[k], Ep = dep[total + k];
+        U.x = gh * inv * (a * D.x - t * Dp.x);
+        U.y = gh * inv * (a * D.y - t * Dp.y);
+        V.x = gl * inv * (a * E.x - t * Ep.x);
+        V.y = gl * inv * (a * E.y - t * Ep.y);
+      } else {
+        U.x = gh * inv * D.x;
+        U.y = gh * inv * D.y;
+        V.x = gl * inv * E.x;
+        V.y = gl * inv * E.y;
+      }
+      uv[k] = U;
+      uv[total + k] = V;
+    }
+  }
+  if (!ctl) return;
+  double v[3];
+  spec_block_sums<R>(s0, c0, s1, c1, l1s, (int64_t)blockIdx.x * blockDim.x < n_l1, v);
+  const bool mx[3] = {false, false, false};
+  if (publish_partials<3>(v, parts, ticket)) {
+    double o[3];
+    gather_partials<3>(o, parts, mx, ticket);
+    if (threadIdx.x == 0) {
+      const double oo[3] = {(o[0] + o[1]) / ((double)N * N), 0.0, o[2]};
+      spec_control(oo, ctl, trace);
+    }
+  }
+}
+
+// Step size for the linear operator (an upper bound of 2 lambda_max):
+// ||P H P^T|| <= max |H2^|, so theta = 2 M max H2^2 (LOW / SINGLE) or
+// 2 M (max g_H^2 max H2^2 + max g_L^2) (FULL).  Also c0 = 0 (the objective
+// is evaluated directly in the image domain).
+template <typename R>
+__global__ void lin_theta_kernel(const R* __restrict__ H2, int64_t n2, const R* __restrict__ gl2,
+                                 const R* __restrict__ gh2, int64_t nspec, int M,
+                                 double* __restrict__ parts, FistaCtl* __restrict__ ctl,
+                                 int32_t* ticket) {
+  double v[3] = {0.0, 0.0, 0.0};
+  const bool mx[3] = {true, true, true};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t k = first; k < n2; k += stride) {
+    const double h = (double)H2[k];
+    v[0] = fmax(v[0], h * h);
+  }
+  if (gl2)
+    for (int64_t k = first; k < nspec; k += stride) {
+      v[1] = fmax(v[1], (double)gh2[k]);
+      v[2] = fmax(v[2], (double)gl2[k]);
+    }
+  block_reduce<3>(v, mx);
+  if (publish_partials<3>(v, parts, ticket)) {
+    double o[3];
+    gather_partials<3>(o, parts, mx, ticket);
+    if (threadIdx.x == 0) {
+      const double kmax = gl2 ? o[1] * o[0] + o[2] : o[0];
+      ctl->kmax = kmax;
+      ctl->theta = 2.0 * M * kmax;
+      ctl->inv_theta = kmax > 0 ? 1.0 / (2.0 * M * kmax) : 0.0;
+      ctl->c0 = 0.0;
+    }
+  }
+}
+
+namespace {
+int lin_rows_grid(int rows) { return std::max(1, std::min(rows, sm_count() * 8)); }
+}  // namespace
+
+template <typename R>
+void launch_lin_pad(const R* x, R* xp, int N, const FistaCtl* ctl, cudaStream_t s) {
+  lin_pad_kernel<R><<<lin_rows_grid(2 * N), kThreads, 0, s>>>(x, xp, N, ctl);
+}
+template <typename R>
+void launch_lin_mul(C2<R>* S, const R* H2, int N, const FistaCtl* ctl, cudaStream_t s) {
+  const int64_t n = (int64_t)2 * N * (N + 1);
+  const R inv = (R)(1.0 / (4.0 * (double)N * N));
+  lin_mul_kernel<R><<<nparts_for(n), kThreads, 0, s>>>(S, H2, n, inv, ctl);
+}
+template <typename R>
+void launch_lin_crop(const R* q, const R* add, R* out, int N, double scale, const FistaCtl* ctl,
+                     cudaStream_t s) {
+  lin_crop_kernel<R><<<lin_rows_grid(N), kThreads, 0, s>>>(q, add, out, N, (R)scale, ctl);
+}
+template <typename R>
+void launch_lin_low_step(const R* q, const R* res, R* ycur, const R* yprev, R* rp, int N,
+                         double* parts, FistaCtl* ctl, double* trace, int32_t* ticket,
+                         const double* l1_parts, int n_l1, cudaStream_t s) {
+  lin_low_step_kernel<R><<<std::min(2 * N, sm_count() * 4), kThreads, 0, s>>>(
+      q, res, ycur, yprev, rp, N, parts, ctl, trace, ticket, l1_parts, n_l1);
+}
+template <typename R>
+void launch_lin_full_diff(const R* q, const R* res, const R* x, const R* l, R* de, int N,
+                          const FistaCtl* ctl, cudaStream_t s) {
+  lin_full_diff_kernel<R><<<lin_rows_grid(N), kThreads, 0, s>>>(q, res, x, l, de, N, ctl);
+}
+template <typename R>
+void launch_lin_full_spec(const C2<R>* dek, const C2<R>* dep, const R* gl2, const R* gh2,
+                          C2<R>* uv, int N, double* parts, FistaCtl* ctl, double* trace,
+                          int32_t* ticket, const double* l1_parts, int n_l1, cudaStream_t s) {
+  lin_full_spec_kernel<R><<<std::min(N, sm_count() * 4), kThreads, 0, s>>>(
+      dek, dep, gl2, gh2, uv, N, parts, ctl, trace, ticket, l1_parts, n_l1);
+}
+template <typename R>
+void launch_lin_theta(const R* H2, int N, const R* gl2, const R* gh2, int M, double* parts,
+                      FistaCtl* ctl, int32_t* ticket, cudaStream_t s) {
+  const int64_t n2 = (int64_t)2 * N * (N + 1);
+  lin_theta_kernel<R><<<nparts_for(n2), kThreads, 0, s>>>(
+      H2, n2, gl2, gh2, (int64_t)N * (N / 2 + 1), M, parts, ctl, ticket);
+}
+
 #define MS_INST(R)                                                                               \
   template void launch_ifftshift_real<R>(const R*, R*, int, cudaStream_t);                       \
   template void launch_real_part_spectrum<R>(const C2<R>*, R*, int, cudaStream_t);               \
@@ -1340,7 +1630,21 @@ void launch_set_lambda(FistaCtl* ctl, int rule, double coef, int n, int first, c
   template void launch_dot<R>(const R*, const R*, int64_t, double*, double*, int32_t*,           \
                               cudaStream_t);                                                     \
   template void launch_normalize<R>(R*, int64_t, const double*, cudaStream_t);                   \
-  template void launch_hash_fill<R>(R*, int64_t, uint64_t, cudaStream_t);
+  template void launch_hash_fill<R>(R*, int64_t, uint64_t, cudaStream_t);                       \
+  template void launch_lin_pad<R>(const R*, R*, int, const FistaCtl*, cudaStream_t);            \
+  template void launch_lin_mul<R>(C2<R>*, const R*, int, const FistaCtl*, cudaStream_t);        \
+  template void launch_lin_crop<R>(const R*, const R*, R*, int, double, const FistaCtl*,        \
+                                   cudaStream_t);                                                \
+  template void launch_lin_low_step<R>(const R*, const R*, R*, const R*, R*, int, double*,      \
+                                       FistaCtl*, double*, int32_t*, const double*, int,         \
+                                       cudaStream_t);                                            \
+  template void launch_lin_full_diff<R>(const R*, const R*, const R*, const R*, R*, int,        \
+                                        const FistaCtl*, cudaStream_t);                          \
+  template void launch_lin_full_spec<R>(const C2<R>*, const C2<R>*, const R*, const R*, C2<R>*, \
+                                        int, double*, FistaCtl*, double*, int32_t*,              \
+                                        const double*, int, cudaStream_t);                       \
+  template void launch_lin_theta<R>(const R*, int, const R*, const R*, int, double*, FistaCtl*, \
+                                    int32_t*, cudaStream_t);
 
 MS_INST(float)
 MS_INST(double)

@@ -54,18 +54,22 @@ def iterations_to(trace, eps: float) -> int:
 
 
 def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 100,
-          n_major_max: int = 7, fista_budget: int = 2000, grid=None, convergence: bool = True):
-    """Run the study on workload w (synth.Workload with a truth image)."""
+          n_major_max: int = 7, fista_budget: int = 2000, grid=None, convergence: bool = True,
+          convolution: str = "circular"):
+    """Run the study on workload w (synth.Workload with a truth image) with
+    the minor cycle's PSF operator `convolution` ("circular" or "linear")."""
     import torch
     truth = w.truth
     tv = None
     out = {"workload": w.name, "npix": w.npix, "nvis": int(w.nvis), "precision": precision,
-           "schedule": f"{n_major} x {fista_iters}", "partitions": []}
+           "schedule": f"{n_major} x {fista_iters}", "convolution": convolution,
+           "partitions": []}
     grid = grid if grid is not None else partitions(w.npix)
     opts = ms.ReconOptions(n_major=n_major, fista_iters=fista_iters)
     single_done = False
     for ell, delta in grid:
-        plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, ell, delta, precision=precision)
+        plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, ell, delta, precision=precision,
+                       convolution=convolution)
         if tv is None:
             tv = torch.from_numpy(w.vis[0]).cuda()
         vis = tv.to(plan.complex_dtype)
@@ -91,7 +95,8 @@ def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 1
         return out
     # major cycles and FISTA iterations at the middle partition
     ell, delta = grid[len(grid) // 2]
-    plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, ell, delta, precision=precision)
+    plan = ms.Plan(w.u[0], w.v[0], w.npix, w.pixel_size, ell, delta, precision=precision,
+                   convolution=convolution)
     vis = tv.to(plan.complex_dtype)
     curve_two, curve_single = [], []
     for n in range(1, n_major_max + 1):
@@ -122,12 +127,13 @@ def main():
     ap.add_argument("--npix", type=int, default=1024)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--convolution", default="circular", choices=("circular", "linear"))
     args = ap.parse_args()
     import synth
     import paper_2406_18356_gb300 as ms
     ms.load_library()
     w = synth.paper_like(args.npix, seed=args.seed, device="cuda")
-    print(json.dumps(study(ms, w, precision=args.precision)))
+    print(json.dumps(study(ms, w, precision=args.precision, convolution=args.convolution)))
 
 
 if __name__ == "__main__":

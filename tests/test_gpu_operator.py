@@ -233,3 +233,20 @@ def test_large_sampled_degrid_fp32(ms):
     exact = np.exp(-2j * np.pi * (np.outer(w.u[0][idx], l) + np.outer(w.v[0][idx], m))) @ x[p, q]
     assert rel(out[idx], exact) <= 1e-5
     plan.close()
+
+
+def test_plans_of_different_dictionary_sizes_coexist(ms):
+    """The device's Daubechies filter table is shared by every plan on it: a
+    plan with fewer bases built later must leave an earlier plan's
+    transforms intact."""
+    N, J = 32, 3
+    w = synth.tiny(npix=N)
+    big = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px, precision="fp64",
+                  levels=J, n_bases=8)
+    small = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px, precision="fp64",
+                    levels=J, n_bases=1)
+    a = np.random.default_rng(3).standard_normal((8, N, N))
+    syn = big.dictionary_synthesis(cuda(a)).cpu().numpy()
+    assert rel(syn, ow.Dictionary(N, 8, J).synth(a)) <= TOL["fp64"]
+    small.close()
+    big.close()

@@ -82,3 +82,35 @@ def test_major_cycle_convergence_on_a_wide_psf(conv, converges):
         assert norms[-1] < 0.1 * norms[0]
     else:
         assert norms[-1] > norms[1], norms
+
+
+def test_splitmix64_published_outputs():
+    """The generator of the power iteration's start vector: the first outputs
+    of SplitMix64 from state 0, and the first from state 1234567, as the
+    generator's reference implementation prints them."""
+    np.testing.assert_array_equal(
+        osv.splitmix64(3, 0),
+        np.array([0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F], dtype=np.uint64))
+    assert int(osv.splitmix64(1, 1234567)[0]) == 6457827717110365317
+    s = osv.power_start((2, 4, 4))
+    assert s.shape == (2, 4, 4) and np.all(s >= -1.0) and np.all(s < 1.0)
+
+
+def test_linear_step_size_is_the_power_estimate_below_the_bound():
+    """The linear reading's step size: 100 power iterations from the fixed
+    start, within 1 % of 2 M lambda_max (dense eigenvalue of the N x N
+    operator, M lambda_max(K) since W W^H = M I) and below the bound."""
+    N, M = 12, 2
+    u, v, dl = _coverage(N, 200, 5)
+    A = og.GriddedOperator(u, v, N, dl)
+    H2 = osv.psf_spectrum(og.GriddedOperator(u, v, 2 * N, dl).psf())
+    from oracle.wavelets import Dictionary
+    W = Dictionary(N, M, 2)
+    prob = osv.Problem("low", W, osv.psf_spectrum(A.psf()), np.zeros((N, N)), 0.0, Hhat2=H2)
+    K = np.stack([prob.H(prob.H(e.reshape(N, N))).ravel() for e in np.eye(N * N)], axis=1)
+    exact = 2.0 * M * float(np.linalg.eigvalsh(0.5 * (K + K.T))[-1])
+    theta = oi._step_size(prob, None)
+    assert theta <= exact * (1 + 1e-9)
+    assert theta >= 0.99 * exact
+    assert exact <= prob.lipschitz_closed_form()
+    assert oi._step_size(prob, 3.5) == 3.5   # computed once per step
