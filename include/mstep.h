@@ -238,6 +238,46 @@ ms_status ms_degrid_batch(ms_plan* plan, int32_t njobs, const int32_t* chans,
                           const int32_t* parts, const void* const* images,
                           const void* const* vis_obs, void* const* vis_out, void* stream);
 
+/* Batched minor cycles (the batched form's "one CUDA graph per minor
+ * cycle"): njobs independent FISTA problems (Algorithm 1 on Eq. LowRes or
+ * FullRes) of this plan's geometry run together, each pass kernel launched
+ * once over all jobs (blockIdx.z = job) and 8 passes per graph launch, each
+ * job stopping on its own (rel_tol, max_iters).  Job j: step steps[j] on
+ * channel chans[j] (its partition's PSF), residual residuals[j] (dev N*N),
+ * for FULL l_lows[j] (dev N*N), sigma2s[j], eta2s[j] (> 0); lambdas[j];
+ * B_0 = 0.  models_out[j] (dev N*N) receives W beta of the job's last prox
+ * output; stats[j] (may be NULL) its iteration count, objective, lambda,
+ * theta and the batch's elapsed time; traces (host, may be NULL)
+ * [njobs][max_iters + 1] receives F(beta_0..) of each job (entries past
+ * stats[j].iterations + 1 unspecified).  All arrays are HOST arrays of njobs
+ * entries.  The workspace (about 155 MB per job at N = 1024, FP32, M = 8)
+ * grows on demand and is kept.  Needs N a power of two, the Daubechies
+ * dictionary and the circular PSF operator (MS_ERR_UNSUPPORTED otherwise). */
+ms_status ms_minor_cycle_batch(ms_plan* plan, int32_t njobs, const int32_t* steps,
+                               const int32_t* chans, const void* const* residuals,
+                               const void* const* l_lows, const double* lambdas,
+                               const double* sigma2s, const double* eta2s, int32_t max_iters,
+                               double rel_tol, void* const* models_out, ms_stats* stats,
+                               double* traces, void* stream);
+
+/* The method on several channels at once (the batched form): as
+ * ms_reconstruct_two_step / ms_reconstruct_single_step for each channel
+ * chans[j] with visibilities vis[j] (dev complex [nvis], original order),
+ * with every major cycle's residual images through one batched degridding
+ * and gridding pass over all jobs and every minor cycle through the batched
+ * FISTA loop of ms_minor_cycle_batch.  low_out[j] / img_out[j]: dev N*N;
+ * stats[j] (may be NULL): per job (elapsed_ms is the whole call's).
+ * opts->warm_start must be NULL.  Same requirements as
+ * ms_minor_cycle_batch. */
+ms_status ms_reconstruct_two_step_batch(ms_plan* plan, int32_t njobs, const int32_t* chans,
+                                        const void* const* vis, const ms_recon_opts* opts,
+                                        void* const* low_out, void* const* img_out,
+                                        ms_stats* stats, void* stream);
+ms_status ms_reconstruct_single_step_batch(ms_plan* plan, int32_t njobs, const int32_t* chans,
+                                           const void* const* vis, const ms_recon_opts* opts,
+                                           void* const* img_out, ms_stats* stats,
+                                           void* stream);
+
 /* Autotuner of the gridding layout: builds a plan from *desc for every grid
  * tile side T in {16, 32} (dividing 2N) and work-item size in {512, 1024,
  * 2048, 4096, 8192} rows, times `reps` degrid + grid pairs of channel chan's

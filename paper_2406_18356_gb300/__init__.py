@@ -96,6 +96,16 @@ _SIGNATURES = {
                       ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
     "ms_degrid_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                         ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "ms_minor_cycle_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                             ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D), ctypes.POINTER(_D), _I32, _D, ctypes.POINTER(_P),
+                             ctypes.POINTER(ms_stats), ctypes.POINTER(_D), _P],
+    "ms_reconstruct_two_step_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_P),
+                                      ctypes.POINTER(ms_recon_opts), ctypes.POINTER(_P),
+                                      ctypes.POINTER(_P), ctypes.POINTER(ms_stats), _P],
+    "ms_reconstruct_single_step_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_P),
+                                         ctypes.POINTER(ms_recon_opts), ctypes.POINTER(_P),
+                                         ctypes.POINTER(ms_stats), _P],
     "ms_plan_autotune": [ctypes.POINTER(ms_plan_desc), _I32, _I32, ctypes.POINTER(_I32),
                          ctypes.POINTER(_I32), ctypes.POINTER(_D)],
     "ms_residual_image": [_P, _I32, _I32, _P, _P, _P, _P],
@@ -445,6 +455,70 @@ class Plan:
             _stream_handle(stream)))
         return model_out, Stats.from_c(st)
 
+    def minor_cycle_batch(self, jobs, max_iters: int, rel_tol: float = 0.0, outs=None,
+                          stream=None):
+        """Batched minor cycles.  jobs: list of dicts with keys step ("low" /
+        "full" / "single"), residual (dev N*N), lam, and for "full" l_low,
+        sigma2, eta2; optional chan (0).  Returns (models, [Stats]) with each
+        Stats' trace the job's F(beta_0..beta_K)."""
+        n = len(jobs)
+        n2 = self.npix ** 2
+        if outs is None:
+            outs = [self._image() for _ in range(n)]
+        steps = (_I32 * n)(*[STEPS[j["step"]] for j in jobs])
+        chans = (_I32 * n)(*[int(j.get("chan", 0)) for j in jobs])
+        res = (_P * n)(*[self._need(j["residual"], self.real_dtype, n2, "residual") for j in jobs])
+        lows = (_P * n)(*[self._need(j["l_low"], self.real_dtype, n2, "l_low")
+                          if j["step"] == "full" else None for j in jobs])
+        lams = (_D * n)(*[float(j["lam"]) for j in jobs])
+        s2 = (_D * n)(*[float(j.get("sigma2", 0.0)) for j in jobs])
+        e2 = (_D * n)(*[float(j.get("eta2", 0.0)) for j in jobs])
+        op = (_P * n)(*[self._need(o, self.real_dtype, n2, "model_out") for o in outs])
+        st = (ms_stats * n)()
+        traces = np.full((n, max_iters + 1), np.nan)
+        self._check(self._lib.ms_minor_cycle_batch(
+            self._h, n, steps, chans, res, lows, lams, s2, e2, max_iters, rel_tol, op, st,
+            traces.ctypes.data_as(ctypes.POINTER(_D)), _stream_handle(stream)))
+        stats = []
+        for j in range(n):
+            s = Stats.from_c(st[j])
+            s.trace = traces[j, :st[j].iterations + 1].copy()
+            stats.append(s)
+        return outs, stats
+
+    def _recon_batch(self, two: bool, vis, opts, chans, low_outs, outs, stream):
+        opts = opts or ReconOptions()
+        n = len(vis)
+        chans = list(range(n)) if chans is None else list(chans)
+        n2 = self.npix ** 2
+        outs = outs if outs is not None else [self._image() for _ in range(n)]
+        ch = (_I32 * n)(*chans)
+        vp = (_P * n)(*[self._need(v, self.complex_dtype, self.nvis, "vis") for v in vis])
+        op = (_P * n)(*[self._need(o, self.real_dtype, n2, "img_out") for o in outs])
+        st = (ms_stats * n)()
+        co = opts.to_c()
+        if two:
+            low_outs = low_outs if low_outs is not None else [self._image() for _ in range(n)]
+            lp = (_P * n)(*[self._need(o, self.real_dtype, n2, "low_out") for o in low_outs])
+            self._check(self._lib.ms_reconstruct_two_step_batch(
+                self._h, n, ch, vp, ctypes.byref(co), lp, op, st, _stream_handle(stream)))
+        else:
+            self._check(self._lib.ms_reconstruct_single_step_batch(
+                self._h, n, ch, vp, ctypes.byref(co), op, st, _stream_handle(stream)))
+        return low_outs if two else None, outs, [Stats.from_c(st[j]) for j in range(n)]
+
+    def reconstruct_two_step_batch(self, vis, opts: Optional[ReconOptions] = None, chans=None,
+                                   low_outs=None, outs=None, stream=None):
+        """The two-step method on several channels at once: vis[j] is channel
+        chans[j]'s visibilities (default chans = 0..len(vis)-1).  Returns
+        (low images, final images, [Stats])."""
+        return self._recon_batch(True, vis, opts, chans, low_outs, outs, stream)
+
+    def reconstruct_single_step_batch(self, vis, opts: Optional[ReconOptions] = None,
+                                      chans=None, outs=None, stream=None):
+        _, outs, st = self._recon_batch(False, vis, opts, chans, None, outs, stream)
+        return outs, st
+
     def reconstruct_two_step(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
                              low_out=None, out=None, model_out=None, stream=None):
         opts = opts or ReconOptions()
@@ -556,6 +630,21 @@ def ms_grid_batch(plan: Plan, jobs, vis, outs=None, stream=None):
 
 def ms_degrid_batch(plan: Plan, jobs, images, vis_obs=None, outs=None, stream=None):
     return plan.degrid_batch(jobs, images, vis_obs, outs, stream)
+
+
+def ms_minor_cycle_batch(plan: Plan, jobs, max_iters: int, rel_tol: float = 0.0, outs=None,
+                         stream=None):
+    return plan.minor_cycle_batch(jobs, max_iters, rel_tol, outs, stream)
+
+
+def ms_reconstruct_two_step_batch(plan: Plan, vis, opts=None, chans=None, low_outs=None,
+                                  outs=None, stream=None):
+    return plan.reconstruct_two_step_batch(vis, opts, chans, low_outs, outs, stream)
+
+
+def ms_reconstruct_single_step_batch(plan: Plan, vis, opts=None, chans=None, outs=None,
+                                     stream=None):
+    return plan.reconstruct_single_step_batch(vis, opts, chans, outs, stream)
 
 
 def ms_plan_autotune(u, v, npix: int, pixel_size: float, ell_px: float, delta_px: float,

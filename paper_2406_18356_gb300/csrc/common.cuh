@@ -290,6 +290,21 @@ void launch_analysis(const R* x, R* coef, R* tmp, WaveletGeom g, cudaStream_t s)
 struct CoarseGroups {
   int first[kMaxBases + 1];
 };
+// Batched minor cycles: `jobs` independent FISTA problems whose state lives
+// in arrays of equal per-job slices; a kernel's blockIdx.z is its job, and
+// each buffer of job z starts z times its stride (elements) after job 0's.
+// The default (one job, zero strides) is the plain minor cycle.
+struct JobStride {
+  int jobs = 1;
+  int64_t coef = 0;    // coefficient ring entries B_k (M N^2)
+  int64_t img = 0;     // images x, gradient (N^2)
+  int64_t tmp = 0;     // wavelet temporaries
+  int64_t spec = 0;    // half-plane spectra and multipliers (N (N/2+1))
+  int64_t parts = 0;   // reduction partials (doubles)
+  int64_t l1 = 0;      // l1 partials of the analysis levels
+  int64_t trace = 0;   // objective trace entries
+};                     // (the control blocks are consecutive: ctl + z)
+
 template <typename R> struct FistaPass {
   R* B0;
   R* B1;
@@ -304,7 +319,24 @@ template <typename R> struct FistaPass {
   int coarse_budget;   // their shared-memory budget per CTA (bytes)
   CoarseGroups coarse_groups;
   int* coarse_bar;     // group barrier state, two ints per basis, zero at rest
+  JobStride js{};      // batched minor cycles (coarse_ctas must then be 0)
 };
+
+// this block's job's view of a (batched) pass
+template <typename R> __device__ __forceinline__ FistaPass<R> job_slice(FistaPass<R> a) {
+  const int64_t z = blockIdx.z;
+  if (z != 0) {
+    a.B0 += z * a.js.coef;
+    a.B1 += z * a.js.coef;
+    a.B2 += z * a.js.coef;
+    a.grad += z * a.js.img;
+    a.x += z * a.js.img;
+    a.tmp += z * a.js.tmp;
+    a.ctl += z;
+    a.l1_parts += z * a.js.l1;
+  }
+  return a;
+}
 // The minor cycle's synthesis levels (J..1) and analysis + FISTA-update
 // levels (1..J), one launch per level.  only_level: 0 = all levels, j > 0 =
 // level j alone, -1 = all levels but level 1.  The analysis takes an optional
@@ -362,7 +394,7 @@ template <typename R>
 cudaError_t launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks,
                             const C2<R>* Bs, const C2<R>* tw, int N, double* parts,
                             const FistaCtl* ctl, const double* l1_parts, int n_l1,
-                            cudaStream_t s);
+                            cudaStream_t s, const JobStride& js = JobStride{});
 int spec_col_blocks(int N, size_t complex_bytes);   // blocks of one launch (0: N unsupported)
 int spec_col_warps(int N, size_t complex_bytes);    // warps of one launch (0: N unsupported)
 // real row transforms of an N x N image (N a power of two, 16 <= N <= 8192)
@@ -371,13 +403,15 @@ int spec_col_warps(int N, size_t complex_bytes);    // warps of one launch (0: N
 // imaginary parts of columns 0 and N/2; tw as for launch_spec_col; both
 // return at once when ctl->done.  With parts non-null, an extra block of the
 // inverse sums the G warp sums launch_spec_col left and runs the iteration
-// control (objective into trace, ctl update).
+// control (objective into trace, ctl update).  js: the batched form, each
+// job's slices of x, Z (and the spectra), parts, trace and its ctl.
 template <typename R>
 cudaError_t launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
-                           cudaStream_t s);
+                           cudaStream_t s, const JobStride& js = JobStride{});
 template <typename R>
 cudaError_t launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
-                           const double* parts, int G, double* trace, cudaStream_t s);
+                           const double* parts, int G, double* trace, cudaStream_t s,
+                           const JobStride& js = JobStride{});
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)
 size_t row_fft_smem(int N, size_t complex_bytes);
 // dynamic shared memory of a block (SIZE_MAX: N unsupported)

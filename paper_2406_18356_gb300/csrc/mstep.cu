@@ -244,6 +244,32 @@ struct PartDev {
   void* Hhat2 = nullptr;   // real spectrum of the PSF on the 2N x 2N field (linear operator)
 };
 
+// Batched minor cycles: each job's FISTA state as one slice of these arrays
+// (JobStride), so one launch of each pass kernel covers every job; the
+// reconstruct call adds each job's model, residual and l images.
+struct FistaBatch {
+  int cap = 0;         // jobs the arrays hold
+  int trace_cap = 0;   // trace entries per job
+  void* B[3] = {};
+  void *x = nullptr, *y = nullptr, *F[2] = {}, *zrow = nullptr, *Ks = nullptr, *Bs = nullptr;
+  void* tmp = nullptr;
+  void *model = nullptr, *res = nullptr, *l = nullptr;
+  FistaCtl* ctl = nullptr;
+  double *trace = nullptr, *parts = nullptr, *l1 = nullptr;
+  int64_t parts_stride = 0;
+  CUtensorMap gmap{};   // the jobs' gradient images stacked: {N, cap N}
+  bool have_gmap = false;
+  cudaGraphExec_t exec = nullptr;
+  int exec_jobs = 0;
+  void release() {
+    for (void* q : {B[0], B[1], B[2], x, y, F[0], F[1], zrow, Ks, Bs, tmp, model, res, l,
+                    (void*)ctl, (void*)trace, (void*)parts, (void*)l1})
+      if (q) cudaFree(q);
+    if (exec) cudaGraphExecDestroy(exec);
+    *this = FistaBatch{};
+  }
+};
+
 struct ChanDev {
   PartDev part[3];
   int64_t counts[4] = {0, 0, 0, 0};
@@ -325,6 +351,7 @@ struct ms_plan {
   void *lde = nullptr, *ldes[2] = {}, *luvs = nullptr, *luv = nullptr;
   cufftHandle r2c2 = 0, c2r2 = 0, r2cb = 0, c2rb = 0;
   cudaGraphExec_t lin_exec[2] = {};   // captured linear passes: LOW / SINGLE, FULL
+  FistaBatch fb;   // batched minor cycles
   // captured FISTA passes
   cudaGraphExec_t fista_exec = nullptr;
   int fista_graph_step = -1;
@@ -655,11 +682,37 @@ template <typename R> FistaPass<R> fista_pass_args(ms_plan* p) {
   return a;
 }
 
-// One FISTA iteration (Algorithm 1): synthesis x = W B_k (levels J..1),
-// X^_k = F x, the spectral step (objective, iteration control, gradient
-// spectrum with the momentum folded in), the inverse FFT to the gradient
-// image, and analysis + prox into B_{k+1} (levels 1..J).
-// x_k = W B_k into xwork (levels J..1)
+// What one FISTA pass reads and writes beyond the pass arguments: the
+// spectra X^_k / X^_k-1 (by pass parity), the row-transform buffer, K^ and
+// B^, the reduction partials, the objective trace and the gradient's TMA
+// descriptor.  The plain minor cycle uses the plan's buffers; the batched one
+// (a.js.jobs > 1) the per-job slices of its workspace.
+template <typename R> struct PassView {
+  FistaPass<R> a;
+  C2<R>* F[2];
+  C2<R>* zrow;
+  const R* Ks;
+  const C2<R>* Bs;
+  double* parts;
+  double* trace;
+  const CUtensorMap* gmap;
+};
+
+template <typename R> PassView<R> plan_view(ms_plan* p) {
+  PassView<R> v;
+  v.a = fista_pass_args<R>(p);
+  v.F[0] = (C2<R>*)p->F[0];
+  v.F[1] = (C2<R>*)p->F[1];
+  v.zrow = (C2<R>*)p->zrow;
+  v.Ks = (const R*)p->Ks;
+  v.Bs = (const C2<R>*)p->Bs;
+  v.parts = p->parts;
+  v.trace = p->trace;
+  v.gmap = p->have_grad_map ? &p->grad_map : nullptr;
+  return v;
+}
+
+// x_k = W B_k into a.x (levels J..1)
 template <typename R> void record_synthesis(ms_plan* p, const FistaPass<R>& a) {
   if (p->dict == MS_DICT_IUWT) {
     KSpan k(p, MS_K_SYNTH_L1);
@@ -675,16 +728,15 @@ template <typename R> void record_synthesis(ms_plan* p, const FistaPass<R>& a) {
   ck(launch_synthesis_pass<R>(a, p->ps, 1), "synthesis");
 }
 
-// B_k+1 = prox(z_k - mu W^H g) from the gradient image g in ywork (levels 1..J)
-template <typename R> void record_analysis(ms_plan* p, const FistaPass<R>& a) {
+// B_k+1 = prox(z_k - mu W^H g) from the gradient image g in a.grad (levels 1..J)
+template <typename R>
+void record_analysis(ms_plan* p, const FistaPass<R>& a, const CUtensorMap* gmap) {
   if (p->dict == MS_DICT_IUWT) {
     KSpan k(p, MS_K_ANALYSIS_L1);
-    ck(launch_iuwt_analysis<R>(&a, (const R*)p->ywork, nullptr, (R*)p->wtmp, p->N, p->J,
-                               p->ps),
+    ck(launch_iuwt_analysis<R>(&a, a.grad, nullptr, (R*)p->wtmp, p->N, p->J, p->ps),
        "IUWT analysis");
     return;
   }
-  const CUtensorMap* gmap = p->have_grad_map ? &p->grad_map : nullptr;
   {
     KSpan k(p, MS_K_ANALYSIS_L1);
     ck(launch_analysis_pass<R>(a, gmap, p->ps, 1), "analysis");
@@ -695,48 +747,52 @@ template <typename R> void record_analysis(ms_plan* p, const FistaPass<R>& a) {
   }
 }
 
-template <typename R> void record_fista_pass(ms_plan* p, int parity) {
-  C2<R>* Fk = (C2<R>*)p->F[parity];
-  C2<R>* Fo = (C2<R>*)p->F[parity ^ 1];
-  const FistaPass<R> a = fista_pass_args<R>(p);
+// One FISTA iteration (Algorithm 1): synthesis x = W B_k (levels J..1),
+// X^_k = F x, the spectral step (objective, iteration control, gradient
+// spectrum with the momentum folded in), the inverse FFT to the gradient
+// image, and analysis + prox into B_{k+1} (levels 1..J).
+template <typename R> void record_fista_pass(ms_plan* p, int parity, const PassView<R>& v) {
+  C2<R>* Fk = v.F[parity];
+  C2<R>* Fo = v.F[parity ^ 1];
+  const FistaPass<R>& a = v.a;
   record_synthesis<R>(p, a);
   if (p->fused_spec) {
     // row transforms, the spectral step with the column transforms fused in,
     // inverse row transforms (whose extra block runs the iteration control)
     const C2<R>* tw = (const C2<R>*)p->twid;
-    C2<R>* Z = (C2<R>*)p->zrow;
     {
       KSpan k(p, MS_K_FFT_R2C);
-      ck(launch_row_r2c<R>((const R*)p->xwork, Z, tw, p->N, p->ctl, p->ps), "row transforms");
+      ck(launch_row_r2c<R>(a.x, v.zrow, tw, p->N, a.ctl, p->ps, a.js), "row transforms");
     }
     {
       KSpan k(p, MS_K_SPEC_MUL);
-      ck(launch_spec_col<R>(Z, Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs, tw, p->N, p->parts,
-                            p->ctl, p->l1parts, p->n_l1, p->ps),
+      ck(launch_spec_col<R>(v.zrow, Fk, Fo, v.Ks, v.Bs, tw, p->N, v.parts, a.ctl, a.l1_parts,
+                            p->n_l1, p->ps, a.js),
          "spectral step");
     }
     {
       KSpan k(p, MS_K_FFT_C2R);
-      ck(launch_row_c2r<R>(Z, (R*)p->ywork, tw, p->N, p->ctl, p->parts,
-                           spec_col_warps(p->N, sizeof(C2<R>)), p->trace, p->ps),
+      ck(launch_row_c2r<R>(v.zrow, (R*)a.grad, tw, p->N, a.ctl, v.parts,
+                           spec_col_warps(p->N, sizeof(C2<R>)), v.trace, p->ps, a.js),
          "inverse row transforms");
     }
   } else {
+    arg(a.js.jobs == 1, "batched minor cycles need the fused spectral step");
     {
       KSpan k(p, MS_K_FFT_R2C);
-      fft_r2c<R>(p, p->xwork, Fk);
+      fft_r2c<R>(p, a.x, Fk);
     }
     {
       KSpan k(p, MS_K_SPEC_MUL);
-      launch_spec_mul<R>(Fk, Fo, (const R*)p->Ks, (const C2<R>*)p->Bs, p->N, p->parts, p->ctl,
-                         p->trace, p->tickets + 0, p->l1parts, p->n_l1, p->ps);
+      launch_spec_mul<R>(Fk, Fo, v.Ks, v.Bs, p->N, v.parts, a.ctl, v.trace, p->tickets + 0,
+                         a.l1_parts, p->n_l1, p->ps);
     }
     {
       KSpan k(p, MS_K_FFT_C2R);
-      fft_c2r<R>(p, Fo, p->ywork);   // gradient image 2 (K W alpha_k - b)
+      fft_c2r<R>(p, Fo, (R*)a.grad);   // gradient image 2 (K W alpha_k - b)
     }
   }
-  record_analysis<R>(p, a);
+  record_analysis<R>(p, a, v.gmap);
 }
 
 // q = P^T-padded x through the 2N x 2N product with H2^ (lq holds the 2N x 2N
@@ -786,14 +842,14 @@ template <typename R> void record_linear_pass(ms_plan* p, int parity, bool full)
     launch_lin_crop<R>((const R*)p->lq, (const R*)p->luv + n2, (R*)p->ywork, N, 2.0, p->ctl,
                        p->ps);
   }
-  record_analysis<R>(p, a);
+  record_analysis<R>(p, a, p->have_grad_map ? &p->grad_map : nullptr);
 }
 
 template <typename R> void record_pass(ms_plan* p, int parity, int step) {
   if (p->conv == MS_CONV_LINEAR)
     record_linear_pass<R>(p, parity, step == MS_STEP_FULL);
   else
-    record_fista_pass<R>(p, parity);
+    record_fista_pass<R>(p, parity, plan_view<R>(p));
 }
 
 // the graph of kPasses passes of `step` (one for the circular operator;
@@ -911,7 +967,8 @@ template <typename R> void power_theta(ms_plan* p, int iters, bool full) {
 // step: LOW/SINGLE use the partition PSF only; FULL adds the filters built
 // from ctl->sigma2, ctl->eta2.
 template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, double ell,
-                                        double delta) {
+                                        double delta, FistaCtl* ctl = nullptr,
+                                        R* Ks = nullptr) {
   ensure_psf<R>(p, pd);
   if (p->conv == MS_CONV_LINEAR) {
     // the problem's H2^ into the buffer the captured passes read
@@ -933,19 +990,39 @@ template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, doubl
     set_theta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->scal + 2);
     return;
   }
+  // (a batched job's own control block and K^ slice, else the plan's)
+  FistaCtl* c = ctl ? ctl : p->ctl;
+  R* K = Ks ? Ks : (R*)p->Ks;
   if (step == MS_STEP_FULL) {
-    check_noise_kernel<<<1, 1, 0, p->ps>>>(p->ctl);
-    launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
+    check_noise_kernel<<<1, 1, 0, p->ps>>>(c);
+    launch_filters<R>(p->N, ell, delta, c, (R*)p->gl2, (R*)p->gh2, p->ps);
     launch_normal_spectrum<R>((const R*)pd.Hhat, (const R*)p->gl2, (const R*)p->gh2, p->N, p->M,
-                              (R*)p->Ks, p->parts, p->ctl, p->tickets + 2, p->ps);
+                              K, p->parts, c, p->tickets + 2, p->ps);
   } else {
-    launch_normal_spectrum<R>((const R*)pd.Hhat, nullptr, nullptr, p->N, p->M, (R*)p->Ks,
-                              p->parts, p->ctl, p->tickets + 2, p->ps);
+    launch_normal_spectrum<R>((const R*)pd.Hhat, nullptr, nullptr, p->N, p->M, K, p->parts, c,
+                              p->tickets + 2, p->ps);
   }
   if (p->dict == MS_DICT_IUWT) {
     // no closed form (T^H T is not a multiple of I): power iteration
     power_theta<R>(p, kPowerIterations, false);
     set_theta_kernel<<<1, 1, 0, p->ps>>>(p->ctl, p->scal + 2);
+  }
+}
+
+// b^ and c0 of the circular operator's problem from the residual (and l_low
+// for FULL; the filters of build_normal) into Bs and ctl
+template <typename R>
+void build_b(ms_plan* p, int step, PartDev& pd, const void* residual, const void* l_low,
+             FistaCtl* ctl, C2<R>* Bs) {
+  fft_r2c<R>(p, residual, p->spec);
+  if (step == MS_STEP_FULL) {
+    fft_r2c<R>(p, l_low, p->spec2);
+    launch_b_spectrum<R>((const C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)pd.Hhat,
+                         (const R*)p->gl2, (const R*)p->gh2, p->N, Bs, p->parts, ctl,
+                         p->tickets + 3, p->ps);
+  } else {
+    launch_b_spectrum<R>((const C2<R>*)p->spec, nullptr, (const R*)pd.Hhat, nullptr, nullptr,
+                         p->N, Bs, p->parts, ctl, p->tickets + 3, p->ps);
   }
 }
 
@@ -970,16 +1047,8 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     } else {
       ck(cudaMemsetAsync(p->ly[1], 0, sizeof(R) * npix2, p->ps), "memset");
     }
-  } else if (step == MS_STEP_FULL) {
-    fft_r2c<R>(p, residual, p->spec);
-    fft_r2c<R>(p, l_low, p->spec2);
-    launch_b_spectrum<R>((const C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)pd.Hhat,
-                         (const R*)p->gl2, (const R*)p->gh2, N, (C2<R>*)p->Bs, p->parts, p->ctl,
-                         p->tickets + 3, p->ps);
   } else {
-    fft_r2c<R>(p, residual, p->spec);
-    launch_b_spectrum<R>((const C2<R>*)p->spec, nullptr, (const R*)pd.Hhat, nullptr, nullptr, N,
-                         (C2<R>*)p->Bs, p->parts, p->ctl, p->tickets + 3, p->ps);
+    build_b<R>(p, step, pd, residual, l_low, p->ctl, (C2<R>*)p->Bs);
   }
   // B[0] = start, B[2] = B[0] and X^_{-1} = 0 (their weight is zero for k < 2)
   ck(cudaMemsetAsync(p->F[1], 0, sizeof(C2<R>) * nspec, p->ps), "memset");
@@ -1557,6 +1626,7 @@ void destroy(ms_plan* p) {
   DeviceGuard guard;
   cudaSetDevice(p->dev);
   drop_graphs(p);
+  p->fb.release();
   for (cufftHandle h : {p->c2c, p->r2c, p->c2r, p->r2c2, p->c2r2, p->r2cb, p->c2rb})
     if (h) cufftDestroy(h);
   for (void* a : p->allocs) cudaFree(a);
@@ -1792,6 +1862,434 @@ void degrid_batch(ms_plan* p, int njobs, const int32_t* chans, const int32_t* pa
                            p->Ng, p->T, p->ntx, p->beta, p->err, p->ps);
   }
   launch_batch_scatter<R>(jd, njobs, sh.max_n, p->ps);
+}
+
+// ------------------------------------------------- batched minor cycles
+// Grow the batched FISTA workspace to `jobs` jobs of up to max_iters
+// iterations (frees and reallocates everything when it grows).
+template <typename R> void ensure_fista_batch(ms_plan* p, int jobs, int max_iters) {
+  FistaBatch& F = p->fb;
+  if (jobs <= F.cap && max_iters + 2 <= F.trace_cap) return;
+  const int cap = std::max(jobs, F.cap);
+  const int tcap = std::max({max_iters + 2, F.trace_cap, 1024});
+  F.release();
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1), ncoef = (int64_t)p->M * n2;
+  for (auto& b : F.B) b = dalloc<R>(ncoef * cap, "batch coefficients");
+  F.x = dalloc<R>(n2 * cap, "batch images");
+  F.y = dalloc<R>(n2 * cap, "batch images");
+  for (auto& f : F.F) f = dalloc<C2<R>>(nspec * cap, "batch spectra");
+  F.zrow = dalloc<C2<R>>(nspec * cap, "batch spectra");
+  F.Ks = dalloc<R>(nspec * cap, "batch spectra");
+  F.Bs = dalloc<C2<R>>(nspec * cap, "batch spectra");
+  F.tmp = dalloc<R>(ncoef * cap, "batch wavelet tmp");
+  F.model = dalloc<R>(n2 * cap, "batch images");
+  F.res = dalloc<R>(n2 * cap, "batch images");
+  F.l = dalloc<R>(n2 * cap, "batch images");
+  F.ctl = dalloc<FistaCtl>(cap, "batch control");
+  F.trace = dalloc<double>((int64_t)tcap * cap, "batch trace");
+  F.parts_stride = std::max(4096, 3 * spec_col_warps(N, sizeof(C2<R>)));
+  F.parts = dalloc<double>(F.parts_stride * cap, "batch partials");
+  F.l1 = dalloc<double>((int64_t)p->n_l1 * cap, "batch partials");
+  ck(cudaMemset(F.ctl, 0, sizeof(FistaCtl) * cap), "memset");
+  F.cap = cap;
+  F.trace_cap = tcap;
+  // the stacked gradient images for the level-1 analysis's TMA window loads
+  unsigned bc = 0, br = 0;
+  analysis_window_box(&bc, &br);
+  if (p->have_grad_map && (unsigned)N >= bc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    ck(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                        &q),
+       "driver entry point");
+    arg(fn != nullptr && q == cudaDriverEntryPointSuccess, "cuTensorMapEncodeTiled unavailable");
+    cuuint64_t gd[2] = {(cuuint64_t)N, (cuuint64_t)N * cap};
+    cuuint64_t gs[1] = {(cuuint64_t)N * sizeof(R)};
+    cuuint32_t gb[2] = {bc, br};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = ((EncodeTiledFn)fn)(
+        &F.gmap, sizeof(R) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+        2, F.y, gd, gs, gb, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Fail{MS_ERR_CUDA, "cuTensorMapEncodeTiled failed (batch)"};
+    F.have_gmap = true;
+  }
+}
+
+template <typename R> PassView<R> batch_view(ms_plan* p, int jobs) {
+  FistaBatch& F = p->fb;
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
+  PassView<R> v;
+  v.a = fista_pass_args<R>(p);
+  v.a.B0 = (R*)F.B[0];
+  v.a.B1 = (R*)F.B[1];
+  v.a.B2 = (R*)F.B[2];
+  v.a.grad = (const R*)F.y;
+  v.a.x = (R*)F.x;
+  v.a.tmp = (R*)F.tmp;
+  v.a.ctl = F.ctl;
+  v.a.l1_parts = F.l1;
+  v.a.coarse_ctas = 0;   // per-level launches: a cooperative launch cannot hold every job
+  JobStride& js = v.a.js;
+  js.jobs = jobs;
+  js.coef = (int64_t)p->M * n2;
+  js.img = n2;
+  js.tmp = (int64_t)p->M * n2;
+  js.spec = nspec;
+  js.parts = F.parts_stride;
+  js.l1 = p->n_l1;
+  js.trace = F.trace_cap;
+  v.F[0] = (C2<R>*)F.F[0];
+  v.F[1] = (C2<R>*)F.F[1];
+  v.zrow = (C2<R>*)F.zrow;
+  v.Ks = (const R*)F.Ks;
+  v.Bs = (const C2<R>*)F.Bs;
+  v.parts = F.parts;
+  v.trace = F.trace;
+  v.gmap = F.have_gmap ? &F.gmap : nullptr;
+  return v;
+}
+
+void check_batchable(ms_plan* p) {
+  if (!p->fused_spec || p->dict != MS_DICT_DAUBECHIES || p->conv != MS_CONV_CIRCULAR)
+    throw Fail{MS_ERR_UNSUPPORTED,
+               "batched minor cycles need N a power of two, the Daubechies dictionary and the "
+               "circular PSF operator"};
+}
+
+// The FISTA loop of `jobs` set-up problems (each job's control block, K^ and
+// b^ slices ready): B_0 = 0, kPasses passes per graph launch, each kernel
+// over all jobs; a job whose control block says done skips its share.
+template <typename R> void run_fista_batch(ms_plan* p, int jobs, int max_iters, double rel_tol) {
+  FistaBatch& F = p->fb;
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
+  const int64_t ncoef = (int64_t)p->M * n2;
+  ck(cudaMemsetAsync(F.B[0], 0, sizeof(R) * ncoef * jobs, p->ps), "memset");
+  ck(cudaMemsetAsync(F.B[2], 0, sizeof(R) * ncoef * jobs, p->ps), "memset");
+  ck(cudaMemsetAsync(F.F[1], 0, sizeof(C2<R>) * nspec * jobs, p->ps), "memset");
+  ck(cudaMemsetAsync(F.l1, 0, sizeof(double) * p->n_l1 * jobs, p->ps), "memset");   // ||B_0||_1
+  for (int j = 0; j < jobs; ++j) set_target_kernel<<<1, 1, 0, p->ps>>>(F.ctl + j, p->obj_target);
+  const PassView<R> v = batch_view<R>(p, jobs);
+  const bool poll = rel_tol > 0 || std::isfinite(p->obj_target);
+  std::vector<FistaCtl> h(jobs);
+  auto all_done = [&]() {
+    ck(cudaMemcpyAsync(h.data(), F.ctl, sizeof(FistaCtl) * jobs, cudaMemcpyDeviceToHost, p->ps),
+       "read ctl");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    for (const FistaCtl& c : h)
+      if (!c.done) return false;
+    return true;
+  };
+  const int passes = max_iters + 1;
+  if (p->prof) {
+    for (int i = 0; i < passes; ++i) {
+      record_fista_pass<R>(p, i & 1, v);
+      if ((i + 1) % kPasses == 0 && p->pending.size() > 4096) harvest(p);
+      if (poll && (i + 1) % (4 * kPasses) == 0 && i + 1 < passes && all_done()) break;
+    }
+    return;
+  }
+  if (F.exec && F.exec_jobs != jobs) {
+    cudaGraphExecDestroy(F.exec);
+    F.exec = nullptr;
+  }
+  if (!F.exec) {
+    cudaGraph_t graph;
+    ck(cudaStreamBeginCapture(p->ps, cudaStreamCaptureModeThreadLocal), "begin capture");
+    p->capturing = true;
+    try {
+      for (int i = 0; i < kPasses; ++i) record_fista_pass<R>(p, i & 1, v);
+    } catch (...) {
+      p->capturing = false;
+      cudaStreamEndCapture(p->ps, &graph);
+      throw;
+    }
+    p->capturing = false;
+    ck(cudaStreamEndCapture(p->ps, &graph), "end capture");
+    ck(cudaGraphInstantiate(&F.exec, graph, 0), "graph instantiate");
+    cudaGraphDestroy(graph);
+    F.exec_jobs = jobs;
+  }
+  int launched = 0;
+  while (launched < passes) {
+    ck(cudaGraphLaunch(F.exec, p->ps), "graph launch");
+    launched += kPasses;
+    if (poll && launched < passes && (launched / kPasses) % 4 == 0 && all_done()) break;
+  }
+}
+
+// job j's results: the statistics (and, with copy_trace, its trace)
+template <typename R> void batch_stats(ms_plan* p, int jobs, ms_stats* stats) {
+  if (!stats) return;
+  FistaBatch& F = p->fb;
+  std::vector<FistaCtl> h(jobs);
+  ck(cudaMemcpyAsync(h.data(), F.ctl, sizeof(FistaCtl) * jobs, cudaMemcpyDeviceToHost, p->ps),
+     "read ctl");
+  ck(cudaStreamSynchronize(p->ps), "synchronize");
+  for (int j = 0; j < jobs; ++j) {
+    if (h[j].error)
+      throw Fail{(ms_status)h[j].error, "non-finite objective or invalid noise levels"};
+    ms_stats& st = stats[j];
+    st.iterations = h[j].k;
+    st.converged = h[j].converged;
+    st.objective = h[j].F_cur;
+    st.lambda = h[j].lam;
+    st.theta = h[j].theta;
+    st.sigma2 = h[j].sigma2;
+    st.eta2 = h[j].eta2;
+    st.objective_trace = nullptr;
+  }
+}
+
+// ms_minor_cycle_batch: set up each job's problem, run the batched loop,
+// copy each job's model image out
+template <typename R>
+void minor_cycle_batch(ms_plan* p, int njobs, const int32_t* steps, const int32_t* chans,
+                       const void* const* residuals, const void* const* l_lows,
+                       const double* lambdas, const double* sigma2s, const double* eta2s,
+                       int max_iters, double rel_tol, void* const* models_out, ms_stats* stats,
+                       double* traces) {
+  check_batchable(p);
+  arg(njobs >= 1 && njobs <= 4096, "njobs must be 1..4096");
+  arg(steps && chans && residuals && lambdas && models_out, "a required array is NULL");
+  arg(max_iters >= 1 && max_iters <= 1000000, "max_iters must be 1..1e6");
+  ensure_fista_batch<R>(p, njobs, max_iters);
+  FistaBatch& F = p->fb;
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
+  for (int j = 0; j < njobs; ++j) {
+    const int step = steps[j];
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
+    arg(residuals[j] && models_out[j], "a job's residual or model pointer is NULL");
+    const bool full = step == MS_STEP_FULL;
+    arg(!full || (l_lows && l_lows[j] && sigma2s && eta2s), "FULL jobs need l_low, sigma2, eta2");
+    arg(lambdas[j] >= 0 && std::isfinite(lambdas[j]), "lambda must be finite and >= 0");
+    PartDev& pd = part_of(p, step_part(step), chans[j]);
+    FistaCtl* c = F.ctl + j;
+    init_ctl_kernel<<<1, 1, 0, p->ps>>>(c, max_iters, rel_tol, lambdas[j], 1,
+                                        full ? sigma2s[j] : 0.0, full ? eta2s[j] : 0.0,
+                                        full ? 1 : 0);
+    build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px, c, (R*)F.Ks + j * nspec);
+    build_b<R>(p, step, pd, residuals[j], full ? l_lows[j] : nullptr, c,
+               (C2<R>*)F.Bs + j * nspec);
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaEventRecord(e0, p->ps), "event");
+  run_fista_batch<R>(p, njobs, max_iters, rel_tol);
+  ck(cudaEventRecord(e1, p->ps), "event");
+  for (int j = 0; j < njobs; ++j)
+    ck(cudaMemcpyAsync(models_out[j], (R*)F.x + j * n2, sizeof(R) * n2, cudaMemcpyDeviceToDevice,
+                       p->ps),
+       "copy");
+  if (traces)   // [njobs][max_iters + 1], F(beta_0..) of each job (NaN past its last)
+    for (int j = 0; j < njobs; ++j)
+      ck(cudaMemcpyAsync(traces + (int64_t)j * (max_iters + 1), F.trace + (int64_t)j * F.trace_cap,
+                         sizeof(double) * (max_iters + 1), cudaMemcpyDeviceToHost, p->ps),
+         "copy");
+  batch_stats<R>(p, njobs, stats);
+  float ms = 0;
+  ck(cudaEventSynchronize(e1), "event");
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int j = 0; j < njobs; ++j) {
+      stats[j].elapsed_ms = stats[j].minor_ms = ms;
+      stats[j].total_iterations = stats[j].iterations;
+    }
+}
+
+// residual images of several channels' partition `part` at once: jobs j get
+// obs = vis[j] (original order), model models + j N^2, residual res + j N^2;
+// one pad / FFT / degridding launch over all jobs, then the residual rows
+// (left in plan order) through one gridding / fold / FFT / crop
+template <typename R>
+void residual_batch(ms_plan* p, int njobs, const int32_t* chans, int part,
+                    const void* const* vis, const R* models, R* res) {
+  const int64_t n2 = (int64_t)p->N * p->N;
+  std::vector<int32_t> parts(njobs, part);
+  std::vector<BatchJob<R>> jobs;
+  const BatchShape sh = batch_jobs<R>(p, njobs, chans, parts.data(), jobs);
+  for (int j = 0; j < njobs; ++j) {
+    arg(vis[j] != nullptr, "a job's visibilities are NULL");
+    jobs[j].user_in = (const C2<R>*)vis[j];
+    jobs[j].image_in = models + j * n2;
+    jobs[j].image_out = res + j * n2;
+  }
+  batch_reserve<R>(p, sh);
+  batch_upload<R>(p, sh, jobs);
+  const BatchJob<R>* jd = (const BatchJob<R>*)p->batch.jobs;
+  launch_batch_gather<R>(jd, njobs, sh.max_n, p->ps);
+  {
+    KSpan k(p, MS_K_PAD_CROP);
+    launch_pad_batch<R>(jd, njobs, (const R*)p->psi, p->N, p->Ng, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    batch_fft<R>(p, CUFFT_FORWARD);
+  }
+  {
+    KSpan k(p, MS_K_DEGRID);
+    launch_degrid_batch<R>(&p->batch.tmap, jd, p->batch.job_of, (int)sh.items, true, p->Ng,
+                           p->T, p->ntx, p->beta, p->err, p->ps);
+  }
+  // grid the residual rows obs - A x where the degridding left them
+  for (auto& b : jobs) std::swap(b.sorted_in, b.sorted_out);
+  ck(cudaMemcpyAsync(p->batch.jobs, jobs.data(), sizeof(BatchJob<R>) * njobs,
+                     cudaMemcpyHostToDevice, p->ps),
+     "job table");
+  {
+    KSpan k(p, MS_K_GRID);
+    if (p->prec == MS_FP32_KAHAN)
+      launch_grid_batch<float, true>((const BatchJob<float>*)jd, p->batch.job_of, (int)sh.items,
+                                     p->batch.scratch, p->T, p->ntx, p->beta, p->ps);
+    else
+      launch_grid_batch<R, false>(jd, p->batch.job_of, (int)sh.items, p->batch.scratch, p->T,
+                                  p->ntx, p->beta, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FOLD);
+    if (p->prec == MS_FP32_KAHAN)
+      launch_fold_batch<float, true>((const BatchJob<float>*)jd, njobs, p->batch.scratch, p->Ng,
+                                     p->T, p->ntx, p->ps);
+    else
+      launch_fold_batch<R, false>(jd, njobs, p->batch.scratch, p->Ng, p->T, p->ntx, p->ps);
+  }
+  {
+    KSpan k(p, MS_K_FFT_GRID);
+    batch_fft<R>(p, CUFFT_INVERSE);
+  }
+  KSpan k(p, MS_K_PAD_CROP);
+  launch_crop_batch<R>(jd, njobs, (const R*)p->psi, p->N, p->Ng, p->ps);
+}
+
+// One step of the method (as run_step) for several channels at once: the
+// major cycles' residuals through residual_batch, every minor cycle through
+// the batched FISTA loop.  low_images: i^_L of each job (FULL); out: each
+// job's final image.
+template <typename R>
+void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
+                    const void* const* vis, const ms_recon_opts& o,
+                    const void* const* low_images, void* const* out, ms_stats* stats) {
+  FistaBatch& F = p->fb;
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
+  const int part = step_part(step);
+  const bool full = step == MS_STEP_FULL;
+  R* model = (R*)F.model;
+  R* res = (R*)F.res;
+  R* l = (R*)F.l;
+  ck(cudaMemsetAsync(model, 0, sizeof(R) * n2 * njobs, p->ps), "memset");
+  const double coef = step == MS_STEP_LOW ? o.lambda_low
+                      : full ? o.lambda_full : o.lambda_single;
+  std::vector<FistaCtl> h(njobs);
+  for (int n = 1; n <= o.n_major; ++n) {
+    residual_batch<R>(p, njobs, chans, part, vis, model, res);
+    for (int j = 0; j < njobs; ++j) {
+      FistaCtl* c = F.ctl + j;
+      R* rj = res + j * n2;
+      PartDev& pd = part_of(p, part, chans[j]);
+      launch_image_norms<R>(rj, n2, p->parts, c, p->tickets + 5, p->ps);
+      if (n == 1) {
+        init_ctl_kernel<<<1, 1, 0, p->ps>>>(
+            c, o.fista_iters, o.rel_tol, 0.0, 0, o.sigma2,
+            o.sigma2 > 0 && o.eta2 > 0 ? o.eta2 : 1e-3 * o.sigma2, o.sigma2 > 0 ? 1 : 0);
+        if (full && !(o.sigma2 > 0)) {
+          launch_sigma2_hat<R>(rj, N, p->parts, c, p->tickets + 6, o.eta2 > 0 ? 0 : 1, p->ps);
+          if (o.eta2 > 0) set_eta_kernel<<<1, 1, 0, p->ps>>>(c, o.eta2);
+        }
+        build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px, c, (R*)F.Ks + j * nspec);
+      }
+      init_ctl_kernel<<<1, 1, 0, p->ps>>>(c, o.fista_iters, o.rel_tol, 0.0, 0, 0, 0, 0);
+      launch_set_lambda(c, o.lambda_rule, coef, n, n == 1 ? 1 : 0, p->ps);
+      if (full) {
+        // l = i^_L - sum i_j, and this job's filters for b^
+        launch_axpby<R>((const R*)low_images[j], model + j * n2, l + j * n2, 1.0, -1.0, n2,
+                        p->ps);
+        launch_filters<R>(N, p->d.ell_px, p->d.delta_px, c, (R*)p->gl2, (R*)p->gh2, p->ps);
+      }
+      build_b<R>(p, step, pd, rj, full ? l + j * n2 : nullptr, c, (C2<R>*)F.Bs + j * nspec);
+    }
+    run_fista_batch<R>(p, njobs, o.fista_iters, o.rel_tol);
+    launch_axpby<R>(model, (const R*)F.x, model, 1.0, 1.0, n2 * njobs, p->ps);   // i^ += W beta
+    ck(cudaMemcpyAsync(h.data(), F.ctl, sizeof(FistaCtl) * njobs, cudaMemcpyDeviceToHost, p->ps),
+       "read ctl");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    for (int j = 0; j < njobs; ++j) {
+      if (h[j].error)
+        throw Fail{(ms_status)h[j].error, "non-finite objective or invalid noise levels"};
+      if (stats) {
+        stats[j].total_iterations += h[j].k;
+        stats[j].gridded_vis += part_of(p, part, chans[j]).n;
+      }
+    }
+  }
+  residual_batch<R>(p, njobs, chans, part, vis, model, res);   // i~_{N+1}
+  for (int j = 0; j < njobs; ++j) {
+    launch_axpby<R>(res + j * n2, model + j * n2, (R*)out[j], 1.0, 1.0, n2, p->ps);
+    if (stats) {
+      stats[j].gridded_vis += part_of(p, part, chans[j]).n;
+      stats[j].major_cycles += o.n_major;
+      stats[j].iterations = h[j].k;
+      stats[j].converged = h[j].converged;
+      stats[j].objective = h[j].F_cur;
+      stats[j].lambda = h[j].lam;
+      stats[j].theta = h[j].theta;
+      stats[j].sigma2 = h[j].sigma2;
+      stats[j].eta2 = h[j].eta2;
+    }
+  }
+}
+
+// ms_reconstruct_two_step_batch / ms_reconstruct_single_step_batch
+template <typename R>
+void reconstruct_batch(ms_plan* p, bool two, int njobs, const int32_t* chans,
+                       const void* const* vis, const ms_recon_opts* o, void* const* low_out,
+                       void* const* img_out, ms_stats* stats, void* stream) {
+  check_batchable(p);
+  validate_opts(o);
+  arg(o->warm_start == nullptr, "the batched calls take no warm start network");
+  arg(njobs >= 1 && njobs <= 4096, "njobs must be 1..4096");
+  arg(chans && vis && img_out && (!two || low_out), "a required array is NULL");
+  for (int j = 0; j < njobs; ++j) {
+    arg(chans[j] >= 0 && chans[j] < (int)p->ch.size(), "channel out of range");
+    arg(vis[j] && img_out[j] && (!two || low_out[j]), "a job's buffer is NULL");
+    const ChanDev& c = p->ch[chans[j]];
+    if (two)
+      arg(c.part[MS_PART_L].n > 0 && c.part[MS_PART_H].n > 0,
+          "both partitions need visibilities");
+    else
+      arg(c.part[MS_PART_ALL].n > 0, "no visibilities");
+  }
+  Scope sc(p, stream);
+  if (stats) std::memset(stats, 0, sizeof(ms_stats) * njobs);
+  ensure_fista_batch<R>(p, njobs, o->fista_iters);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaEventRecord(e0, p->ps), "event");
+  if (two) {
+    run_step_batch<R>(p, MS_STEP_LOW, njobs, chans, vis, *o, nullptr, low_out, stats);
+    run_step_batch<R>(p, MS_STEP_FULL, njobs, chans, vis, *o, (const void* const*)low_out,
+                      img_out, stats);
+  } else {
+    run_step_batch<R>(p, MS_STEP_SINGLE, njobs, chans, vis, *o, nullptr, img_out, stats);
+  }
+  ck(cudaEventRecord(e1, p->ps), "event");
+  check_device_error(p);
+  float ms = 0;
+  ck(cudaEventSynchronize(e1), "event");
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int j = 0; j < njobs; ++j) stats[j].elapsed_ms = ms;
+  sc.finish();
 }
 
 }  // namespace
@@ -2216,6 +2714,42 @@ ms_status ms_grid_batch(ms_plan* p, int32_t njobs, const int32_t* chans, const i
     Scope sc(p, stream);
     DISPATCH(p, grid_batch<R>(p, njobs, chans, parts, vis, dirty));
     sc.finish();
+  });
+}
+
+ms_status ms_minor_cycle_batch(ms_plan* p, int32_t njobs, const int32_t* steps,
+                               const int32_t* chans, const void* const* residuals,
+                               const void* const* l_lows, const double* lambdas,
+                               const double* sigma2s, const double* eta2s, int32_t max_iters,
+                               double rel_tol, void* const* models_out, ms_stats* stats,
+                               double* traces, void* stream) {
+  return guarded(p, [&] {
+    arg(rel_tol >= 0, "rel_tol must be >= 0");
+    if (stats && njobs > 0) std::memset(stats, 0, sizeof(ms_stats) * njobs);
+    Scope sc(p, stream);
+    DISPATCH(p, minor_cycle_batch<R>(p, njobs, steps, chans, residuals, l_lows, lambdas, sigma2s,
+                                     eta2s, max_iters, rel_tol, models_out, stats, traces));
+    sc.finish();
+  });
+}
+
+ms_status ms_reconstruct_two_step_batch(ms_plan* p, int32_t njobs, const int32_t* chans,
+                                        const void* const* vis, const ms_recon_opts* o,
+                                        void* const* low_out, void* const* img_out,
+                                        ms_stats* stats, void* stream) {
+  return guarded(p, [&] {
+    DISPATCH(p, reconstruct_batch<R>(p, true, njobs, chans, vis, o, low_out, img_out, stats,
+                                     stream));
+  });
+}
+
+ms_status ms_reconstruct_single_step_batch(ms_plan* p, int32_t njobs, const int32_t* chans,
+                                           const void* const* vis, const ms_recon_opts* o,
+                                           void* const* img_out, ms_stats* stats,
+                                           void* stream) {
+  return guarded(p, [&] {
+    DISPATCH(p, reconstruct_batch<R>(p, false, njobs, chans, vis, o, nullptr, img_out, stats,
+                                     stream));
   });
 }
 

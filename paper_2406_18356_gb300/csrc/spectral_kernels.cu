@@ -640,8 +640,19 @@ __global__ void __launch_bounds__(ColCfg<R, LOGN>::THREADS, 1) spec_col_kernel(
     C2<R>* __restrict__ Z, C2<R>* __restrict__ Xk, const C2<R>* __restrict__ Xprev,
     const R* __restrict__ Ks, const C2<R>* __restrict__ Bs, const C2<R>* __restrict__ tw_g,
     double* __restrict__ parts, const FistaCtl* __restrict__ ctl,
-    const double* __restrict__ l1_parts, int n_l1) {
+    const double* __restrict__ l1_parts, int n_l1, JobStride js) {
   using Cfg = ColCfg<R, LOGN>;
+  if (blockIdx.z != 0) {   // this block's job (batched form)
+    const int64_t z = blockIdx.z;
+    Z += z * js.spec;
+    Xk += z * js.spec;
+    Xprev += z * js.spec;
+    Ks += z * js.spec;
+    Bs += z * js.spec;
+    parts += z * js.parts;
+    ctl += z;
+    l1_parts += z * js.l1;
+  }
   constexpr int N = Cfg::N, CB = Cfg::CB, T = Cfg::THREADS, P = seq_pitch(N);
   constexpr bool PF = Cfg::PF;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -826,8 +837,14 @@ template <typename R, int LOGN> struct RowCfg {
 template <typename R, int LOGN>
 __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_r2c_kernel(
     const R* __restrict__ x, C2<R>* __restrict__ Z, const C2<R>* __restrict__ tw_g,
-    const FistaCtl* __restrict__ ctl) {
+    const FistaCtl* __restrict__ ctl, JobStride js) {
   using Cfg = RowCfg<R, LOGN>;
+  if (blockIdx.z != 0) {   // this block's job (batched form)
+    const int64_t z = blockIdx.z;
+    x += z * js.img;
+    Z += z * js.spec;
+    ctl += z;
+  }
   constexpr int M = Cfg::M, RB = Cfg::RB, P = seq_pitch(M), nc = M + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* b0 = reinterpret_cast<C2<R>*>(smem_raw);   // [RB][P]
@@ -878,8 +895,16 @@ template <typename R, int LOGN>
 __global__ void __launch_bounds__(RowCfg<R, LOGN>::THREADS) row_c2r_kernel(
     const C2<R>* __restrict__ Z, R* __restrict__ x, const C2<R>* __restrict__ tw_g,
     FistaCtl* __restrict__ ctl, const double* __restrict__ parts, int G,
-    double* __restrict__ trace) {
+    double* __restrict__ trace, JobStride js) {
   using Cfg = RowCfg<R, LOGN>;
+  if (blockIdx.z != 0) {   // this block's job (batched form)
+    const int64_t z = blockIdx.z;
+    Z += z * js.spec;
+    x += z * js.img;
+    ctl += z;
+    if (parts) parts += z * js.parts;
+    trace += z * js.trace;
+  }
   constexpr int M = Cfg::M, RB = Cfg::RB, P = seq_pitch(M), nc = M + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<R>* b0 = reinterpret_cast<C2<R>*>(smem_raw);   // [RB][P]
@@ -1030,11 +1055,12 @@ template <typename R> struct ColLaunch {
   template <int LOGN> struct At {
     static cudaError_t go(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks, const C2<R>* Bs,
                           const C2<R>* tw, double* parts, const FistaCtl* ctl,
-                          const double* l1_parts, int n_l1, cudaStream_t s) {
+                          const double* l1_parts, int n_l1, cudaStream_t s, JobStride js) {
       using Cfg = ColCfg<R, LOGN>;
       return launch_fft(spec_col_kernel<R, LOGN>,
-                        dim3((Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB), dim3(Cfg::THREADS),
-                        Cfg::SMEM, s, Z, Xk, Xprev, Ks, Bs, tw, parts, ctl, l1_parts, n_l1);
+                        dim3((Cfg::N / 2 + 1 + Cfg::CB - 1) / Cfg::CB, 1, js.jobs),
+                        dim3(Cfg::THREADS), Cfg::SMEM, s, Z, Xk, Xprev, Ks, Bs, tw, parts, ctl,
+                        l1_parts, n_l1, js);
     }
   };
   template <int LOGN> struct Info {
@@ -1050,18 +1076,20 @@ template <typename R> struct ColLaunch {
 template <typename R> struct RowLaunch {
   template <int LOGN> struct R2C {
     static cudaError_t go(const R* x, C2<R>* Z, const C2<R>* tw, const FistaCtl* ctl,
-                          cudaStream_t s) {
+                          cudaStream_t s, JobStride js) {
       using Cfg = RowCfg<R, LOGN>;
-      return launch_fft(row_r2c_kernel<R, LOGN>, dim3(Cfg::N / Cfg::RB), dim3(Cfg::THREADS),
-                        Cfg::SMEM, s, x, Z, tw, ctl);
+      return launch_fft(row_r2c_kernel<R, LOGN>, dim3(Cfg::N / Cfg::RB, 1, js.jobs),
+                        dim3(Cfg::THREADS), Cfg::SMEM, s, x, Z, tw, ctl, js);
     }
   };
   template <int LOGN> struct C2R {
     static cudaError_t go(const C2<R>* Z, R* x, const C2<R>* tw, FistaCtl* ctl,
-                          const double* parts, int G, double* trace, cudaStream_t s) {
+                          const double* parts, int G, double* trace, cudaStream_t s,
+                          JobStride js) {
       using Cfg = RowCfg<R, LOGN>;
-      return launch_fft(row_c2r_kernel<R, LOGN>, dim3(Cfg::N / Cfg::RB + (parts ? 1 : 0)),
-                        dim3(Cfg::THREADS), Cfg::SMEM, s, Z, x, tw, ctl, parts, G, trace);
+      return launch_fft(row_c2r_kernel<R, LOGN>,
+                        dim3(Cfg::N / Cfg::RB + (parts ? 1 : 0), 1, js.jobs), dim3(Cfg::THREADS),
+                        Cfg::SMEM, s, Z, x, tw, ctl, parts, G, trace, js);
     }
   };
   template <int LOGN> struct Info {
@@ -1110,19 +1138,21 @@ template <typename R>
 cudaError_t launch_spec_col(C2<R>* Z, C2<R>* Xk, const C2<R>* Xprev, const R* Ks,
                             const C2<R>* Bs, const C2<R>* tw, int N, double* parts,
                             const FistaCtl* ctl, const double* l1_parts, int n_l1,
-                            cudaStream_t s) {
+                            cudaStream_t s, const JobStride& js) {
   return by_logn<ColLaunch<R>::template At>(log2_exact(N), Z, Xk, Xprev, Ks, Bs, tw, parts,
-                                            ctl, l1_parts, n_l1, s);
+                                            ctl, l1_parts, n_l1, s, js);
 }
 template <typename R>
 cudaError_t launch_row_r2c(const R* x, C2<R>* Z, const C2<R>* tw, int N, const FistaCtl* ctl,
-                           cudaStream_t s) {
-  return by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s);
+                           cudaStream_t s, const JobStride& js) {
+  return by_logn<RowLaunch<R>::template R2C>(log2_exact(N), x, Z, tw, ctl, s, js);
 }
 template <typename R>
 cudaError_t launch_row_c2r(const C2<R>* Z, R* x, const C2<R>* tw, int N, FistaCtl* ctl,
-                           const double* parts, int G, double* trace, cudaStream_t s) {
-  return by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, parts, G, trace, s);
+                           const double* parts, int G, double* trace, cudaStream_t s,
+                           const JobStride& js) {
+  return by_logn<RowLaunch<R>::template C2R>(log2_exact(N), Z, x, tw, ctl, parts, G, trace, s,
+                                             js);
 }
 
 template <typename R>
@@ -1611,12 +1641,14 @@ void launch_lin_theta(const R* H2, int N, const R* gl2, const R* gh2, int M, dou
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
                                      int, C2<R>*, double*, FistaCtl*, int32_t*, cudaStream_t);   \
   template cudaError_t launch_row_r2c<R>(const R*, C2<R>*, const C2<R>*, int,                \
-                                         const FistaCtl*, cudaStream_t);                         \
+                                         const FistaCtl*, cudaStream_t, const JobStride&);       \
   template cudaError_t launch_row_c2r<R>(const C2<R>*, R*, const C2<R>*, int, FistaCtl*,      \
-                                         const double*, int, double*, cudaStream_t);             \
+                                         const double*, int, double*, cudaStream_t,              \
+                                         const JobStride&);                                      \
   template cudaError_t launch_spec_col<R>(C2<R>*, C2<R>*, const C2<R>*, const R*,             \
                                           const C2<R>*, const C2<R>*, int, double*,              \
-                                          const FistaCtl*, const double*, int, cudaStream_t);    \
+                                          const FistaCtl*, const double*, int, cudaStream_t,     \
+                                          const JobStride&);                                     \
   template void launch_spec_mul<R>(const C2<R>*, C2<R>*, const R*, const C2<R>*, int, double*,  \
                                    FistaCtl*,                                                    \
                                    double*, int32_t*, const double*, int, cudaStream_t);         \

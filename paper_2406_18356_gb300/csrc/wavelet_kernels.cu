@@ -613,7 +613,8 @@ __global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
 // read before the first load.
 template <typename R, int ST>
 __global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
-    synthesis_level_kernel(FistaPass<R> a, int j) {
+    synthesis_level_kernel(FistaPass<R> a_, int j) {
+  const FistaPass<R> a = job_slice(a_);   // blockIdx.z: the job (batched form)
   pdl_wait();
   pdl_trigger();
   const int done = a.ctl->done;
@@ -817,7 +818,7 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
                                               const R* ll_in, R* ll_out, R* out_plain,
                                               const R* cur, const R* prev, R* next, R t, R mu,
                                               R thr, int N, int j, int J, int tile,
-                                              FistaCtl* ctl, KSum<R>& l1) {
+                                              FistaCtl* ctl, KSum<R>& l1, int tma_y0 = 0) {
   constexpr int m = MB;
   const AnaSmem<R, G> sm(base);
   R* sIn = sm.sIn;
@@ -861,7 +862,7 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
         // the asynchronous copy overwrites it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(sm.bar, (unsigned)(G::In * G::InS * sizeof(R)));
-        tma_load_2d(sIn, xmap, p0x, p0y, sm.bar);
+        tma_load_2d(sIn, xmap, p0x, p0y + tma_y0, sm.bar);
       } else if (ctl) {
         atomicExch(&ctl->error, 8);
       }
@@ -1013,9 +1014,10 @@ __global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
 // the next spectral kernel adds them up (fixed order).
 template <typename R, int AT>
 __global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
-    analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a, int j,
+    analysis_level_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a_, int j,
                           int use_tma, int part_base) {
   using G = AG<AT>;
+  const FistaPass<R> a = job_slice(a_);   // blockIdx.z: the job (batched form)
   pdl_wait();
   pdl_trigger();
   const int done = a.ctl->done;
@@ -1043,7 +1045,8 @@ __global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
 #define MS_ANA(MBV)                                                                          \
   case MBV:                                                                                  \
     analysis_item<R, 1, MBV, G>(base, &xmap, tma, phase, a.grad, ll_in, ll_out, nullptr, cur, \
-                                prev, next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1);  \
+                                prev, next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1,   \
+                                (int)blockIdx.z * a.N);                                       \
     break;
     MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
 #undef MS_ANA
@@ -1083,9 +1086,10 @@ template <typename R> struct AnaTile {
 
 template <typename R>
 __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
-    analysis_l1_tile_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a,
+    analysis_l1_tile_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a_,
                             int use_tma, int part_base) {
   using A = AnaTile<R>;
+  const FistaPass<R> a = job_slice(a_);   // blockIdx.z: the job (batched form)
   using G = typename A::G;
   constexpr int T = A::T;
   pdl_wait();
@@ -1156,7 +1160,7 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
       if (aligned) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, (unsigned)(G::In * G::InS * sizeof(R)));
-        tma_load_2d(sIn, &xmap, p0x, p0y, bar);
+        tma_load_2d(sIn, &xmap, p0x, p0y + (int)blockIdx.z * N, bar);
       } else {
         atomicExch(&a.ctl->error, 8);
       }
@@ -1433,13 +1437,13 @@ void analysis_window_box(unsigned* cols, unsigned* rows) {
 
 template <typename R>
 cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int only_level) {
-  if (only_level < 0 && a.coarse_ctas > 0)   // levels J..2 as one cooperative launch
+  if (only_level < 0 && a.coarse_ctas > 0 && a.js.jobs == 1)   // levels J..2, one cooperative launch
     return launch_coarse<R>(a, false, 0, 0, s);
   for (int j = a.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
     if (only_level < 0 && j == 1) continue;
     int n = 2 * (a.N >> j), TS = syn_tile(n);
-    dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M);
+    dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M, a.js.jobs);
     auto go = [&](auto kern, int threads, size_t smem) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       return launch_pdl(kern, grid, dim3(threads), smem, s, a, j);
@@ -1459,7 +1463,7 @@ template <typename R>
 cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_map,
                                  cudaStream_t s, int only_level) {
   const CUtensorMap m = grad_map ? *grad_map : CUtensorMap{};
-  if (only_level < 0 && a.coarse_ctas > 0) {   // levels 2..J as one cooperative launch
+  if (only_level < 0 && a.coarse_ctas > 0 && a.js.jobs == 1) {   // levels 2..J, one cooperative launch
     const WaveletGeom g{a.N, a.J, a.M};
     return launch_coarse<R>(a, true, level1_partials(g), analysis_prox_partials(g), s);
   }
@@ -1474,14 +1478,14 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
         const size_t smem = AnaTile<R>::bytes();
         auto kern = analysis_l1_tile_kernel<R>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const cudaError_t e = launch_pdl(kern, dim3(tiles), dim3(AG<kAT>::Threads), smem, s, m,
-                                         a, 1, part_base);
+        const cudaError_t e = launch_pdl(kern, dim3(tiles, 1, a.js.jobs), dim3(AG<kAT>::Threads),
+                                         smem, s, m, a, 1, part_base);
         if (e != cudaSuccess) return e;
         done_here = true;
       }
     }
     if (run && !done_here) {
-      dim3 grid(tiles, a.M);
+      dim3 grid(tiles, a.M, a.js.jobs);
       auto go = [&](auto kern, int threads, size_t smem) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         return launch_pdl(kern, grid, dim3(threads), smem, s, m, a, j, grad_map ? 1 : 0,
