@@ -63,6 +63,39 @@ template <> __device__ __forceinline__ float fg<float>(int m, int k) { return c_
 template <> __device__ __forceinline__ double fh<double>(int m, int k) { return c_hd[m][k]; }
 template <> __device__ __forceinline__ double fg<double>(int m, int k) { return c_gd[m][k]; }
 
+// Filter pairs on the FP32 pipe's packed form (fma.rn.f32x2: two lanes of
+// FP32 fused multiply-add per instruction, each lane rounded as fmaf): the
+// two outputs of a synthesis filter step that share their input, in the same
+// order of operations as the scalar chains, so results are bit-identical
+// (measured at 1024^2: synthesis levels 4..2 30.5 -> 26.5 us, level 1
+// 36.4 -> 33.1 us per FISTA iteration).
+#ifndef MS_PACKED_F32
+#define MS_PACKED_F32 1
+#endif
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+// (a, d) = (ca x + a, cd x + d); PACK = false keeps two scalar chains (the
+// analysis filters, measured no faster packed: their taps' coefficient pairs
+// cost as much to form as the packed FMA saves)
+template <typename R, bool PACK = true>
+__device__ __forceinline__ void fma_pair(R ca, R cd, R x, R& a, R& d) {
+  if constexpr (sizeof(R) == 4 && MS_PACKED_F32 && PACK) {
+    const float2 r = ffma2(make_float2(ca, cd), make_float2(x, x), make_float2(a, d));
+    a = r.x;
+    d = r.y;
+  } else {
+    a = fma(ca, x, a);
+    d = fma(cd, x, d);
+  }
+}
+
 constexpr int kP = 8;   // outputs per thread and direction
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) / 4 * 4; }
@@ -149,11 +182,16 @@ __host__ __device__ __forceinline__ int fit_tile(int t, int n) {
 #ifndef MS_SYN_T1B
 #define MS_SYN_T1B MS_SYN_T1   // synthesis output tile for 512 <= n < 1024
 #endif
-__host__ __device__ __forceinline__ int syn_tile(int n) {   // synthesis output side
+// wide: the batched minor cycles, whose launches have blocks to spare (the
+// jobs multiply them), take the widest tiles at every level: the per-tile
+// staging and set-up dominate the narrow tiles of the coarse levels.
+__host__ __device__ __forceinline__ int syn_tile(int n, bool wide = false) {   // output side
+  if (wide) return fit_tile(kST, n);
   return fit_tile(n >= 1024 ? MS_SYN_T1 : (n >= 512 ? MS_SYN_T1B : (n >= 256 ? MS_SYN_T2 : MS_SYN_T3)),
                   n);
 }
-__host__ __device__ __forceinline__ int ana_tile(int h) {   // analysis subband side
+__host__ __device__ __forceinline__ int ana_tile(int h, bool wide = false) {   // subband side
+  if (wide) return fit_tile(kAT, h);
   return fit_tile(h >= 256 ? MS_ANA_T1 : (h >= 128 ? MS_ANA_T2 : 16), h);
 }
 // geometry (template argument) serving a tile side
@@ -236,10 +274,8 @@ __device__ __forceinline__ void fir_down8(const R* x, R* lo, R* hi) {
   for (int j = 0; j < kP; ++j) {
     R a = 0, d = 0;
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-      a += fh<R>(MB, k) * x[2 * j + k];
-      d += fg<R>(MB, k) * x[2 * j + k];
-    }
+    for (int k = 0; k < L; ++k)
+      fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), x[2 * j + k], a, d);
     lo[j] = a;
     hi[j] = d;
   }
@@ -250,18 +286,20 @@ __device__ __forceinline__ void fir_down8(const R* x, R* lo, R* hi) {
 template <typename R, int MB>
 __device__ __forceinline__ void fir_up8(const R* lo, const R* hi, R* out) {
   constexpr int L = 2 * (MB + 1);
+  // one fused multiply-add per tap and band (a chain, no separate product
+  // and sum); outputs 2m and 2m + 1 read the same inputs (with the even and
+  // the odd taps), so they run as one pair
 #pragma unroll
-  for (int r = 0; r < kP; ++r) {
-    // one fused multiply-add per tap and band (a chain, no separate
-    // product and sum)
-    R s = 0;
+  for (int r = 0; r < kP; r += 2) {
+    R e = 0, o = 0;
 #pragma unroll
-    for (int k = (r & 1); k < L; k += 2) {
-      const int i = (r - k) / 2 + L / 2 - 1;
-      s = fma(fh<R>(MB, k), lo[i], s);
-      s = fma(fg<R>(MB, k), hi[i], s);
+    for (int m = 0; m < L / 2; ++m) {
+      const int i = r / 2 - m + L / 2 - 1;
+      fma_pair<R>(fh<R>(MB, 2 * m), fh<R>(MB, 2 * m + 1), lo[i], e, o);
+      fma_pair<R>(fg<R>(MB, 2 * m), fg<R>(MB, 2 * m + 1), hi[i], e, o);
     }
-    out[r] = s;
+    out[r] = e;
+    out[r + 1] = o;
   }
 }
 
@@ -368,10 +406,8 @@ __device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, in
       for (int kk = 0; kk < L / 2; ++kk) {
         const int i = first + rr - kk + L / 2 - 1;
         const R x = s0[i * G::SubS], y = s1[i * G::SubS];
-        e = fma(fh<R>(MB, 2 * kk), x, e);
-        e = fma(fg<R>(MB, 2 * kk), y, e);
-        o = fma(fh<R>(MB, 2 * kk + 1), x, o);
-        o = fma(fg<R>(MB, 2 * kk + 1), y, o);
+        fma_pair<R>(fh<R>(MB, 2 * kk), fh<R>(MB, 2 * kk + 1), x, e, o);
+        fma_pair<R>(fg<R>(MB, 2 * kk), fg<R>(MB, 2 * kk + 1), y, e, o);
       }
       z[(2 * rr) * G::ZS] = e;
       z[(2 * rr + 1) * G::ZS] = o;
@@ -392,10 +428,8 @@ __device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, in
 #pragma unroll
       for (int kk = 0; kk < L / 2; ++kk) {
         const int i = rr - kk + L / 2 - 1;
-        e = fma(fh<R>(MB, 2 * kk), lr[i], e);
-        e = fma(fg<R>(MB, 2 * kk), hr[i], e);
-        o = fma(fh<R>(MB, 2 * kk + 1), lr[i], o);
-        o = fma(fg<R>(MB, 2 * kk + 1), hr[i], o);
+        fma_pair<R>(fh<R>(MB, 2 * kk), fh<R>(MB, 2 * kk + 1), lr[i], e, o);
+        fma_pair<R>(fg<R>(MB, 2 * kk), fg<R>(MB, 2 * kk + 1), hr[i], e, o);
       }
       if (kP * seg + 2 * rr < TS) dst[2 * rr] = e;
       if (kP * seg + 2 * rr + 1 < TS) dst[2 * rr + 1] = o;
@@ -476,13 +510,13 @@ template <typename R, class G>
 __device__ __forceinline__ void synth_item(unsigned char* smem_raw, const R* __restrict__ coef,
                                            const R* __restrict__ ll_in, R* __restrict__ ll_out,
                                            R* __restrict__ x, int N, int j, int J, int M,
-                                           int tile, int mb) {
+                                           int tile, int mb, bool wide = false) {
   R* subs = reinterpret_cast<R*>(smem_raw);          // [2][4][G::In][G::SubS]
   R* zlo = subs + 2 * G::SubSz;                       // [G::T][G::ZS]
   R* zhi = zlo + G::T * G::ZS;
   int2* tab = reinterpret_cast<int2*>(zhi + G::T * G::ZS);   // [K][G::Threads]
   const int h = N >> j, n = 2 * h;
-  const int TS = syn_tile(n);
+  const int TS = syn_tile(n, wide);
   const int lts = 31 - __clz(TS);
   const int cnt = TS / 2 + kMaxTaps / 2 - 1;
   const int tiles_x = n / TS;
@@ -626,7 +660,7 @@ __global__ void __launch_bounds__(SG<ST>::Threads, 512 / SG<ST>::Threads)
   const R* ll_in = (j == a.J) ? nullptr : a.tmp + ((j + 1) & 1) * half;
   R* ll_out = a.tmp + (j & 1) * half;
   synth_item<R, SG<ST>>(smem_raw, coef, ll_in, ll_out, a.x, a.N, j, a.J, a.M, blockIdx.x,
-                        blockIdx.y);
+                        blockIdx.y, a.js.jobs > 1);
 }
 
 namespace {
@@ -693,9 +727,7 @@ __device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R*
       R a = 0, d = 0;
 #pragma unroll
       for (int k = 0; k < L; ++k) {
-        const R x = xc[(2 * r + k) * G::InS];
-        a += fh<R>(MB, k) * x;
-        d += fg<R>(MB, k) * x;
+        fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), xc[(2 * r + k) * G::InS], a, d);
       }
       ylo[(kP * part + r) * G::YS + col] = a;
       yhi[(kP * part + r) * G::YS + col] = d;
@@ -714,9 +746,7 @@ __device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R*
     R a = 0, d = 0;
 #pragma unroll
     for (int k = 0; k < L; ++k) {
-      const R x = yrow[2 * q + k];
-      a += fh<R>(MB, k) * x;
-      d += fg<R>(MB, k) * x;
+      fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), yrow[2 * q + k], a, d);
     }
     o_lo[q] = a;
     o_hi[q] = d;
@@ -818,14 +848,15 @@ __device__ __forceinline__ void analysis_item(unsigned char* base, const CUtenso
                                               const R* ll_in, R* ll_out, R* out_plain,
                                               const R* cur, const R* prev, R* next, R t, R mu,
                                               R thr, int N, int j, int J, int tile,
-                                              FistaCtl* ctl, KSum<R>& l1, int tma_y0 = 0) {
+                                              FistaCtl* ctl, KSum<R>& l1, int tma_y0 = 0,
+                                              bool wide = false) {
   constexpr int m = MB;
   const AnaSmem<R, G> sm(base);
   R* sIn = sm.sIn;
   R* gout = sIn;
 
   const int n = N >> (j - 1), h = n / 2;
-  const int TO = ana_tile(h);
+  const int TO = ana_tile(h, wide);
   const int TOe = TO < kP ? kP : TO;             // outputs computed per side
   const int lt = 31 - __clz(TOe);
   const int lto = 31 - __clz(TO);
@@ -1046,7 +1077,7 @@ __global__ void __launch_bounds__(AG<AT>::Threads, 512 / AG<AT>::Threads)
   case MBV:                                                                                  \
     analysis_item<R, 1, MBV, G>(base, &xmap, tma, phase, a.grad, ll_in, ll_out, nullptr, cur, \
                                 prev, next, t, mu, thr, a.N, j, a.J, blockIdx.x, a.ctl, l1,   \
-                                (int)blockIdx.z * a.N);                                       \
+                                (int)blockIdx.z * a.N, a.js.jobs > 1);                        \
     break;
     MS_ANA(0) MS_ANA(1) MS_ANA(2) MS_ANA(3) MS_ANA(4) MS_ANA(5) MS_ANA(6) MS_ANA(7)
 #undef MS_ANA
@@ -1442,7 +1473,7 @@ cudaError_t launch_synthesis_pass(const FistaPass<R>& a, cudaStream_t s, int onl
   for (int j = a.J; j >= 1; --j) {
     if (only_level > 0 && j != only_level) continue;
     if (only_level < 0 && j == 1) continue;
-    int n = 2 * (a.N >> j), TS = syn_tile(n);
+    int n = 2 * (a.N >> j), TS = syn_tile(n, a.js.jobs > 1);
     dim3 grid((n / TS) * (n / TS), j == 1 ? 1 : a.M, a.js.jobs);
     auto go = [&](auto kern, int threads, size_t smem) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1469,7 +1500,7 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
   }
   int part_base = 0;
   for (int j = 1; j <= a.J; ++j) {
-    const int h = a.N >> j, TO = ana_tile(h);
+    const int h = a.N >> j, TO = ana_tile(h, a.js.jobs > 1);
     const int tiles = (h / TO) * (h / TO);
     const bool run = only_level == 0 || j == only_level || (only_level < 0 && j > 1);
     bool done_here = false;
