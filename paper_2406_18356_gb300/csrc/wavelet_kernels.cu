@@ -37,6 +37,11 @@ __constant__ double c_hd[kMaxBases][kMaxTaps];
 __constant__ double c_gd[kMaxBases][kMaxTaps];
 __constant__ float c_hf[kMaxBases][kMaxTaps];
 __constant__ float c_gf[kMaxBases][kMaxTaps];
+// FP32 coefficient pairs for the packed filters: (h_k, g_k) of the analysis
+// tap k, (h_2m, h_2m+1) and (g_2m, g_2m+1) of the synthesis output pair
+__constant__ float2 c_hg2[kMaxBases][kMaxTaps];
+__constant__ float2 c_hh2[kMaxBases][kMaxTaps / 2];
+__constant__ float2 c_gg2[kMaxBases][kMaxTaps / 2];
 
 void set_wavelet_filters(const double* h, const int* len, int nbases) {
   double hd[kMaxBases][kMaxTaps] = {}, gd[kMaxBases][kMaxTaps] = {};
@@ -53,6 +58,19 @@ void set_wavelet_filters(const double* h, const int* len, int nbases) {
   cudaMemcpyToSymbol(c_gd, gd, sizeof(gd));
   cudaMemcpyToSymbol(c_hf, hf, sizeof(hf));
   cudaMemcpyToSymbol(c_gf, gf, sizeof(gf));
+  float2 hg[kMaxBases][kMaxTaps] = {}, hh[kMaxBases][kMaxTaps / 2] = {},
+         gg[kMaxBases][kMaxTaps / 2] = {};
+  for (int m = 0; m < kMaxBases; ++m)
+    for (int k = 0; k < kMaxTaps; ++k) {
+      hg[m][k] = make_float2(hf[m][k], gf[m][k]);
+      if (k % 2 == 0) {
+        hh[m][k / 2] = make_float2(hf[m][k], hf[m][k + 1]);
+        gg[m][k / 2] = make_float2(gf[m][k], gf[m][k + 1]);
+      }
+    }
+  cudaMemcpyToSymbol(c_hg2, hg, sizeof(hg));
+  cudaMemcpyToSymbol(c_hh2, hh, sizeof(hh));
+  cudaMemcpyToSymbol(c_gg2, gg, sizeof(gg));
 }
 
 namespace {
@@ -65,36 +83,59 @@ template <> __device__ __forceinline__ double fg<double>(int m, int k) { return 
 
 // Filter pairs on the FP32 pipe's packed form (fma.rn.f32x2: two lanes of
 // FP32 fused multiply-add per instruction, each lane rounded as fmaf): the
-// two outputs of a synthesis filter step that share their input, in the same
-// order of operations as the scalar chains, so results are bit-identical
-// (measured at 1024^2: synthesis levels 4..2 30.5 -> 26.5 us, level 1
-// 36.4 -> 33.1 us per FISTA iteration).
+// two outputs of a filter step that share their input (analysis: the low and
+// high band of tap k; synthesis: outputs 2m and 2m + 1), in the same order of
+// operations as the scalar chains, so results are bit-identical.  The
+// coefficient pairs come from constant memory as one 64-bit operand.
+// Measured at 1024^2 (FP32, M = 8, J = 4), per FISTA iteration: synthesis
+// levels 4..2 29.8 -> 26.8 us, level 1 36.0 -> 33.3 us, analysis levels 2..4
+// 35.5 -> 33.6 us, level 1 37.1 -> 35.1 us (144.9 -> 136.0 us in all).
 #ifndef MS_PACKED_F32
 #define MS_PACKED_F32 1
 #endif
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+// (d.x, d.y) = (c.x x + acc.x, c.y x + acc.y), c a coefficient pair read from
+// constant memory as one 64-bit operand
+__device__ __forceinline__ float2 ffma2_cx(const float2& c, float x, float2 acc) {
   float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+  const unsigned long long cc = *reinterpret_cast<const unsigned long long*>(&c);
+  asm("{\n\t.reg .b64 rx, ra, rd;\n\t"
+      "mov.b64 rx, {%3, %3};\n\tmov.b64 ra, {%4, %5};\n\t"
+      "fma.rn.f32x2 rd, %2, rx, ra;\n\tmov.b64 {%0, %1}, rd;\n\t}"
       : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+      : "l"(cc), "f"(x), "f"(acc.x), "f"(acc.y));
   return d;
 }
-// (a, d) = (ca x + a, cd x + d); PACK = false keeps two scalar chains (the
-// analysis filters, measured no faster packed: their taps' coefficient pairs
-// cost as much to form as the packed FMA saves)
-template <typename R, bool PACK = true>
-__device__ __forceinline__ void fma_pair(R ca, R cd, R x, R& a, R& d) {
+// analysis tap k of basis MB on input x: (a, d) += (h_k, g_k) x
+template <typename R, int MB, bool PACK>
+__device__ __forceinline__ void tap_hg(int k, R x, R& a, R& d) {
   if constexpr (sizeof(R) == 4 && MS_PACKED_F32 && PACK) {
-    const float2 r = ffma2(make_float2(ca, cd), make_float2(x, x), make_float2(a, d));
+    const float2 r = ffma2_cx(c_hg2[MB][k], x, make_float2(a, d));
     a = r.x;
     d = r.y;
   } else {
-    a = fma(ca, x, a);
-    d = fma(cd, x, d);
+    a = fma(fh<R>(MB, k), x, a);
+    d = fma(fg<R>(MB, k), x, d);
   }
 }
+// synthesis taps 2m, 2m + 1 of basis MB on low input x and high input y:
+// (e, o) += (h_2m, h_2m+1) x, then (e, o) += (g_2m, g_2m+1) y
+template <typename R, int MB>
+__device__ __forceinline__ void tap_syn(int m, R x, R y, R& e, R& o) {
+  if constexpr (sizeof(R) == 4 && MS_PACKED_F32) {
+    float2 r = ffma2_cx(c_hh2[MB][m], x, make_float2(e, o));
+    r = ffma2_cx(c_gg2[MB][m], y, r);
+    e = r.x;
+    o = r.y;
+  } else {
+    e = fma(fh<R>(MB, 2 * m), x, e);
+    e = fma(fg<R>(MB, 2 * m), y, e);
+    o = fma(fh<R>(MB, 2 * m + 1), x, o);
+    o = fma(fg<R>(MB, 2 * m + 1), y, o);
+  }
+}
+#ifndef MS_PACKED_ANALYSIS
+#define MS_PACKED_ANALYSIS 1
+#endif
 
 constexpr int kP = 8;   // outputs per thread and direction
 
@@ -274,8 +315,7 @@ __device__ __forceinline__ void fir_down8(const R* x, R* lo, R* hi) {
   for (int j = 0; j < kP; ++j) {
     R a = 0, d = 0;
 #pragma unroll
-    for (int k = 0; k < L; ++k)
-      fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), x[2 * j + k], a, d);
+    for (int k = 0; k < L; ++k) tap_hg<R, MB, MS_PACKED_ANALYSIS>(k, x[2 * j + k], a, d);
     lo[j] = a;
     hi[j] = d;
   }
@@ -295,8 +335,7 @@ __device__ __forceinline__ void fir_up8(const R* lo, const R* hi, R* out) {
 #pragma unroll
     for (int m = 0; m < L / 2; ++m) {
       const int i = r / 2 - m + L / 2 - 1;
-      fma_pair<R>(fh<R>(MB, 2 * m), fh<R>(MB, 2 * m + 1), lo[i], e, o);
-      fma_pair<R>(fg<R>(MB, 2 * m), fg<R>(MB, 2 * m + 1), hi[i], e, o);
+      tap_syn<R, MB>(m, lo[i], hi[i], e, o);
     }
     out[r] = e;
     out[r + 1] = o;
@@ -406,8 +445,7 @@ __device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, in
       for (int kk = 0; kk < L / 2; ++kk) {
         const int i = first + rr - kk + L / 2 - 1;
         const R x = s0[i * G::SubS], y = s1[i * G::SubS];
-        fma_pair<R>(fh<R>(MB, 2 * kk), fh<R>(MB, 2 * kk + 1), x, e, o);
-        fma_pair<R>(fg<R>(MB, 2 * kk), fg<R>(MB, 2 * kk + 1), y, e, o);
+        tap_syn<R, MB>(kk, x, y, e, o);
       }
       z[(2 * rr) * G::ZS] = e;
       z[(2 * rr + 1) * G::ZS] = o;
@@ -428,8 +466,7 @@ __device__ __forceinline__ void synth_basis_compact(int TS, int lts, int cnt, in
 #pragma unroll
       for (int kk = 0; kk < L / 2; ++kk) {
         const int i = rr - kk + L / 2 - 1;
-        fma_pair<R>(fh<R>(MB, 2 * kk), fh<R>(MB, 2 * kk + 1), lr[i], e, o);
-        fma_pair<R>(fg<R>(MB, 2 * kk), fg<R>(MB, 2 * kk + 1), hr[i], e, o);
+        tap_syn<R, MB>(kk, lr[i], hr[i], e, o);
       }
       if (kP * seg + 2 * rr < TS) dst[2 * rr] = e;
       if (kP * seg + 2 * rr + 1 < TS) dst[2 * rr + 1] = o;
@@ -727,7 +764,7 @@ __device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R*
       R a = 0, d = 0;
 #pragma unroll
       for (int k = 0; k < L; ++k) {
-        fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), xc[(2 * r + k) * G::InS], a, d);
+        tap_hg<R, MB, MS_PACKED_ANALYSIS>(k, xc[(2 * r + k) * G::InS], a, d);
       }
       ylo[(kP * part + r) * G::YS + col] = a;
       yhi[(kP * part + r) * G::YS + col] = d;
@@ -746,7 +783,7 @@ __device__ __forceinline__ void analysis_filter_compact(const R* sIn, R* ylo, R*
     R a = 0, d = 0;
 #pragma unroll
     for (int k = 0; k < L; ++k) {
-      fma_pair<R, false>(fh<R>(MB, k), fg<R>(MB, k), yrow[2 * q + k], a, d);
+      tap_hg<R, MB, MS_PACKED_ANALYSIS>(k, yrow[2 * q + k], a, d);
     }
     o_lo[q] = a;
     o_hi[q] = d;
@@ -1118,9 +1155,12 @@ template <typename R> struct AnaTile {
 template <typename R>
 __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
     analysis_l1_tile_kernel(const __grid_constant__ CUtensorMap xmap, FistaPass<R> a_,
-                            int use_tma, int part_base) {
+                            int use_tma, int part_base, int split) {
   using A = AnaTile<R>;
   const FistaPass<R> a = job_slice(a_);   // blockIdx.z: the job (batched form)
+  // blockIdx.y: the basis group, bases [0, split) or [split, M) (split = M:
+  // one group)
+  const int m_lo = blockIdx.y == 0 ? 0 : split, m_hi = blockIdx.y == 0 ? split : a.M;
   using G = typename A::G;
   constexpr int T = A::T;
   pdl_wait();
@@ -1214,7 +1254,7 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
     }
   }
   cp_async_commit();   // (empty on the TMA path)
-  prefetch(0);
+  prefetch(m_lo);
   bool skip = false;
   if (tma) {
     unsigned phase = 0;
@@ -1237,10 +1277,10 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
   // switch over the bases raised register pressure into spills)
   auto step = [&](auto mb) {
     constexpr int m = decltype(mb)::value;
-    if (m >= a.M) return;
-    if (m + 1 < a.M) prefetch(m + 1);
+    if (m < m_lo || m >= m_hi) return;   // uniform over the block
+    if (m + 1 < m_hi) prefetch(m + 1);
     analysis_filter<R, m, G, true>(sIn, ylo, yhi, gout, T, lto);
-    if (m + 1 < a.M) cp_async_wait<1>();
+    if (m + 1 < m_hi) cp_async_wait<1>();
     else cp_async_wait<0>();
     __syncthreads();   // the filter's outputs and basis m's prefetch are visible
     const R* pc = pf + (m & 1) * (2 * 3 * T * T);
@@ -1292,8 +1332,11 @@ __global__ void __launch_bounds__(AG<kAT>::Threads, 2)
   if (threadIdx.x == 0) {
     double sum = 0.0;
     for (int q = 0; q < G::Threads / 32; ++q) sum += red[q];
-    a.l1_parts[part_base + tile] = sum;
-    for (int m = 1; m < a.M; ++m) a.l1_parts[part_base + (int64_t)m * gridDim.x + tile] = 0.0;
+    // slot (group, tile); the first group also zeroes the slots no group uses
+    a.l1_parts[part_base + (int64_t)blockIdx.y * gridDim.x + tile] = sum;
+    if (blockIdx.y == 0)
+      for (int m = gridDim.y; m < a.M; ++m)
+        a.l1_parts[part_base + (int64_t)m * gridDim.x + tile] = 0.0;
   }
 }
 
@@ -1317,6 +1360,33 @@ size_t coarse_smem(bool analysis, WaveletGeom g, const CoarseGroups& gr, int bud
   int cs_min = 1 << 30;
   for (int m = 0; m < g.M; ++m) cs_min = std::min(cs_min, gr.first[m + 1] - gr.first[m]);
   return strip_smem_bytes(analysis, g.N, g.J, cs_min, sizeof(R), (size_t)budget);
+}
+
+// The level-1 analysis tile kernel's basis groups: bases [0, split) and
+// [split, M), split where the work (2 (m + 1) taps + MS_L1_WFIX per basis)
+// is closest to half; split = M (one group) when MS_L1_GROUPS is 1.
+#ifndef MS_L1_GROUPS
+#define MS_L1_GROUPS 1   // 2 measured no faster at 1024^2 (37.4 vs 37.2 us)
+#endif
+#ifndef MS_L1_WFIX
+#define MS_L1_WFIX 10
+#endif
+int l1_basis_split(int M) {
+  if (MS_L1_GROUPS < 2 || M < 2) return M;
+  double total = 0.0;
+  for (int m = 0; m < M; ++m) total += 2.0 * (m + 1) + MS_L1_WFIX;
+  double acc = 0.0;
+  int best = 1;
+  double best_d = 1e30;
+  for (int sp = 1; sp < M; ++sp) {
+    acc += 2.0 * sp + MS_L1_WFIX;   // work of bases 0..sp-1
+    const double d = std::fabs(2.0 * acc - total);
+    if (d < best_d) {
+      best_d = d;
+      best = sp;
+    }
+  }
+  return best;
 }
 
 // l1 partial slots of level 1 (the per-tile kernel's share) and in all
@@ -1509,8 +1579,12 @@ cudaError_t launch_analysis_pass(const FistaPass<R>& a, const CUtensorMap* grad_
         const size_t smem = AnaTile<R>::bytes();
         auto kern = analysis_l1_tile_kernel<R>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        const cudaError_t e = launch_pdl(kern, dim3(tiles, 1, a.js.jobs), dim3(AG<kAT>::Threads),
-                                         smem, s, m, a, 1, part_base);
+        // two block groups over the bases, split where the filter work
+        // (taps plus a fixed per-basis share) is about equal
+        const int split = l1_basis_split(a.M);
+        const cudaError_t e =
+            launch_pdl(kern, dim3(tiles, split < a.M ? 2 : 1, a.js.jobs), dim3(AG<kAT>::Threads),
+                       smem, s, m, a, 1, part_base, split);
         if (e != cudaSuccess) return e;
         done_here = true;
       }
