@@ -81,6 +81,21 @@ __device__ __forceinline__ float exp2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// packed FP32 pair FMA (fma.rn.f32x2): d = a b + c in both lanes, each
+// rounded as fmaf
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+#ifndef MS_DEGRID_PACKED
+#define MS_DEGRID_PACKED 1
+#endif
+
 template <typename R>
 __device__ __forceinline__ void es_weights(R f, R beta, R* w) {
   const R c = (R)(4.0 / (kW * kW));
@@ -238,18 +253,33 @@ __device__ __forceinline__ void degrid_item(const CUtensorMap* tmap, int tma_y0,
     es_weights<R>(f.x, beta, wu);
     es_weights<R>(f.y, beta, wv);
     R accr = 0, acci = 0;
+    if constexpr (sizeof(R) == 4 && MS_DEGRID_PACKED) {
+      // the real and imaginary chains as packed FP32 pairs (same operations)
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < kW; ++j) {
-      const C2<R>* row = tile + (lv + j) * S + lu;
-      R rr = 0, ri = 0;
+      for (int j = 0; j < kW; ++j) {
+        const float2* row = reinterpret_cast<const float2*>(tile + (lv + j) * S + lu);
+        float2 r = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < kW; ++i) {
-        C2<R> g = row[i];
-        rr += wu[i] * g.x;
-        ri += wu[i] * g.y;
+        for (int i = 0; i < kW; ++i) r = ffma2(make_float2(wu[i], wu[i]), row[i], r);
+        acc = ffma2(make_float2(wv[j], wv[j]), r, acc);
       }
-      accr += wv[j] * rr;
-      acci += wv[j] * ri;
+      accr = acc.x;
+      acci = acc.y;
+    } else {
+#pragma unroll
+      for (int j = 0; j < kW; ++j) {
+        const C2<R>* row = tile + (lv + j) * S + lu;
+        R rr = 0, ri = 0;
+#pragma unroll
+        for (int i = 0; i < kW; ++i) {
+          C2<R> g = row[i];
+          rr = fma(wu[i], g.x, rr);
+          ri = fma(wu[i], g.y, ri);
+        }
+        accr = fma(wv[j], rr, accr);
+        acci = fma(wv[j], ri, acci);
+      }
     }
     C2<R> o;
     if (HAS_OBS) {
