@@ -554,6 +554,9 @@ void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const 
                                  Ng, tile, ntx, (R)beta);
 }
 
+// Cells are walked x-stride over the whole grid (dense tiles, with many
+// items, spread over all blocks); a cell's items are read four at a time
+// (independent loads in flight) and added in item order.
 template <typename R, bool KAHAN>
 __device__ __forceinline__ void fold_cells(const typename ScratchOf<R, KAHAN>::T* __restrict__ scratch,
                                            const int32_t* __restrict__ tile_items, int Ng, int T,
@@ -561,11 +564,11 @@ __device__ __forceinline__ void fold_cells(const typename ScratchOf<R, KAHAN>::T
   using Acc = typename ScratchOf<R, KAHAN>::T;
   const int S = T + kW - 1;
   const int cells = S * S;
-  int64_t total = (int64_t)Ng * Ng;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    int cv = (int)(k / Ng), cu = (int)(k % Ng);
-    int tx = cu / T, ty = cv / T, ou = cu - tx * T, ov = cv - ty * T;
+  const int lt = __ffs(T) - 1;   // T is a power of two
+  const int total = Ng * Ng;     // < 2^31 (Ng <= 32768)
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+    const int cv = k / Ng, cu = k - cv * Ng;
+    const int tx = cu >> lt, ty = cv >> lt, ou = cu & (T - 1), ov = cv & (T - 1);
     Acc sum;
     sum.x = 0;
     sum.y = 0;
@@ -578,11 +581,22 @@ __device__ __forceinline__ void fold_cells(const typename ScratchOf<R, KAHAN>::T
         int stx = tx - dx, sty = ty - dy;
         stx += stx < 0 ? ntx : 0;
         sty += sty < 0 ? ntx : 0;
-        int t = sty * ntx + stx;
-        int off = (ov + dy * T) * S + (ou + dx * T);
-        int e = tile_items[t + 1];
-        for (int i = tile_items[t]; i < e; ++i) {
-          Acc a = scratch[(int64_t)i * cells + off];
+        const int t = sty * ntx + stx;
+        const int off = (ov + dy * T) * S + (ou + dx * T);
+        const int e = tile_items[t + 1];
+        int i = tile_items[t];
+        for (; i + 4 <= e; i += 4) {
+          Acc a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = scratch[(int64_t)(i + u) * cells + off];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            sum.x += a[u].x;
+            sum.y += a[u].y;
+          }
+        }
+        for (; i < e; ++i) {
+          const Acc a = scratch[(int64_t)i * cells + off];
           sum.x += a.x;
           sum.y += a.y;
         }
