@@ -663,15 +663,23 @@ def batched_leg(ms, dev, nchan, precision, steps=3):
     workload, uv scaled per channel over 350-1050 MHz, U(0, 0.5) random
     flagging per channel): one degrid + grid pass over both partitions of
     every channel, as one batched call pair against one call pair per
-    (channel, partition) job.  Visibility values are random (the operator's
-    time does not depend on them)."""
+    (channel, partition) job; every channel's step-one minor cycle as one
+    batched call against one call per channel; and the whole two-step
+    reconstruction of every channel (5 + 5 major cycles of 100 iterations)
+    as one batched call against one call per channel.  The gridding layout
+    (tile side, rows per work item) is the autotuner's pick on channel 0.
+    Visibility values are random (the kernels' time does not depend on
+    them)."""
     import torch
     import synth
     t0 = time.perf_counter()
     w = synth.multi_channel(npix=1024, nchan=nchan, seed=11)
     gen_s = time.perf_counter() - t0
+    tile, chunk, tune_ms = ms.ms_plan_autotune(w.u[:1], w.v[:1], w.npix, w.pixel_size, w.ell_px,
+                                               w.delta_px, flags=w.flags[:1],
+                                               precision=precision, device=dev.index or 0)
     plan = ms.Plan(w.u, w.v, w.npix, w.pixel_size, w.ell_px, w.delta_px, flags=w.flags,
-                   precision=precision, device=dev.index or 0)
+                   precision=precision, device=dev.index or 0, tile=tile, chunk=chunk)
     del w.u, w.v
     g = torch.Generator(device=dev).manual_seed(3)
     jobs = [(c, p) for c in range(nchan) for p in ("L", "H")]
@@ -696,7 +704,8 @@ def batched_leg(ms, dev, nchan, precision, steps=3):
     out = {"workload": f"{nchan} channels x 1024^2, 350-1050 MHz, U(0,0.5) flagging, "
                        f"L and H partitions of every channel ({len(jobs)} jobs)",
            "rows_per_pass": int(rows), "precision": precision,
-           "host_uv_generation_s": round(gen_s, 1)}
+           "host_uv_generation_s": round(gen_s, 1),
+           "autotuned_layout": {"tile": tile, "chunk": chunk, "degrid_grid_ms_chan0": tune_ms}}
     for name, fn in (("batched", batched_pass), ("per_job", per_job_pass)):
         fn()
         torch.cuda.synchronize()
@@ -738,6 +747,29 @@ def batched_leg(ms, dev, nchan, precision, steps=3):
         "batched_job_iterations_per_s": job_its / (bst[0].minor_ms / 1000.0),
         "per_job_iterations_per_s": job_its / (per_job_ms / 1000.0),
         "speedup_batched_vs_per_job": per_job_ms / bst[0].minor_ms}
+    # the whole method on every channel (config 4's end-to-end form)
+    opts = ms.ReconOptions(n_major=N_MAJOR, fista_iters=FISTA_ITERS)
+    vlist = [vis[c] for c in range(nchan)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    _, _, rst = plan.reconstruct_two_step_batch(vlist, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    batched_ms = e0.elapsed_time(e1)
+    e0.record()
+    for c in range(nchan):
+        plan.reconstruct_two_step(vlist[c], opts, chan=c)
+    e1.record()
+    torch.cuda.synchronize()
+    per_ch_ms = e0.elapsed_time(e1)
+    gridded = sum(st.gridded_vis for st in rst)
+    out["two_step"] = {
+        "channels": nchan, "schedule": f"{N_MAJOR} + {N_MAJOR} major cycles x {FISTA_ITERS}",
+        "batched_ms": batched_ms, "per_channel_ms": per_ch_ms,
+        "speedup_batched_vs_per_channel": per_ch_ms / batched_ms,
+        "fista_iterations": int(sum(st.total_iterations for st in rst)),
+        "gridded_vis": int(gridded), "gridded_vis_per_s": gridded / (batched_ms / 1000.0)}
     plan.close()
     return out
 
