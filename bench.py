@@ -376,9 +376,12 @@ def record_traffic(paths, precision):
             for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
                 b += float(r[idx[m]].replace(",", "")) * scale[units[idx[m]]]
             launches.append((name, b))
-        syn = [b for n, b in launches if "synthesis_level_kernel" in n]
+        # (levels J..2 are one cooperative launch, or one launch per level)
+        syn = [b for n, b in launches
+               if "synthesis_level_kernel" in n or "coarse_synthesis_kernel" in n]
         ana = [b for n, b in launches
-               if "analysis_level_kernel" in n or "analysis_l1_tile_kernel" in n]
+               if "analysis_level_kernel" in n or "analysis_l1_tile_kernel" in n
+               or "coarse_analysis_kernel" in n]
         if syn:
             fams["synth"], fams["synth_l1"] = sum(syn[:-1]), syn[-1]
         if ana:
@@ -873,7 +876,8 @@ def kernel_source_digest(fam):
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2406_18356_gb300", "csrc")
-    for f in (FAMILY_SOURCE[fam], "common.cuh"):
+    extra = ("coarse_levels.cuh",) if FAMILY_SOURCE[fam] == "wavelet_kernels.cu" else ()
+    for f in (FAMILY_SOURCE[fam], "common.cuh") + extra:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
