@@ -78,8 +78,16 @@ typedef enum { MS_CONV_CIRCULAR = 0, MS_CONV_LINEAR = 1 } ms_convolution;
 typedef enum { MS_PART_L = 0, MS_PART_H = 1, MS_PART_ALL = 2 } ms_part;
 
 /* Minor-cycle problems: LOW = Eq. LowRes (Sect. 3.2) on V_L, FULL = Eq. FullRes
- * (Sect. 3.3) on V_H, SINGLE = the LowRes problem on all rows (Sect. 5). */
-typedef enum { MS_STEP_LOW = 0, MS_STEP_FULL = 1, MS_STEP_SINGLE = 2 } ms_step;
+ * (Sect. 3.3) on V_H, SINGLE = the LowRes problem on all rows (Sect. 5).  The
+ * interleaved pipeline (ms_reconstruct_interleaved) adds LOW_H = the LowRes
+ * problem on V_H, and FULL_L = Eq. FullRes on V_L with the two sides of the
+ * band exchanged: data term ||G'_L (i~ - H x)||^2, prior ||G'_H (l - x)||^2,
+ * G'_L, G'_H Sect. 3.3's filters with sigma^2 and eta^2 exchanged (weight
+ * 1/sigma^2 below ell - delta on the data, 1/eta^2 above ell + delta on the
+ * prior image). */
+typedef enum {
+  MS_STEP_LOW = 0, MS_STEP_FULL = 1, MS_STEP_SINGLE = 2, MS_STEP_LOW_H = 3, MS_STEP_FULL_L = 4
+} ms_step;
 
 /* lambda rules: NORM2_2N is lambda_n = c ||i~_n||_2 2^n (Sect. 5, App. A.2);
  * MAX_FIXED is lambda = c max|i~_1|, held for all cycles of a step. */
@@ -360,6 +368,26 @@ ms_status ms_reconstruct_two_step(ms_plan* plan, int32_t chan, const void* vis,
                                   const ms_recon_opts* opts, void* img_low_out,
                                   void* img_out, void* model_out, ms_stats* stats,
                                   void* stream);
+
+/* The interleaved two-image pipeline (Sect. 6, Fig. InterleavedMultiStepPipeline),
+ * in this reading: node L (V_L) and node H (V_H) each keep a model; in major
+ * cycle 1 each solves Eq. LowRes on its residual (LOW, LOW_H); from cycle 2
+ * node H solves Eq. FullRes with l = model_L - model_H (FULL) and node L the
+ * mirrored problem with l = model_H - model_L (FULL_L), both on the models
+ * of the previous cycle, so the two minor cycles of a major cycle run as one
+ * batched launch (the pipeline's parallelism on one GPU).  sigma^2 of each
+ * node: Sect. 4.3's estimate on its first residual, eta^2 = 1e-3 sigma^2
+ * (opts->sigma2 / eta2 are not used); lambda_n = c ||i~_n||_2 2^n with c =
+ * lambda_low (node L), lambda_full (node H).  Node images: last residual +
+ * model (node_l_out, node_h_out, dev N*N, may be NULL); the combined image
+ * (img_out, dev N*N) takes eta_H^2 g_L^2 of node L's image and sigma_H^2
+ * g_H^2 of node H's in the Fourier domain (weights that sum to one; g_L, g_H
+ * node H's filters).  stats: NULL or [2] (node L, node H).  Requirements of
+ * ms_minor_cycle_batch; opts->warm_start must be NULL. */
+ms_status ms_reconstruct_interleaved(ms_plan* plan, int32_t chan, const void* vis,
+                                     const ms_recon_opts* opts, void* img_out,
+                                     void* node_l_out, void* node_h_out, ms_stats* stats,
+                                     void* stream);
 
 /* The single-step baseline (Sect. 5): step one's problem on V_L u V_H. */
 ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vis,

@@ -23,7 +23,7 @@ MS_OK, MS_ERR_ARG, MS_ERR_CUDA, MS_ERR_OOM, MS_ERR_NUMERIC = 0, 1, 2, 3, 4
 MS_ERR_TIMEOUT, MS_ERR_NOT_CONVERGED, MS_ERR_STATE, MS_ERR_UNSUPPORTED = 5, 6, 7, 8
 MS_FP64, MS_FP32, MS_FP32_KAHAN = 0, 1, 2
 MS_PART_L, MS_PART_H, MS_PART_ALL = 0, 1, 2
-MS_STEP_LOW, MS_STEP_FULL, MS_STEP_SINGLE = 0, 1, 2
+MS_STEP_LOW, MS_STEP_FULL, MS_STEP_SINGLE, MS_STEP_LOW_H, MS_STEP_FULL_L = 0, 1, 2, 3, 4
 MS_LAMBDA_NORM2_2N, MS_LAMBDA_MAX_FIXED = 0, 1
 
 PRECISIONS = {"fp64": MS_FP64, "fp32": MS_FP32, "fp32_kahan": MS_FP32_KAHAN}
@@ -32,7 +32,8 @@ DICTIONARIES = {"daubechies": MS_DICT_DAUBECHIES, "iuwt": MS_DICT_IUWT}
 MS_CONV_CIRCULAR, MS_CONV_LINEAR = 0, 1
 CONVOLUTIONS = {"circular": MS_CONV_CIRCULAR, "linear": MS_CONV_LINEAR}
 PARTS = {"L": MS_PART_L, "H": MS_PART_H, "ALL": MS_PART_ALL}
-STEPS = {"low": MS_STEP_LOW, "full": MS_STEP_FULL, "single": MS_STEP_SINGLE}
+STEPS = {"low": MS_STEP_LOW, "full": MS_STEP_FULL, "single": MS_STEP_SINGLE,
+         "low_h": MS_STEP_LOW_H, "full_l": MS_STEP_FULL_L}
 
 
 class MsError(RuntimeError):
@@ -106,6 +107,8 @@ _SIGNATURES = {
     "ms_reconstruct_single_step_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_P),
                                          ctypes.POINTER(ms_recon_opts), ctypes.POINTER(_P),
                                          ctypes.POINTER(ms_stats), _P],
+    "ms_reconstruct_interleaved": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P, _P,
+                                   ctypes.POINTER(ms_stats), _P],
     "ms_plan_autotune": [ctypes.POINTER(ms_plan_desc), _I32, _I32, ctypes.POINTER(_I32),
                          ctypes.POINTER(_I32), ctypes.POINTER(_D)],
     "ms_residual_image": [_P, _I32, _I32, _P, _P, _P, _P],
@@ -519,6 +522,23 @@ class Plan:
         _, outs, st = self._recon_batch(False, vis, opts, chans, None, outs, stream)
         return outs, st
 
+    def reconstruct_interleaved(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
+                                out=None, node_l=None, node_h=None, stream=None):
+        """The interleaved two-image pipeline (ms_reconstruct_interleaved):
+        returns (combined image, node L's image, node H's image,
+        [Stats of node L, Stats of node H])."""
+        opts = opts or ReconOptions()
+        out, node_l, node_h = self._image(out), self._image(node_l), self._image(node_h)
+        co = opts.to_c()
+        st = (ms_stats * 2)()
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_reconstruct_interleaved(
+            self._h, chan, self._need(vis, self.complex_dtype, self.nvis, "vis"), ctypes.byref(co),
+            self._need(out, self.real_dtype, n2, "img_out"),
+            self._need(node_l, self.real_dtype, n2, "node_l_out"),
+            self._need(node_h, self.real_dtype, n2, "node_h_out"), st, _stream_handle(stream)))
+        return out, node_l, node_h, [Stats.from_c(st[0]), Stats.from_c(st[1])]
+
     def reconstruct_two_step(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
                              low_out=None, out=None, model_out=None, stream=None):
         opts = opts or ReconOptions()
@@ -630,6 +650,10 @@ def ms_grid_batch(plan: Plan, jobs, vis, outs=None, stream=None):
 
 def ms_degrid_batch(plan: Plan, jobs, images, vis_obs=None, outs=None, stream=None):
     return plan.degrid_batch(jobs, images, vis_obs, outs, stream)
+
+
+def ms_reconstruct_interleaved(plan: Plan, vis, opts=None, chan: int = 0, stream=None):
+    return plan.reconstruct_interleaved(vis, opts, chan, stream=stream)
 
 
 def ms_minor_cycle_batch(plan: Plan, jobs, max_iters: int, rel_tol: float = 0.0, outs=None,

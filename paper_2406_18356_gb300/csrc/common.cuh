@@ -377,7 +377,10 @@ template <typename R>
 void launch_real_part_spectrum(const C2<R>* in, R* out, int n, cudaStream_t s);
 template <typename R>
 void launch_filters(int N, double ell, double delta, const FistaCtl* ctl, R* gl2, R* gh2,
-                    cudaStream_t s);
+                    cudaStream_t s, int mirror = 0);
+template <typename R>
+void launch_combine_spectra(C2<R>* a, const C2<R>* b, const R* gl2, const R* gh2,
+                            const FistaCtl* ctl, int N, cudaStream_t s);
 template <typename R>
 void launch_normal_spectrum(const R* Hhat, const R* gl2, const R* gh2, int N, int M, R* Ks,
                             double* parts, FistaCtl* ctl, int32_t* ticket, cudaStream_t s);

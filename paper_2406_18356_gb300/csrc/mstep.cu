@@ -231,6 +231,9 @@ __global__ void check_noise_kernel(FistaCtl* ctl) {
 }  // namespace
 
 // ====================================================================== plan
+// FULL-kind problems (Eq. FullRes, and its mirror on V_L)
+inline bool step_full(int step) { return step == MS_STEP_FULL || step == MS_STEP_FULL_L; }
+
 struct PartDev {
   int64_t n = 0;
   int32_t* idx = nullptr;
@@ -847,7 +850,7 @@ template <typename R> void record_linear_pass(ms_plan* p, int parity, bool full)
 
 template <typename R> void record_pass(ms_plan* p, int parity, int step) {
   if (p->conv == MS_CONV_LINEAR)
-    record_linear_pass<R>(p, parity, step == MS_STEP_FULL);
+    record_linear_pass<R>(p, parity, step_full(step));
   else
     record_fista_pass<R>(p, parity, plan_view<R>(p));
 }
@@ -856,7 +859,7 @@ template <typename R> void record_pass(ms_plan* p, int parity, int step) {
 // for the linear one, one per problem kind)
 template <typename R> cudaGraphExec_t ensure_fista_graph(ms_plan* p, int step) {
   cudaGraphExec_t* exec = p->conv == MS_CONV_LINEAR
-                              ? &p->lin_exec[step == MS_STEP_FULL ? 1 : 0]
+                              ? &p->lin_exec[step_full(step) ? 1 : 0]
                               : &p->fista_exec;
   if (*exec) return *exec;
   cudaGraph_t graph;
@@ -975,10 +978,11 @@ template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, doubl
     ck(cudaMemcpyAsync(p->lh2, pd.Hhat2, sizeof(R) * 2 * p->N * (p->N + 1),
                        cudaMemcpyDeviceToDevice, p->ps),
        "copy");
-    const bool full = step == MS_STEP_FULL;
+    const bool full = step_full(step);
     if (full) {
       check_noise_kernel<<<1, 1, 0, p->ps>>>(p->ctl);
-      launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
+      launch_filters<R>(p->N, ell, delta, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps,
+                        step == MS_STEP_FULL_L);
     }
     // the bound (and c0 = 0), then the step size itself: the operator is not
     // circulant, so the closed form is only a bound; power iteration from
@@ -993,9 +997,10 @@ template <typename R> void build_normal(ms_plan* p, int step, PartDev& pd, doubl
   // (a batched job's own control block and K^ slice, else the plan's)
   FistaCtl* c = ctl ? ctl : p->ctl;
   R* K = Ks ? Ks : (R*)p->Ks;
-  if (step == MS_STEP_FULL) {
+  if (step_full(step)) {
     check_noise_kernel<<<1, 1, 0, p->ps>>>(c);
-    launch_filters<R>(p->N, ell, delta, c, (R*)p->gl2, (R*)p->gh2, p->ps);
+    launch_filters<R>(p->N, ell, delta, c, (R*)p->gl2, (R*)p->gh2, p->ps,
+                      step == MS_STEP_FULL_L);
     launch_normal_spectrum<R>((const R*)pd.Hhat, (const R*)p->gl2, (const R*)p->gh2, p->N, p->M,
                               K, p->parts, c, p->tickets + 2, p->ps);
   } else {
@@ -1015,7 +1020,7 @@ template <typename R>
 void build_b(ms_plan* p, int step, PartDev& pd, const void* residual, const void* l_low,
              FistaCtl* ctl, C2<R>* Bs) {
   fft_r2c<R>(p, residual, p->spec);
-  if (step == MS_STEP_FULL) {
+  if (step_full(step)) {
     fft_r2c<R>(p, l_low, p->spec2);
     launch_b_spectrum<R>((const C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)pd.Hhat,
                          (const R*)p->gl2, (const R*)p->gh2, p->N, Bs, p->parts, ctl,
@@ -1040,7 +1045,7 @@ void run_fista(ms_plan* p, int step, PartDev& pd, const void* residual, const vo
     // spectra of pass -1 zero (their weight t_0 is zero, but must be finite)
     ck(cudaMemcpyAsync(p->lres, residual, sizeof(R) * npix2, cudaMemcpyDeviceToDevice, p->ps),
        "copy");
-    if (step == MS_STEP_FULL) {
+    if (step_full(step)) {
       ck(cudaMemcpyAsync(p->ll, l_low, sizeof(R) * npix2, cudaMemcpyDeviceToDevice, p->ps),
          "copy");
       ck(cudaMemsetAsync(p->ldes[1], 0, sizeof(C2<R>) * 2 * nspec, p->ps), "memset");
@@ -1122,7 +1127,11 @@ template <typename R> void fill_stats(ms_plan* p, ms_stats* st, bool copy_trace)
 }
 
 int step_part(int step) {
-  return step == MS_STEP_LOW ? MS_PART_L : (step == MS_STEP_FULL ? MS_PART_H : MS_PART_ALL);
+  switch (step) {
+    case MS_STEP_LOW: case MS_STEP_FULL_L: return MS_PART_L;
+    case MS_STEP_FULL: case MS_STEP_LOW_H: return MS_PART_H;
+    default: return MS_PART_ALL;
+  }
 }
 
 // ------------------------------------------------------- learned warm start
@@ -1567,7 +1576,7 @@ void lipschitz(ms_plan* p, int step, int chan, double sigma2, double eta2, int p
   if (closed) *closed = h.theta;
   if (power) *power = 0.0;
   if (power_iters <= 0) return;
-  power_theta<R>(p, power_iters, step == MS_STEP_FULL);
+  power_theta<R>(p, power_iters, step_full(step));
   double* sc = p->scal;
   double rho = 0;
   ck(cudaMemcpyAsync(&rho, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, p->ps), "copy");
@@ -1581,12 +1590,12 @@ void minor_cycle(ms_plan* p, int step, int chan, const void* residual, const voi
                  void* beta_inout, void* model_out, ms_stats* st) {
   PartDev& pd = part_of(p, step_part(step), chan);
   arg(residual != nullptr && model_out != nullptr, "residual and model_out are required");
-  arg(step != MS_STEP_FULL || l_low != nullptr, "FULL needs l_low");
+  arg(!step_full(step) || l_low != nullptr, "FULL needs l_low");
   arg(max_iters >= 1 && max_iters <= 1000000, "max_iters must be 1..1e6");
   arg(lambda >= 0 && std::isfinite(lambda), "lambda must be finite and >= 0");
   ensure_trace(p, max_iters);
   init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, max_iters, rel_tol, lambda, 1, sigma2, eta2,
-                                      step == MS_STEP_FULL ? 1 : 0);
+                                      step_full(step) ? 1 : 0);
   build_normal<R>(p, step, pd, p->d.ell_px, p->d.delta_px);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ck(cudaEventCreate(&e0), "event");
@@ -2062,9 +2071,9 @@ void minor_cycle_batch(ms_plan* p, int njobs, const int32_t* steps, const int32_
   const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
   for (int j = 0; j < njobs; ++j) {
     const int step = steps[j];
-    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_FULL_L, "unknown step");
     arg(residuals[j] && models_out[j], "a job's residual or model pointer is NULL");
-    const bool full = step == MS_STEP_FULL;
+    const bool full = step_full(step);
     arg(!full || (l_lows && l_lows[j] && sigma2s && eta2s), "FULL jobs need l_low, sigma2, eta2");
     arg(lambdas[j] >= 0 && std::isfinite(lambdas[j]), "lambda must be finite and >= 0");
     PartDev& pd = part_of(p, step_part(step), chans[j]);
@@ -2104,17 +2113,17 @@ void minor_cycle_batch(ms_plan* p, int njobs, const int32_t* steps, const int32_
     }
 }
 
-// residual images of several channels' partition `part` at once: jobs j get
-// obs = vis[j] (original order), model models + j N^2, residual res + j N^2;
+// residual images of several (channel, partition) jobs at once: job j takes
+// partition parts[j] of channel chans[j], obs = vis[j] (original order),
+// model models + j N^2, residual res + j N^2;
 // one pad / FFT / degridding launch over all jobs, then the residual rows
 // (left in plan order) through one gridding / fold / FFT / crop
 template <typename R>
-void residual_batch(ms_plan* p, int njobs, const int32_t* chans, int part,
+void residual_batch(ms_plan* p, int njobs, const int32_t* chans, const int32_t* parts,
                     const void* const* vis, const R* models, R* res) {
   const int64_t n2 = (int64_t)p->N * p->N;
-  std::vector<int32_t> parts(njobs, part);
   std::vector<BatchJob<R>> jobs;
-  const BatchShape sh = batch_jobs<R>(p, njobs, chans, parts.data(), jobs);
+  const BatchShape sh = batch_jobs<R>(p, njobs, chans, parts, jobs);
   for (int j = 0; j < njobs; ++j) {
     arg(vis[j] != nullptr, "a job's visibilities are NULL");
     jobs[j].user_in = (const C2<R>*)vis[j];
@@ -2180,6 +2189,7 @@ void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
   const int N = p->N;
   const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
   const int part = step_part(step);
+  const std::vector<int32_t> parts(njobs, part);
   const bool full = step == MS_STEP_FULL;
   R* model = (R*)F.model;
   R* res = (R*)F.res;
@@ -2189,7 +2199,7 @@ void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
                       : full ? o.lambda_full : o.lambda_single;
   std::vector<FistaCtl> h(njobs);
   for (int n = 1; n <= o.n_major; ++n) {
-    residual_batch<R>(p, njobs, chans, part, vis, model, res);
+    residual_batch<R>(p, njobs, chans, parts.data(), vis, model, res);
     for (int j = 0; j < njobs; ++j) {
       FistaCtl* c = F.ctl + j;
       R* rj = res + j * n2;
@@ -2229,7 +2239,7 @@ void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
       }
     }
   }
-  residual_batch<R>(p, njobs, chans, part, vis, model, res);   // i~_{N+1}
+  residual_batch<R>(p, njobs, chans, parts.data(), vis, model, res);   // i~_{N+1}
   for (int j = 0; j < njobs; ++j) {
     launch_axpby<R>(res + j * n2, model + j * n2, (R*)out[j], 1.0, 1.0, n2, p->ps);
     if (stats) {
@@ -2244,6 +2254,119 @@ void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
       stats[j].eta2 = h[j].eta2;
     }
   }
+}
+
+// The interleaved two-image pipeline (ms_reconstruct_interleaved): node L
+// (job 0, V_L) and node H (job 1, V_H) of channel `chan`; each major cycle
+// one batched residual pass and one batched minor cycle serve both nodes.
+template <typename R>
+void interleaved(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, void* img_out,
+                 void* node_l_out, void* node_h_out, ms_stats* stats, void* stream) {
+  check_batchable(p);
+  validate_opts(o);
+  arg(o->warm_start == nullptr, "the interleaved pipeline takes no warm start network");
+  arg(vis && img_out, "vis and img_out are required");
+  arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+  arg(p->ch[chan].part[MS_PART_L].n > 0 && p->ch[chan].part[MS_PART_H].n > 0,
+      "both partitions need visibilities");
+  Scope sc(p, stream);
+  if (stats) std::memset(stats, 0, sizeof(ms_stats) * 2);
+  ensure_fista_batch<R>(p, 2, o->fista_iters);
+  FistaBatch& F = p->fb;
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N, nspec = (int64_t)N * (N / 2 + 1);
+  R* model = (R*)F.model;   // [node L, node H]
+  R* res = (R*)F.res;
+  R* l = (R*)F.l;
+  const int32_t chans[2] = {chan, chan}, parts[2] = {MS_PART_L, MS_PART_H};
+  const void* const visv[2] = {vis, vis};
+  const double coef[2] = {o->lambda_low, o->lambda_full};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaEventRecord(e0, p->ps), "event");
+  ck(cudaMemsetAsync(model, 0, sizeof(R) * 2 * n2, p->ps), "memset");
+  std::vector<FistaCtl> h(2);
+  for (int n = 1; n <= o->n_major; ++n) {
+    residual_batch<R>(p, 2, chans, parts, visv, model, res);
+    // cycle 1: Eq. LowRes on each node's data; then node L the mirrored
+    // FullRes problem, node H Eq. FullRes, each against the other's model
+    const int kind[2] = {n == 1 ? MS_STEP_LOW : MS_STEP_FULL_L,
+                         n == 1 ? MS_STEP_LOW_H : MS_STEP_FULL};
+    for (int j = 0; j < 2; ++j) {
+      FistaCtl* c = F.ctl + j;
+      R* rj = res + j * n2;
+      PartDev& pd = part_of(p, parts[j], chan);
+      launch_image_norms<R>(rj, n2, p->parts, c, p->tickets + 5, p->ps);
+      if (n == 1) {
+        init_ctl_kernel<<<1, 1, 0, p->ps>>>(c, o->fista_iters, o->rel_tol, 0.0, 0, 0, 0, 0);
+        // sigma^2 on the node's first residual, eta^2 = 1e-3 sigma^2
+        launch_sigma2_hat<R>(rj, N, p->parts, c, p->tickets + 6, 1, p->ps);
+      }
+      init_ctl_kernel<<<1, 1, 0, p->ps>>>(c, o->fista_iters, o->rel_tol, 0.0, 0, 0, 0, 0);
+      if (n <= 2)   // the problem's operator changes once, at cycle 2
+        build_normal<R>(p, kind[j], pd, p->d.ell_px, p->d.delta_px, c, (R*)F.Ks + j * nspec);
+      launch_set_lambda(c, o->lambda_rule, coef[j], n, n == 1 ? 1 : 0, p->ps);
+      R* lj = nullptr;
+      if (n >= 2) {
+        lj = l + j * n2;   // the other node's model minus this one's
+        launch_axpby<R>(model + (1 - j) * n2, model + j * n2, lj, 1.0, -1.0, n2, p->ps);
+        launch_filters<R>(N, p->d.ell_px, p->d.delta_px, c, (R*)p->gl2, (R*)p->gh2, p->ps,
+                          kind[j] == MS_STEP_FULL_L);
+      }
+      build_b<R>(p, kind[j], pd, rj, lj, c, (C2<R>*)F.Bs + j * nspec);
+    }
+    run_fista_batch<R>(p, 2, o->fista_iters, o->rel_tol);
+    launch_axpby<R>(model, (const R*)F.x, model, 1.0, 1.0, 2 * n2, p->ps);
+    ck(cudaMemcpyAsync(h.data(), F.ctl, sizeof(FistaCtl) * 2, cudaMemcpyDeviceToHost, p->ps),
+       "read ctl");
+    ck(cudaStreamSynchronize(p->ps), "synchronize");
+    for (int j = 0; j < 2; ++j) {
+      if (h[j].error)
+        throw Fail{(ms_status)h[j].error, "non-finite objective or invalid noise levels"};
+      if (stats) {
+        stats[j].total_iterations += h[j].k;
+        stats[j].gridded_vis += part_of(p, parts[j], chan).n;
+      }
+    }
+  }
+  residual_batch<R>(p, 2, chans, parts, visv, model, res);   // i~_{N+1} of both nodes
+  R* fin = (R*)F.l;   // the nodes' final images: last residual + model
+  launch_axpby<R>(res, model, fin, 1.0, 1.0, 2 * n2, p->ps);
+  if (node_l_out)
+    ck(cudaMemcpyAsync(node_l_out, fin, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps), "copy");
+  if (node_h_out)
+    ck(cudaMemcpyAsync(node_h_out, fin + n2, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps),
+       "copy");
+  // combination with node H's filters: eta^2 g_L^2 F(node L) + sigma^2 g_H^2 F(node H)
+  launch_filters<R>(N, p->d.ell_px, p->d.delta_px, F.ctl + 1, (R*)p->gl2, (R*)p->gh2, p->ps);
+  fft_r2c<R>(p, fin, p->spec);
+  fft_r2c<R>(p, fin + n2, p->spec2);
+  launch_combine_spectra<R>((C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)p->gl2,
+                            (const R*)p->gh2, F.ctl + 1, N, p->ps);
+  fft_c2r<R>(p, p->spec, img_out);
+  ck(cudaEventRecord(e1, p->ps), "event");
+  check_device_error(p);
+  float ms = 0;
+  ck(cudaEventSynchronize(e1), "event");
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int j = 0; j < 2; ++j) {
+      ms_stats& st = stats[j];
+      st.gridded_vis += part_of(p, parts[j], chan).n;
+      st.major_cycles = o->n_major;
+      st.iterations = h[j].k;
+      st.converged = h[j].converged;
+      st.objective = h[j].F_cur;
+      st.lambda = h[j].lam;
+      st.theta = h[j].theta;
+      st.sigma2 = h[j].sigma2;
+      st.eta2 = h[j].eta2;
+      st.elapsed_ms = ms;
+    }
+  sc.finish();
 }
 
 // ms_reconstruct_two_step_batch / ms_reconstruct_single_step_batch
@@ -2570,8 +2693,8 @@ ms_status ms_lipschitz(ms_plan* p, int32_t step, int32_t chan, double sigma2, do
                        int32_t power_iters, double* theta_closed, double* theta_power,
                        void* stream) {
   return guarded(p, [&] {
-    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
-    arg(step != MS_STEP_FULL || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_FULL_L, "unknown step");
+    arg(!step_full(step) || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
     Scope sc(p, stream);
     DISPATCH(p, lipschitz<R>(p, step, chan, sigma2, eta2, power_iters, theta_closed,
                              theta_power));
@@ -2584,8 +2707,8 @@ ms_status ms_minor_cycle(ms_plan* p, int32_t step, int32_t chan, const void* res
                          int32_t max_iters, double rel_tol, void* beta_inout, void* model_out,
                          ms_stats* st, void* stream) {
   return guarded(p, [&] {
-    arg(step >= MS_STEP_LOW && step <= MS_STEP_SINGLE, "unknown step");
-    arg(step != MS_STEP_FULL || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
+    arg(step >= MS_STEP_LOW && step <= MS_STEP_FULL_L, "unknown step");
+    arg(!step_full(step) || (sigma2 > 0 && eta2 > 0), "FULL needs sigma2, eta2 > 0");
     arg(rel_tol >= 0, "rel_tol must be >= 0");
     if (st) std::memset(st, 0, sizeof(*st));
     Scope sc(p, stream);
@@ -2743,6 +2866,14 @@ ms_status ms_reconstruct_two_step_batch(ms_plan* p, int32_t njobs, const int32_t
   return guarded(p, [&] {
     DISPATCH(p, reconstruct_batch<R>(p, true, njobs, chans, vis, o, low_out, img_out, stats,
                                      stream));
+  });
+}
+
+ms_status ms_reconstruct_interleaved(ms_plan* p, int32_t chan, const void* vis,
+                                     const ms_recon_opts* o, void* img_out, void* node_l_out,
+                                     void* node_h_out, ms_stats* stats, void* stream) {
+  return guarded(p, [&] {
+    DISPATCH(p, interleaved<R>(p, chan, vis, o, img_out, node_l_out, node_h_out, stats, stream));
   });
 }
 

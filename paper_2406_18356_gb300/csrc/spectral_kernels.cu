@@ -157,10 +157,12 @@ void launch_real_part_spectrum(const C2<R>* in, R* out, int n, cudaStream_t s) {
 // r = sqrt(kx^2 + ky^2) on the rfft half-plane, pixel units.  Squares stored.
 template <typename R>
 __global__ void filters_kernel(int N, double ell, double delta, const FistaCtl* __restrict__ ctl,
-                               R* __restrict__ gl2, R* __restrict__ gh2) {
+                               R* __restrict__ gl2, R* __restrict__ gh2, int mirror) {
   const int nc = N / 2 + 1;
   const int64_t total = (int64_t)N * nc;
-  const double s2 = ctl->sigma2, e2 = ctl->eta2;
+  // mirror: the sides exchanged (sigma^2 and eta^2 swapped, data weights on
+  // the low side into gh2, prior weights on the high side into gl2)
+  const double s2 = mirror ? ctl->eta2 : ctl->sigma2, e2 = mirror ? ctl->sigma2 : ctl->eta2;
   const double pi = 3.141592653589793238462643383279502884;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -180,15 +182,43 @@ __global__ void filters_kernel(int N, double ell, double delta, const FistaCtl* 
       l2 = a2 * (1.0 - sn) * (1.0 - sn);
       h2 = a2 * (1.0 + sn) * (1.0 + sn);
     }
-    gl2[k] = (R)l2;
-    gh2[k] = (R)h2;
+    gl2[k] = (R)(mirror ? h2 : l2);
+    gh2[k] = (R)(mirror ? l2 : h2);
   }
 }
 
 template <typename R>
 void launch_filters(int N, double ell, double delta, const FistaCtl* ctl, R* gl2, R* gh2,
-                    cudaStream_t s) {
-  filters_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(N, ell, delta, ctl, gl2, gh2);
+                    cudaStream_t s, int mirror) {
+  filters_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(N, ell, delta, ctl, gl2, gh2,
+                                                              mirror);
+}
+
+// a = (eta^2 g_L^2 a + sigma^2 g_H^2 b) / N^2 on the half-plane (sigma^2, eta^2
+// from ctl, g_L^2, g_H^2 the unscaled filters of launch_filters): the
+// interleaved pipeline's combination of its two nodes' images
+template <typename R>
+__global__ void combine_spectra_kernel(C2<R>* __restrict__ a, const C2<R>* __restrict__ b,
+                                       const R* __restrict__ gl2, const R* __restrict__ gh2,
+                                       const FistaCtl* __restrict__ ctl, int N) {
+  const int64_t total = (int64_t)N * (N / 2 + 1);
+  const double inv = 1.0 / ((double)N * N);
+  const R cl = (R)(ctl->eta2 * inv), ch = (R)(ctl->sigma2 * inv);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const R wl = cl * gl2[k], wh = ch * gh2[k];
+    const C2<R> x = a[k], y = b[k];
+    C2<R> o;
+    o.x = wl * x.x + wh * y.x;
+    o.y = wl * x.y + wh * y.y;
+    a[k] = o;
+  }
+}
+
+template <typename R>
+void launch_combine_spectra(C2<R>* a, const C2<R>* b, const R* gl2, const R* gh2,
+                            const FistaCtl* ctl, int N, cudaStream_t s) {
+  combine_spectra_kernel<R><<<spectral_partials(N), kThreads, 0, s>>>(a, b, gl2, gh2, ctl, N);
 }
 
 // ------------------------------------------------------------- K^ and theta
@@ -1635,7 +1665,10 @@ void launch_lin_theta(const R* H2, int N, const R* gl2, const R* gh2, int M, dou
 #define MS_INST(R)                                                                               \
   template void launch_ifftshift_real<R>(const R*, R*, int, cudaStream_t);                       \
   template void launch_real_part_spectrum<R>(const C2<R>*, R*, int, cudaStream_t);               \
-  template void launch_filters<R>(int, double, double, const FistaCtl*, R*, R*, cudaStream_t);   \
+  template void launch_filters<R>(int, double, double, const FistaCtl*, R*, R*, cudaStream_t,    \
+                                  int);                                                          \
+  template void launch_combine_spectra<R>(C2<R>*, const C2<R>*, const R*, const R*,              \
+                                          const FistaCtl*, int, cudaStream_t);                   \
   template void launch_normal_spectrum<R>(const R*, const R*, const R*, int, int, R*, double*,   \
                                           FistaCtl*, int32_t*, cudaStream_t);                    \
   template void launch_b_spectrum<R>(const C2<R>*, const C2<R>*, const R*, const R*, const R*,   \
