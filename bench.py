@@ -530,6 +530,22 @@ def main():
                "d2h_bytes_per_step": int(2 * hlow.numel() * hlow.element_size()),
                "ms_per_step": 1000 * e2e_s / args.steps}
 
+    # the interleaved two-image pipeline (Sect. 6's sketch) on the same data
+    # and schedule: n_major cycles per node, both nodes' minor cycles batched
+    interleaved = None
+    if rank == 0:
+        plan.reconstruct_interleaved(vis, opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, _, ist = plan.reconstruct_interleaved(vis, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        interleaved = {"ms": e0.elapsed_time(e1), "two_step_ms": ms_per_step,
+                       "fista_iterations": int(sum(s_.total_iterations for s_ in ist)),
+                       "note": "node L (V_L) and node H (V_H), each n_major cycles of "
+                               "fista_iters; the two-step runs n_major per step in sequence"}
+
     tte = None
     errors = {}
     if rank == 0 and not args.no_time_to_eps:
@@ -566,7 +582,7 @@ def main():
                                       "minor_cycles": tot["minor_ms"] / args.steps},
                 "gpu_launches": gpu_launches,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "time_to_eps": tte, "batched": batched,
+                "time_to_eps": tte, "batched": batched, "interleaved": interleaved,
                 "image_rel_l2_errors": errors or None,
                 "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()}
                 if prof else None}

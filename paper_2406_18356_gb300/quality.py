@@ -55,9 +55,11 @@ def iterations_to(trace, eps: float) -> int:
 
 def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 100,
           n_major_max: int = 7, fista_budget: int = 2000, grid=None, convergence: bool = True,
-          convolution: str = "circular"):
+          convolution: str = "circular", interleaved: bool = True):
     """Run the study on workload w (synth.Workload with a truth image) with
-    the minor cycle's PSF operator `convolution` ("circular" or "linear")."""
+    the minor cycle's PSF operator `convolution` ("circular" or "linear");
+    interleaved adds the interleaved two-image pipeline's images (Sect. 6's
+    sketch, n_major cycles per node) where the plan supports it."""
     import torch
     truth = w.truth
     tv = None
@@ -82,6 +84,14 @@ def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 1
                "psnr_low": psnr(low.double().cpu().numpy(), truth),
                "fista_iterations": st.total_iterations,
                "seconds": time.perf_counter() - t0}
+        if interleaved and convolution == "circular":   # (a batched-form feature)
+            t1 = time.perf_counter()
+            il, il_l, il_h, ist = plan.reconstruct_interleaved(vis, opts)
+            torch.cuda.synchronize()
+            rec["psnr_interleaved"] = psnr(il.double().cpu().numpy(), truth)
+            rec["psnr_interleaved_node_l"] = psnr(il_l.double().cpu().numpy(), truth)
+            rec["psnr_interleaved_node_h"] = psnr(il_h.double().cpu().numpy(), truth)
+            rec["interleaved_seconds"] = time.perf_counter() - t1
         out["partitions"].append(rec)
         if not single_done:
             single, _ = plan.reconstruct_single_step(vis, opts)

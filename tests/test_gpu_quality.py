@@ -40,6 +40,13 @@ def test_study_psnrs_match_the_oracle(ms):
     want = oi.psnr(single.image, w.truth)
     print(f"single step: library {got['psnr_single_step']:.4f} dB, oracle {want:.4f} dB")
     assert abs(got["psnr_single_step"] - want) <= 1e-3
+    # the interleaved pipeline's combined image, first partition
+    from oracle import interleaved as oil
+    (ell, delta), rec = grid[0], got["partitions"][0]
+    il = oil.reconstruct_interleaved(vis, u, v, 128, w.pixel_size, ell, delta, ro)
+    want = oi.psnr(il.image, w.truth)
+    print(f"interleaved: library {rec['psnr_interleaved']:.4f} dB, oracle {want:.4f} dB")
+    assert abs(rec["psnr_interleaved"] - want) <= 1e-3
 
 
 def test_study_reports_every_measure(ms):
