@@ -333,6 +333,7 @@ struct ms_plan {
   float* ws_out = nullptr;
   void* ws_x0 = nullptr;
   void* ws_beta = nullptr;
+  void* il_buf = nullptr;   // interleaved pipeline without the batched form: 6 images
   // profiling: CUDA-event spans per kernel family
   bool prof = false;
   bool capturing = false;
@@ -2256,13 +2257,122 @@ void run_step_batch(ms_plan* p, int step, int njobs, const int32_t* chans,
   }
 }
 
+// The interleaved pipeline on plans the batched form does not serve (the
+// linear PSF operator, the IUWT dictionary, N not a power of two): the two
+// nodes' minor cycles of a major cycle run one after the other on the plan's
+// own minor-cycle state, both reading the models of the previous cycle, so
+// the result is the batched form's.  Per node the plan's K^ and step size are
+// rebuilt for every minor cycle (one problem of each node at a time); the
+// lambda rule must be NORM2_2N.
+template <typename R>
+void interleaved_seq(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o,
+                     void* img_out, void* node_l_out, void* node_h_out, ms_stats* stats) {
+  arg(o->lambda_rule == MS_LAMBDA_NORM2_2N,
+      "the interleaved pipeline on this plan needs the NORM2_2N lambda rule");
+  const int N = p->N;
+  const int64_t n2 = (int64_t)N * N;
+  if (!p->il_buf) p->il_buf = p->alloc<R>(6 * n2, "interleaved images");
+  R* model = (R*)p->il_buf;   // [node L, node H]
+  R* res = model + 2 * n2;
+  R* l = res + 2 * n2;
+  ensure_trace(p, o->fista_iters);
+  const int parts[2] = {MS_PART_L, MS_PART_H};
+  const double coef[2] = {o->lambda_low, o->lambda_full};
+  double s2[2] = {0, 0}, e2[2] = {0, 0};
+  int64_t iters[2] = {0, 0};
+  FistaCtl h{};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ck(cudaEventCreate(&e0), "event");
+  ck(cudaEventCreate(&e1), "event");
+  ck(cudaEventRecord(e0, p->ps), "event");
+  ck(cudaMemsetAsync(model, 0, sizeof(R) * 2 * n2, p->ps), "memset");
+  auto residuals = [&]() {
+    for (int j = 0; j < 2; ++j) {
+      PartDev& pd = part_of(p, parts[j], chan);
+      launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+      residual_sorted<R>(p, pd, p->vis_a, model + j * n2, res + j * n2, nullptr);
+    }
+  };
+  for (int n = 1; n <= o->n_major; ++n) {
+    residuals();
+    if (n >= 2)   // the other node's model minus this one's, both of cycle n - 1
+      for (int j = 0; j < 2; ++j)
+        launch_axpby<R>(model + (1 - j) * n2, model + j * n2, l + j * n2, 1.0, -1.0, n2, p->ps);
+    const int kind[2] = {n == 1 ? MS_STEP_LOW : MS_STEP_FULL_L,
+                         n == 1 ? MS_STEP_LOW_H : MS_STEP_FULL};
+    for (int j = 0; j < 2; ++j) {
+      PartDev& pd = part_of(p, parts[j], chan);
+      R* rj = res + j * n2;
+      init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, o->fista_iters, o->rel_tol, 0.0, 0, s2[j],
+                                          e2[j], n > 1 ? 1 : 0);
+      launch_image_norms<R>(rj, n2, p->parts, p->ctl, p->tickets + 5, p->ps);
+      if (n == 1) {   // sigma^2 on the node's first residual, eta^2 = 1e-3 sigma^2
+        launch_sigma2_hat<R>(rj, N, p->parts, p->ctl, p->tickets + 6, 1, p->ps);
+        ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+        ck(cudaStreamSynchronize(p->ps), "synchronize");
+        s2[j] = h.sigma2;
+        e2[j] = h.eta2;
+      }
+      launch_set_lambda(p->ctl, o->lambda_rule, coef[j], n, n == 1 ? 1 : 0, p->ps);
+      build_normal<R>(p, kind[j], pd, p->d.ell_px, p->d.delta_px);
+      run_fista<R>(p, kind[j], pd, rj, n >= 2 ? l + j * n2 : nullptr, nullptr, o->fista_iters,
+                   o->rel_tol);
+      launch_axpby<R>(model + j * n2, (const R*)p->xwork, model + j * n2, 1.0, 1.0, n2, p->ps);
+      ck(cudaMemcpyAsync(&h, p->ctl, sizeof(h), cudaMemcpyDeviceToHost, p->ps), "read ctl");
+      ck(cudaStreamSynchronize(p->ps), "synchronize");
+      if (h.error) throw Fail{(ms_status)h.error, "non-finite objective or invalid noise levels"};
+      iters[j] += h.k;
+      if (stats) {
+        ms_stats& st = stats[j];
+        st.total_iterations = (int32_t)iters[j];
+        st.gridded_vis += pd.n;
+        st.iterations = h.k;
+        st.converged = h.converged;
+        st.objective = h.F_cur;
+        st.lambda = h.lam;
+        st.theta = h.theta;
+        st.sigma2 = s2[j];
+        st.eta2 = e2[j];
+        st.major_cycles = o->n_major;
+      }
+    }
+  }
+  residuals();   // i~_{N+1} of both nodes
+  R* fin = l;    // the nodes' final images: last residual + model
+  launch_axpby<R>(res, model, fin, 1.0, 1.0, 2 * n2, p->ps);
+  if (node_l_out)
+    ck(cudaMemcpyAsync(node_l_out, fin, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps), "copy");
+  if (node_h_out)
+    ck(cudaMemcpyAsync(node_h_out, fin + n2, sizeof(R) * n2, cudaMemcpyDeviceToDevice, p->ps),
+       "copy");
+  // combination with node H's filters
+  init_ctl_kernel<<<1, 1, 0, p->ps>>>(p->ctl, 1, 0.0, 0.0, 0, s2[1], e2[1], 1);
+  launch_filters<R>(N, p->d.ell_px, p->d.delta_px, p->ctl, (R*)p->gl2, (R*)p->gh2, p->ps);
+  fft_r2c<R>(p, fin, p->spec);
+  fft_r2c<R>(p, fin + n2, p->spec2);
+  launch_combine_spectra<R>((C2<R>*)p->spec, (const C2<R>*)p->spec2, (const R*)p->gl2,
+                            (const R*)p->gh2, p->ctl, N, p->ps);
+  fft_c2r<R>(p, p->spec, img_out);
+  ck(cudaEventRecord(e1, p->ps), "event");
+  check_device_error(p);
+  float ms = 0;
+  ck(cudaEventSynchronize(e1), "event");
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int j = 0; j < 2; ++j) {
+      stats[j].gridded_vis += part_of(p, parts[j], chan).n;
+      stats[j].elapsed_ms = ms;
+    }
+}
+
 // The interleaved two-image pipeline (ms_reconstruct_interleaved): node L
 // (job 0, V_L) and node H (job 1, V_H) of channel `chan`; each major cycle
 // one batched residual pass and one batched minor cycle serve both nodes.
 template <typename R>
 void interleaved(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, void* img_out,
                  void* node_l_out, void* node_h_out, ms_stats* stats, void* stream) {
-  check_batchable(p);
   validate_opts(o);
   arg(o->warm_start == nullptr, "the interleaved pipeline takes no warm start network");
   arg(vis && img_out, "vis and img_out are required");
@@ -2271,6 +2381,13 @@ void interleaved(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, 
       "both partitions need visibilities");
   Scope sc(p, stream);
   if (stats) std::memset(stats, 0, sizeof(ms_stats) * 2);
+  const bool batchable =
+      p->fused_spec && p->dict == MS_DICT_DAUBECHIES && p->conv == MS_CONV_CIRCULAR;
+  if (!batchable) {
+    interleaved_seq<R>(p, chan, vis, o, img_out, node_l_out, node_h_out, stats);
+    sc.finish();
+    return;
+  }
   ensure_fista_batch<R>(p, 2, o->fista_iters);
   FistaBatch& F = p->fb;
   const int N = p->N;

@@ -59,7 +59,7 @@ def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 1
     """Run the study on workload w (synth.Workload with a truth image) with
     the minor cycle's PSF operator `convolution` ("circular" or "linear");
     interleaved adds the interleaved two-image pipeline's images (Sect. 6's
-    sketch, n_major cycles per node) where the plan supports it."""
+    sketch, n_major cycles per node)."""
     import torch
     truth = w.truth
     tv = None
@@ -84,7 +84,7 @@ def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 1
                "psnr_low": psnr(low.double().cpu().numpy(), truth),
                "fista_iterations": st.total_iterations,
                "seconds": time.perf_counter() - t0}
-        if interleaved and convolution == "circular":   # (a batched-form feature)
+        if interleaved:
             t1 = time.perf_counter()
             il, il_l, il_h, ist = plan.reconstruct_interleaved(vis, opts)
             torch.cuda.synchronize()

@@ -112,3 +112,25 @@ def test_interleaved_pipeline_recovers_the_sky_with_complete_coverage(ms):
     print(f"interleaved, complete coverage: {e:.2e}")
     assert e <= 1e-4
     plan.close()
+
+
+@pytest.mark.parametrize("N,convolution", [(32, "linear"), (48, "circular")])
+def test_interleaved_pipeline_without_the_batched_form_matches_oracle(ms, N, convolution):
+    """Plans the batched form does not serve (the linear PSF operator; N = 48,
+    not a power of two) run the two nodes' minor cycles one after the other:
+    the same images as the oracle's pipeline (FP64)."""
+    w = synth.tiny(npix=N, n_ant=12, n_dumps=10, seed=9)
+    plan = ms.Plan(w.u[0], w.v[0], N, w.pixel_size, w.ell_px, w.delta_px, precision="fp64",
+                   levels=3, n_bases=4, convolution=convolution)
+    opts = ms.ReconOptions(n_major=3, fista_iters=20)
+    ro = oi.ReconOptions(n_major=3, fista_iters=20, levels=3, n_bases=4, convolution=convolution)
+    img, node_l, node_h, st = plan.reconstruct_interleaved(cuda(w.vis[0]), opts)
+    ref = oil.reconstruct_interleaved(w.vis[0], w.u[0], w.v[0], N, w.pixel_size, w.ell_px,
+                                      w.delta_px, ro)
+    errs = [rel(node_l.cpu().numpy(), ref.node_l.image), rel(node_h.cpu().numpy(), ref.node_h.image),
+            rel(img.cpu().numpy(), ref.image)]
+    print(f"interleaved {convolution} N={N}: node L {errs[0]:.2e} node H {errs[1]:.2e} "
+          f"combined {errs[2]:.2e}")
+    assert max(errs) <= 1e-8
+    assert [s.total_iterations for s in st] == [60, 60]
+    plan.close()
