@@ -389,6 +389,19 @@ ms_status ms_reconstruct_interleaved(ms_plan* plan, int32_t chan, const void* vi
                                      void* node_l_out, void* node_h_out, ms_stats* stats,
                                      void* stream);
 
+/* One step of the method on its own, n_major major cycles: LOW (Eq. LowRes
+ * on V_L), FULL (Eq. FullRes on V_H, l_n = low_image - sum_{j<n} i_j, the
+ * filters at the plan's ell, delta) or SINGLE; the step's image (last
+ * residual + model) to img_out (dev N*N), the model to model_out (optional).
+ * The method with K > 2 bands (Sect. 6's "more than 2-steps"; bands V_1 =
+ * {r <= ell_1 + delta}, V_k = {ell_k-1 - delta <= r <= ell_k + delta}, V_K =
+ * {r >= ell_K-1 - delta}) runs LOW on a plan with ell_1 and FULL on, for each
+ * later band k, a plan with ell_k-1 whose flags drop the rows above
+ * ell_k + delta, each FULL step taking the previous step's image. */
+ms_status ms_reconstruct_step(ms_plan* plan, int32_t step, int32_t chan, const void* vis,
+                              const ms_recon_opts* opts, const void* low_image, void* img_out,
+                              void* model_out, ms_stats* stats, void* stream);
+
 /* The single-step baseline (Sect. 5): step one's problem on V_L u V_H. */
 ms_status ms_reconstruct_single_step(ms_plan* plan, int32_t chan, const void* vis,
                                      const ms_recon_opts* opts, void* img_out,

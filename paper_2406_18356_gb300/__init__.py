@@ -107,6 +107,8 @@ _SIGNATURES = {
     "ms_reconstruct_single_step_batch": [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_P),
                                          ctypes.POINTER(ms_recon_opts), ctypes.POINTER(_P),
                                          ctypes.POINTER(ms_stats), _P],
+    "ms_reconstruct_step": [_P, _I32, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P, _P,
+                            ctypes.POINTER(ms_stats), _P],
     "ms_reconstruct_interleaved": [_P, _I32, _P, ctypes.POINTER(ms_recon_opts), _P, _P, _P,
                                    ctypes.POINTER(ms_stats), _P],
     "ms_plan_autotune": [ctypes.POINTER(ms_plan_desc), _I32, _I32, ctypes.POINTER(_I32),
@@ -521,6 +523,23 @@ class Plan:
                                       chans=None, outs=None, stream=None):
         _, outs, st = self._recon_batch(False, vis, opts, chans, None, outs, stream)
         return outs, st
+
+    def reconstruct_step(self, step: str, vis, opts: Optional[ReconOptions] = None,
+                         low_image=None, chan: int = 0, out=None, model_out=None, stream=None):
+        """One step of the method (ms_reconstruct_step): returns (image, Stats)."""
+        opts = opts or ReconOptions()
+        out = self._image(out)
+        co = opts.to_c()
+        st = ms_stats()
+        n2 = self.npix ** 2
+        self._check(self._lib.ms_reconstruct_step(
+            self._h, STEPS[step], chan, self._need(vis, self.complex_dtype, self.nvis, "vis"),
+            ctypes.byref(co),
+            self._need(low_image, self.real_dtype, n2, "low_image") if low_image is not None else None,
+            self._need(out, self.real_dtype, n2, "img_out"),
+            self._need(model_out, self.real_dtype, n2, "model_out") if model_out is not None else None,
+            ctypes.byref(st), _stream_handle(stream)))
+        return out, Stats.from_c(st)
 
     def reconstruct_interleaved(self, vis, opts: Optional[ReconOptions] = None, chan: int = 0,
                                 out=None, node_l=None, node_h=None, stream=None):

@@ -1286,6 +1286,32 @@ void two_step(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, voi
   sc.finish();
 }
 
+// ms_reconstruct_step: one step of the method on this plan's partition
+template <typename R>
+void one_step(ms_plan* p, int step, int chan, const void* vis, const ms_recon_opts* o,
+              const void* low_image, void* img_out, void* model_out, ms_stats* st,
+              void* stream) {
+  Scope sc(p, stream);
+  Timer tm(p);
+  ensure_trace(p, o->fista_iters);
+  if (st) std::memset(st, 0, sizeof(*st));
+  int t0 = tm.mark();
+  PartDev& pd = p->ch[chan].part[step_part(step)];
+  launch_gather_vis<R>(pd.idx, pd.n, (const C2<R>*)vis, (C2<R>*)p->vis_a, p->ps);
+  run_step<R>(p, step, chan, *o, low_image, img_out, model_out, st, tm);
+  int t1 = tm.mark();
+  check_device_error(p);
+  if (st) {
+    float ms = 0;
+    ck(cudaEventElapsedTime(&ms, p->tev[t0], p->tev[t1]), "event time");
+    st->elapsed_ms = ms;
+    st->grid_ms = tm.total(0);
+    st->fft_ms = tm.total(1);
+    st->minor_ms = tm.total(2);
+  }
+  sc.finish();
+}
+
 template <typename R>
 void single_step(ms_plan* p, int chan, const void* vis, const ms_recon_opts* o, void* img_out,
                  void* model_out, ms_stats* st, void* stream) {
@@ -2845,6 +2871,22 @@ ms_status ms_reconstruct_two_step(ms_plan* p, int32_t chan, const void* vis,
     arg(p->ch[chan].part[MS_PART_L].n > 0 && p->ch[chan].part[MS_PART_H].n > 0,
         "both partitions need visibilities");
     DISPATCH(p, two_step<R>(p, chan, vis, o, low_out, img_out, model_out, st, stream));
+  });
+}
+
+ms_status ms_reconstruct_step(ms_plan* p, int32_t step, int32_t chan, const void* vis,
+                              const ms_recon_opts* o, const void* low_image, void* img_out,
+                              void* model_out, ms_stats* st, void* stream) {
+  return guarded(p, [&] {
+    validate_opts(o);
+    arg(step == MS_STEP_LOW || step == MS_STEP_FULL || step == MS_STEP_SINGLE,
+        "step must be LOW, FULL or SINGLE");
+    arg(vis && img_out, "vis and img_out are required");
+    arg(step != MS_STEP_FULL || low_image != nullptr, "FULL needs the previous step's image");
+    arg(o->warm_start == nullptr, "the warm start belongs to ms_reconstruct_two_step");
+    arg(chan >= 0 && chan < (int)p->ch.size(), "channel out of range");
+    arg(p->ch[chan].part[step_part(step)].n > 0, "the step's partition has no visibilities");
+    DISPATCH(p, one_step<R>(p, step, chan, vis, o, low_image, img_out, model_out, st, stream));
   });
 }
 

@@ -55,7 +55,7 @@ def iterations_to(trace, eps: float) -> int:
 
 def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 100,
           n_major_max: int = 7, fista_budget: int = 2000, grid=None, convergence: bool = True,
-          convolution: str = "circular", interleaved: bool = True):
+          convolution: str = "circular", interleaved: bool = True, multi_step: bool = True):
     """Run the study on workload w (synth.Workload with a truth image) with
     the minor cycle's PSF operator `convolution` ("circular" or "linear");
     interleaved adds the interleaved two-image pipeline's images (Sect. 6's
@@ -98,6 +98,22 @@ def study(ms, w, precision: str = "fp32", n_major: int = 5, fista_iters: int = 1
             out["psnr_single_step"] = psnr(single.double().cpu().numpy(), truth)
             single_done = True
         plan.close()
+    if multi_step:
+        # three bands at the smallest and largest ell of the grid (delta of the
+        # middle partition), Sect. 6's "more than 2-steps"
+        from . import multistep
+        ells = sorted({round(e, 6) for e, _ in grid})
+        if len(ells) >= 2:
+            ells3 = [ells[0], ells[-1]]
+            d = grid[len(grid) // 2][1]
+            t0 = time.perf_counter()
+            imgs, _ = multistep.reconstruct_multi_step(
+                ms, w.u[0], w.v[0], tv, w.npix, w.pixel_size, ells3, d, opts,
+                precision=precision, convolution=convolution)
+            out["multi_step"] = {"ell_px": ells3, "delta_px": d,
+                                 "psnr_per_step": [psnr(i.double().cpu().numpy(), truth)
+                                                   for i in imgs],
+                                 "seconds": time.perf_counter() - t0}
     best = max(r["psnr_two_step"] for r in out["partitions"])
     for r in out["partitions"]:
         r["psnr_normalized"] = r["psnr_two_step"] / best
