@@ -356,10 +356,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 def record_traffic(paths, precision):
     """DRAM bytes per span of the FISTA kernel families from ncu raw-page CSV
-    exports of one FISTA pass captured in launch order (synthesis levels
-    J..1, the spectral step's kernels, analysis levels 1..J)."""
+    exports of one FISTA pass, the files (one kernel each, or several) given
+    in launch order (synthesis levels J..1, the spectral step's kernels,
+    analysis levels 1..J)."""
     import csv
     fams = {}
+    launches = []
     for path in paths:
         with open(path) as f:
             rows = [r for r in csv.reader(f)]
@@ -369,31 +371,30 @@ def record_traffic(paths, precision):
         units = rows[1]
         idx = {n: i for i, n in enumerate(h)}
         scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-        launches = []
         for r in rows[2:]:
             name = r[idx["Kernel Name"]]
             b = 0.0
             for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
                 b += float(r[idx[m]].replace(",", "")) * scale[units[idx[m]]]
             launches.append((name, b))
-        # (levels J..2 are one cooperative launch, or one launch per level)
-        syn = [b for n, b in launches
-               if "synthesis_level_kernel" in n or "coarse_synthesis_kernel" in n]
-        ana = [b for n, b in launches
-               if "analysis_level_kernel" in n or "analysis_l1_tile_kernel" in n
-               or "coarse_analysis_kernel" in n]
-        if syn:
-            fams["synth"], fams["synth_l1"] = sum(syn[:-1]), syn[-1]
-        if ana:
-            fams["analysis_l1"], fams["analysis"] = ana[0], sum(ana[1:])
-        for n, b in launches:
-            base = n.split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
-            # (the operator kernels' traffic depends on the call's partition, so
-            # only the per-pass families are recorded)
-            for fam, kname in (("spec_mul", "spec_mul_kernel"), ("spec_mul", "spec_col_kernel"),
-                               ("fft_r2c", "row_r2c_kernel"), ("fft_c2r", "row_c2r_kernel")):
-                if base == kname and fam not in fams:
-                    fams[fam] = b
+    # (levels J..2 are one cooperative launch, or one launch per level)
+    syn = [b for n, b in launches
+           if "synthesis_level_kernel" in n or "coarse_synthesis_kernel" in n]
+    ana = [b for n, b in launches
+           if "analysis_level_kernel" in n or "analysis_l1_tile_kernel" in n
+           or "coarse_analysis_kernel" in n]
+    if syn:
+        fams["synth"], fams["synth_l1"] = sum(syn[:-1]), syn[-1]
+    if ana:
+        fams["analysis_l1"], fams["analysis"] = ana[0], sum(ana[1:])
+    for n, b in launches:
+        base = n.split("(")[0].split("<")[0].split("::")[-1].replace("void ", "").strip()
+        # (the operator kernels' traffic depends on the call's partition, so
+        # only the per-pass families are recorded)
+        for fam, kname in (("spec_mul", "spec_mul_kernel"), ("spec_mul", "spec_col_kernel"),
+                           ("fft_r2c", "row_r2c_kernel"), ("fft_c2r", "row_c2r_kernel")):
+            if base == kname and fam not in fams:
+                fams[fam] = b
     rec = {"precision": precision, "workload": "ska-mid-like-1024px-9266880vis",
            "note": "DRAM read + write bytes per span of each kernel family, from ncu; valid "
                    "while the kernel sources hash to source_sha256",
