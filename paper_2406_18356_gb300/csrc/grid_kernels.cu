@@ -517,24 +517,213 @@ __device__ __forceinline__ void grid_item(const WorkItem it, const uint32_t* __r
 }
 
 
+// Plain FP32 form: a lane per row instead of a lane per tap.  A warp's rows
+// are cut into 32 contiguous slots, one per lane.  A lane walks its slot and
+// sums in registers the 49 taps' contributions wu_i (wv_j v) of the rows that
+// share its current anchor cell (packed FP32 pairs, real and imaginary part
+// together); the next row's cell, offsets and value are loaded a step ahead.
+// When its anchor changes, and after its slot's last row, the lane's sums
+// are flushed: the flushing lanes of a step, up to kStageRows at a time in
+// ascending lane order, write their sums to rows of the warp's staging
+// buffer, and the warp adds each staged row, lane per tap, into its sub-tile
+// (one fixed order, so the result does not depend on timing).  Per row a
+// lane issues its 14 ES weights and 56 packed multiply-adds, against the
+// lane-per-tap form's staging, broadcast reads and unpacked FMAs of every
+// tap.
+#ifndef MS_GRID_LANE_ROWS
+#define MS_GRID_LANE_ROWS 1
+#endif
+#ifndef MS_GRID_STAGE_ROWS
+#define MS_GRID_STAGE_ROWS 8
+#endif
+constexpr int kLaneWarps = 4;          // warps per block of the lane-per-row form
+constexpr int kStageQuads = 25;        // float4 per staging row: 49 taps + 1 pad
+constexpr int kStageRows = MS_GRID_STAGE_ROWS;   // staging rows per warp (<= 32)
+static_assert(kStageRows >= 1 && kStageRows <= 32, "staging rows per warp");
+
+__host__ __device__ constexpr size_t grid_lanes_smem(int S) {
+  return (size_t)kLaneWarps * kStageRows * kStageQuads * 16 +
+         (size_t)kLaneWarps * kStageRows * 4 + (size_t)kLaneWarps * S * S * 8;
+}
+
+__device__ __forceinline__ void grid_item_lanes(const WorkItem it,
+                                                const uint32_t* __restrict__ cell,
+                                                const float2* __restrict__ frac,
+                                                const float2* __restrict__ vis,
+                                                float2* __restrict__ scratch,
+                                                int64_t scratch_tile, int T, int ntx,
+                                                float beta) {
+  constexpr int NW = kLaneWarps;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int S = T + kW - 1;
+  const int cells = S * S;
+  float4* stage = reinterpret_cast<float4*>(smem_raw);   // [NW][kStageRows][25]
+  int* stage_a = reinterpret_cast<int*>(stage + NW * kStageRows * kStageQuads);
+  float2* tiles = reinterpret_cast<float2*>(stage_a + NW * kStageRows);   // [NW][cells]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ox = (it.tile % ntx) * T, oy = (it.tile / ntx) * T;
+  for (int c = threadIdx.x; c < NW * cells; c += blockDim.x) tiles[c] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  float2* my = tiles + warp * cells;
+  float4* st = stage + warp * kStageRows * kStageQuads;
+  int* sa = stage_a + warp * kStageRows;
+  // lane-per-tap cells of the adds: tap t = (i, j) = (t mod 7, t div 7)
+  const int off1 = (lane / kW) * S + lane % kW;
+  const bool two = lane + 32 < kW * kW;
+  const int off2 = ((lane + 32) / kW) * S + (lane + 32) % kW;
+
+  const int per = (it.count + NW - 1) / NW;
+  const int ws = it.start + warp * per;
+  int we = ws + per;
+  if (we > it.start + it.count) we = it.start + it.count;
+  const int len = we - ws;
+  const int PL = len > 0 ? (len + 31) / 32 : 0;   // rows per lane slot
+  const int ms = ws + lane * PL;
+  const int me = ms + PL < we ? ms + PL : we;     // this lane's slot [ms, me)
+
+  float2 acc[2 * kStageQuads];   // 49 taps; the last entry stays zero (staging pad)
+#pragma unroll
+  for (int t = 0; t < 2 * kStageQuads; ++t) acc[t] = make_float2(0.f, 0.f);
+  int cur = -1;   // anchor (tile-local cell index) of the sums held
+  uint32_t pc_n = 0;
+  float2 f_n = make_float2(0.f, 0.f), v_n = make_float2(0.f, 0.f);
+  if (ms < me) {
+    pc_n = cell[ms];
+    f_n = frac[ms];
+    v_n = vis[ms];
+  }
+  for (int m = 0; m <= PL; ++m) {   // the extra step flushes the slots' last sums
+    const int k = ms + m;
+    const bool valid = k < me;
+    const int a = valid ? ((int)(pc_n >> 16) - oy) * S + (int)(pc_n & 0xffffu) - ox : -1;
+    const float2 f = f_n, v = v_n;
+    if (k + 1 < me) {
+      pc_n = cell[k + 1];
+      f_n = frac[k + 1];
+      v_n = vis[k + 1];
+    }
+    const bool fl = cur >= 0 && a != cur;
+    const unsigned fm = __ballot_sync(0xffffffffu, fl);
+    for (unsigned todo = fm; todo;) {
+      // the next (up to) kStageRows flushing lanes, lowest lanes first
+      unsigned later = todo;
+#pragma unroll
+      for (int c = 0; c < kStageRows; ++c) later &= later - 1;
+      const unsigned batch = todo ^ later;
+      todo = later;
+      if ((batch >> lane) & 1u) {
+        const int r = __popc(batch & ((1u << lane) - 1u));
+#pragma unroll
+        for (int q = 0; q < kStageQuads; ++q)
+          st[r * kStageQuads + q] =
+              make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
+        sa[r] = cur;
+      }
+      __syncwarp();
+      const int nb = __popc(batch);
+      for (int r = 0; r < nb; ++r) {
+        const float2* row = reinterpret_cast<const float2*>(st + r * kStageQuads);
+        const int c0 = sa[r];
+        float2 s1 = row[lane];
+        float2 o1 = my[c0 + off1];
+        o1.x += s1.x;
+        o1.y += s1.y;
+        my[c0 + off1] = o1;
+        if (two) {
+          float2 s2 = row[lane + 32];
+          float2 o2 = my[c0 + off2];
+          o2.x += s2.x;
+          o2.y += s2.y;
+          my[c0 + off2] = o2;
+        }
+        __syncwarp();   // this row's cells (and staging reads) before the next
+      }
+    }
+    if (fl) {
+#pragma unroll
+      for (int t = 0; t < kW * kW; ++t) acc[t] = make_float2(0.f, 0.f);
+    }
+    cur = a;
+    if (valid) {
+      float wu[kW], wv[kW];
+      es_weights<float>(f.x, beta, wu);
+      es_weights<float>(f.y, beta, wv);
+#pragma unroll
+      for (int j = 0; j < kW; ++j) {
+        const float2 wvv = make_float2(wv[j] * v.x, wv[j] * v.y);
+#pragma unroll
+        for (int i = 0; i < kW; ++i)
+          acc[j * kW + i] = ffma2(make_float2(wu[i], wu[i]), wvv, acc[j * kW + i]);
+      }
+    }
+  }
+  __syncthreads();
+  float2* dst = scratch + scratch_tile * cells;
+  for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const float2 a = tiles[w * cells + c];
+      s.x += a.x;
+      s.y += a.y;
+    }
+    dst[c] = s;
+  }
+}
+
+// the plain FP32 form takes the lane-per-row item when it is enabled
+template <typename R, bool KAHAN> __host__ __device__ constexpr bool grid_lane_rows() {
+  return MS_GRID_LANE_ROWS && sizeof(R) == 4 && !KAHAN;
+}
+template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_block_threads() {
+  return grid_lane_rows<R, KAHAN>() ? 32 * kLaneWarps : 32 * grid_warps<R, KAHAN>();
+}
+// resident blocks per SM the lane-per-row form is compiled for (its register
+// budget: 65536 / (4 x 128) = 128 per thread)
+template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_min_blocks() {
+  return grid_lane_rows<R, KAHAN>() ? 4 : 1;
+}
+template <typename R, bool KAHAN> size_t grid_smem_bytes(int tile) {
+  const int S = tile + kW - 1;
+  if (grid_lane_rows<R, KAHAN>()) return grid_lanes_smem(S);
+  constexpr int NW = grid_warps<R, KAHAN>();
+  return (size_t)NW * S * S * sizeof(C2<R>) * (KAHAN ? 2 : 1) +
+         (size_t)NW * 32 * (2 * kW * sizeof(R) + sizeof(C2<R>) + sizeof(int));
+}
+
 template <typename R, bool KAHAN>
-__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
+__device__ __forceinline__ void grid_any_item(const WorkItem it, const uint32_t* cell,
+                                              const C2<R>* frac, const C2<R>* vis,
+                                              typename ScratchOf<R, KAHAN>::T* scratch,
+                                              int64_t scratch_tile, int T, int ntx, R beta) {
+  if constexpr (grid_lane_rows<R, KAHAN>())
+    grid_item_lanes(it, cell, reinterpret_cast<const float2*>(frac),
+                    reinterpret_cast<const float2*>(vis), reinterpret_cast<float2*>(scratch),
+                    scratch_tile, T, ntx, (float)beta);
+  else
+    grid_item<R, KAHAN>(it, cell, frac, vis, scratch, scratch_tile, T, ntx, beta);
+}
+
+template <typename R, bool KAHAN>
+__global__ void __launch_bounds__(grid_block_threads<R, KAHAN>(), grid_min_blocks<R, KAHAN>())
     grid_kernel(const WorkItem* __restrict__ items, const uint32_t* __restrict__ cell,
                 const C2<R>* __restrict__ frac, const C2<R>* __restrict__ vis,
                 typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int Ng, int T, int ntx,
                 R beta) {
-  grid_item<R, KAHAN>(items[blockIdx.x], cell, frac, vis, scratch, blockIdx.x, T, ntx, beta);
+  grid_any_item<R, KAHAN>(items[blockIdx.x], cell, frac, vis, scratch, blockIdx.x, T, ntx, beta);
 }
 
 // Stacked form: one block per work item of all jobs (scratch tile = the
 // item's index over all jobs).
 template <typename R, bool KAHAN>
-__global__ void __launch_bounds__(32 * grid_warps<R, KAHAN>())
+__global__ void __launch_bounds__(grid_block_threads<R, KAHAN>(), grid_min_blocks<R, KAHAN>())
     grid_batch_kernel(const BatchJob<R>* __restrict__ jobs, const int32_t* __restrict__ job_of,
                       typename ScratchOf<R, KAHAN>::T* __restrict__ scratch, int T, int ntx,
                       R beta) {
   const BatchJob<R> jb = jobs[job_of[blockIdx.x]];
-  grid_item<R, KAHAN>(jb.items[blockIdx.x - jb.item_base], jb.cell, jb.frac, jb.sorted_in,
+  grid_any_item<R, KAHAN>(jb.items[blockIdx.x - jb.item_base], jb.cell, jb.frac, jb.sorted_in,
                       scratch, blockIdx.x, T, ntx, beta);
 }
 
@@ -543,13 +732,10 @@ void launch_grid(const WorkItem* items, int nitems, const uint32_t* cell, const 
                  const C2<R>* vis, void* scratch, int Ng, int tile, int ntx, double beta,
                  cudaStream_t s) {
   if (nitems <= 0) return;
-  constexpr int NW = grid_warps<R, KAHAN>();
-  const int S = tile + kW - 1;
-  size_t smem = (size_t)NW * S * S * sizeof(C2<R>) * (KAHAN ? 2 : 1) +
-                (size_t)NW * 32 * (2 * kW * sizeof(R) + sizeof(C2<R>) + sizeof(int));
+  const size_t smem = grid_smem_bytes<R, KAHAN>(tile);
   auto k = grid_kernel<R, KAHAN>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<nitems, 32 * NW, smem, s>>>(items, cell, frac, vis,
+  k<<<nitems, grid_block_threads<R, KAHAN>(), smem, s>>>(items, cell, frac, vis,
                                  reinterpret_cast<typename ScratchOf<R, KAHAN>::T*>(scratch),
                                  Ng, tile, ntx, (R)beta);
 }
@@ -737,13 +923,10 @@ template <typename R, bool KAHAN>
 void launch_grid_batch(const BatchJob<R>* jobs, const int32_t* job_of, int total_items,
                        void* scratch, int tile, int ntx, double beta, cudaStream_t s) {
   if (total_items <= 0) return;
-  constexpr int NW = grid_warps<R, KAHAN>();
-  const int S = tile + kW - 1;
-  size_t smem = (size_t)NW * S * S * sizeof(C2<R>) * (KAHAN ? 2 : 1) +
-                (size_t)NW * 32 * (2 * kW * sizeof(R) + sizeof(C2<R>) + sizeof(int));
+  const size_t smem = grid_smem_bytes<R, KAHAN>(tile);
   auto k = grid_batch_kernel<R, KAHAN>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<total_items, 32 * NW, smem, s>>>(
+  k<<<total_items, grid_block_threads<R, KAHAN>(), smem, s>>>(
       jobs, job_of, reinterpret_cast<typename ScratchOf<R, KAHAN>::T*>(scratch), tile, ntx,
       (R)beta);
 }
