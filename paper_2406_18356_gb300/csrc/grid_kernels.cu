@@ -682,8 +682,11 @@ template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_block_t
 }
 // resident blocks per SM the lane-per-row form is compiled for (its register
 // budget: 65536 / (4 x 128) = 128 per thread)
+#ifndef MS_GRID_LANE_MINB
+#define MS_GRID_LANE_MINB 4
+#endif
 template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_min_blocks() {
-  return grid_lane_rows<R, KAHAN>() ? 4 : 1;
+  return grid_lane_rows<R, KAHAN>() ? MS_GRID_LANE_MINB : 1;
 }
 template <typename R, bool KAHAN> size_t grid_smem_bytes(int tile) {
   const int S = tile + kW - 1;
