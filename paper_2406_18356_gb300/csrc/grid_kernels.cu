@@ -546,46 +546,26 @@ __host__ __device__ constexpr size_t grid_lanes_smem(int S) {
          (size_t)kLaneWarps * kStageRows * 4 + (size_t)kLaneWarps * S * S * 8;
 }
 
-__device__ __forceinline__ void grid_item_lanes(const WorkItem it,
-                                                const uint32_t* __restrict__ cell,
+// One walk of a warp's slots for the tap rows j in [J0, J0 + NJ) of the
+// footprint (all seven taps i of each): register sums, flushes through the
+// staging rows, lane-per-tap adds into the warp's sub-tile `my`.
+template <int J0, int NJ>
+__device__ __forceinline__ void grid_lanes_pass(const uint32_t* __restrict__ cell,
                                                 const float2* __restrict__ frac,
-                                                const float2* __restrict__ vis,
-                                                float2* __restrict__ scratch,
-                                                int64_t scratch_tile, int T, int ntx,
-                                                float beta) {
-  constexpr int NW = kLaneWarps;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int S = T + kW - 1;
-  const int cells = S * S;
-  float4* stage = reinterpret_cast<float4*>(smem_raw);   // [NW][kStageRows][25]
-  int* stage_a = reinterpret_cast<int*>(stage + NW * kStageRows * kStageQuads);
-  float2* tiles = reinterpret_cast<float2*>(stage_a + NW * kStageRows);   // [NW][cells]
+                                                const float2* __restrict__ vis, float2* my,
+                                                float4* st, int* sa, int lane, int ms, int me,
+                                                int PL, int ox, int oy, int S, float beta) {
+  constexpr int NT = NJ * kW;            // taps of this walk
+  constexpr int NQ = (NT + 1) / 2;       // float4 per staging row
+  // lane-per-tap cells of the adds: tap t = (i, j) = (t mod 7, J0 + t div 7)
+  const bool one = lane < NT;
+  const int off1 = (J0 + lane / kW) * S + lane % kW;
+  const bool two = lane + 32 < NT;
+  const int off2 = (J0 + (lane + 32) / kW) * S + (lane + 32) % kW;
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ox = (it.tile % ntx) * T, oy = (it.tile / ntx) * T;
-  for (int c = threadIdx.x; c < NW * cells; c += blockDim.x) tiles[c] = make_float2(0.f, 0.f);
-  __syncthreads();
-
-  float2* my = tiles + warp * cells;
-  float4* st = stage + warp * kStageRows * kStageQuads;
-  int* sa = stage_a + warp * kStageRows;
-  // lane-per-tap cells of the adds: tap t = (i, j) = (t mod 7, t div 7)
-  const int off1 = (lane / kW) * S + lane % kW;
-  const bool two = lane + 32 < kW * kW;
-  const int off2 = ((lane + 32) / kW) * S + (lane + 32) % kW;
-
-  const int per = (it.count + NW - 1) / NW;
-  const int ws = it.start + warp * per;
-  int we = ws + per;
-  if (we > it.start + it.count) we = it.start + it.count;
-  const int len = we - ws;
-  const int PL = len > 0 ? (len + 31) / 32 : 0;   // rows per lane slot
-  const int ms = ws + lane * PL;
-  const int me = ms + PL < we ? ms + PL : we;     // this lane's slot [ms, me)
-
-  float2 acc[2 * kStageQuads];   // 49 taps; the last entry stays zero (staging pad)
+  float2 acc[2 * NQ];   // NT taps; an odd count leaves the last entry zero (staging pad)
 #pragma unroll
-  for (int t = 0; t < 2 * kStageQuads; ++t) acc[t] = make_float2(0.f, 0.f);
+  for (int t = 0; t < 2 * NQ; ++t) acc[t] = make_float2(0.f, 0.f);
   int cur = -1;   // anchor (tile-local cell index) of the sums held
   uint32_t pc_n = 0;
   float2 f_n = make_float2(0.f, 0.f), v_n = make_float2(0.f, 0.f);
@@ -616,7 +596,7 @@ __device__ __forceinline__ void grid_item_lanes(const WorkItem it,
       if ((batch >> lane) & 1u) {
         const int r = __popc(batch & ((1u << lane) - 1u));
 #pragma unroll
-        for (int q = 0; q < kStageQuads; ++q)
+        for (int q = 0; q < NQ; ++q)
           st[r * kStageQuads + q] =
               make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y);
         sa[r] = cur;
@@ -626,11 +606,13 @@ __device__ __forceinline__ void grid_item_lanes(const WorkItem it,
       for (int r = 0; r < nb; ++r) {
         const float2* row = reinterpret_cast<const float2*>(st + r * kStageQuads);
         const int c0 = sa[r];
-        float2 s1 = row[lane];
-        float2 o1 = my[c0 + off1];
-        o1.x += s1.x;
-        o1.y += s1.y;
-        my[c0 + off1] = o1;
+        if (one) {
+          float2 s1 = row[lane];
+          float2 o1 = my[c0 + off1];
+          o1.x += s1.x;
+          o1.y += s1.y;
+          my[c0 + off1] = o1;
+        }
         if (two) {
           float2 s2 = row[lane + 32];
           float2 o2 = my[c0 + off2];
@@ -643,7 +625,7 @@ __device__ __forceinline__ void grid_item_lanes(const WorkItem it,
     }
     if (fl) {
 #pragma unroll
-      for (int t = 0; t < kW * kW; ++t) acc[t] = make_float2(0.f, 0.f);
+      for (int t = 0; t < NT; ++t) acc[t] = make_float2(0.f, 0.f);
     }
     cur = a;
     if (valid) {
@@ -651,14 +633,49 @@ __device__ __forceinline__ void grid_item_lanes(const WorkItem it,
       es_weights<float>(f.x, beta, wu);
       es_weights<float>(f.y, beta, wv);
 #pragma unroll
-      for (int j = 0; j < kW; ++j) {
-        const float2 wvv = make_float2(wv[j] * v.x, wv[j] * v.y);
+      for (int j = 0; j < NJ; ++j) {
+        const float2 wvv = make_float2(wv[J0 + j] * v.x, wv[J0 + j] * v.y);
 #pragma unroll
         for (int i = 0; i < kW; ++i)
           acc[j * kW + i] = ffma2(make_float2(wu[i], wu[i]), wvv, acc[j * kW + i]);
       }
     }
   }
+}
+
+__device__ __forceinline__ void grid_item_lanes(const WorkItem it,
+                                                const uint32_t* __restrict__ cell,
+                                                const float2* __restrict__ frac,
+                                                const float2* __restrict__ vis,
+                                                float2* __restrict__ scratch,
+                                                int64_t scratch_tile, int T, int ntx,
+                                                float beta) {
+  constexpr int NW = kLaneWarps;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int S = T + kW - 1;
+  const int cells = S * S;
+  float4* stage = reinterpret_cast<float4*>(smem_raw);   // [NW][kStageRows][25]
+  int* stage_a = reinterpret_cast<int*>(stage + NW * kStageRows * kStageQuads);
+  float2* tiles = reinterpret_cast<float2*>(stage_a + NW * kStageRows);   // [NW][cells]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ox = (it.tile % ntx) * T, oy = (it.tile / ntx) * T;
+  for (int c = threadIdx.x; c < NW * cells; c += blockDim.x) tiles[c] = make_float2(0.f, 0.f);
+  __syncthreads();
+
+  float2* my = tiles + warp * cells;
+  float4* st = stage + warp * kStageRows * kStageQuads;
+  int* sa = stage_a + warp * kStageRows;
+
+  const int per = (it.count + NW - 1) / NW;
+  const int ws = it.start + warp * per;
+  int we = ws + per;
+  if (we > it.start + it.count) we = it.start + it.count;
+  const int len = we - ws;
+  const int PL = len > 0 ? (len + 31) / 32 : 0;   // rows per lane slot
+  const int ms = ws + lane * PL;
+  const int me = ms + PL < we ? ms + PL : we;     // this lane's slot [ms, me)
+  grid_lanes_pass<0, kW>(cell, frac, vis, my, st, sa, lane, ms, me, PL, ox, oy, S, beta);
   __syncthreads();
   float2* dst = scratch + scratch_tile * cells;
   for (int c = threadIdx.x; c < cells; c += blockDim.x) {
@@ -680,10 +697,13 @@ template <typename R, bool KAHAN> __host__ __device__ constexpr bool grid_lane_r
 template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_block_threads() {
   return grid_lane_rows<R, KAHAN>() ? 32 * kLaneWarps : 32 * grid_warps<R, KAHAN>();
 }
-// resident blocks per SM the lane-per-row form is compiled for (its register
-// budget: 65536 / (4 x 128) = 128 per thread)
+// Resident blocks per SM the lane-per-row form is compiled for: 3, so up to
+// 170 registers a thread (the tap sums take 98), 12 warps.  Measured at
+// 1024 px, 9.27M rows: 215 us, against 242 us with 4 blocks (128
+// registers, 16 warps): more independent weight and multiply-add chains per
+// warp pay more than the extra warps.
 #ifndef MS_GRID_LANE_MINB
-#define MS_GRID_LANE_MINB 4
+#define MS_GRID_LANE_MINB 3
 #endif
 template <typename R, bool KAHAN> __host__ __device__ constexpr int grid_min_blocks() {
   return grid_lane_rows<R, KAHAN>() ? MS_GRID_LANE_MINB : 1;
