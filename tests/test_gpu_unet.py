@@ -59,7 +59,9 @@ def _case(ms, levels, width, side, seed):
         torch.from_numpy(t.astype(np.float32)).cuda()
 
 
-@pytest.mark.parametrize("levels,width,side", [(3, 16, 32), (2, 8, 16), (3, 16, 48)])
+# (6, 6, 128): the configured warm-start network's shape (6 levels, base width
+# 6: 1,106,455 parameters) on the smallest image its 5 poolings take
+@pytest.mark.parametrize("levels,width,side", [(3, 16, 32), (2, 8, 16), (3, 16, 48), (6, 6, 128)])
 def test_forward_matches_oracle(ms, levels, width, side):
     net, spec, params, x, t, xd, td = _case(ms, levels, width, side, 1)
     y = net.forward(xd).cpu().numpy()
@@ -84,7 +86,7 @@ def _flips(got, want):
     return n, float(np.max(d / np.maximum(ulp, floor)))
 
 
-@pytest.mark.parametrize("levels,width,side", [(3, 16, 32), (2, 8, 16), (3, 16, 48)])
+@pytest.mark.parametrize("levels,width,side", [(3, 16, 32), (2, 8, 16), (3, 16, 48), (6, 6, 128)])
 def test_gradients_match_oracle_layer_by_layer(ms, levels, width, side):
     """Every layer's weight and bias gradient against the oracle's products
     of the device's own stored bfloat16 input activation and pre-activation
