@@ -15,6 +15,7 @@
 // pre-activation gradient before it enters a product.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -44,7 +45,9 @@ __device__ __forceinline__ unsigned su32(const void* p) {
 // C[M][N] = A[M][K] . Bt[N][K]^T (+ bias[n]) (ReLU), bf16 operands, FP32
 // accumulation; K a multiple of 16, M and N arbitrary.  Block tile 64 x 64,
 // four warps of 32 x 32, k-tiles of 32 staged by cp.async (zero-filled past
-// the matrix edges), double-buffered.
+// the matrix edges), double-buffered.  Split over K: block z takes the k in
+// [z kchunk, (z + 1) kchunk) (kchunk a multiple of 32) and writes its
+// partial product to C + z M ldc (FP32 output, no bias or ReLU).
 constexpr int GT = 64, GK = 32, GS = 40;   // tile, k-tile, padded smem row (bf16)
 
 __device__ __forceinline__ void cp16(void* dst, const void* src, bool ok) {
@@ -58,12 +61,15 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16* __restrict__ A
                                                       const bf16* __restrict__ Bt, int ldb,
                                                       void* __restrict__ C, int ldc, int M, int N,
                                                       int K, const float* __restrict__ bias,
-                                                      int relu) {
+                                                      int relu, int kchunk) {
   __shared__ __align__(16) bf16 sA[2][GT][GS];
   __shared__ __align__(16) bf16 sB[2][GT][GS];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gid = lane >> 2, tig = lane & 3;
   const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  if (!OUT_BF16 && gridDim.z > 1) C = static_cast<float*>(C) + (size_t)blockIdx.z * M * ldc;
   const int wm = (warp & 1) * 32, wn = (warp >> 1) * 32;
   float acc[2][4][4];
 #pragma unroll
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16* __restrict__ A
 #pragma unroll
     for (int c = tid; c < GT * (GK / 8); c += 128) {
       const int r = c >> 2, kc = (c & 3) * 8;
-      const bool kok = k0 + kc < K;
+      const bool kok = k0 + kc < kend;
       const int gm = m0 + r, gn = n0 + r;
       const bool aok = kok && gm < M, bok = kok && gn < N;
       cp16(&sA[buf][r][kc], aok ? A + (size_t)gm * lda + k0 + kc : A, aok);
@@ -85,12 +91,12 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16* __restrict__ A
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  const int nk = (K + GK - 1) / GK;
-  load(0, 0);
+  const int nk = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
+  if (nk > 0) load(0, kbeg);
   for (int kt = 0; kt < nk; ++kt) {
     const int buf = kt & 1;
     if (kt + 1 < nk) {
-      load(buf ^ 1, (kt + 1) * GK);
+      load(buf ^ 1, kbeg + (kt + 1) * GK);
       asm volatile("cp.async.wait_group 1;" ::: "memory");
     } else {
       asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -149,9 +155,44 @@ void gemm_tn(const bf16* A, int lda, const bf16* Bt, int ldb, void* C, int ldc, 
              int K, const float* bias, bool relu, bool out_bf16, cudaStream_t s) {
   dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
   if (out_bf16)
-    gemm_tn_kernel<true><<<grid, 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, bias, relu);
+    gemm_tn_kernel<true><<<grid, 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, bias, relu, K);
   else
-    gemm_tn_kernel<false><<<grid, 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, bias, relu);
+    gemm_tn_kernel<false><<<grid, 128, 0, s>>>(A, lda, Bt, ldb, C, ldc, M, N, K, bias, relu, K);
+}
+
+// out[i] = sum over z of part[z n + i], z in order (a fixed summation order)
+__global__ void sum_splits_kernel(const float* __restrict__ part, int splits, int64_t n,
+                                  float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float a = 0.0f;
+    for (int z = 0; z < splits; ++z) a += part[(int64_t)z * n + i];
+    out[i] = a;
+  }
+}
+
+// K (pixels) per split of the weight-gradient products, and the most splits
+constexpr int kSplitRows = 4096, kMaxSplits = 64;
+int splits_for(int64_t K) {
+  return (int)std::min<int64_t>(kMaxSplits, std::max<int64_t>(1, K / kSplitRows));
+}
+
+// C[M][N] (ldc = N) as gemm_tn's FP32 form, with K split over `splits`
+// blocks in z whose partial products go to `part` (splits M N floats) and
+// are then summed in split order.
+void gemm_tn_splitk(const bf16* A, int lda, const bf16* Bt, int ldb, float* part, float* C,
+                    int M, int N, int K, int splits, cudaStream_t s) {
+  if (splits <= 1) {
+    gemm_tn(A, lda, Bt, ldb, C, N, M, N, K, nullptr, false, false, s);
+    return;
+  }
+  const int kchunk = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+  const int z = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, z);
+  gemm_tn_kernel<false><<<grid, 128, 0, s>>>(A, lda, Bt, ldb, part, N, M, N, K, nullptr, 0,
+                                             kchunk);
+  const int64_t n = (int64_t)M * N;
+  sum_splits_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(part, z, n, C);
 }
 
 // ------------------------------------------------------------------ layers
@@ -447,6 +488,7 @@ struct ms_unet {
   bf16 *bot_a = nullptr, *bot_b = nullptr;
   bf16 *cols = nullptr, *colsT = nullptr, *dz = nullptr, *dzT = nullptr;
   float *head = nullptr, *g = nullptr, *dcols = nullptr, *dA = nullptr, *dB = nullptr;
+  float* wsplit = nullptr;   // split-K partial products of the weight gradients
   std::vector<float*> dskip;
   double* parts = nullptr;
   int adam_t = 0;
@@ -508,8 +550,8 @@ void conv_backward(ms_unet* u, Layer& l, const float* g, int ldg, int H, int W, 
   colsum_kernel<<<l.co, kT, 0, s>>>(u->dz, P, l.cop, l.gb);
   transpose_kernel<<<blocks(P * l.cop), kT, 0, s>>>(u->dz, P, l.cop, u->dzT);
   im2col_t_kernel<<<blocks(P * l.kp), kT, 0, s>>>(l.in, H, W, l.ci, l.kp, u->colsT);
-  gemm_tn(u->dzT, (int)P, u->colsT, (int)P, l.gw, l.kp, l.co, l.kp, (int)P, nullptr, false,
-          false, s);
+  gemm_tn_splitk(u->dzT, (int)P, u->colsT, (int)P, u->wsplit, l.gw, l.co, l.kp, (int)P,
+                 splits_for(P), s);
   if (dx) {
     gemm_tn(u->dz, l.cop, l.Wt, l.cop, u->dcols, l.kp, (int)P, l.kp, l.cop, nullptr, false,
             false, s);
@@ -683,6 +725,7 @@ ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64
        "init");
     const int64_t P0 = (int64_t)max_side * max_side;
     int kmax = 0, cmax = 16;
+    size_t wsplit_n = 1;
     for (Layer& l : u->L) {
       l.gw = u->alloc<float>((size_t)l.co * l.kp);
       l.gb = u->alloc<float>(l.co);
@@ -701,7 +744,9 @@ ms_status ms_unet_create(int32_t levels, int32_t width, int32_t max_side, uint64
       if (l.relu) l.out = u->alloc<bf16>((size_t)Pl * l.co);
       kmax = std::max(kmax, l.kp);
       cmax = std::max(cmax, std::max(l.cop, l.ci));
+      wsplit_n = std::max(wsplit_n, (size_t)splits_for(Pl) * l.co * l.kp);
     }
+    u->wsplit = u->alloc<float>(wsplit_n);
     u->xin = u->alloc<bf16>((size_t)P0 * 2);
     for (int lv = 0; lv < levels - 1; ++lv) {
       const int64_t Pl = P0 >> (2 * lv);
