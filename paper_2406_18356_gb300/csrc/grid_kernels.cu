@@ -2,7 +2,8 @@
 //   pad   : D Z   (deapodize, zero-pad N -> Ng, checkerboard so the FFT is centred)
 //   crop  : Z^H D^H (real part of the centred inverse FFT, deapodize, 1/sum w)
 //   degrid: G     (TMA-staged grid tile, W x W ES taps per visibility)
-//   grid  : G^H   (warp-private shared-memory sub-tiles, no global atomics)
+//   grid  : G^H   (register sums per anchor run, warp-private shared-memory
+//                  sub-tiles, no global atomics)
 //   fold  : sums the per-work-item tiles (with their halos) into the grid.
 #include "common.cuh"
 
@@ -400,6 +401,7 @@ template <typename R, bool KAHAN> struct TapSum {
   __device__ __forceinline__ void clear() { sr = si = cr = ci = (R)0; }
 };
 
+// FP64 and compensated FP32 forms (the plain FP32 form: grid_item_lanes).
 // A warp grids its share of the work item's rows, which the plan sorts by
 // anchor cell inside the tile: lane t takes tap t (t < 32) and lanes 0..16
 // also tap t + 32 (tap (i, j) = (t mod 7, t div 7)).  While consecutive rows
