@@ -145,8 +145,62 @@ def evaluate(ms, net, seeds, npix: int, rel_tol: float = 1e-6, max_iters: int = 
     return out
 
 
+def conv_flops(levels: int, width: int, side: int) -> int:
+    """Convolution FLOPs of one forward pass (2 per multiply-add), in the
+    network's execution order: per encoder level two convs, the bottom
+    level, per decoder level two convs on the upsampled-and-concatenated
+    input, the head."""
+    shapes, lv = [], []
+    cin = 2
+    for l in range(levels):
+        c = width << l
+        shapes += [(c, cin), (c, c)]
+        lv += [l, l]
+        cin = c
+    for l in range(levels - 2, -1, -1):
+        c = width << l
+        shapes += [(c, (width << (l + 1)) + c), (c, c)]
+        lv += [l, l]
+    shapes.append((1, width))
+    lv.append(0)
+    return sum(2 * 9 * ci * co * (side >> l) ** 2 for (co, ci), l in zip(shapes, lv))
+
+
+def time_network(ms, levels: int, width: int, side: int, reps: int = 10, warmup: int = 3):
+    """CUDA-event times of a training step (forward, backward, Adam) and of a
+    forward pass on random [side, side, 2] inputs, and the rates they give."""
+    import torch
+    net = ms.WarmStartNet(levels=levels, width=width, max_side=side, seed=1)
+    x = torch.randn(side, side, 2, device="cuda")
+    t = torch.randn(side, side, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    step_ms = timed(lambda: net.train_step(x, t, 1e-4))
+    fwd_ms = timed(lambda: net.forward(x))
+    f = conv_flops(levels, width, side)
+    rec = {"levels": levels, "width": width, "params": net.param_count(), "side": side,
+           "train_step_ms": step_ms, "forward_ms": fwd_ms, "forward_gflop": f / 1e9,
+           "train_step_tflops": 3 * f / step_ms / 1e9, "forward_tflops": f / fwd_ms / 1e9}
+    net.close()
+    return rec
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time", action="store_true",
+                    help="only time a training step and a forward pass of the network "
+                         "(--levels, --width) at --train-npix and --eval-npix")
     ap.add_argument("--train", type=int, default=512, help="training skies (seeds 1..n)")
     ap.add_argument("--eval", type=int, default=16, help="held-out skies")
     ap.add_argument("--train-npix", type=int, default=512)
@@ -159,6 +213,10 @@ def main():
     args = ap.parse_args()
     import paper_2406_18356_gb300 as ms
     ms.load_library()
+    if args.time:
+        for side in sorted({args.train_npix, args.eval_npix}):
+            print(json.dumps(time_network(ms, args.levels, args.width, side)))
+        return
     t0 = time.perf_counter()
     pairs = [make_pair(ms, s, args.train_npix) for s in range(1, args.train + 1)]
     t1 = time.perf_counter()
